@@ -1,0 +1,156 @@
+"""Pins for oracle/precond.py and oracle/solvers.py: exact solves by dense
+LU / sparse factorisation, the paper's printed iteration counts (Table
+tab:3D_its, Table tab:td_its), and planted mistakes that the pins must
+catch."""
+
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import constants as cst
+from oracle import precond as pc
+from oracle import solvers
+from oracle.operator import Plan
+from paper_1802_03770_gb300 import inputs
+
+
+def test_dst_solve_equals_sparse_solve():
+    n = (9, 12)
+    p = Plan(2, n, 0.05, 1.3)
+    r = np.random.default_rng(5).standard_normal(n)
+    z = pc.solve_box(p, r)
+    z2 = spla.spsolve(pc.fd_matrix(p).tocsc(), r.ravel()).reshape(n)
+    assert np.allclose(z, z2, rtol=0, atol=1e-12 * abs(z2).max())
+    # the shifted (time-step) version
+    z = pc.solve_box(p, r, 1.0, 0.3)
+    A = pc.fd_matrix(p) * 0.3 + np.eye(np.prod(n))
+    z2 = np.linalg.solve(A, r.ravel()).reshape(n)
+    assert np.allclose(z, z2, rtol=0, atol=1e-12 * abs(z2).max())
+
+
+def test_fd_part_is_the_stencil_of_M():
+    """C h^d L carries exactly the (A2+A3) part of M: M - C h^d L has the
+    pure kernel entries -C h^d |y_i - y_j|^{-(d+alpha)} off the diagonal."""
+    n = 6
+    p = Plan(3, n, 1.0 / (n + 1), 1.1)
+    M = p.dense_matrix()
+    L = pc.fd_matrix(p).toarray()
+    K = M - L
+    pts = p.points()
+    dist = np.sqrt(((pts[:, None, :] - pts[None, :, :]) ** 2).sum(-1)) * p.h
+    off = ~np.eye(len(pts), dtype=bool)
+    expect = -p.C * p.h ** 3 * dist[off] ** (-(3 + 1.1))
+    assert np.allclose(K[off], expect, rtol=1e-13, atol=0)
+
+
+def test_pcg_matches_dense_lu_config_64():
+    """64 x 64, alpha = 1, 8 Gaussians: PCG to 1e-10 vs dense LU."""
+    n = 64
+    p = Plan(2, n, 1.0 / (n + 1), 1.0)
+    f = inputs.gaussian_mixture(n, 2, 8, 0, 0.05, 0.2)
+    u_lu = np.linalg.solve(p.dense_matrix(), f.ravel()).reshape(n, n)
+    u, its, ok, _ = solvers.solve_elliptic(p, f, 1e-10, 1000)
+    assert ok and its > 5
+    assert np.linalg.norm(u - u_lu) <= 1e-8 * np.linalg.norm(u_lu)
+    res = np.linalg.norm(f - p.apply(u)) / np.linalg.norm(f)
+    assert res <= 1.5e-10
+
+
+def test_table_3d_its(golden):
+    """Preconditioned counts within 3 of the paper's (exact for 1.5 and
+    1.75), unpreconditioned within 15% (the paper does not state its RHS;
+    f = 1 is used)."""
+    for n, alpha, its_p, its_c in golden("table_3d_its.txt"):
+        n = int(n)
+        p = Plan(3, n, 1.0 / (n + 1), alpha)
+        f = np.ones((n, n, n))
+        _, ip, okp, _ = solvers.solve_elliptic(p, f, 1e-9, 250, True)
+        _, ic, okc, _ = solvers.solve_elliptic(p, f, 1e-9, 250, False)
+        assert okp and okc
+        assert abs(ip - its_p) <= 3, (alpha, ip, its_p)
+        assert abs(ic - its_c) <= 0.15 * its_c, (alpha, ic, its_c)
+
+
+@pytest.mark.slow
+def test_table_td_its(golden):
+    """A single Crank-Nicolson system (I + dt/2 M) x = b, b random, dt =
+    1/(n+1), from x = 0: preconditioned counts exact, CG within 20%."""
+    for d, n, alpha, its_p, its_c in golden("table_td_its.txt"):
+        d, n = int(d), int(n)
+        p = Plan(d, n, 1.0 / (n + 1), alpha)
+        b = inputs.random_field(n, d, 0)
+        dt = 1.0 / (n + 1)
+        _, ip, okp, _ = solvers.pcg(lambda v: v + 0.5 * dt * p.apply(v), b,
+                                    lambda r: pc.solve_box(p, r, 1.0, 0.5 * dt),
+                                    None, 1e-9, 1000)
+        assert okp and ip == its_p, (d, n, alpha, ip, its_p)
+        if d == 2:
+            _, ic, okc, _ = solvers.pcg(lambda v: v + 0.5 * dt * p.apply(v), b,
+                                        None, None, 1e-9, 1000)
+            assert okc and abs(ic - its_c) <= 0.2 * its_c, (alpha, ic, its_c)
+
+
+@pytest.mark.parametrize("theta", [0.5, 1.0])
+def test_theta_step_dense(theta):
+    n = 12
+    p = Plan(2, n, 1.0 / (n + 1), 1.5)
+    rng = np.random.default_rng(6)
+    u0 = rng.standard_normal((n, n))
+    f0 = rng.standard_normal((n, n))
+    f1 = rng.standard_normal((n, n))
+    dt = 0.01
+    M = p.dense_matrix()
+    I = np.eye(n * n)
+    rhs = (I - (1 - theta) * dt * M) @ u0.ravel() + dt * (theta * f1 + (1 - theta) * f0).ravel()
+    exact = np.linalg.solve(I + theta * dt * M, rhs).reshape(n, n)
+    u, its, ok, _ = solvers.theta_step(p, u0, dt, theta, f0, f1, tol=1e-12)
+    assert ok
+    assert np.linalg.norm(u - exact) <= 1e-10 * np.linalg.norm(exact)
+
+
+def test_refine_mixed_reaches_fp64_accuracy():
+    n = 48
+    p = Plan(2, n, 1.0 / (n + 1), 1.5)
+    f = inputs.gaussian_mixture(n, 2, 8, 3)
+    u, outer, inner, rel = solvers.refine_mixed(p, f, 1e-10, 1e-4)
+    assert rel <= 1e-10 and outer >= 2
+    u_lu = np.linalg.solve(p.dense_matrix(), f.ravel()).reshape(n, n)
+    assert np.linalg.norm(u - u_lu) <= 1e-8 * np.linalg.norm(u_lu)
+
+
+# -- planted mistakes: the pins above must reject them --------------------
+
+def _gauss_rate(plan_factory, d=2, alpha=1.5):
+    w = 0.1
+    errs = []
+    for n in (31, 63):
+        g = np.meshgrid(*inputs.grid_axes(n, d), indexing="ij")
+        rho2 = sum((gi - 0.5) ** 2 for gi in g) / w ** 2
+        from tests.test_oracle_operator import gaussian_exact
+        f = w ** (-alpha) * gaussian_exact(d, alpha, rho2)
+        p = plan_factory(d, n, alpha)
+        errs.append(np.linalg.norm(p.apply(np.exp(-rho2)) - f) / np.linalg.norm(f))
+    return math.log2(errs[0] / errs[1])
+
+
+def test_planted_dropped_a3_is_caught(monkeypatch):
+    good = _gauss_rate(lambda d, n, a: Plan(d, n, 1.0 / (n + 1), a))
+    monkeypatch.setattr(cst, "a3", lambda d, alpha, h, delta: 0.0)
+    bad = _gauss_rate(lambda d, n, a: Plan(d, n, 1.0 / (n + 1), a))
+    assert good > 1.9 and bad < 1.0
+
+
+def test_planted_2_to_the_d_stencil_is_caught(golden):
+    """With the printed "2^d" diagonal the 3D PCG count leaves the paper's."""
+    n, alpha, its_p = 31, 1.5, 14
+    p = Plan(3, n, 1.0 / (n + 1), alpha)
+    shift = (2 ** 3 - 2 * 3) * p.C * p.h ** 3 * (p.A2 + p.A3) / p.h ** 2
+
+    def apply_bad(u):
+        return p.apply(u) - shift * u
+
+    _, ip, _, _ = solvers.pcg(apply_bad, np.ones((n, n, n)),
+                              lambda r: pc.solve_box(p, r), None, 1e-9, 250)
+    assert abs(ip - its_p) > 3
