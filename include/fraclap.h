@@ -1,0 +1,167 @@
+/*
+ * fraclap -- C ABI of the GB300 (sm_103a) solver for the fractional
+ * Laplacian (-Delta)^{alpha/2} with extended (homogeneous) Dirichlet
+ * conditions, after Minden & Ying, "A simple solver for the fractional
+ * Laplacian in multiple dimensions" (arXiv:1802.03770).
+ *
+ * The discrete operator M is the paper's singularity-subtracted trapezoidal
+ * rule (Sec. 2, eq. linearelliptic): on a box of n_0 x ... x n_{d-1}
+ * interior points with spacing h,
+ *
+ *   (M u)_i = C_{alpha,d} h^d [ A_1 u_i - sum_{j != i} u_j / |y_i - y_j|^{d+alpha}
+ *                               + (A_2 + A_3) L_FD u_i ],
+ *
+ * applied as a zero-padded FFT convolution (Sec. 3.1).  Solves use
+ * conjugate gradients preconditioned with the finite-difference part
+ * C h^d L of M (Sec. 3.1), applied by discrete sine transforms on the box.
+ *
+ * Conventions (every entry point):
+ *  - Arrays are row-major with the last axis fastest, length N = prod n_i,
+ *    one value per interior grid point.  Pointers named *_dev are device
+ *    pointers on the plan's device; *_host are host pointers.  The caller
+ *    owns every array it passes; the plan owns its tables and workspaces.
+ *  - Work is enqueued on the plan's CUDA stream (fl_opts.stream; NULL =
+ *    the legacy default stream).  fl_apply* and fl_precond* return without
+ *    waiting; the solve and time-step calls wait for their own work (they
+ *    read convergence flags back) and fill fl_solve_info before returning.
+ *  - Values outside Omega (mask == 0) are ignored on input and written as 0
+ *    (the extended Dirichlet condition u = 0 off Omega, eq. fracelliptic).
+ *  - Nothing throws across the ABI.  Every call returns an fl_status; on an
+ *    error fl_last_error_string() describes it (thread-local).
+ */
+#ifndef FRACLAP_H
+#define FRACLAP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FL_OK = 0,
+  FL_INVALID_ARG = 1,     /* bad size, alpha, h, pointer or mode          */
+  FL_NOT_CONVERGED = 2,   /* iteration cap hit; the iterate is written    */
+  FL_BREAKDOWN = 3,       /* p^T A p <= 0 or a NaN in CG                  */
+  FL_DEVICE_TIMEOUT = 4,  /* a bounded device wait gave up                */
+  FL_CUDA_ERROR = 5,      /* a CUDA runtime call failed                   */
+  FL_OOM = 6              /* device allocation failed                     */
+} fl_status;
+
+/* Solve modes (argument `mode` of the solve calls): precision in bits 0-3,
+ * preconditioner in bits 4-7. */
+enum {
+  FL_MODE_F64 = 0,        /* plain FP64 CG                                 */
+  FL_MODE_MIXED = 1,      /* FP32 inner CG inside FP64 iterative refinement */
+  FL_PRECOND_FD = 0x00,   /* FD-Laplacian preconditioner (Sec. 3.1, 3.2)   */
+  FL_PRECOND_NONE = 0x10, /* plain CG                                      */
+  FL_PRECOND_AUTO = 0x20  /* FD preconditioner for alpha >= 1, none below
+                             (Sec. 4.2: for alpha < 1 no preconditioning is
+                             needed)                                       */
+};
+
+typedef struct fl_plan fl_plan;
+
+typedef struct {
+  double rho;        /* window radius delta / h; <= 0 selects the paper's 20 */
+  void* stream;      /* cudaStream_t the plan enqueues on; NULL = default    */
+  double inner_tol;  /* FL_MODE_MIXED: inner relative tolerance; <= 0: 1e-4  */
+  int max_outer;     /* FL_MODE_MIXED: refinement steps; <= 0: 20            */
+} fl_opts;
+
+typedef struct {
+  int iterations;        /* CG iterations (operator applications in the loop) */
+  int outer_iterations;  /* FP64 refinement steps (FL_MODE_MIXED), else 0     */
+  double rel_residual;   /* ||b - A u||_2 / ||b||_2 at return (FP64 estimate)  */
+  int converged;         /* 1 if rel_residual <= tol                          */
+  int status;            /* fl_status of the solve                            */
+} fl_solve_info;
+
+typedef struct {
+  int d;
+  int64_t n[3];          /* interior points per axis                       */
+  int64_t fft_len[3];    /* padded FFT length L_i >= 2 n_i - 1 (power of 2) */
+  double h, alpha, rho;
+  double c_alpha_d;      /* C_{alpha,d}                                    */
+  double lattice_zeta;   /* Z_d = sum_{m != 0} |m|^{-(d+alpha)}, A_1 = h^{-(d+alpha)} Z_d */
+  double window_corr;    /* a = (A_2 + A_3) h^{d+alpha-2} (< 0)             */
+  double kernel0;        /* M_ii                                           */
+  int64_t workspace_bytes;
+} fl_plan_desc;
+
+/* Create a plan for the operator of eq. linearelliptic (Sec. 3.1).
+ *   d      : 2 or 3
+ *   n      : host array of d extents n_i >= 1 (n_i <= 2048)
+ *   h      : grid spacing > 0 (the unit box has h = 1/(n+1))
+ *   alpha  : order, 0 < alpha < 2
+ *   mask   : nullable host array of N bytes, nonzero = point of Omega
+ *            (occluded Cartesian grids, Sec. 1.1); NULL = the full box
+ *   opts   : nullable; see fl_opts
+ *   out    : receives the plan
+ * Computes C_{alpha,d}, A_1..A_3 (eq. int1constants, eq. a3), the kernel
+ * symbol (FP64 FFT on the device) and the sine-transform tables; allocates
+ * every workspace the other calls use.  Errors: FL_INVALID_ARG, FL_OOM,
+ * FL_CUDA_ERROR. */
+fl_status fl_plan_create(int d, const int64_t* n, double h, double alpha,
+                         const uint8_t* mask, const fl_opts* opts, fl_plan** out);
+
+/* Release a plan and its device memory (waits for its stream). */
+fl_status fl_plan_destroy(fl_plan* plan);
+
+/* Constants and sizes of a plan (host struct filled). */
+fl_status fl_plan_describe(const fl_plan* plan, fl_plan_desc* desc);
+
+/* y = M u (Sec. 3.1, BTTB apply by FFT), FP64 throughout.  u_dev, y_dev:
+ * device arrays of N doubles; they may not alias. */
+fl_status fl_apply(fl_plan* plan, const double* u_dev, double* y_dev);
+
+/* y = M u in FP32 (FP32 FFTs and symbol). */
+fl_status fl_apply_f32(fl_plan* plan, const float* u_dev, float* y_dev);
+
+/* z = (shift I + scale C h^d L)^{-1} r on the full box (Sec. 3.1 with
+ * shift = 0, scale = 1; Sec. 3.2 with shift = 1, scale = theta dt).
+ * Requires a plan without mask.  r_dev, z_dev: N doubles, may not alias. */
+fl_status fl_precond(fl_plan* plan, double shift, double scale, const double* r_dev,
+                     double* z_dev);
+fl_status fl_precond_f32(fl_plan* plan, double shift, double scale, const float* r_dev,
+                         float* z_dev);
+
+/* Solve M u = f (eq. matelliptic) to ||f - M u|| <= tol ||f||.
+ *   f_dev : N doubles (device)
+ *   u_dev : N doubles (device); in: initial guess (ignored unless
+ *           x0_nonzero), out: solution
+ *   mode  : FL_MODE_* | FL_PRECOND_*
+ *   maxit : cap on CG iterations (per inner solve in FL_MODE_MIXED)
+ *   info  : nullable, filled on return
+ * Returns FL_OK, FL_NOT_CONVERGED (u holds the last iterate), FL_BREAKDOWN,
+ * FL_INVALID_ARG (a preconditioned solve on a masked plan). */
+fl_status fl_solve_elliptic(fl_plan* plan, const double* f_dev, double* u_dev, int x0_nonzero,
+                            double tol, int maxit, int mode, fl_solve_info* info);
+
+/* The same solve with host arrays: copies f to the device, solves, copies
+ * u back (the end-to-end call). */
+fl_status fl_solve_elliptic_host(fl_plan* plan, const double* f_host, double* u_host,
+                                 double tol, int maxit, int mode, fl_solve_info* info);
+
+/* One implicit theta step of the diffusion problem (eq. timestepping with
+ * theta = 1/2; theta = 1 is backward Euler):
+ *   (I + theta dt M) u_next = (I - (1-theta) dt M) u_prev
+ *                             + dt (theta f_next + (1-theta) f_prev),
+ * preconditioned with I + theta dt C h^d L (Sec. 3.2) and warm-started
+ * from u_prev (Sec. 4.5).  f_prev_dev / f_next_dev are nullable (= 0).
+ * u_next_dev may equal u_prev_dev. */
+fl_status fl_time_step(fl_plan* plan, double dt, double theta, const double* u_prev_dev,
+                       const double* f_prev_dev, const double* f_next_dev, double* u_next_dev,
+                       double tol, int maxit, int mode, fl_solve_info* info);
+
+/* Wait for all work on the plan's stream. */
+fl_status fl_sync(fl_plan* plan);
+
+/* Description of the last error on this thread ("" if none). */
+const char* fl_last_error_string(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FRACLAP_H */

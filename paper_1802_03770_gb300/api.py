@@ -1,0 +1,145 @@
+"""Thin Python API over the C ABI, for torch CUDA tensors.
+
+Each method marshals tensor pointers, sizes and the current torch CUDA
+stream into the matching ``fl_*`` call; all arithmetic happens in
+``libfraclap.so``.
+"""
+
+import ctypes
+
+import numpy as np
+
+from . import _lib as L
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check_tensor(t, dtype, numel, what):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{what} must have dtype {dtype}")
+    if t.numel() != numel or not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous with {numel} elements")
+
+
+class Plan:
+    """Operator plan: fl_plan_create(d, n, h, alpha, mask) on the current
+    device and torch stream (or the given one)."""
+
+    def __init__(self, d, n, h, alpha, mask=None, rho=0.0, stream=None, inner_tol=0.0,
+                 max_outer=0):
+        import torch
+        lib = L.load()
+        n = [int(v) for v in np.broadcast_to(np.asarray(n), (d,))]
+        self.d, self.n = d, tuple(n)
+        self.N = int(np.prod(n))
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        opts = L.FlOpts(float(rho), ctypes.c_void_p(stream.cuda_stream), float(inner_tol),
+                        int(max_outer))
+        narr = (ctypes.c_int64 * d)(*n)
+        mptr = None
+        if mask is not None:
+            m = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8).reshape(-1))
+            if m.size != self.N:
+                raise ValueError("mask must have prod(n) entries")
+            self._mask = m
+            mptr = m.ctypes.data_as(ctypes.c_void_p)
+        handle = ctypes.c_void_p()
+        L.check(lib.fl_plan_create(int(d), narr, float(h), float(alpha), mptr,
+                                   ctypes.byref(opts), ctypes.byref(handle)), "fl_plan_create")
+        self._h = handle
+        self._lib = lib
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fl_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def describe(self):
+        d = L.FlPlanDesc()
+        L.check(self._lib.fl_plan_describe(self._h, ctypes.byref(d)), "fl_plan_describe")
+        return {"d": d.d, "n": tuple(d.n[: d.d]), "fft_len": tuple(d.fft_len[: d.d]),
+                "h": d.h, "alpha": d.alpha, "rho": d.rho, "c_alpha_d": d.c_alpha_d,
+                "lattice_zeta": d.lattice_zeta, "window_corr": d.window_corr,
+                "kernel0": d.kernel0, "workspace_bytes": d.workspace_bytes}
+
+    # -- operator ------------------------------------------------------------
+    def apply(self, u, out=None):
+        import torch
+        f32 = u.dtype == torch.float32
+        dt = torch.float32 if f32 else torch.float64
+        _check_tensor(u, dt, self.N, "u")
+        y = torch.empty_like(u) if out is None else out
+        _check_tensor(y, dt, self.N, "out")
+        fn = self._lib.fl_apply_f32 if f32 else self._lib.fl_apply
+        L.check(fn(self._h, _ptr(u), _ptr(y)), "fl_apply")
+        return y
+
+    def precond(self, r, shift=0.0, scale=1.0, out=None):
+        import torch
+        f32 = r.dtype == torch.float32
+        dt = torch.float32 if f32 else torch.float64
+        _check_tensor(r, dt, self.N, "r")
+        z = torch.empty_like(r) if out is None else out
+        _check_tensor(z, dt, self.N, "out")
+        fn = self._lib.fl_precond_f32 if f32 else self._lib.fl_precond
+        L.check(fn(self._h, float(shift), float(scale), _ptr(r), _ptr(z)), "fl_precond")
+        return z
+
+    # -- solves ----------------------------------------------------------------
+    def solve(self, f, u=None, tol=1e-8, maxit=1000, mode=L.FL_MODE_MIXED, raise_on_fail=True):
+        """Solve M u = f; returns (u, info dict)."""
+        import torch
+        _check_tensor(f, torch.float64, self.N, "f")
+        x0 = u is not None
+        if u is None:
+            u = torch.zeros_like(f)
+        _check_tensor(u, torch.float64, self.N, "u")
+        info = L.FlSolveInfo()
+        st = self._lib.fl_solve_elliptic(self._h, _ptr(f), _ptr(u), int(x0), float(tol),
+                                         int(maxit), int(mode), ctypes.byref(info))
+        if raise_on_fail:
+            L.check(st, "fl_solve_elliptic")
+        return u, info.as_dict()
+
+    def solve_host(self, f, tol=1e-8, maxit=1000, mode=L.FL_MODE_MIXED):
+        """The same solve on host arrays (numpy float64, C order)."""
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        if f.size != self.N:
+            raise ValueError("f must have prod(n) entries")
+        u = np.empty_like(f)
+        info = L.FlSolveInfo()
+        st = self._lib.fl_solve_elliptic_host(self._h, f.ctypes.data_as(ctypes.c_void_p),
+                                              u.ctypes.data_as(ctypes.c_void_p), float(tol),
+                                              int(maxit), int(mode), ctypes.byref(info))
+        L.check(st, "fl_solve_elliptic_host")
+        return u, info.as_dict()
+
+    def time_step(self, u_prev, dt, theta=1.0, f_prev=None, f_next=None, out=None, tol=1e-8,
+                  maxit=1000, mode=L.FL_MODE_MIXED):
+        import torch
+        _check_tensor(u_prev, torch.float64, self.N, "u_prev")
+        u_next = torch.empty_like(u_prev) if out is None else out
+        info = L.FlSolveInfo()
+        fp = _ptr(f_prev) if f_prev is not None else None
+        fn = _ptr(f_next) if f_next is not None else None
+        st = self._lib.fl_time_step(self._h, float(dt), float(theta), _ptr(u_prev), fp, fn,
+                                    _ptr(u_next), float(tol), int(maxit), int(mode),
+                                    ctypes.byref(info))
+        L.check(st, "fl_time_step")
+        return u_next, info.as_dict()
+
+    def sync(self):
+        L.check(self._lib.fl_sync(self._h), "fl_sync")

@@ -1,0 +1,117 @@
+// Internal interfaces between the host plan code (plan.cu), the kernel
+// launchers (ops.cu) and the host constants (consts.cpp).
+#pragma once
+
+#include <complex>
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+namespace fl {
+
+// --- consts.cpp ------------------------------------------------------------
+double c_alpha_d(double alpha, int d);
+double upper_gamma(double a, double x);
+double lattice_zeta(int d, double alpha);
+double window_corr(int d, double alpha, double rho);
+void host_fft(std::vector<std::complex<long double>>& a);
+
+// --- geometry of a plan ------------------------------------------------------
+struct Geo {
+  int d;
+  int n[3];
+  int L[3];
+  int lg[3];
+  int lgmax;
+  int H;          // L[d-1]/2 + 1
+  long long N;    // prod n
+  long long spec; // complex entries of the operator spectrum workspace
+};
+
+struct PcgState;
+
+// Device tables and workspaces of one precision.
+template <typename T>
+struct Tables {
+  typedef typename std::conditional<sizeof(T) == 4, float2, double2>::type C;
+  C* tw = nullptr;            // exp(-2 pi i k / Lmax)
+  T* sig = nullptr;           // kernel symbol / prod L
+  C* chirp[3] = {nullptr, nullptr, nullptr};
+  C* bhat[3] = {nullptr, nullptr, nullptr};
+  C* S = nullptr;             // operator spectrum workspace
+  T* t = nullptr;             // preconditioner workspace (N)
+};
+
+// Inputs and outputs of one operator apply.
+template <typename T>
+struct ApplyIO {
+  int pre = 0;                // PRE_NONE / PRE_PUPDATE / PRE_ACCUM
+  const T* u = nullptr;       // PRE_NONE: input; PRE_PUPDATE: z
+  T* p = nullptr;             // PRE_PUPDATE
+  double* acc = nullptr;      // PRE_ACCUM
+  const float* x32 = nullptr; // PRE_ACCUM
+  const uint8_t* mask = nullptr;
+  PcgState* st = nullptr;
+  // epilogue: out = cm M x + cx x + cb b
+  T* out = nullptr;
+  float* out32 = nullptr;
+  const T* x = nullptr;
+  const T* b = nullptr;
+  double cm = 1.0, cx = 0.0, cb = 0.0;
+  const T* dotw = nullptr;
+  double* partials = nullptr;
+  int dot_self = 0;
+};
+
+// Inputs and outputs of one preconditioner solve.
+template <typename T>
+struct PrecIO {
+  int pre = 0;                // DPRE_NONE / DPRE_UPDATE
+  const T* in = nullptr;
+  T* out = nullptr;
+  double shift = 0.0, scale = 1.0;
+  T* x = nullptr; T* r = nullptr; const T* p = nullptr; const T* q = nullptr;
+  const double* pq_part = nullptr; int pq_count = 0;
+  double* rr_part = nullptr;
+  const T* dotw = nullptr; double* dot_part = nullptr;
+  PcgState* st = nullptr;
+};
+
+// --- ops.cu: launchers (return the first CUDA error) --------------------------
+template <typename T>
+cudaError_t launch_apply(const Geo& g, const Tables<T>& tb, cudaStream_t s, const ApplyIO<T>& io);
+template <typename T>
+int apply_partials(const Geo& g);  // partials written by the apply epilogue
+template <typename T>
+cudaError_t launch_precond(const Geo& g, const Tables<T>& tb, const double* const* mu,
+                           cudaStream_t s, const PrecIO<T>& io);
+template <typename T>
+int precond_partials(const Geo& g);  // partials of the first / last DST pass
+template <typename T>
+cudaError_t launch_noprec_update(long long N, cudaStream_t s, PcgState* st, T* x, T* r,
+                                 const T* p, const T* q, const double* pq_part, int pq_count,
+                                 double* rr_part, int* count);
+template <typename T>
+cudaError_t launch_dot(long long N, cudaStream_t s, const T* a, const T* b, double* part,
+                       int* count);
+template <typename T>
+cudaError_t launch_copy_cast(long long N, cudaStream_t s, const double* src, T* dst);
+template <typename T>
+cudaError_t launch_axpby(long long N, cudaStream_t s, double a, const T* x, double b, T* y);
+template <typename T>
+cudaError_t launch_mask_copy_dot(long long N, cudaStream_t s, const T* src, const uint8_t* mask, T* dst,
+                                 double* part, int* count);
+cudaError_t launch_accum_f32(long long N, cudaStream_t s, double* u, const float* x);
+cudaError_t launch_pcg_init(cudaStream_t s, PcgState* st, const double* bb_part, int bb_count,
+                            const double* rr_part, int rr_count, const double* rz_part, int rz_count,
+                            double tol, int maxit);
+cudaError_t launch_pcg_scalar(cudaStream_t s, PcgState* st, const double* rr_part, int rr_count,
+                              const double* rz_part, int rz_count);
+cudaError_t launch_sum(cudaStream_t s, const double* part, int count, double* out);
+cudaError_t build_symbol(const Geo& g, double c, double Z, double a, double expo, cudaStream_t s,
+                         double* sig64, float* sig32, const double2* tw64);
+size_t partial_capacity(const Geo& g);
+cudaError_t configure_kernels();
+
+}  // namespace fl

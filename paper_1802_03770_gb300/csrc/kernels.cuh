@@ -1,0 +1,476 @@
+// Pass kernels of the operator apply (paper Sec. 3.1, "Forward operator and
+// application with FFT"), of the finite-difference preconditioner solve
+// (Sec. 3.1, "Preconditioning"; Sec. 3.2) and of preconditioned CG.
+//
+// Data layout (row-major, last axis fastest):
+//   real fields        n_0 x ... x n_{d-1}
+//   operator spectrum  S: complex; axis d-1 holds H = L_{d-1}/2 + 1
+//                      half-spectrum entries; in 3D the middle axis has room
+//                      for L_1 entries: S[z][y][kx], z < n_0, y < L_1.
+//   kernel symbol      sig: real, (L_0/2+1) x ... x (L_{d-1}/2+1), the even
+//                      real DFT of the circularly embedded kernel, already
+//                      divided by prod L_i.
+//
+// One operator apply is, for d = 2:  rows_fwd (masked R2C along x),
+// cols CONV (FFT along y, x sig, inverse FFT), rows_inv (C2R along x,
+// restrict, epilogue); for d = 3 a FWD and an INV cols pass along y wrap
+// the CONV pass along z.
+//
+// The preconditioner z = (shift + scale C h^d L)^{-1} r is a DST-I along
+// every axis, a divide by the eigenvalue, and the DST-I again.  Each DST-I
+// of length n is a chirp-z (Bluestein) product: with c_m = exp(i pi m^2 /
+// (2(n+1))), sin(pi jk/(n+1)) = Im(c_j c_k conj(c_{k-j})), so
+// X_k = Im(c_k sum_j (c_j x_j) conj(c_{k-j})) -- a linear convolution of
+// length-n sequences done with FFTs of the operator's length L >= 2n - 1.
+#pragma once
+
+#include "fft_core.cuh"
+
+namespace fl {
+
+// Device-resident state of one CG solve (all reductions in FP64).
+struct PcgState {
+  double rz;       // r^T z of the current iterate
+  double bb;       // ||b||^2
+  double tol2;     // tol^2 ||b||^2
+  double rr;       // ||r||^2 of the current iterate
+  double beta;     // p = z + beta p for the next iteration
+  double alpha;    // last step length
+  double pq;       // last p^T A p
+  int it;          // iterations done
+  int maxit;
+  int done;        // 1: stop (converged, failed or hit maxit)
+  int status;      // 0 ok/converged, 2 not converged, 3 breakdown
+};
+
+enum { PRE_NONE = 0, PRE_PUPDATE = 1, PRE_ACCUM = 2 };
+enum { COLS_FWD = 0, COLS_CONV = 1, COLS_INV = 2, COLS_FULL = 3 };
+enum { DST_ONE = 0, DST_DIV_DST = 1 };
+enum { DPRE_NONE = 0, DPRE_UPDATE = 1 };
+
+// Sum `count` per-CTA partials in a fixed order (deterministic); every
+// thread of the CTA gets the result.  Uses `red` (>= 32 doubles) of shared
+// memory.
+__device__ __forceinline__ double cta_sum_partials(const double* __restrict__ part, int count,
+                                                   double* red) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) s += part[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[w] = s;
+  __syncthreads();
+  double t = 0.0;
+  for (int i = 0; i < nw; ++i) t += red[i];
+  __syncthreads();
+  return t;
+}
+
+// CTA-wide sum of one value per thread; result valid in thread 0.
+__device__ __forceinline__ double cta_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < nw; ++i) t += red[i];
+  __syncthreads();
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// Operator pass 1: masked real-to-complex FFT along the last axis.
+// Two real rows ra, rb are packed as ra + i rb, zero-padded to L and
+// transformed together; X_a[k] = (Z[k] + conj Z[L-k]) / 2 and
+// X_b[k] = (Z[k] - conj Z[L-k]) / (2i), k = 0..H-1.
+template <typename T>
+struct RowsFwdArgs {
+  const T* u;              // PRE_NONE: input field; PRE_PUPDATE: z
+  T* p;                    // PRE_PUPDATE: p (in: old p, out: z + beta p)
+  double* acc;             // PRE_ACCUM: FP64 field updated as acc += x32 and transformed
+  const float* x32;        // PRE_ACCUM
+  const uint8_t* mask;     // nullable: Omega inside the box
+  typename Cplx<T>::type* S;
+  const typename Cplx<T>::type* tw;
+  const PcgState* st;
+  int rows, n, H, lg, lgmax;
+  int rows_per_plane, plane_stride;  // spectrum row = (r / rpp) * ps + r % rpp
+  int pre;
+};
+
+template <typename T, int THREADS, int VPT>
+__global__ void __launch_bounds__(THREADS) k_rows_fwd(RowsFwdArgs<T> a) {
+  typedef typename Cplx<T>::type C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  if (a.st && a.st->done) return;
+  const int L = 1 << a.lg;
+  const int ls = L + 2;
+  const int NL = (VPT * THREADS) / L;       // complex lines (row pairs) per CTA
+  const int pair0 = blockIdx.x * NL;
+  const int npairs = (a.rows + 1) / 2;
+  const int nl = min(NL, npairs - pair0);
+  const T beta = (a.pre == PRE_PUPDATE) ? (T)a.st->beta : (T)0;
+  for (int e = threadIdx.x; e < nl * L; e += THREADS) {
+    const int q = e / L, j = e - q * L;
+    const int ra = 2 * (pair0 + q), rb = ra + 1;
+    T va = 0, vb = 0;
+    if (j < a.n) {
+      const size_t ia = (size_t)ra * a.n + j, ib = (size_t)rb * a.n + j;
+      const bool hb = rb < a.rows;
+      if (a.pre == PRE_PUPDATE) {
+        // beta == 0 (first iteration): p = z, without reading the old p
+        va = beta != (T)0 ? a.u[ia] + beta * a.p[ia] : a.u[ia];
+        a.p[ia] = va;
+        if (hb) { vb = beta != (T)0 ? a.u[ib] + beta * a.p[ib] : a.u[ib]; a.p[ib] = vb; }
+      } else if (a.pre == PRE_ACCUM) {
+        double da = a.acc[ia] + (double)a.x32[ia];
+        a.acc[ia] = da;
+        va = (T)da;
+        if (hb) { double db = a.acc[ib] + (double)a.x32[ib]; a.acc[ib] = db; vb = (T)db; }
+      } else {
+        va = a.u[ia];
+        if (hb) vb = a.u[ib];
+      }
+      if (a.mask) {
+        if (!a.mask[ia]) va = 0;
+        if (hb && !a.mask[ib]) vb = 0;
+      }
+    }
+    buf[q * ls + j] = cmake<C>(va, vb);
+  }
+  __syncthreads();
+  fft_lines<VPT>(buf, a.lg, ls, nl, a.tw, a.lgmax, false);
+  for (int e = threadIdx.x; e < nl * a.H; e += THREADS) {
+    const int q = e / a.H, k = e - q * a.H;
+    const int ra = 2 * (pair0 + q), rb = ra + 1;
+    const C z = buf[q * ls + k];
+    const C w = cconj(buf[q * ls + ((L - k) & (L - 1))]);
+    const C xa = cmake<C>((z.x + w.x) * (T)0.5, (z.y + w.y) * (T)0.5);
+    const C xb = cmake<C>((z.y - w.y) * (T)0.5, (w.x - z.x) * (T)0.5);
+    const size_t sa = ((size_t)(ra / a.rows_per_plane) * a.plane_stride + ra % a.rows_per_plane) * a.H;
+    a.S[sa + k] = xa;
+    if (rb < a.rows) {
+      const size_t sb = ((size_t)(rb / a.rows_per_plane) * a.plane_stride + rb % a.rows_per_plane) * a.H;
+      a.S[sb + k] = xb;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Operator strided pass: complex FFTs along a slow axis for a tile of TX
+// consecutive half-spectrum columns kx.  Line element r of column kx at
+// outer index o is S[o * ostride + r * lstride + kx].
+template <typename T>
+struct ColsArgs {
+  typename Cplx<T>::type* S;
+  const typename Cplx<T>::type* tw;
+  const T* sig;            // COLS_CONV: symbol
+  const PcgState* st;
+  int H, lg, lgmax;
+  int rows_in, rows_out;
+  long long ostride, lstride;
+  int nouter;
+  int mode;
+  // symbol index = kk * sig_line + min(o, Lo - o) * sig_outer + kx, kk = min(k, L-k)
+  long long sig_line, sig_outer;
+  int Lo;                  // length of the outer axis in the spectrum (3D: L_1), 0 if unused
+  int tx;                  // columns per CTA
+};
+
+template <typename T, int THREADS, int VPT>
+__global__ void __launch_bounds__(THREADS) k_cols(ColsArgs<T> a) {
+  typedef typename Cplx<T>::type C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  if (a.st && a.st->done) return;
+  const int L = 1 << a.lg;
+  const int ls = L + 2;
+  const int TX = a.tx;
+  const int kx0 = blockIdx.x * TX;
+  const int o = blockIdx.y;
+  const int ncol = min(TX, a.H - kx0);
+  C* base = a.S + (size_t)o * a.ostride + kx0;
+  for (int e = threadIdx.x; e < TX * L; e += THREADS) {
+    const int r = e / TX, c = e - r * TX;
+    C v = cmake<C>((T)0, (T)0);
+    if (r < a.rows_in && c < ncol) v = base[(size_t)r * a.lstride + c];
+    buf[c * ls + r] = v;
+  }
+  __syncthreads();
+  const bool inv_only = (a.mode == COLS_INV);
+  fft_lines<VPT>(buf, a.lg, ls, TX, a.tw, a.lgmax, inv_only);
+  if (a.mode == COLS_CONV) {
+    const size_t soff = a.Lo ? (size_t)min(o, a.Lo - o) * a.sig_outer : 0;
+    for (int e = threadIdx.x; e < TX * L; e += THREADS) {
+      const int c = e / L, k = e - c * L;
+      if (c < ncol) {
+        const int kk = min(k, L - k);
+        const T s = a.sig[(size_t)kk * a.sig_line + soff + kx0 + c];
+        buf[c * ls + k] = cscale(buf[c * ls + k], s);
+      }
+    }
+    __syncthreads();
+    fft_lines<VPT>(buf, a.lg, ls, TX, a.tw, a.lgmax, true);
+  }
+  for (int e = threadIdx.x; e < TX * a.rows_out; e += THREADS) {
+    const int r = e / TX, c = e - r * TX;
+    if (c < ncol) base[(size_t)r * a.lstride + c] = buf[c * ls + r];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Operator last pass: complex-to-real inverse FFT along the last axis,
+// restriction to the first n entries and to Omega, and the epilogue
+//   out = cm * (M x) + cx * x + cb * b          (x = the apply's input)
+// optionally also written as float (out32), and per-CTA partial sums of
+// out . dotw (dotw nullable; dotw == out gives ||out||^2).
+template <typename T>
+struct RowsInvArgs {
+  const typename Cplx<T>::type* S;
+  const typename Cplx<T>::type* tw;
+  const uint8_t* mask;
+  const PcgState* st;
+  T* out;                  // nullable
+  float* out32;            // nullable
+  const T* x;              // nullable
+  const T* b;              // nullable
+  const T* dotw;           // nullable; if equals out, squares
+  double* partials;        // nullable: one per CTA
+  double cm, cx, cb;
+  int rows, n, H, lg, lgmax;
+  int rows_per_plane, plane_stride;
+  int dot_self;            // 1: partial = sum out^2
+};
+
+template <typename T, int THREADS, int VPT>
+__global__ void __launch_bounds__(THREADS) k_rows_inv(RowsInvArgs<T> a) {
+  typedef typename Cplx<T>::type C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  __shared__ double red[32];
+  if (a.st && a.st->done) return;
+  const int L = 1 << a.lg;
+  const int ls = L + 2;
+  const int NL = (VPT * THREADS) / L;
+  const int pair0 = blockIdx.x * NL;
+  const int npairs = (a.rows + 1) / 2;
+  const int nl = min(NL, npairs - pair0);
+  for (int e = threadIdx.x; e < nl * a.H; e += THREADS) {
+    const int q = e / a.H, k = e - q * a.H;
+    const int ra = 2 * (pair0 + q), rb = ra + 1;
+    const size_t sa = ((size_t)(ra / a.rows_per_plane) * a.plane_stride + ra % a.rows_per_plane) * a.H;
+    const C xa = a.S[sa + k];
+    C xb = cmake<C>((T)0, (T)0);
+    if (rb < a.rows) {
+      const size_t sb = ((size_t)(rb / a.rows_per_plane) * a.plane_stride + rb % a.rows_per_plane) * a.H;
+      xb = a.S[sb + k];
+    }
+    // Z[k] = Xa[k] + i Xb[k];  Z[L-k] = conj(Xa[k]) + i conj(Xb[k])
+    buf[q * ls + k] = cmake<C>(xa.x - xb.y, xa.y + xb.x);
+    if (k > 0 && k < a.H - 1) buf[q * ls + (L - k)] = cmake<C>(xa.x + xb.y, xb.x - xa.y);
+  }
+  __syncthreads();
+  fft_lines<VPT>(buf, a.lg, ls, nl, a.tw, a.lgmax, true);
+  double part = 0.0;
+  for (int e = threadIdx.x; e < nl * 2 * a.n; e += THREADS) {
+    const int q = e / (2 * a.n), rem = e - q * 2 * a.n;
+    const int half = rem / a.n, j = rem - half * a.n;
+    const int row = 2 * (pair0 + q) + half;
+    if (row >= a.rows) continue;
+    const size_t idx = (size_t)row * a.n + j;
+    const C z = buf[q * ls + j];
+    double v = (double)(half ? z.y : z.x) * a.cm;
+    if (a.x && a.cx != 0.0) v += a.cx * (double)a.x[idx];
+    if (a.b && a.cb != 0.0) v += a.cb * (double)a.b[idx];
+    if (a.mask && !a.mask[idx]) v = 0.0;
+    const T tv = (T)v;
+    if (a.out) a.out[idx] = tv;
+    if (a.out32) a.out32[idx] = (float)v;
+    if (a.partials) part += a.dot_self ? (double)tv * (double)tv : (double)tv * (double)a.dotw[idx];
+  }
+  if (a.partials) {
+    const double s = cta_sum(part, red);
+    if (threadIdx.x == 0) a.partials[blockIdx.x] = s;
+  }
+}
+
+// In place on `nl` lines of length L in shared memory: y = IFFT(FFT(v) * bhat),
+// the chirp-z convolution of the DST-I (bhat already holds the 1/L).
+template <int VPT, typename C>
+__device__ __forceinline__ void chirp_conv(C* buf, int ls, int nl, int L, int lg, int lgmax,
+                                           const C* __restrict__ tw, const C* __restrict__ bhat) {
+  fft_lines<VPT>(buf, lg, ls, nl, tw, lgmax, false);
+  for (int e = threadIdx.x; e < nl * L; e += blockDim.x) {
+    const int q = e / L, k = e - q * L;
+    buf[q * ls + k] = cmul(buf[q * ls + k], bhat[k]);
+  }
+  __syncthreads();
+  fft_lines<VPT>(buf, lg, ls, nl, tw, lgmax, true);
+}
+
+// ---------------------------------------------------------------------------
+// Preconditioner: DST-I along the last axis (rows of length n), by chirp-z.
+// DPRE_UPDATE fuses the CG update before the transform:
+//   alpha = rz / sum(pq partials); x += alpha p; r -= alpha q,
+// writing x and r and per-CTA partials of ||r||^2.  The transformed row
+// is multiplied by `post` (per-axis DST normalisation) and written to
+// `out`; with `dotw` set, per-CTA partials of out . dotw are written.
+template <typename T>
+struct DstRowsArgs {
+  const T* in;             // DPRE_NONE: input rows
+  T* out;
+  const typename Cplx<T>::type* tw;
+  const typename Cplx<T>::type* chirp;   // c_{j+1}, j = 0..n-1
+  const typename Cplx<T>::type* bhat;    // FFT_L of conj(c_m) embedded circularly, / L
+  const PcgState* st;
+  // DPRE_UPDATE
+  T* x; T* r; const T* p; const T* q;
+  const double* pq_part; int pq_count;
+  double* rr_part;         // per-CTA ||r||^2 (after update)
+  const T* dotw; double* dot_part;
+  double post;
+  int rows, n, lg, lgmax;
+  int pre;
+};
+
+template <typename T, int THREADS, int VPT>
+__global__ void __launch_bounds__(THREADS) k_dst_rows(DstRowsArgs<T> a) {
+  typedef typename Cplx<T>::type C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  __shared__ double red[32];
+  __shared__ double s_alpha;
+  if (a.st && a.st->done) return;
+  const int L = 1 << a.lg;
+  const int ls = L + 2;
+  const int NL = (VPT * THREADS) / L;
+  const int row0 = blockIdx.x * NL;
+  const int nl = min(NL, a.rows - row0);
+  double rr = 0.0;
+  if (a.pre == DPRE_UPDATE) {
+    const double pq = cta_sum_partials(a.pq_part, a.pq_count, red);
+    if (threadIdx.x == 0) s_alpha = a.st->rz / pq;
+    __syncthreads();
+    const T al = (T)s_alpha;
+    for (int e = threadIdx.x; e < nl * L; e += THREADS) {
+      const int q = e / L, j = e - q * L;
+      C v = cmake<C>((T)0, (T)0);
+      if (j < a.n) {
+        const size_t idx = (size_t)(row0 + q) * a.n + j;
+        const T xn = a.x[idx] + al * a.p[idx];
+        const T rn = a.r[idx] - al * a.q[idx];
+        a.x[idx] = xn;
+        a.r[idx] = rn;
+        rr += (double)rn * (double)rn;
+        v = cscale(a.chirp[j], rn);
+      }
+      buf[q * ls + j] = v;
+    }
+  } else {
+    for (int e = threadIdx.x; e < nl * L; e += THREADS) {
+      const int q = e / L, j = e - q * L;
+      C v = cmake<C>((T)0, (T)0);
+      if (j < a.n) v = cscale(a.chirp[j], a.in[(size_t)(row0 + q) * a.n + j]);
+      buf[q * ls + j] = v;
+    }
+  }
+  __syncthreads();
+  fft_lines<VPT>(buf, a.lg, ls, nl, a.tw, a.lgmax, false);
+  for (int e = threadIdx.x; e < nl * L; e += THREADS) {
+    const int q = e / L, k = e - q * L;
+    buf[q * ls + k] = cmul(buf[q * ls + k], a.bhat[k]);
+  }
+  __syncthreads();
+  fft_lines<VPT>(buf, a.lg, ls, nl, a.tw, a.lgmax, true);
+  double dp = 0.0;
+  for (int e = threadIdx.x; e < nl * a.n; e += THREADS) {
+    const int q = e / a.n, k = e - q * a.n;
+    const C y = cmul(a.chirp[k], buf[q * ls + k]);
+    const size_t idx = (size_t)(row0 + q) * a.n + k;
+    const T v = (T)((double)y.y * a.post);
+    a.out[idx] = v;
+    if (a.dotw) dp += (double)v * (double)a.dotw[idx];
+  }
+  if (a.pre == DPRE_UPDATE) {
+    const double s = cta_sum(rr, red);
+    if (threadIdx.x == 0) a.rr_part[blockIdx.x] = s;
+  }
+  if (a.dotw) {
+    const double s = cta_sum(dp, red);
+    if (threadIdx.x == 0) a.dot_part[blockIdx.x] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Preconditioner strided pass: DST-I along a slow axis for a tile of TX
+// consecutive columns of a real field; line element r of column c at outer
+// index o is v[o * ostride + r * lstride + c0 + c].  DST_DIV_DST divides
+// between two transforms by shift + scale * sum_i mu_i(k_i), where
+// mu_i are per-axis eigenvalue tables; the index along this axis is k,
+// along the column axis kx = c0 + c and along the outer axis `o`.
+template <typename T>
+struct DstColsArgs {
+  T* v;
+  const typename Cplx<T>::type* tw;
+  const typename Cplx<T>::type* chirp;
+  const typename Cplx<T>::type* bhat;
+  const PcgState* st;
+  const double* mu_line;   // eigen table of this axis (length n)
+  const double* mu_col;    // eigen table of the column axis
+  const double* mu_outer;  // nullable (2D): eigen table of the outer axis
+  double shift, scale, post;
+  int n, ncols, lg, lgmax;
+  long long ostride, lstride;
+  int mode, tx;
+};
+
+template <typename T, int THREADS, int VPT>
+__global__ void __launch_bounds__(THREADS) k_dst_cols(DstColsArgs<T> a) {
+  typedef typename Cplx<T>::type C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  if (a.st && a.st->done) return;
+  const int L = 1 << a.lg;
+  const int ls = L + 2;
+  const int TX = a.tx;
+  const int c0 = blockIdx.x * TX;
+  const int o = blockIdx.y;
+  const int ncol = min(TX, a.ncols - c0);
+  T* base = a.v + (size_t)o * a.ostride + c0;
+  for (int e = threadIdx.x; e < TX * L; e += THREADS) {
+    const int r = e / TX, c = e - r * TX;
+    C val = cmake<C>((T)0, (T)0);
+    if (r < a.n && c < ncol) val = cscale(a.chirp[r], base[(size_t)r * a.lstride + c]);
+    buf[c * ls + r] = val;
+  }
+  __syncthreads();
+  chirp_conv<VPT>(buf, ls, TX, L, a.lg, a.lgmax, a.tw, a.bhat);
+  if (a.mode == DST_DIV_DST) {
+    // X_k = Im(c_k y_k); divide by the eigenvalue; re-chirp for the second DST
+    const double muo = a.mu_outer ? a.mu_outer[o] : 0.0;
+    for (int e = threadIdx.x; e < TX * L; e += THREADS) {
+      const int c = e / L, k = e - c * L;
+      C val = cmake<C>((T)0, (T)0);
+      if (k < a.n && c < ncol) {
+        const C y = cmul(a.chirp[k], buf[c * ls + k]);
+        const double lam = a.shift + a.scale * (a.mu_line[k] + a.mu_col[c0 + c] + muo);
+        val = cscale(a.chirp[k], (T)((double)y.y / lam));
+      }
+      buf[c * ls + k] = val;
+    }
+    __syncthreads();
+    chirp_conv<VPT>(buf, ls, TX, L, a.lg, a.lgmax, a.tw, a.bhat);
+  }
+  for (int e = threadIdx.x; e < TX * a.n; e += THREADS) {
+    const int r = e / TX, c = e - r * TX;
+    if (c < ncol) {
+      const C y = cmul(a.chirp[r], buf[c * ls + r]);
+      base[(size_t)r * a.lstride + c] = (T)((double)y.y * a.post);
+    }
+  }
+}
+
+}  // namespace fl

@@ -1,0 +1,540 @@
+// Kernel launchers: the operator apply chain, the preconditioner chain, CG
+// vector and scalar kernels, and the plan-time symbol build.
+#include <algorithm>
+
+#include "internal.h"
+#include "kernels.cuh"
+
+namespace fl {
+
+// Launch shapes.  Row passes keep VPT * THREADS complex values of a CTA in
+// shared memory (FP32: 8192, FP64: 4096); strided passes twice that, so a
+// tile of columns reads at least 64 contiguous bytes per line element.
+template <typename T> struct Cfg;
+template <> struct Cfg<float> {
+  static constexpr int RT = 512, RV = 16;   // rows: threads, values per thread
+  static constexpr int CT = 512, CV = 32;   // strided passes
+};
+template <> struct Cfg<double> {
+  static constexpr int RT = 512, RV = 8;
+  static constexpr int CT = 512, CV = 16;
+};
+
+static constexpr int kVecBlocks = 608;   // 4 x 152 SMs, fixed for deterministic partials
+static constexpr int kVecThreads = 256;
+static constexpr int kMaxTx = 64;
+static constexpr int kSmemLimit = 200 * 1024;
+
+template <typename T> static inline int row_lines(int L) { return (Cfg<T>::RT * Cfg<T>::RV) / L; }
+template <typename T> static inline int col_tx(int L) {
+  return std::min(kMaxTx, (Cfg<T>::CT * Cfg<T>::CV) / L);
+}
+template <typename T> static inline size_t smem_bytes(int lines, int L) {
+  return (size_t)lines * (L + 2) * sizeof(typename Cplx<T>::type);
+}
+
+// ---------------------------------------------------------------------------
+// CG vector kernels (grid-stride, kVecBlocks CTAs, one partial per CTA).
+
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_noprec_update(PcgState* st, T* x, T* r, const T* p,
+                                                              const T* q, const double* pq_part,
+                                                              int pq_count, double* rr_part,
+                                                              long long N) {
+  __shared__ double red[32];
+  __shared__ double s_alpha;
+  if (st->done) return;
+  const double pq = cta_sum_partials(pq_part, pq_count, red);
+  if (threadIdx.x == 0) {
+    s_alpha = st->rz / pq;
+    if (blockIdx.x == 0) { st->pq = pq; st->alpha = s_alpha; }
+  }
+  __syncthreads();
+  const T al = (T)s_alpha;
+  double rr = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    x[i] += al * p[i];
+    const T rn = r[i] - al * q[i];
+    r[i] = rn;
+    rr += (double)rn * (double)rn;
+  }
+  const double s = cta_sum(rr, red);
+  if (threadIdx.x == 0) rr_part[blockIdx.x] = s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_dot(const T* a, const T* b, double* part,
+                                                    long long N) {
+  __shared__ double red[32];
+  double v = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    v += (double)a[i] * (double)b[i];
+  const double s = cta_sum(v, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+template <typename T>
+__global__ void k_copy_cast(const double* src, T* dst, long long N) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (T)src[i];
+}
+
+template <typename T>
+__global__ void k_axpby(double a, const T* x, double b, T* y, long long N) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = (T)(a * (double)x[i] + b * (double)y[i]);
+}
+
+// dst = mask ? src : 0 (dst nullable), per-CTA partials of sum (masked src)^2.
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_mask_copy_dot(const T* src, const uint8_t* mask, T* dst,
+                                                              double* part, long long N) {
+  __shared__ double red[32];
+  double v = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const T x = (mask && !mask[i]) ? (T)0 : src[i];
+    if (dst) dst[i] = x;
+    v += (double)x * (double)x;
+  }
+  const double s = cta_sum(v, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_accum_f32(double* u, const float* x, long long N) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    u[i] += (double)x[i];
+}
+
+// Scalar bookkeeping of CG (one CTA).
+__global__ void k_pcg_init(PcgState* st, const double* bb_part, int bb_count, const double* rr_part,
+                           int rr_count, const double* rz_part, int rz_count, double tol, int maxit) {
+  __shared__ double red[32];
+  const double bb = cta_sum_partials(bb_part, bb_count, red);
+  const double rr = cta_sum_partials(rr_part, rr_count, red);
+  const double rz = cta_sum_partials(rz_part, rz_count, red);
+  if (threadIdx.x == 0) {
+    st->bb = bb;
+    st->rr = rr;
+    st->rz = rz;
+    st->tol2 = tol * tol * bb;
+    st->beta = 0.0;
+    st->alpha = 0.0;
+    st->pq = 0.0;
+    st->it = 0;
+    st->maxit = maxit;
+    st->status = 0;
+    st->done = (bb == 0.0 || rr <= st->tol2) ? 1 : 0;
+    if (!(rz > 0.0) && !st->done) { st->done = 1; st->status = 3; }
+  }
+}
+
+__global__ void k_pcg_scalar(PcgState* st, const double* rr_part, int rr_count, const double* rz_part,
+                             int rz_count) {
+  __shared__ double red[32];
+  if (st->done) return;
+  const double rr = cta_sum_partials(rr_part, rr_count, red);
+  const double rz = cta_sum_partials(rz_part, rz_count, red);
+  if (threadIdx.x == 0) {
+    st->it += 1;
+    st->rr = rr;
+    const double pq = st->pq;
+    if (!(pq > 0.0) || rr != rr || rz != rz) {
+      st->done = 1;
+      st->status = 3;
+    } else if (rr <= st->tol2) {
+      st->done = 1;
+      st->status = 0;
+    } else if (st->it >= st->maxit) {
+      st->done = 1;
+      st->status = 2;
+    } else if (!(rz > 0.0)) {
+      st->done = 1;
+      st->status = 3;
+    } else {
+      st->beta = rz / st->rz;
+      st->rz = rz;
+    }
+  }
+}
+
+__global__ void k_sum(const double* part, int count, double* out) {
+  __shared__ double red[32];
+  const double s = cta_sum_partials(part, count, red);
+  if (threadIdx.x == 0) *out = s;
+}
+
+// The DST-rows kernel computes alpha from the pq partials but only CTA 0 of
+// k_noprec_update stores it; this small kernel stores pq for the scalar
+// kernel's breakdown test when the preconditioned path runs.
+__global__ void k_store_pq(PcgState* st, const double* pq_part, int pq_count) {
+  __shared__ double red[32];
+  if (st->done) return;
+  const double pq = cta_sum_partials(pq_part, pq_count, red);
+  if (threadIdx.x == 0) st->pq = pq;
+}
+
+// ---------------------------------------------------------------------------
+// Plan-time symbol: fill the circular embedding of k(m) (FP64, complex),
+// FFT along every axis, keep the real part on [0, L_i/2]^d / prod L.
+
+// Circular embedding of the kernel (grid units, c = C h^{-alpha}):
+// k(0) = c (Z - 2d a), k(m) = c (-|m|^{-expo} + a [|m|_1 = 1]) for
+// 0 < |m_i| <= n_i - 1, zero elsewhere (including the index L_i / 2);
+// expo = d + alpha.
+__global__ void k_fill_kernel(double2* buf, int d, int L0, int L1, int L2, int n0, int n1, int n2,
+                               double c, double Z, double a, double expo, long long total) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int Ls[3] = {L0, L1, L2};
+  const int ns[3] = {n0, n1, n2};
+  long long rem = i;
+  int m[3] = {0, 0, 0};
+  for (int ax = d - 1; ax >= 0; --ax) {
+    const int idx = (int)(rem % Ls[ax]);
+    rem /= Ls[ax];
+    m[ax] = idx <= Ls[ax] / 2 ? idx : idx - Ls[ax];
+  }
+  bool inside = true;
+  double r2 = 0.0;
+  int l1 = 0;
+  for (int ax = 0; ax < d; ++ax) {
+    if (abs(m[ax]) > ns[ax] - 1) inside = false;
+    r2 += (double)m[ax] * m[ax];
+    l1 += abs(m[ax]);
+  }
+  double v = 0.0;
+  if (inside) {
+    if (l1 == 0) v = c * (Z - 2.0 * d * a);
+    else v = c * (-pow(r2, -0.5 * expo) + (l1 == 1 ? a : 0.0));
+  }
+  buf[i] = make_double2(v, 0.0);
+}
+
+template <int THREADS, int VPT>
+__global__ void __launch_bounds__(THREADS) k_rows_c2c(double2* buf, int rows, int lg, int lgmax,
+                                                     const double2* tw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* sb = reinterpret_cast<double2*>(smem_raw);
+  const int L = 1 << lg, ls = L + 2;
+  const int NL = (VPT * THREADS) / L;
+  const int r0 = blockIdx.x * NL;
+  const int nl = min(NL, rows - r0);
+  for (int e = threadIdx.x; e < nl * L; e += THREADS) {
+    const int q = e / L, j = e - q * L;
+    sb[q * ls + j] = buf[(size_t)(r0 + q) * L + j];
+  }
+  __syncthreads();
+  fft_lines<VPT>(sb, lg, ls, nl, tw, lgmax, false);
+  for (int e = threadIdx.x; e < nl * L; e += THREADS) {
+    const int q = e / L, j = e - q * L;
+    buf[(size_t)(r0 + q) * L + j] = sb[q * ls + j];
+  }
+}
+
+__global__ void k_extract_symbol(const double2* buf, int d, int L0, int L1, int L2, double inv,
+                                 double* sig64, float* sig32, long long total) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int Ls[3] = {L0, L1, L2};
+  long long rem = i, src = 0, mul = 1;
+  for (int ax = d - 1; ax >= 0; --ax) {
+    const int h = Ls[ax] / 2 + 1;
+    const int k = (int)(rem % h);
+    rem /= h;
+    src += (long long)k * mul;
+    mul *= Ls[ax];
+  }
+  const double v = buf[src].x * inv;
+  sig64[i] = v;
+  sig32[i] = (float)v;
+}
+
+// ---------------------------------------------------------------------------
+
+static cudaError_t set_smem(const void* f) {
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+}
+
+cudaError_t configure_kernels() {
+  cudaError_t e = cudaSuccess;
+#define FL_SET(...)                                                         \
+  if (e == cudaSuccess) e = set_smem(reinterpret_cast<const void*>(&__VA_ARGS__));
+  FL_SET(k_rows_fwd<float, Cfg<float>::RT, Cfg<float>::RV>);
+  FL_SET(k_rows_fwd<double, Cfg<double>::RT, Cfg<double>::RV>);
+  FL_SET(k_rows_inv<float, Cfg<float>::RT, Cfg<float>::RV>);
+  FL_SET(k_rows_inv<double, Cfg<double>::RT, Cfg<double>::RV>);
+  FL_SET(k_cols<float, Cfg<float>::CT, Cfg<float>::CV>);
+  FL_SET(k_cols<double, Cfg<double>::CT, Cfg<double>::CV>);
+  FL_SET(k_dst_rows<float, Cfg<float>::RT, Cfg<float>::RV>);
+  FL_SET(k_dst_rows<double, Cfg<double>::RT, Cfg<double>::RV>);
+  FL_SET(k_dst_cols<float, Cfg<float>::CT, Cfg<float>::CV>);
+  FL_SET(k_dst_cols<double, Cfg<double>::CT, Cfg<double>::CV>);
+  FL_SET(k_rows_c2c<Cfg<double>::RT, Cfg<double>::RV>);
+#undef FL_SET
+  return e;
+}
+
+size_t partial_capacity(const Geo& g) {
+  long long rows = g.N / g.n[g.d - 1];
+  size_t c = (size_t)kVecBlocks;
+  // row kernels of both precisions: one partial per CTA
+  const int L = g.L[g.d - 1];
+  c = std::max(c, (size_t)((rows + 1) / 2 + 1));
+  c = std::max(c, (size_t)(rows / std::max(1, row_lines<double>(L)) + 2));
+  c = std::max(c, (size_t)(rows / std::max(1, row_lines<float>(L)) + 2));
+  return c;
+}
+
+template <typename T>
+int apply_partials(const Geo& g) {
+  const long long rows = g.N / g.n[g.d - 1];
+  const int NL = row_lines<T>(g.L[g.d - 1]);
+  return (int)(((rows + 1) / 2 + NL - 1) / NL);
+}
+
+template <typename T>
+int precond_partials(const Geo& g) {
+  const long long rows = g.N / g.n[g.d - 1];
+  const int NL = row_lines<T>(g.L[g.d - 1]);
+  return (int)((rows + NL - 1) / NL);
+}
+
+template <typename T>
+cudaError_t launch_apply(const Geo& g, const Tables<T>& tb, cudaStream_t s, const ApplyIO<T>& io) {
+  typedef Cfg<T> K;
+  const int d = g.d;
+  const int Lx = g.L[d - 1];
+  const long long rows = g.N / g.n[d - 1];
+  const int NL = row_lines<T>(Lx);
+  const int rblocks = (int)(((rows + 1) / 2 + NL - 1) / NL);
+  const int rpp = d == 3 ? g.n[1] : (int)rows;
+  const int pstride = d == 3 ? g.L[1] : 0;
+  {
+    RowsFwdArgs<T> a;
+    a.u = io.u; a.p = io.p; a.acc = io.acc; a.x32 = io.x32; a.mask = io.mask;
+    a.S = tb.S; a.tw = tb.tw; a.st = io.st;
+    a.rows = (int)rows; a.n = g.n[d - 1]; a.H = g.H; a.lg = g.lg[d - 1]; a.lgmax = g.lgmax;
+    a.rows_per_plane = rpp; a.plane_stride = pstride; a.pre = io.pre;
+    k_rows_fwd<T, K::RT, K::RV><<<rblocks, K::RT, smem_bytes<T>(NL, Lx), s>>>(a);
+  }
+  auto cols = [&](int axis, int mode, int rows_in, int rows_out, long long lstride,
+                  long long ostride, int nouter, long long sig_line, long long sig_outer, int Lo) {
+    ColsArgs<T> a;
+    a.S = tb.S; a.tw = tb.tw; a.sig = tb.sig; a.st = io.st;
+    a.H = g.H; a.lg = g.lg[axis]; a.lgmax = g.lgmax;
+    a.rows_in = rows_in; a.rows_out = rows_out; a.lstride = lstride; a.ostride = ostride;
+    a.nouter = nouter; a.mode = mode; a.sig_line = sig_line; a.sig_outer = sig_outer; a.Lo = Lo;
+    const int L = g.L[axis];
+    a.tx = col_tx<T>(L);
+    dim3 grid((g.H + a.tx - 1) / a.tx, nouter);
+    k_cols<T, K::CT, K::CV><<<grid, K::CT, smem_bytes<T>(a.tx, L), s>>>(a);
+  };
+  if (d == 2) {
+    cols(0, COLS_CONV, g.n[0], g.n[0], g.H, 0, 1, g.H, 0, 0);
+  } else {
+    const long long H = g.H, L1 = g.L[1];
+    cols(1, COLS_FWD, g.n[1], g.L[1], H, L1 * H, g.n[0], 0, 0, 0);
+    cols(0, COLS_CONV, g.n[0], g.n[0], L1 * H, H, g.L[1], (L1 / 2 + 1) * H, H, g.L[1]);
+    cols(1, COLS_INV, g.L[1], g.n[1], H, L1 * H, g.n[0], 0, 0, 0);
+  }
+  {
+    RowsInvArgs<T> a;
+    a.S = tb.S; a.tw = tb.tw; a.mask = io.mask; a.st = io.st;
+    a.out = io.out; a.out32 = io.out32;
+    // the epilogue's x is the apply input (after any pre-op)
+    a.x = io.x; a.b = io.b; a.dotw = io.dotw; a.partials = io.partials;
+    a.cm = io.cm; a.cx = io.cx; a.cb = io.cb;
+    a.rows = (int)rows; a.n = g.n[d - 1]; a.H = g.H; a.lg = g.lg[d - 1]; a.lgmax = g.lgmax;
+    a.rows_per_plane = rpp; a.plane_stride = pstride; a.dot_self = io.dot_self;
+    k_rows_inv<T, K::RT, K::RV><<<rblocks, K::RT, smem_bytes<T>(NL, Lx), s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_precond(const Geo& g, const Tables<T>& tb, const double* const* mu,
+                           cudaStream_t s, const PrecIO<T>& io) {
+  typedef Cfg<T> K;
+  const int d = g.d;
+  const int nx = g.n[d - 1], Lx = g.L[d - 1];
+  const long long rows = g.N / nx;
+  const int NL = row_lines<T>(Lx);
+  const int rblocks = (int)((rows + NL - 1) / NL);
+  double post = 1.0;
+  for (int i = 0; i < d; ++i) post *= 2.0 / (g.n[i] + 1.0);
+  {
+    DstRowsArgs<T> a;
+    a.in = io.in; a.out = tb.t; a.tw = tb.tw; a.chirp = tb.chirp[d - 1]; a.bhat = tb.bhat[d - 1];
+    a.st = io.st; a.x = io.x; a.r = io.r; a.p = io.p; a.q = io.q;
+    a.pq_part = io.pq_part; a.pq_count = io.pq_count; a.rr_part = io.rr_part;
+    a.dotw = nullptr; a.dot_part = nullptr; a.post = 1.0;
+    a.rows = (int)rows; a.n = nx; a.lg = g.lg[d - 1]; a.lgmax = g.lgmax; a.pre = io.pre;
+    k_dst_rows<T, K::RT, K::RV><<<rblocks, K::RT, smem_bytes<T>(NL, Lx), s>>>(a);
+  }
+  auto cols = [&](int axis, int mode, long long lstride, long long ostride, int nouter,
+                  const double* mu_line, const double* mu_col, const double* mu_outer) {
+    DstColsArgs<T> a;
+    a.v = tb.t; a.tw = tb.tw; a.chirp = tb.chirp[axis]; a.bhat = tb.bhat[axis]; a.st = io.st;
+    a.mu_line = mu_line; a.mu_col = mu_col; a.mu_outer = mu_outer;
+    a.shift = io.shift; a.scale = io.scale; a.post = 1.0;
+    a.n = g.n[axis]; a.ncols = nx; a.lg = g.lg[axis]; a.lgmax = g.lgmax;
+    a.ostride = ostride; a.lstride = lstride; a.mode = mode;
+    const int L = g.L[axis];
+    a.tx = col_tx<T>(L);
+    dim3 grid((nx + a.tx - 1) / a.tx, nouter);
+    k_dst_cols<T, K::CT, K::CV><<<grid, K::CT, smem_bytes<T>(a.tx, L), s>>>(a);
+  };
+  if (d == 2) {
+    cols(0, DST_DIV_DST, nx, 0, 1, mu[0], mu[1], nullptr);
+  } else {
+    const long long n1 = g.n[1], n2 = g.n[2];
+    cols(1, DST_ONE, n2, n1 * n2, g.n[0], nullptr, nullptr, nullptr);
+    cols(0, DST_DIV_DST, n1 * n2, n2, g.n[1], mu[0], mu[2], mu[1]);
+    cols(1, DST_ONE, n2, n1 * n2, g.n[0], nullptr, nullptr, nullptr);
+  }
+  {
+    DstRowsArgs<T> a;
+    a.in = tb.t; a.out = io.out; a.tw = tb.tw; a.chirp = tb.chirp[d - 1]; a.bhat = tb.bhat[d - 1];
+    a.st = io.st; a.dotw = io.dotw; a.dot_part = io.dot_part; a.post = post;
+    a.rows = (int)rows; a.n = nx; a.lg = g.lg[d - 1]; a.lgmax = g.lgmax; a.pre = DPRE_NONE;
+    k_dst_rows<T, K::RT, K::RV><<<rblocks, K::RT, smem_bytes<T>(NL, Lx), s>>>(a);
+  }
+  if (io.pre == DPRE_UPDATE) k_store_pq<<<1, 256, 0, s>>>(io.st, io.pq_part, io.pq_count);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_noprec_update(long long N, cudaStream_t s, PcgState* st, T* x, T* r, const T* p,
+                                 const T* q, const double* pq_part, int pq_count, double* rr_part,
+                                 int* count) {
+  k_noprec_update<T><<<kVecBlocks, kVecThreads, 0, s>>>(st, x, r, p, q, pq_part, pq_count, rr_part, N);
+  *count = kVecBlocks;
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_dot(long long N, cudaStream_t s, const T* a, const T* b, double* part, int* count) {
+  k_dot<T><<<kVecBlocks, kVecThreads, 0, s>>>(a, b, part, N);
+  *count = kVecBlocks;
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_copy_cast(long long N, cudaStream_t s, const double* src, T* dst) {
+  k_copy_cast<T><<<kVecBlocks, kVecThreads, 0, s>>>(src, dst, N);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_axpby(long long N, cudaStream_t s, double a, const T* x, double b, T* y) {
+  k_axpby<T><<<kVecBlocks, kVecThreads, 0, s>>>(a, x, b, y, N);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_mask_copy_dot(long long N, cudaStream_t s, const T* src, const uint8_t* mask, T* dst,
+                                 double* part, int* count) {
+  k_mask_copy_dot<T><<<kVecBlocks, kVecThreads, 0, s>>>(src, mask, dst, part, N);
+  *count = kVecBlocks;
+  return cudaGetLastError();
+}
+template cudaError_t launch_mask_copy_dot<float>(long long, cudaStream_t, const float*, const uint8_t*, float*, double*, int*);
+template cudaError_t launch_mask_copy_dot<double>(long long, cudaStream_t, const double*, const uint8_t*, double*, double*, int*);
+
+cudaError_t launch_accum_f32(long long N, cudaStream_t s, double* u, const float* x) {
+  k_accum_f32<<<kVecBlocks, kVecThreads, 0, s>>>(u, x, N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_init(cudaStream_t s, PcgState* st, const double* bb_part, int bb_count,
+                            const double* rr_part, int rr_count, const double* rz_part, int rz_count,
+                            double tol, int maxit) {
+  k_pcg_init<<<1, 256, 0, s>>>(st, bb_part, bb_count, rr_part, rr_count, rz_part, rz_count, tol, maxit);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_scalar(cudaStream_t s, PcgState* st, const double* rr_part, int rr_count,
+                              const double* rz_part, int rz_count) {
+  k_pcg_scalar<<<1, 256, 0, s>>>(st, rr_part, rr_count, rz_part, rz_count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum(cudaStream_t s, const double* part, int count, double* out) {
+  k_sum<<<1, 256, 0, s>>>(part, count, out);
+  return cudaGetLastError();
+}
+
+cudaError_t build_symbol(const Geo& g, double c, double Z, double a, double expo, cudaStream_t s,
+                         double* sig64, float* sig32, const double2* tw64) {
+  typedef Cfg<double> K;
+  const int d = g.d;
+  long long total = 1, half = 1;
+  int Ls[3] = {1, 1, 1}, ns[3] = {1, 1, 1};
+  for (int i = 0; i < d; ++i) {
+    total *= g.L[i];
+    half *= g.L[i] / 2 + 1;
+    Ls[i] = g.L[i];
+    ns[i] = g.n[i];
+  }
+  double2* buf = nullptr;
+  cudaError_t e = cudaMallocAsync(&buf, total * sizeof(double2), s);
+  if (e != cudaSuccess) return e;
+  const int bt = 256;
+  k_fill_kernel<<<(unsigned)((total + bt - 1) / bt), bt, 0, s>>>(buf, d, Ls[0], Ls[1], Ls[2], ns[0],
+                                                                 ns[1], ns[2], c, Z, a, expo, total);
+  // last axis: contiguous lines
+  {
+    const int L = g.L[d - 1];
+    const long long rows = total / L;
+    const int NL = row_lines<double>(L);
+    k_rows_c2c<K::RT, K::RV><<<(unsigned)((rows + NL - 1) / NL), K::RT, smem_bytes<double>(NL, L), s>>>(
+        buf, (int)rows, g.lg[d - 1], g.lgmax, tw64);
+  }
+  // slower axes: strided lines, full length in and out
+  for (int axis = d - 2; axis >= 0; --axis) {
+    ColsArgs<double> ca;
+    ca.S = buf; ca.tw = tw64; ca.sig = nullptr; ca.st = nullptr;
+    ca.H = Ls[d - 1]; ca.lg = g.lg[axis]; ca.lgmax = g.lgmax;
+    ca.rows_in = Ls[axis]; ca.rows_out = Ls[axis]; ca.mode = COLS_FULL;
+    ca.sig_line = 0; ca.sig_outer = 0; ca.Lo = 0;
+    if (d == 2) { ca.lstride = Ls[1]; ca.ostride = 0; ca.nouter = 1; }
+    else if (axis == 1) { ca.lstride = Ls[2]; ca.ostride = (long long)Ls[1] * Ls[2]; ca.nouter = Ls[0]; }
+    else { ca.lstride = (long long)Ls[1] * Ls[2]; ca.ostride = Ls[2]; ca.nouter = Ls[1]; }
+    ca.tx = col_tx<double>(Ls[axis]);
+    dim3 grid((ca.H + ca.tx - 1) / ca.tx, ca.nouter);
+    k_cols<double, K::CT, K::CV><<<grid, K::CT, smem_bytes<double>(ca.tx, Ls[axis]), s>>>(ca);
+  }
+  double inv = 1.0;
+  for (int i = 0; i < d; ++i) inv /= (double)g.L[i];
+  k_extract_symbol<<<(unsigned)((half + bt - 1) / bt), bt, 0, s>>>(buf, d, Ls[0], Ls[1], Ls[2], inv,
+                                                                  sig64, sig32, half);
+  e = cudaGetLastError();
+  cudaError_t e2 = cudaFreeAsync(buf, s);
+  return e != cudaSuccess ? e : e2;
+}
+
+// explicit instantiations
+template cudaError_t launch_apply<float>(const Geo&, const Tables<float>&, cudaStream_t, const ApplyIO<float>&);
+template cudaError_t launch_apply<double>(const Geo&, const Tables<double>&, cudaStream_t, const ApplyIO<double>&);
+template int apply_partials<float>(const Geo&);
+template int apply_partials<double>(const Geo&);
+template int precond_partials<float>(const Geo&);
+template int precond_partials<double>(const Geo&);
+template cudaError_t launch_precond<float>(const Geo&, const Tables<float>&, const double* const*, cudaStream_t, const PrecIO<float>&);
+template cudaError_t launch_precond<double>(const Geo&, const Tables<double>&, const double* const*, cudaStream_t, const PrecIO<double>&);
+template cudaError_t launch_noprec_update<float>(long long, cudaStream_t, PcgState*, float*, float*, const float*, const float*, const double*, int, double*, int*);
+template cudaError_t launch_noprec_update<double>(long long, cudaStream_t, PcgState*, double*, double*, const double*, const double*, const double*, int, double*, int*);
+template cudaError_t launch_dot<float>(long long, cudaStream_t, const float*, const float*, double*, int*);
+template cudaError_t launch_dot<double>(long long, cudaStream_t, const double*, const double*, double*, int*);
+template cudaError_t launch_copy_cast<float>(long long, cudaStream_t, const double*, float*);
+template cudaError_t launch_copy_cast<double>(long long, cudaStream_t, const double*, double*);
+template cudaError_t launch_axpby<float>(long long, cudaStream_t, double, const float*, double, float*);
+template cudaError_t launch_axpby<double>(long long, cudaStream_t, double, const double*, double, double*);
+
+}  // namespace fl

@@ -1,0 +1,62 @@
+"""The C-ABI library loads and exports every function include/fraclap.h
+declares (no GPU needed: nothing is called but the error-string getter and
+argument checks that fail before touching the device)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1802_03770_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(fl_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(_lib.LIB_PATH):
+        from paper_1802_03770_gb300 import build
+        build.build()
+    return _lib.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_the_header():
+    assert sorted(_lib.SIGNATURES) == declared_functions()
+
+
+def test_invalid_arguments_fail_before_the_device(lib):
+    n = (ctypes.c_int64 * 2)(8, 8)
+    h = ctypes.c_void_p()
+    assert lib.fl_plan_create(4, n, 0.1, 1.0, None, None, ctypes.byref(h)) == _lib.FL_INVALID_ARG
+    assert "d must be" in _lib.last_error()
+    assert lib.fl_plan_create(2, n, 0.1, 2.5, None, None, ctypes.byref(h)) == _lib.FL_INVALID_ARG
+    assert lib.fl_plan_create(2, n, -1.0, 1.0, None, None, ctypes.byref(h)) == _lib.FL_INVALID_ARG
+    bad = (ctypes.c_int64 * 2)(0, 8)
+    assert lib.fl_plan_create(2, bad, 0.1, 1.0, None, None, ctypes.byref(h)) == _lib.FL_INVALID_ARG
+    assert lib.fl_apply(None, None, None) == _lib.FL_INVALID_ARG
+    assert lib.fl_plan_destroy(None) == _lib.FL_OK
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "absent.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        _lib.load()

@@ -1,0 +1,268 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (relative 2-norms unless stated):
+* FP64 apply / preconditioner: 1e-10 (the FP64 target of the build);
+  FFT roundoff is about eps64 * log2(L) * cond, far below it.
+* FP32 apply: 2e-5 for random fields (eps32 ~ 6e-8 times the log2 L ~ 11
+  radix stages of the three passes times a safety factor of ~30 for the
+  symbol's dynamic range), FP32 preconditioner: 2e-5.
+* Solves: the FP64 relative residual computed by the oracle <= the requested
+  tolerance (x 1.05 for the residual recomputed in another summation order),
+  and the solution within cond-scaled distance of the oracle's.
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import precond as opc  # noqa: E402
+from oracle import solvers as osv  # noqa: E402
+from oracle.operator import Plan as OPlan  # noqa: E402
+from paper_1802_03770_gb300 import _lib, inputs  # noqa: E402
+from paper_1802_03770_gb300.api import Plan  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def gpu(x, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(x), dtype=dtype, device=DEV)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+SHAPES = [
+    (2, (64, 64)),        # the 64 x 64 solve case (L = 128)
+    (2, (37, 53)),        # ragged, different L per axis
+    (2, (1, 7)),          # degenerate axis
+    (2, (3, 2)),
+    (2, (130, 9)),        # rows far beyond one CTA, odd number of rows
+    (3, (12, 9, 17)),
+    (3, (5, 1, 6)),
+    (3, (33, 20, 31)),
+]
+
+
+@pytest.mark.parametrize("d,n", SHAPES)
+@pytest.mark.parametrize("alpha", [0.5, 1.5])
+def test_apply_f64_matches_oracle(d, n, alpha):
+    h = 1.0 / (max(n) + 1)
+    op = OPlan(d, n, h, alpha)
+    u = np.random.default_rng(10).standard_normal(n)
+    y_ref = op.apply(u)
+    p = Plan(d, n, h, alpha)
+    y = host(p.apply(gpu(u)))
+    assert rel(y, y_ref) <= 1e-10
+
+
+@pytest.mark.parametrize("d,n", [(2, (64, 64)), (2, (37, 53)), (3, (12, 9, 17))])
+def test_apply_direct_sum_small(d, n):
+    """Against the O(N^2) definition, not only the oracle's FFT."""
+    h = 0.03
+    op = OPlan(d, n, h, 1.2)
+    u = np.random.default_rng(11).standard_normal(n)
+    y = host(Plan(d, n, h, 1.2).apply(gpu(u)))
+    assert rel(y, op.apply_direct(u)) <= 1e-10
+
+
+@pytest.mark.parametrize("d,n", [(2, (64, 64)), (2, (37, 53)), (3, (33, 20, 31))])
+def test_apply_f32(d, n):
+    h = 1.0 / (max(n) + 1)
+    op = OPlan(d, n, h, 1.3)
+    rng = np.random.default_rng(12)
+    u = rng.standard_normal(n)
+    y = host(Plan(d, n, h, 1.3).apply(gpu(u, torch.float32)))
+    assert rel(y, op.apply(u.astype(np.float32).astype(np.float64))) <= 2e-5
+
+
+def test_apply_masked():
+    n = (41, 30)
+    rng = np.random.default_rng(13)
+    mask = rng.random(n) < 0.8
+    op = OPlan(2, n, 0.02, 1.1, mask=mask)
+    u = rng.standard_normal(n)
+    y = host(Plan(2, n, 0.02, 1.1, mask=mask).apply(gpu(u)))
+    assert np.all(y[~mask] == 0.0)
+    assert rel(y, op.apply(u)) <= 1e-10
+
+
+def test_apply_is_deterministic():
+    n = (96, 80)
+    p = Plan(2, n, 0.01, 0.9)
+    u = gpu(np.random.default_rng(14).standard_normal(n))
+    a, b = host(p.apply(u)), host(p.apply(u))
+    assert np.array_equal(a, b)
+
+
+def test_plan_constants_match_oracle():
+    for d, n, alpha in [(2, (64, 64), 1.0), (3, (10, 12, 14), 1.7), (2, (5, 9), 0.2)]:
+        h = 1.0 / 65
+        op = OPlan(d, n, h, alpha)
+        desc = Plan(d, n, h, alpha).describe()
+        assert desc["c_alpha_d"] == pytest.approx(op.C, rel=1e-13)
+        assert desc["lattice_zeta"] == pytest.approx(op.A1 * h ** (d + alpha), rel=1e-12)
+        assert desc["window_corr"] == pytest.approx((op.A2 + op.A3) * h ** (d + alpha - 2), rel=1e-11)
+        assert desc["kernel0"] == pytest.approx(float(op.entry(np.zeros(d))), rel=1e-11)
+        assert all(L >= 2 * v - 1 for L, v in zip(desc["fft_len"], n))
+
+
+@pytest.mark.parametrize("d,n", [(2, (64, 64)), (2, (37, 53)), (2, (1, 6)), (3, (12, 9, 17)),
+                                 (3, (33, 20, 31))])
+@pytest.mark.parametrize("shift,scale", [(0.0, 1.0), (1.0, 2e-3)])
+def test_precond_matches_oracle(d, n, shift, scale):
+    h = 1.0 / (max(n) + 1)
+    op = OPlan(d, n, h, 1.4)
+    r = np.random.default_rng(15).standard_normal(n)
+    z_ref = opc.solve_box(op, r, shift, scale)
+    p = Plan(d, n, h, 1.4)
+    z = host(p.precond(gpu(r), shift, scale))
+    assert rel(z, z_ref) <= 1e-10
+    z32 = host(p.precond(gpu(r, torch.float32), shift, scale))
+    assert rel(z32, z_ref) <= 2e-5
+
+
+def test_solve_64_f64_matches_dense_lu():
+    """64 x 64, alpha = 1, 8 Gaussians, FP64 PCG to 1e-10; dense LU check."""
+    n = 64
+    h = 1.0 / (n + 1)
+    f = inputs.gaussian_mixture(n, 2, 8, 0, 0.05, 0.2)
+    op = OPlan(2, n, h, 1.0)
+    u_lu = np.linalg.solve(op.dense_matrix(), f.ravel()).reshape(n, n)
+    p = Plan(2, (n, n), h, 1.0)
+    u, info = p.solve(gpu(f), tol=1e-10, mode=_lib.FL_MODE_F64)
+    u = host(u)
+    assert info["converged"] == 1 and info["iterations"] > 5
+    assert rel(op.apply(u), f) <= 1.05e-10
+    assert rel(u, u_lu) <= 1e-8
+
+
+@pytest.mark.parametrize("alpha", [0.5, 1.0, 1.5])
+@pytest.mark.parametrize("mode", [_lib.FL_MODE_F64, _lib.FL_MODE_MIXED])
+def test_solve_255(alpha, mode):
+    n = 255
+    h = 1.0 / (n + 1)
+    f = inputs.gaussian_mixture(n, 2, 32, 1)
+    op = OPlan(2, n, h, alpha)
+    p = Plan(2, (n, n), h, alpha)
+    u, info = p.solve(gpu(f), tol=1e-8, mode=mode | _lib.FL_PRECOND_AUTO, maxit=2000)
+    u = host(u)
+    assert info["converged"] == 1
+    assert rel(op.apply(u), f) <= 1.05e-8
+    u_ref, _, ok, _ = osv.solve_elliptic(op, f, 1e-12, 4000, alpha >= 1.0)
+    assert ok
+    assert rel(u, u_ref) <= 1e-5
+
+
+def test_solve_host_arrays():
+    n = 48
+    f = inputs.gaussian_mixture(n, 2, 8, 2)
+    op = OPlan(2, n, 1.0 / (n + 1), 1.25)
+    p = Plan(2, (n, n), 1.0 / (n + 1), 1.25)
+    u, info = p.solve_host(f, tol=1e-9)
+    assert info["converged"] == 1
+    assert rel(op.apply(u), f) <= 1.05e-9
+
+
+def test_solve_masked_plain_cg():
+    n = (40, 40)
+    ax = np.linspace(-1, 1, 40)
+    X, Y = np.meshgrid(ax, ax, indexing="ij")
+    mask = X ** 2 + Y ** 2 < 0.9
+    op = OPlan(2, n, 0.05, 0.75, mask=mask)
+    f = np.where(mask, 1.0, 0.0)
+    p = Plan(2, n, 0.05, 0.75, mask=mask)
+    u, info = p.solve(gpu(f), tol=1e-9, mode=_lib.FL_MODE_F64 | _lib.FL_PRECOND_NONE)
+    u = host(u)
+    assert np.all(u[~mask] == 0.0)
+    assert rel(op.apply(u), f) <= 1.05e-9
+
+
+def test_preconditioned_solve_on_masked_plan_is_rejected():
+    mask = np.ones((16, 16), bool)
+    mask[0, 0] = False
+    p = Plan(2, (16, 16), 0.05, 1.5, mask=mask)
+    with pytest.raises(_lib.FracLapError, match="INVALID_ARG"):
+        p.solve(gpu(np.ones((16, 16))), mode=_lib.FL_MODE_F64 | _lib.FL_PRECOND_FD)
+
+
+@pytest.mark.parametrize("theta", [1.0, 0.5])
+@pytest.mark.parametrize("mode", [_lib.FL_MODE_F64, _lib.FL_MODE_MIXED])
+def test_time_step_3d(theta, mode):
+    n = 24
+    h = 1.0 / (n + 1)
+    op = OPlan(3, n, h, 1.5)
+    u0 = inputs.gaussian_mixture(n, 3, 16, 4, 0.05, 0.15)
+    f0 = inputs.gaussian_mixture(n, 3, 4, 5)
+    f1 = inputs.gaussian_mixture(n, 3, 4, 6)
+    dt = 1e-3
+    u_ref, _, ok, _ = osv.theta_step(op, u0, dt, theta, f0, f1, tol=1e-13)
+    assert ok
+    p = Plan(3, (n, n, n), h, 1.5)
+    u, info = p.time_step(gpu(u0), dt, theta, gpu(f0), gpu(f1), tol=1e-10, mode=mode)
+    assert info["converged"] == 1
+    assert rel(host(u), u_ref) <= 1e-9
+
+
+def test_breakdown_and_cap_statuses():
+    n = 32
+    p = Plan(2, (n, n), 1.0 / (n + 1), 1.5)
+    f = gpu(inputs.gaussian_mixture(n, 2, 8, 7))
+    u, info = p.solve(f, tol=1e-12, maxit=2, mode=_lib.FL_MODE_F64, raise_on_fail=False)
+    assert info["status"] == _lib.FL_NOT_CONVERGED and info["converged"] == 0
+    nan = gpu(np.full((n, n), np.nan))
+    u, info = p.solve(nan, tol=1e-8, mode=_lib.FL_MODE_F64, raise_on_fail=False)
+    assert info["status"] in (_lib.FL_BREAKDOWN, _lib.FL_NOT_CONVERGED)
+    zero = gpu(np.zeros((n, n)))
+    u, info = p.solve(zero, tol=1e-8, mode=_lib.FL_MODE_MIXED)
+    assert info["converged"] == 1 and float(u.abs().max()) == 0.0
+
+
+# -- full sizes ---------------------------------------------------------------
+
+def test_full_size_2d_1024_apply_and_mixed_solve():
+    """1024 x 1024 (2048^2 padded FFT), alpha = 1.5, 32 Gaussians."""
+    n = 1024
+    h = 1.0 / (n + 1)
+    f = inputs.gaussian_mixture(n, 2, 32, 0)
+    op = OPlan(2, n, h, 1.5)
+    p = Plan(2, (n, n), h, 1.5)
+    y = host(p.apply(gpu(f)))
+    assert rel(y, op.apply(f)) <= 1e-10
+    u, info = p.solve(gpu(f), tol=1e-8, mode=_lib.FL_MODE_MIXED)
+    assert info["converged"] == 1
+    assert rel(op.apply(host(u)), f) <= 1.05e-8
+
+
+def _direct_samples(op, u, idx):
+    """(M u)_i at sample points i by the plain definition (O(N) each)."""
+    pts = op.points()
+    vals = u[tuple(pts.T)]
+    out = []
+    for i in idx:
+        k = op.entry(pts - np.asarray(i)[None, :])
+        out.append(float(np.dot(k, vals)))
+    return np.array(out)
+
+
+def test_full_size_3d_256_apply_samples():
+    """256^3 (512^3 padded FFT), alpha = 1.5: sampled outputs by direct sum."""
+    n = 256
+    h = 1.0 / (n + 1)
+    u = inputs.gaussian_mixture(n, 3, 16, 3, 0.05, 0.15)
+    op = OPlan(3, n, h, 1.5)
+    p = Plan(3, (n, n, n), h, 1.5)
+    y = host(p.apply(gpu(u)))
+    rng = np.random.default_rng(16)
+    idx = [tuple(rng.integers(0, n, 3)) for _ in range(6)] + [(0, 0, 0), (255, 255, 255), (128, 0, 77)]
+    ref = _direct_samples(op, u, idx)
+    got = np.array([y[i] for i in idx])
+    scale = np.abs(y).max()
+    assert np.max(np.abs(got - ref)) <= 1e-10 * scale
