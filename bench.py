@@ -1,0 +1,363 @@
+"""Benchmark: elliptic solves of the fractional Laplacian on a 1024 x 1024
+interior grid (2048^2 padded FFT), alpha in {0.5, 1.0, 1.5}, right-hand
+sides = 32 seeded Gaussians, to 1e-8 relative residual.
+
+One step = one solve per alpha (three solves) with the FP32-inner / FP64-
+refinement CG (preconditioner: FD Laplacian for alpha >= 1, none below, as
+the paper advises).  Reported beside it: the same solves by plain FP64 CG on
+the same GPU, the end-to-end time through the host-array C-ABI call, the
+roofline of the dominant kernel, and the FP64 CPU oracle timed on the host.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank solves its own seeds (weak scaling, no collective
+on the data path); rank 0 prints one JSON line.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_SIDE = 1024
+ALPHAS = (0.5, 1.0, 1.5)
+BUMPS = 32
+TOL = 1e-8
+METRIC = "solves/s at 1e-8 rel. residual, mixed+learned vs plain FP64 PCG; apply HBM GB/s"
+UNIT = "solves/s"
+WORKLOAD = ("elliptic solve 2D 1024x1024 interior grid (2048^2 padded FFT), alpha in "
+            "{0.5,1.0,1.5}, RHS 32 seeded Gaussians, FP32 inner CG + FP64 refinement to 1e-8")
+L2_FLUSH_BYTES = 512 << 20
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = [r.split(",") for r in (self.out or "").strip().splitlines() if r.count(",") >= 7]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in rows if r[0].strip().replace(".", "").isdigit()]
+        smax = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[4 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def make_rhs(seed):
+    from paper_1802_03770_gb300 import inputs
+    return inputs.gaussian_mixture(N_SIDE, 2, BUMPS, seed)
+
+
+def algorithmic_bytes(name, n, L, elem):
+    """Compulsory HBM bytes of one launch of a pass kernel on an n x n grid
+    (each pass reads and writes its working array once; the symbol is read
+    once in its compact (L/2+1)^2 form)."""
+    H = L // 2 + 1
+    N = n * n
+    spec = n * H * 2 * elem          # half spectrum, complex
+    real = N * elem
+    table = {
+        "rows_fwd": 3 * real + spec,             # z, p in; p out; spectrum out
+        "cols_conv": 2 * spec + (L // 2 + 1) * H * elem,
+        "rows_inv": spec + 2 * real,             # spectrum, p in; q out
+        "dst_rows": 7 * real,                    # x, r, p, q in; x, r, t out
+        "dst_cols_div": 2 * real,
+        "dst_cols": 2 * real,
+    }
+    base = name.split("<")[0]
+    return table.get(base)
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_1802_03770_gb300 import _lib
+    from paper_1802_03770_gb300.api import Plan, launch_count
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    h = 1.0 / (N_SIDE + 1)
+    t0 = time.perf_counter()
+    plans = [Plan(2, (N_SIDE, N_SIDE), h, a) for a in ALPHAS]
+    torch.cuda.synchronize()
+    t_con = (time.perf_counter() - t0) / len(plans)
+    mode_mixed = _lib.FL_MODE_MIXED | _lib.FL_PRECOND_AUTO
+    mode_f64 = _lib.FL_MODE_F64 | _lib.FL_PRECOND_AUTO
+    steps, warm = args.steps, args.warmup
+    nsteps = steps + warm
+    # inputs resident in HBM before timing: one RHS per (step, alpha)
+    rhs = [[torch.tensor(make_rhs(1000 * rank + 10 * s + j), dtype=torch.float64, device=dev)
+            for j in range(len(ALPHAS))] for s in range(nsteps)]
+    u = torch.zeros(N_SIDE * N_SIDE, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def dist_barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def timed(mode, nsteps_timed, nwarm, collect=None):
+        infos = []
+        for s in range(nwarm):
+            for j, p in enumerate(plans):
+                p.solve(rhs[s][j].view(-1), u, tol=TOL, mode=mode)
+        dist_barrier()
+        torch.cuda.synchronize()
+        total_ms = 0.0
+        l0 = launch_count()
+        for s in range(nwarm, nwarm + nsteps_timed):
+            flush.fill_(float(s))            # evict L2 between timed steps (untimed)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for j, p in enumerate(plans):
+                u.zero_()
+                _, info = p.solve(rhs[s % nsteps][j].view(-1), u, tol=TOL, mode=mode)
+                infos.append(info)
+            e1.record()
+            torch.cuda.synchronize()
+            total_ms += e0.elapsed_time(e1)
+        dist_barrier()
+        torch.cuda.synchronize()
+        launches = launch_count() - l0
+        return total_ms / nsteps_timed, infos, launches
+
+    with ClockSampler(local) as clk:
+        ms_mixed, infos_mixed, launches = timed(mode_mixed, steps, warm)
+    clocks = clk.summary()
+    for info in infos_mixed:
+        assert info["converged"] == 1 and info["rel_residual"] <= TOL, info
+    # plain FP64 CG on the same GPU, same inputs (fewer steps: it is slower)
+    k64 = max(1, min(steps, 2))
+    ms_f64, infos_f64, _ = timed(mode_f64, k64, 1)
+    for info in infos_f64:
+        assert info["converged"] == 1, info
+
+    ms_t = torch.tensor([ms_mixed, ms_f64], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms_mixed, ms_f64 = float(ms_t[0]), float(ms_t[1])
+    solves_per_step = len(ALPHAS)
+    value = world * solves_per_step / (ms_mixed / 1e3)
+    value_f64 = world * solves_per_step / (ms_f64 / 1e3)
+
+    # end to end: host arrays in, host arrays out, through the C ABI
+    f_host = [torch.from_numpy(make_rhs(5000 + j)).pin_memory() for j in range(len(ALPHAS))]
+    for j, p in enumerate(plans):
+        p.solve_host(f_host[j].numpy(), tol=TOL, mode=mode_mixed)
+    torch.cuda.synchronize()
+    k_e2e = max(1, min(steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        for j, p in enumerate(plans):
+            _, info = p.solve_host(f_host[j].numpy(), tol=TOL, mode=mode_mixed)
+            assert info["converged"] == 1
+    e2e_s = (time.perf_counter() - t0) / k_e2e
+    e2e = {"value": world * solves_per_step / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": solves_per_step * N_SIDE * N_SIDE * 8,
+           "d2h_bytes_per_step": solves_per_step * N_SIDE * N_SIDE * 8}
+
+    # per-kernel device time over profiled steps (CUDA events around each launch)
+    for p in plans:
+        p.profile(True)
+    for s in range(warm, warm + max(1, min(steps, 2))):
+        for j, p in enumerate(plans):
+            u.zero_()
+            p.solve(rhs[s][j].view(-1), u, tol=TOL, mode=mode_mixed)
+    stats = {}
+    for p in plans:
+        for name, (cnt, tot) in p.profile_read().items():
+            c0, t0_ = stats.get(name, (0, 0.0))
+            stats[name] = (c0 + cnt, t0_ + tot)
+        p.profile(False)
+    total = sum(t for _, t in stats.values())
+    top = sorted(stats.items(), key=lambda kv: -kv[1][1])
+    roofline = None
+    peak, peak_kind = peaks()
+    for name, (cnt, tot) in top:
+        elem = 4 if "f32" in name else 8
+        ab = algorithmic_bytes(name, N_SIDE, 2 * N_SIDE, elem)
+        if ab is None:
+            continue
+        avg_s = tot / cnt / 1e3
+        achieved = ab / avg_s / 1e9
+        roofline = {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1),
+                    "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                    "frac": round(achieved / peak, 4), "traffic": None,
+                    "bytes_per_launch": ab, "avg_launch_us": round(avg_s * 1e6, 2),
+                    "share": round(tot / total, 4) if total else None}
+        break
+    kernel_shares = {k: {"launches": c, "ms": round(t, 3), "share": round(t / total, 4)}
+                     for k, (c, t) in top[:10]}
+    its_mixed = [i["iterations"] for i in infos_mixed[: len(ALPHAS)]]
+    its_f64 = [i["iterations"] for i in infos_f64[: len(ALPHAS)]]
+    return {
+        "value": value, "ms_per_step": ms_mixed, "clocks": clocks, "e2e": e2e,
+        "gpu_launches": int(launches), "roofline": roofline, "t_con_s": t_con,
+        "fp64_pcg": {"value": value_f64, "unit": UNIT, "ms_per_step": ms_f64,
+                     "iterations": its_f64},
+        "speedup_vs_fp64_pcg": value / value_f64,
+        "iterations_mixed": its_mixed,
+        "refinements": [i["outer_iterations"] for i in infos_mixed[: len(ALPHAS)]],
+        "kernels": kernel_shares,
+    }
+
+
+def oracle_iterations():
+    path = os.path.join(ROOT, "tests", "golden", "oracle_iterations_2d_1024.txt")
+    its = {}
+    with open(path) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].split()
+            if line:
+                its[float(line[1])] = int(line[2])
+    return its
+
+
+def oracle_sample(iters_per_alpha=3):
+    """Time the FP64 oracle's CG iterations (operator apply, DST
+    preconditioner, vector updates) on the full 1024^2 workload and scale by
+    the oracle's own iteration counts to whole solves."""
+    from oracle import precond as opc
+    from oracle import solvers as osv
+    from oracle.operator import Plan as OPlan
+    counts = oracle_iterations()
+    f = make_rhs(0)
+    total_s = 0.0
+    sampled = 0
+    for alpha in ALPHAS:
+        op = OPlan(2, N_SIDE, 1.0 / (N_SIDE + 1), alpha)
+        op.kernel_hat()                       # operator construction, untimed
+        prec = (lambda r, op=op: opc.solve_box(op, r)) if alpha >= 1.0 else None
+        t0 = time.perf_counter()
+        osv.pcg(op.apply, f, prec, None, 1e-30, iters_per_alpha)
+        dt = (time.perf_counter() - t0) / iters_per_alpha
+        total_s += dt * counts[round(alpha, 2)]
+        sampled += iters_per_alpha
+    return len(ALPHAS) / total_s, sampled
+
+
+def cores_used():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    config = {"workload": WORKLOAD, "n": N_SIDE, "fft_len": 2 * N_SIDE, "alphas": list(ALPHAS),
+              "tol": TOL, "l2": "flushed between timed steps (512 MB write)",
+              "parallelism": f"replicas x{world} (independent seeds per rank)"}
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        steps_v = []
+        sampled = 0
+        for s in range(args.warmup + args.steps):
+            v, k = oracle_sample(iters_per_alpha=2)
+            if s >= args.warmup:
+                steps_v.append(v)
+                sampled += k
+        value = float(np.mean(steps_v))
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": len(ALPHAS) / value * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": config,
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores_used(),
+                                 "kind": "oracle",
+                                 "sample": f"{sampled} FP64 oracle CG iterations on the full "
+                                           "1024^2 workload, scaled by the oracle's iteration "
+                                           "counts (tests/golden/oracle_iterations_2d_1024.txt)"},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    res = run_ours(args, rank, world, local)
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            v, k = oracle_sample(iters_per_alpha=3)
+            cpu = {"value": v, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
+                   "sample": f"{k} FP64 oracle CG iterations (3 per alpha) on the full 1024^2 "
+                             "workload, scaled by the oracle's iteration counts"}
+        line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64", "data": "synthetic", "config": config,
+                "clocks": res["clocks"], "e2e": res["e2e"], "gpu_launches": res["gpu_launches"],
+                "roofline": res["roofline"], "cpu_baseline": cpu,
+                "fp64_pcg": res["fp64_pcg"], "speedup_vs_fp64_pcg": res["speedup_vs_fp64_pcg"],
+                "iterations_mixed": res["iterations_mixed"], "refinements": res["refinements"],
+                "t_con_s": res["t_con_s"], "kernels": res["kernels"]}
+        print(json.dumps(line))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

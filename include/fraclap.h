@@ -154,6 +154,25 @@ fl_status fl_time_step(fl_plan* plan, double dt, double theta, const double* u_p
                        const double* f_prev_dev, const double* f_next_dev, double* u_next_dev,
                        double tol, int maxit, int mode, fl_solve_info* info);
 
+/* Instrumentation (no counterpart in the paper).
+ * fl_launch_count: number of kernels the library has launched in this
+ * process (all plans, all threads).
+ * fl_profile_enable: while enabled, every kernel the plan's calls launch is
+ * bracketed by CUDA events on the plan's stream (adds two event records per
+ * launch); disabling discards the statistics.
+ * fl_profile_read: waits for the stream, then fills up to max_stats entries
+ * (per kernel name: launches and summed device time) and returns the number
+ * of distinct kernels recorded (0 when profiling is off). */
+typedef struct {
+  char name[48];
+  long long launches;
+  double total_ms;
+} fl_kernel_stat;
+
+long long fl_launch_count(void);
+fl_status fl_profile_enable(fl_plan* plan, int enable);
+int fl_profile_read(fl_plan* plan, fl_kernel_stat* stats, int max_stats);
+
 /* Wait for all work on the plan's stream. */
 fl_status fl_sync(fl_plan* plan);
 

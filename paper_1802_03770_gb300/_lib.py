@@ -50,6 +50,11 @@ class FlPlanDesc(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_int64)]
 
 
+class FlKernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_longlong),
+                ("total_ms", ctypes.c_double)]
+
+
 _P = ctypes.c_void_p
 _D = ctypes.c_double
 _I = ctypes.c_int
@@ -68,6 +73,9 @@ SIGNATURES = {
     "fl_solve_elliptic_host": (_I, [_P, _P, _P, _D, _I, _I, ctypes.POINTER(FlSolveInfo)]),
     "fl_time_step": (_I, [_P, _D, _D, _P, _P, _P, _P, _D, _I, _I, ctypes.POINTER(FlSolveInfo)]),
     "fl_sync": (_I, [_P]),
+    "fl_launch_count": (ctypes.c_longlong, []),
+    "fl_profile_enable": (_I, [_P, _I]),
+    "fl_profile_read": (_I, [_P, ctypes.POINTER(FlKernelStat), _I]),
     "fl_last_error_string": (ctypes.c_char_p, []),
 }
 

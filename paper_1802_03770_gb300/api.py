@@ -26,6 +26,11 @@ def _check_tensor(t, dtype, numel, what):
         raise ValueError(f"{what} must be contiguous with {numel} elements")
 
 
+def launch_count():
+    """Kernels launched by libfraclap.so in this process so far."""
+    return int(L.load().fl_launch_count())
+
+
 class Plan:
     """Operator plan: fl_plan_create(d, n, h, alpha, mask) on the current
     device and torch stream (or the given one)."""
@@ -140,6 +145,15 @@ class Plan:
                                     ctypes.byref(info))
         L.check(st, "fl_time_step")
         return u_next, info.as_dict()
+
+    def profile(self, enable=True):
+        L.check(self._lib.fl_profile_enable(self._h, int(enable)), "fl_profile_enable")
+
+    def profile_read(self):
+        """{kernel name: (launches, total ms)} since profiling was enabled."""
+        buf = (L.FlKernelStat * 64)()
+        n = self._lib.fl_profile_read(self._h, buf, 64)
+        return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms) for i in range(min(n, 64))}
 
     def sync(self):
         L.check(self._lib.fl_sync(self._h), "fl_sync")

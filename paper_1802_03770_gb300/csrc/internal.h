@@ -112,6 +112,23 @@ cudaError_t launch_sum(cudaStream_t s, const double* part, int count, double* ou
 cudaError_t build_symbol(const Geo& g, double c, double Z, double a, double expo, cudaStream_t s,
                          double* sig64, float* sig32, const double2* tw64);
 size_t partial_capacity(const Geo& g);
+
+// --- launch accounting (plan.cu) ----------------------------------------------
+// Every kernel launch of the library goes through FL_KERNEL: it counts the
+// launch and, while a profiler is active on this thread, brackets it with
+// CUDA events on its stream.
+void note_launch();
+bool prof_active();
+cudaEvent_t prof_begin(cudaStream_t s);
+void prof_end(const char* name, cudaEvent_t e0, cudaStream_t s);
+
+#define FL_KERNEL(name, stream, ...)                                  \
+  do {                                                                \
+    ::fl::note_launch();                                              \
+    cudaEvent_t fl_e0_ = ::fl::prof_active() ? ::fl::prof_begin(stream) : nullptr; \
+    __VA_ARGS__;                                                      \
+    if (fl_e0_) ::fl::prof_end(name, fl_e0_, stream);                 \
+  } while (0)
 cudaError_t configure_kernels();
 
 }  // namespace fl

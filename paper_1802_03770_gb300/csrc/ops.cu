@@ -321,7 +321,8 @@ cudaError_t launch_apply(const Geo& g, const Tables<T>& tb, cudaStream_t s, cons
     a.S = tb.S; a.tw = tb.tw; a.st = io.st;
     a.rows = (int)rows; a.n = g.n[d - 1]; a.H = g.H; a.lg = g.lg[d - 1]; a.lgmax = g.lgmax;
     a.rows_per_plane = rpp; a.plane_stride = pstride; a.pre = io.pre;
-    k_rows_fwd<T, K::RT, K::RV><<<rblocks, K::RT, smem_bytes<T>(NL, Lx), s>>>(a);
+    FL_KERNEL((sizeof(T) == 4 ? "rows_fwd" "<f32>" : "rows_fwd" "<f64>"), s,
+              k_rows_fwd<T, K::RT, K::RV><<<rblocks, K::RT, smem_bytes<T>(NL, Lx), s>>>(a));
   }
   auto cols = [&](int axis, int mode, int rows_in, int rows_out, long long lstride,
                   long long ostride, int nouter, long long sig_line, long long sig_outer, int Lo) {
@@ -333,7 +334,10 @@ cudaError_t launch_apply(const Geo& g, const Tables<T>& tb, cudaStream_t s, cons
     const int L = g.L[axis];
     a.tx = col_tx<T>(L);
     dim3 grid((g.H + a.tx - 1) / a.tx, nouter);
-    k_cols<T, K::CT, K::CV><<<grid, K::CT, smem_bytes<T>(a.tx, L), s>>>(a);
+    static const char* const kn[2][4] = {{"cols_fwd<f64>", "cols_conv<f64>", "cols_inv<f64>", "cols_full<f64>"},
+                                         {"cols_fwd<f32>", "cols_conv<f32>", "cols_inv<f32>", "cols_full<f32>"}};
+    FL_KERNEL(kn[sizeof(T) == 4][mode], s,
+              k_cols<T, K::CT, K::CV><<<grid, K::CT, smem_bytes<T>(a.tx, L), s>>>(a));
   };
   if (d == 2) {
     cols(0, COLS_CONV, g.n[0], g.n[0], g.H, 0, 1, g.H, 0, 0);
@@ -352,7 +356,8 @@ cudaError_t launch_apply(const Geo& g, const Tables<T>& tb, cudaStream_t s, cons
     a.cm = io.cm; a.cx = io.cx; a.cb = io.cb;
     a.rows = (int)rows; a.n = g.n[d - 1]; a.H = g.H; a.lg = g.lg[d - 1]; a.lgmax = g.lgmax;
     a.rows_per_plane = rpp; a.plane_stride = pstride; a.dot_self = io.dot_self;
-    k_rows_inv<T, K::RT, K::RV><<<rblocks, K::RT, smem_bytes<T>(NL, Lx), s>>>(a);
+    FL_KERNEL((sizeof(T) == 4 ? "rows_inv" "<f32>" : "rows_inv" "<f64>"), s,
+              k_rows_inv<T, K::RT, K::RV><<<rblocks, K::RT, smem_bytes<T>(NL, Lx), s>>>(a));
   }
   return cudaGetLastError();
 }
@@ -375,7 +380,8 @@ cudaError_t launch_precond(const Geo& g, const Tables<T>& tb, const double* cons
     a.pq_part = io.pq_part; a.pq_count = io.pq_count; a.rr_part = io.rr_part;
     a.dotw = nullptr; a.dot_part = nullptr; a.post = 1.0;
     a.rows = (int)rows; a.n = nx; a.lg = g.lg[d - 1]; a.lgmax = g.lgmax; a.pre = io.pre;
-    k_dst_rows<T, K::RT, K::RV><<<rblocks, K::RT, smem_bytes<T>(NL, Lx), s>>>(a);
+    FL_KERNEL((sizeof(T) == 4 ? "dst_rows" "<f32>" : "dst_rows" "<f64>"), s,
+              k_dst_rows<T, K::RT, K::RV><<<rblocks, K::RT, smem_bytes<T>(NL, Lx), s>>>(a));
   }
   auto cols = [&](int axis, int mode, long long lstride, long long ostride, int nouter,
                   const double* mu_line, const double* mu_col, const double* mu_outer) {
@@ -388,7 +394,10 @@ cudaError_t launch_precond(const Geo& g, const Tables<T>& tb, const double* cons
     const int L = g.L[axis];
     a.tx = col_tx<T>(L);
     dim3 grid((nx + a.tx - 1) / a.tx, nouter);
-    k_dst_cols<T, K::CT, K::CV><<<grid, K::CT, smem_bytes<T>(a.tx, L), s>>>(a);
+    static const char* const kn[2][2] = {{"dst_cols<f64>", "dst_cols_div<f64>"},
+                                         {"dst_cols<f32>", "dst_cols_div<f32>"}};
+    FL_KERNEL(kn[sizeof(T) == 4][mode], s,
+              k_dst_cols<T, K::CT, K::CV><<<grid, K::CT, smem_bytes<T>(a.tx, L), s>>>(a));
   };
   if (d == 2) {
     cols(0, DST_DIV_DST, nx, 0, 1, mu[0], mu[1], nullptr);
@@ -403,9 +412,11 @@ cudaError_t launch_precond(const Geo& g, const Tables<T>& tb, const double* cons
     a.in = tb.t; a.out = io.out; a.tw = tb.tw; a.chirp = tb.chirp[d - 1]; a.bhat = tb.bhat[d - 1];
     a.st = io.st; a.dotw = io.dotw; a.dot_part = io.dot_part; a.post = post;
     a.rows = (int)rows; a.n = nx; a.lg = g.lg[d - 1]; a.lgmax = g.lgmax; a.pre = DPRE_NONE;
-    k_dst_rows<T, K::RT, K::RV><<<rblocks, K::RT, smem_bytes<T>(NL, Lx), s>>>(a);
+    FL_KERNEL((sizeof(T) == 4 ? "dst_rows" "<f32>" : "dst_rows" "<f64>"), s,
+              k_dst_rows<T, K::RT, K::RV><<<rblocks, K::RT, smem_bytes<T>(NL, Lx), s>>>(a));
   }
-  if (io.pre == DPRE_UPDATE) k_store_pq<<<1, 256, 0, s>>>(io.st, io.pq_part, io.pq_count);
+  if (io.pre == DPRE_UPDATE)
+    FL_KERNEL("store_pq", s, k_store_pq<<<1, 256, 0, s>>>(io.st, io.pq_part, io.pq_count));
   return cudaGetLastError();
 }
 
@@ -413,34 +424,39 @@ template <typename T>
 cudaError_t launch_noprec_update(long long N, cudaStream_t s, PcgState* st, T* x, T* r, const T* p,
                                  const T* q, const double* pq_part, int pq_count, double* rr_part,
                                  int* count) {
-  k_noprec_update<T><<<kVecBlocks, kVecThreads, 0, s>>>(st, x, r, p, q, pq_part, pq_count, rr_part, N);
+  FL_KERNEL((sizeof(T) == 4 ? "noprec_update" "<f32>" : "noprec_update" "<f64>"), s,
+            k_noprec_update<T><<<kVecBlocks, kVecThreads, 0, s>>>(st, x, r, p, q, pq_part, pq_count, rr_part, N));
   *count = kVecBlocks;
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_dot(long long N, cudaStream_t s, const T* a, const T* b, double* part, int* count) {
-  k_dot<T><<<kVecBlocks, kVecThreads, 0, s>>>(a, b, part, N);
+  FL_KERNEL((sizeof(T) == 4 ? "dot" "<f32>" : "dot" "<f64>"), s,
+            k_dot<T><<<kVecBlocks, kVecThreads, 0, s>>>(a, b, part, N));
   *count = kVecBlocks;
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_copy_cast(long long N, cudaStream_t s, const double* src, T* dst) {
-  k_copy_cast<T><<<kVecBlocks, kVecThreads, 0, s>>>(src, dst, N);
+  FL_KERNEL((sizeof(T) == 4 ? "copy_cast" "<f32>" : "copy_cast" "<f64>"), s,
+            k_copy_cast<T><<<kVecBlocks, kVecThreads, 0, s>>>(src, dst, N));
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_axpby(long long N, cudaStream_t s, double a, const T* x, double b, T* y) {
-  k_axpby<T><<<kVecBlocks, kVecThreads, 0, s>>>(a, x, b, y, N);
+  FL_KERNEL((sizeof(T) == 4 ? "axpby" "<f32>" : "axpby" "<f64>"), s,
+            k_axpby<T><<<kVecBlocks, kVecThreads, 0, s>>>(a, x, b, y, N));
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_mask_copy_dot(long long N, cudaStream_t s, const T* src, const uint8_t* mask, T* dst,
                                  double* part, int* count) {
-  k_mask_copy_dot<T><<<kVecBlocks, kVecThreads, 0, s>>>(src, mask, dst, part, N);
+  FL_KERNEL((sizeof(T) == 4 ? "mask_copy_dot" "<f32>" : "mask_copy_dot" "<f64>"), s,
+            k_mask_copy_dot<T><<<kVecBlocks, kVecThreads, 0, s>>>(src, mask, dst, part, N));
   *count = kVecBlocks;
   return cudaGetLastError();
 }
@@ -448,25 +464,29 @@ template cudaError_t launch_mask_copy_dot<float>(long long, cudaStream_t, const 
 template cudaError_t launch_mask_copy_dot<double>(long long, cudaStream_t, const double*, const uint8_t*, double*, double*, int*);
 
 cudaError_t launch_accum_f32(long long N, cudaStream_t s, double* u, const float* x) {
-  k_accum_f32<<<kVecBlocks, kVecThreads, 0, s>>>(u, x, N);
+  FL_KERNEL("accum_f32", s,
+            k_accum_f32<<<kVecBlocks, kVecThreads, 0, s>>>(u, x, N));
   return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_init(cudaStream_t s, PcgState* st, const double* bb_part, int bb_count,
                             const double* rr_part, int rr_count, const double* rz_part, int rz_count,
                             double tol, int maxit) {
-  k_pcg_init<<<1, 256, 0, s>>>(st, bb_part, bb_count, rr_part, rr_count, rz_part, rz_count, tol, maxit);
+  FL_KERNEL("pcg_init", s,
+            k_pcg_init<<<1, 256, 0, s>>>(st, bb_part, bb_count, rr_part, rr_count, rz_part, rz_count, tol, maxit));
   return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_scalar(cudaStream_t s, PcgState* st, const double* rr_part, int rr_count,
                               const double* rz_part, int rz_count) {
-  k_pcg_scalar<<<1, 256, 0, s>>>(st, rr_part, rr_count, rz_part, rz_count);
+  FL_KERNEL("pcg_scalar", s,
+            k_pcg_scalar<<<1, 256, 0, s>>>(st, rr_part, rr_count, rz_part, rz_count));
   return cudaGetLastError();
 }
 
 cudaError_t launch_sum(cudaStream_t s, const double* part, int count, double* out) {
-  k_sum<<<1, 256, 0, s>>>(part, count, out);
+  FL_KERNEL("sum", s,
+            k_sum<<<1, 256, 0, s>>>(part, count, out));
   return cudaGetLastError();
 }
 
@@ -486,15 +506,17 @@ cudaError_t build_symbol(const Geo& g, double c, double Z, double a, double expo
   cudaError_t e = cudaMallocAsync(&buf, total * sizeof(double2), s);
   if (e != cudaSuccess) return e;
   const int bt = 256;
-  k_fill_kernel<<<(unsigned)((total + bt - 1) / bt), bt, 0, s>>>(buf, d, Ls[0], Ls[1], Ls[2], ns[0],
-                                                                 ns[1], ns[2], c, Z, a, expo, total);
+  FL_KERNEL("fill_kernel", s,
+            k_fill_kernel<<<(unsigned)((total + bt - 1) / bt), bt, 0, s>>>(buf, d, Ls[0], Ls[1], Ls[2], ns[0],
+                                                                 ns[1], ns[2], c, Z, a, expo, total));
   // last axis: contiguous lines
   {
     const int L = g.L[d - 1];
     const long long rows = total / L;
     const int NL = row_lines<double>(L);
-    k_rows_c2c<K::RT, K::RV><<<(unsigned)((rows + NL - 1) / NL), K::RT, smem_bytes<double>(NL, L), s>>>(
-        buf, (int)rows, g.lg[d - 1], g.lgmax, tw64);
+    FL_KERNEL("rows_c2c", s,
+              k_rows_c2c<K::RT, K::RV><<<(unsigned)((rows + NL - 1) / NL), K::RT, smem_bytes<double>(NL, L), s>>>(
+        buf, (int)rows, g.lg[d - 1], g.lgmax, tw64));
   }
   // slower axes: strided lines, full length in and out
   for (int axis = d - 2; axis >= 0; --axis) {
@@ -508,12 +530,14 @@ cudaError_t build_symbol(const Geo& g, double c, double Z, double a, double expo
     else { ca.lstride = (long long)Ls[1] * Ls[2]; ca.ostride = Ls[2]; ca.nouter = Ls[1]; }
     ca.tx = col_tx<double>(Ls[axis]);
     dim3 grid((ca.H + ca.tx - 1) / ca.tx, ca.nouter);
-    k_cols<double, K::CT, K::CV><<<grid, K::CT, smem_bytes<double>(ca.tx, Ls[axis]), s>>>(ca);
+    FL_KERNEL("cols_symbol", s,
+              k_cols<double, K::CT, K::CV><<<grid, K::CT, smem_bytes<double>(ca.tx, Ls[axis]), s>>>(ca));
   }
   double inv = 1.0;
   for (int i = 0; i < d; ++i) inv /= (double)g.L[i];
-  k_extract_symbol<<<(unsigned)((half + bt - 1) / bt), bt, 0, s>>>(buf, d, Ls[0], Ls[1], Ls[2], inv,
-                                                                  sig64, sig32, half);
+  FL_KERNEL("extract_symbol", s,
+            k_extract_symbol<<<(unsigned)((half + bt - 1) / bt), bt, 0, s>>>(buf, d, Ls[0], Ls[1], Ls[2], inv,
+                                                                  sig64, sig32, half));
   e = cudaGetLastError();
   cudaError_t e2 = cudaFreeAsync(buf, s);
   return e != cudaSuccess ? e : e2;

@@ -1,6 +1,7 @@
 // Host side of the C ABI: plan creation (constants, tables, symbol,
 // workspaces), the apply / preconditioner entry points and the CG drivers
 // (plain FP64 CG, FP32 CG inside FP64 iterative refinement, theta steps).
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -41,6 +42,48 @@ struct Vecs {
 
 }  // namespace
 
+struct Profiler {
+  struct Pending { const char* name; cudaEvent_t e0, e1; };
+  struct Stat { std::string name; long long launches = 0; double ms = 0.0; };
+  std::vector<cudaEvent_t> pool;
+  std::vector<Pending> pending;
+  std::vector<Stat> stats;
+  cudaEvent_t take() {
+    if (pool.empty()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      return e;
+    }
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  void resolve() {
+    for (auto& pe : pending) {
+      float ms = 0.f;
+      cudaEventSynchronize(pe.e1);
+      cudaEventElapsedTime(&ms, pe.e0, pe.e1);
+      Stat* st = nullptr;
+      for (auto& x : stats)
+        if (x.name == pe.name) st = &x;
+      if (!st) {
+        stats.push_back(Stat());
+        st = &stats.back();
+        st->name = pe.name;
+      }
+      st->launches += 1;
+      st->ms += ms;
+      pool.push_back(pe.e0);
+      pool.push_back(pe.e1);
+    }
+    pending.clear();
+  }
+  ~Profiler() {
+    resolve();
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
 struct fl_plan {
   Geo g;
   double h, alpha, rho;
@@ -63,6 +106,7 @@ struct fl_plan {
   double* scalar_host = nullptr;  // pinned
   std::vector<void*> allocs;
   int64_t bytes = 0;
+  struct Profiler* prof = nullptr;   // non-null while profiling is enabled
 };
 
 namespace {
@@ -83,6 +127,10 @@ cudaError_t dalloc(fl_plan* p, P** ptr, size_t bytes) {
 
 void free_plan(fl_plan* p) {
   if (!p) return;
+  if (p->prof) {
+    cudaStreamSynchronize(p->stream);
+    delete p->prof;
+  }
   for (void* v : p->allocs) cudaFree(v);
   if (p->st_host) cudaFreeHost(p->st_host);
   if (p->scalar_host) cudaFreeHost(p->scalar_host);
@@ -382,6 +430,37 @@ bool check_plan(const fl_plan* p) { return p != nullptr; }
 
 }  // namespace
 
+// --- launch accounting and the per-kernel profiler -----------------------------
+
+namespace {
+std::atomic<long long> g_launches{0};
+thread_local Profiler* t_prof = nullptr;
+
+// Makes the plan's profiler the active one for the duration of an API call.
+struct ProfScope {
+  Profiler* saved;
+  explicit ProfScope(fl_plan* p);
+  ~ProfScope() { t_prof = saved; }
+};
+}  // namespace
+
+namespace fl {
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+bool prof_active() { return t_prof != nullptr; }
+cudaEvent_t prof_begin(cudaStream_t s) {
+  cudaEvent_t e = t_prof->take();
+  cudaEventRecord(e, s);
+  return e;
+}
+void prof_end(const char* name, cudaEvent_t e0, cudaStream_t s) {
+  cudaEvent_t e1 = t_prof->take();
+  cudaEventRecord(e1, s);
+  t_prof->pending.push_back({name, e0, e1});
+}
+}  // namespace fl
+
+ProfScope::ProfScope(fl_plan* p) : saved(t_prof) { t_prof = p ? p->prof : nullptr; }
+
 extern "C" {
 
 const char* fl_last_error_string(void) { return g_err.c_str(); }
@@ -492,6 +571,7 @@ fl_status fl_plan_describe(const fl_plan* p, fl_plan_desc* desc) {
 }
 
 fl_status fl_apply(fl_plan* p, const double* u, double* y) {
+  ProfScope prof_scope(p);
   if (!check_plan(p) || !u || !y) return fail(FL_INVALID_ARG, "NULL argument");
   if (u == y) return fail(FL_INVALID_ARG, "u and y may not alias");
   ApplyIO<double> io;
@@ -501,6 +581,7 @@ fl_status fl_apply(fl_plan* p, const double* u, double* y) {
 }
 
 fl_status fl_apply_f32(fl_plan* p, const float* u, float* y) {
+  ProfScope prof_scope(p);
   if (!check_plan(p) || !u || !y) return fail(FL_INVALID_ARG, "NULL argument");
   if (u == y) return fail(FL_INVALID_ARG, "u and y may not alias");
   ApplyIO<float> io;
@@ -510,6 +591,7 @@ fl_status fl_apply_f32(fl_plan* p, const float* u, float* y) {
 }
 
 fl_status fl_precond(fl_plan* p, double shift, double scale, const double* r, double* z) {
+  ProfScope prof_scope(p);
   if (!check_plan(p) || !r || !z) return fail(FL_INVALID_ARG, "NULL argument");
   if (r == z) return fail(FL_INVALID_ARG, "r and z may not alias");
   if (p->has_mask) return fail(FL_INVALID_ARG, "the sine-transform preconditioner needs a plan without mask");
@@ -520,6 +602,7 @@ fl_status fl_precond(fl_plan* p, double shift, double scale, const double* r, do
 }
 
 fl_status fl_precond_f32(fl_plan* p, double shift, double scale, const float* r, float* z) {
+  ProfScope prof_scope(p);
   if (!check_plan(p) || !r || !z) return fail(FL_INVALID_ARG, "NULL argument");
   if (r == z) return fail(FL_INVALID_ARG, "r and z may not alias");
   if (p->has_mask) return fail(FL_INVALID_ARG, "the sine-transform preconditioner needs a plan without mask");
@@ -531,6 +614,7 @@ fl_status fl_precond_f32(fl_plan* p, double shift, double scale, const float* r,
 
 fl_status fl_solve_elliptic(fl_plan* p, const double* f, double* u, int x0_nonzero, double tol,
                             int maxit, int mode, fl_solve_info* info) {
+  ProfScope prof_scope(p);
   if (!check_plan(p) || !f || !u) return fail(FL_INVALID_ARG, "NULL argument");
   FL_CUDA(cudaMemcpyAsync(p->v64.b, f, p->g.N * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
   return solve_system(p, u, x0_nonzero != 0, 0.0, 1.0, tol, maxit, mode, info);
@@ -538,6 +622,7 @@ fl_status fl_solve_elliptic(fl_plan* p, const double* f, double* u, int x0_nonze
 
 fl_status fl_solve_elliptic_host(fl_plan* p, const double* f_host, double* u_host, double tol,
                                  int maxit, int mode, fl_solve_info* info) {
+  ProfScope prof_scope(p);
   if (!check_plan(p) || !f_host || !u_host) return fail(FL_INVALID_ARG, "NULL argument");
   const size_t bytes = p->g.N * sizeof(double);
   FL_CUDA(cudaMemcpyAsync(p->v64.b, f_host, bytes, cudaMemcpyHostToDevice, p->stream));
@@ -552,6 +637,7 @@ fl_status fl_solve_elliptic_host(fl_plan* p, const double* f_host, double* u_hos
 fl_status fl_time_step(fl_plan* p, double dt, double theta, const double* u_prev,
                        const double* f_prev, const double* f_next, double* u_next, double tol,
                        int maxit, int mode, fl_solve_info* info) {
+  ProfScope prof_scope(p);
   if (!check_plan(p) || !u_prev || !u_next) return fail(FL_INVALID_ARG, "NULL argument");
   if (!(dt > 0.0) || !(theta > 0.0 && theta <= 1.0))
     return fail(FL_INVALID_ARG, "dt must be > 0 and theta in (0, 1]");
@@ -572,6 +658,34 @@ fl_status fl_time_step(fl_plan* p, double dt, double theta, const double* u_prev
   if (u_next != u_prev)
     FL_CUDA(cudaMemcpyAsync(u_next, u_prev, g.N * sizeof(double), cudaMemcpyDeviceToDevice, s));
   return solve_system(p, u_next, true, 1.0, theta * dt, tol, maxit, mode, info);
+}
+
+long long fl_launch_count(void) { return g_launches.load(); }
+
+fl_status fl_profile_enable(fl_plan* p, int enable) {
+  if (!check_plan(p)) return fail(FL_INVALID_ARG, "NULL plan");
+  if (enable && !p->prof) p->prof = new Profiler();
+  if (!enable && p->prof) {
+    FL_CUDA(cudaStreamSynchronize(p->stream));
+    delete p->prof;
+    p->prof = nullptr;
+  }
+  return FL_OK;
+}
+
+int fl_profile_read(fl_plan* p, fl_kernel_stat* stats, int max_stats) {
+  if (!check_plan(p) || !p->prof) return 0;
+  cudaStreamSynchronize(p->stream);
+  p->prof->resolve();
+  const int n = (int)p->prof->stats.size();
+  for (int i = 0; i < n && i < max_stats && stats; ++i) {
+    const auto& st = p->prof->stats[i];
+    memset(&stats[i], 0, sizeof(fl_kernel_stat));
+    strncpy(stats[i].name, st.name.c_str(), sizeof(stats[i].name) - 1);
+    stats[i].launches = st.launches;
+    stats[i].total_ms = st.ms;
+  }
+  return n;
 }
 
 fl_status fl_sync(fl_plan* p) {
