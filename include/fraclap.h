@@ -173,6 +173,29 @@ long long fl_launch_count(void);
 fl_status fl_profile_enable(fl_plan* plan, int enable);
 int fl_profile_read(fl_plan* plan, fl_kernel_stat* stats, int max_stats);
 
+/* y = M u in FP32, like fl_apply_f32, but its one scratch buffer (the
+ * half-spectrum workspace of the FFT passes) is a fixed, library-owned
+ * device array instead of the plan's workspace, and the call allocates
+ * nothing: no cudaMalloc, cudaFree or allocating library routine.  The
+ * paper has no counterpart; this entry exists for callers that cannot call
+ * cudaMalloc at the point where they apply the operator -- code that runs
+ * while a CUDA stream is being captured into a graph, or a host whose device
+ * memory is owned by another runtime's allocator -- and who created the plan
+ * earlier, at set-up time.
+ *   - Limit: the plan's spectrum must fit the array, 2^21 complex floats
+ *     (16 MiB): n_0 * (L_1/2 + 1) <= 2^21 in 2D (1024 x 1024 fits),
+ *     n_0 * L_1 * (L_2/2 + 1) <= 2^21 in 3D (64^3 fits).  Larger plans get
+ *     FL_INVALID_ARG and nothing runs.
+ *   - Every GPU that loads the library holds the 16 MiB array until the
+ *     process exits.
+ *   - The first call on a device looks the array's device address up (with
+ *     that device current); make that first call before any stream capture.
+ *   - All calls, on every plan and stream of a device, share the one array
+ *     and it keeps the last call's contents: calls that overlap on the GPU
+ *     race and give wrong results.  Nothing in it needs to start at zero.
+ *   - Arguments, layout and errors are those of fl_apply_f32. */
+fl_status fl_apply_f32_static(fl_plan* plan, const float* u_dev, float* y_dev);
+
 /* Wait for all work on the plan's stream. */
 fl_status fl_sync(fl_plan* plan);
 

@@ -6,6 +6,7 @@
 #include <complex>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -686,6 +687,54 @@ int fl_profile_read(fl_plan* p, fl_kernel_stat* stats, int max_stats) {
     stats[i].total_ms = st.ms;
   }
   return n;
+}
+
+}  // extern "C"
+
+// --- allocation-free FP32 apply ----------------------------------------------
+// The half-spectrum workspace of fl_apply_f32_static.  In host code the name
+// g_static_spec is only a stand-in: the kernels get the device address that
+// cudaGetSymbolAddress returns for the current device.
+namespace {
+constexpr long long kStaticSpecElems = 1LL << 21;  // complex floats, 16 MiB
+__device__ __align__(256) float2 g_static_spec[kStaticSpecElems];
+std::mutex g_static_mu;
+float2* g_static_addr[256] = {nullptr};
+
+// Device address of g_static_spec on the current device, looked up once per
+// device.
+fl_status static_spec_address(float2** out) {
+  int dev = 0;
+  FL_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return fail(FL_INVALID_ARG, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* ptr = nullptr;
+    FL_CUDA(cudaGetSymbolAddress(&ptr, g_static_spec));
+    g_static_addr[dev] = reinterpret_cast<float2*>(ptr);
+  }
+  *out = g_static_addr[dev];
+  return FL_OK;
+}
+}  // namespace
+
+extern "C" {
+
+fl_status fl_apply_f32_static(fl_plan* p, const float* u, float* y) {
+  ProfScope prof_scope(p);
+  if (!check_plan(p) || !u || !y) return fail(FL_INVALID_ARG, "NULL argument");
+  if (u == y) return fail(FL_INVALID_ARG, "u and y may not alias");
+  if (p->g.spec > kStaticSpecElems)
+    return fail(FL_INVALID_ARG, "plan too large for the static scratch (2^21 complex floats)");
+  float2* scratch = nullptr;
+  fl_status st = static_spec_address(&scratch);
+  if (st != FL_OK) return st;
+  Tables<float> tb = p->t32;
+  tb.S = scratch;
+  ApplyIO<float> io;
+  io.u = u; io.mask = p->mask; io.out = y;
+  FL_CUDA(launch_apply<float>(p->g, tb, p->stream, io));
+  return FL_OK;
 }
 
 fl_status fl_sync(fl_plan* p) {
