@@ -90,7 +90,8 @@ class ClockSampler:
         sm = [float(r[0]) for r in rows if r[0].strip().replace(".", "").isdigit()]
         smax = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[4 + i]})
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if r[4 + i].strip() == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
                 "samples": len(rows)}

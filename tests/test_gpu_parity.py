@@ -266,3 +266,49 @@ def test_full_size_3d_256_apply_samples():
     got = np.array([y[i] for i in idx])
     scale = np.abs(y).max()
     assert np.max(np.abs(got - ref)) <= 1e-10 * scale
+
+
+def test_table_td_its_on_gpu(golden):
+    """Table tab:td_its on the GPU: one Crank-Nicolson system with random RHS
+    from a zero start (u_prev = 0, f_prev = f_next = b / dt), FP64 CG with the
+    I + dt/2 C h^d L preconditioner: the paper's preconditioned counts."""
+    for d, n, alpha, its_p, _ in golden("table_td_its.txt"):
+        d, n = int(d), int(n)
+        if d == 3:
+            continue
+        dt = 1.0 / (n + 1)
+        b = inputs.random_field(n, d, 0)
+        p = Plan(d, (n,) * d, 1.0 / (n + 1), alpha)
+        zero = gpu(np.zeros((n,) * d))
+        f = gpu(b / dt)
+        _, info = p.time_step(zero, dt, 0.5, f, f, tol=1e-9, mode=_lib.FL_MODE_F64)
+        assert info["iterations"] == int(its_p), (alpha, info)
+
+
+def test_table_3d_its_on_gpu(golden):
+    """Table tab:3D_its preconditioned counts (f = 1, 31^3, 1e-9) on the GPU."""
+    for n, alpha, its_p, _ in golden("table_3d_its.txt"):
+        n = int(n)
+        p = Plan(3, (n, n, n), 1.0 / (n + 1), alpha)
+        _, info = p.solve(gpu(np.ones((n, n, n))), tol=1e-9, mode=_lib.FL_MODE_F64)
+        assert abs(info["iterations"] - its_p) <= 3, (alpha, info)
+
+
+def test_full_size_3d_256_backward_euler_step():
+    """256^3, alpha = 1.5, dt = 1e-3, u0 = 16 Gaussians (widths U(0.05, 0.15)),
+    f = 0: one mixed-precision backward-Euler step to 1e-8; the residual
+    u + dt M u - u0 is checked at sampled points by direct summation."""
+    n = 256
+    h = 1.0 / (n + 1)
+    dt = 1e-3
+    u0 = inputs.gaussian_mixture(n, 3, 16, 3, 0.05, 0.15)
+    p = Plan(3, (n, n, n), h, 1.5)
+    u1, info = p.time_step(gpu(u0), dt, 1.0, tol=1e-8, mode=_lib.FL_MODE_MIXED)
+    assert info["converged"] == 1 and info["rel_residual"] <= 1e-8
+    u1 = host(u1)
+    op = OPlan(3, n, h, 1.5)
+    rng = np.random.default_rng(17)
+    idx = [tuple(rng.integers(0, n, 3)) for _ in range(4)] + [(128, 128, 128), (5, 250, 131)]
+    mu = _direct_samples(op, u1, idx)
+    res = np.array([u1[i] + dt * m - u0[i] for i, m in zip(idx, mu)])
+    assert np.max(np.abs(res)) <= 1e-7 * np.abs(u0).max()
