@@ -290,6 +290,19 @@ def oracle_sample(iters_per_alpha=3):
     return len(ALPHAS) / total_s, sampled
 
 
+def profile_case():
+    """The workload's alpha = 1.5 solve, twice (the second is the captured one)."""
+    import torch
+    from paper_1802_03770_gb300 import _lib
+    from paper_1802_03770_gb300.api import Plan
+    p = Plan(2, (N_SIDE, N_SIDE), 1.0 / (N_SIDE + 1), 1.5)
+    f = torch.tensor(make_rhs(0), dtype=torch.float64, device="cuda:0").view(-1)
+    for _ in range(2):
+        u, info = p.solve(f, tol=TOL, mode=_lib.FL_MODE_MIXED | _lib.FL_PRECOND_AUTO)
+    torch.cuda.synchronize()
+    print(json.dumps(info))
+
+
 def cores_used():
     try:
         return len(os.sched_getaffinity(0))
@@ -304,7 +317,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run two mixed solves at alpha = 1.5 and exit (for ncu captures)")
     args = ap.parse_args()
+    if args.profile_case:
+        profile_case()
+        return
     rank, world, local = dist_env()
     config = {"workload": WORKLOAD, "n": N_SIDE, "fft_len": 2 * N_SIDE, "alphas": list(ALPHAS),
               "tol": TOL, "l2": "flushed between timed steps (512 MB write)",

@@ -196,6 +196,23 @@ int fl_profile_read(fl_plan* plan, fl_kernel_stat* stats, int max_stats);
  *   - Arguments, layout and errors are those of fl_apply_f32. */
 fl_status fl_apply_f32_static(fl_plan* plan, const float* u_dev, float* y_dev);
 
+/* Solve count independent problems M_i u_i = f_i (each eq. matelliptic with
+ * its own plan: size, h, alpha) to ||f_i - M_i u_i|| <= tol ||f_i||, in
+ * lockstep.  With FL_MODE_MIXED every pass of the FP64 residual, of the FP32
+ * CG start-up and of a CG iteration is one launch over all problems, and the
+ * CG iterations run as a captured CUDA graph on a private stream (ordered
+ * after and before the plans' streams).  FL_MODE_F64 solves the problems one
+ * after another with fl_solve_elliptic.
+ *   plans : host array of count distinct plans, all of the same d
+ *   f_dev : host array of count device pointers (N_i doubles each)
+ *   u_dev : host array of count device pointers, out: solutions (x0 = 0)
+ *   infos : nullable host array of count entries
+ * Returns FL_OK when every problem converged, FL_NOT_CONVERGED if one did
+ * not (all solutions are written), FL_INVALID_ARG, FL_CUDA_ERROR. */
+fl_status fl_solve_elliptic_batched(fl_plan* const* plans, int count, const double* const* f_dev,
+                                    double* const* u_dev, double tol, int maxit, int mode,
+                                    fl_solve_info* infos);
+
 /* Wait for all work on the plan's stream. */
 fl_status fl_sync(fl_plan* plan);
 

@@ -73,6 +73,9 @@ SIGNATURES = {
     "fl_solve_elliptic_host": (_I, [_P, _P, _P, _D, _I, _I, ctypes.POINTER(FlSolveInfo)]),
     "fl_time_step": (_I, [_P, _D, _D, _P, _P, _P, _P, _D, _I, _I, ctypes.POINTER(FlSolveInfo)]),
     "fl_apply_f32_static": (_I, [_P, _P, _P]),
+    "fl_solve_elliptic_batched": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P),
+                                       ctypes.POINTER(_P), _D, _I, _I,
+                                       ctypes.POINTER(FlSolveInfo)]),
     "fl_sync": (_I, [_P]),
     "fl_launch_count": (ctypes.c_longlong, []),
     "fl_profile_enable": (_I, [_P, _I]),

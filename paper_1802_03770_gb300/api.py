@@ -31,6 +31,26 @@ def launch_count():
     return int(L.load().fl_launch_count())
 
 
+def solve_batched(plans, fs, tol=1e-8, maxit=1000, mode=L.FL_MODE_MIXED | L.FL_PRECOND_AUTO,
+                  raise_on_fail=True):
+    """fl_solve_elliptic_batched over lists of plans and float64 CUDA tensors;
+    returns (solutions, list of info dicts)."""
+    import torch
+    n = len(plans)
+    us = []
+    for p, f in zip(plans, fs):
+        _check_tensor(f, torch.float64, p.N, "f")
+        us.append(torch.empty_like(f))
+    hp = (ctypes.c_void_p * n)(*[p._h.value for p in plans])
+    fp = (ctypes.c_void_p * n)(*[f.data_ptr() for f in fs])
+    up = (ctypes.c_void_p * n)(*[u.data_ptr() for u in us])
+    infos = (L.FlSolveInfo * n)()
+    st = L.load().fl_solve_elliptic_batched(hp, n, fp, up, float(tol), int(maxit), int(mode), infos)
+    if raise_on_fail:
+        L.check(st, "fl_solve_elliptic_batched")
+    return us, [infos[i].as_dict() for i in range(n)]
+
+
 class Plan:
     """Operator plan: fl_plan_create(d, n, h, alpha, mask) on the current
     device and torch stream (or the given one)."""

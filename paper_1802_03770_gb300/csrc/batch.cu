@@ -1,0 +1,282 @@
+// Batched launches: one grid runs one pass for many independent problems of
+// different sizes.  CTA b belongs to problem i with off[i] <= b < off[i+1];
+// its local index l = b - off[i] is split as (l mod gx[i], l div gx[i]) into
+// the (x, y) block index the single-problem kernel would have had.  The
+// per-problem argument structs live in device memory and are the same the
+// single-problem launchers build, so a batched pass computes exactly what
+// the single launches compute.
+#include "chain.cuh"
+
+namespace fl {
+
+__device__ __forceinline__ int batch_problem(const int* __restrict__ off, int nprob) {
+  __shared__ int s_i;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = nprob - 1;
+    const int b = blockIdx.x;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (off[mid] <= b) lo = mid;
+      else hi = mid - 1;
+    }
+    s_i = lo;
+  }
+  __syncthreads();
+  return s_i;
+}
+
+#define FL_BATCHED_KERNEL(NAME, ARGS)                                                          \
+  template <typename T, int THREADS, int VPT>                                                  \
+  __global__ void __launch_bounds__(THREADS)                                                   \
+      kb_##NAME(const ARGS<T>* __restrict__ args, const int* __restrict__ off,                 \
+                const int* __restrict__ gx, int nprob) {                                       \
+    const int i = batch_problem(off, nprob);                                                   \
+    const ARGS<T> a = args[i];                                                                 \
+    const int l = blockIdx.x - off[i];                                                         \
+    body_##NAME<T, THREADS, VPT>(a, l % gx[i], l / gx[i]);                                     \
+  }
+
+FL_BATCHED_KERNEL(rows_fwd, RowsFwdArgs)
+FL_BATCHED_KERNEL(cols, ColsArgs)
+FL_BATCHED_KERNEL(rows_inv, RowsInvArgs)
+FL_BATCHED_KERNEL(dst_rows, DstRowsArgs)
+FL_BATCHED_KERNEL(dst_cols, DstColsArgs)
+
+#undef FL_BATCHED_KERNEL
+
+// --- batched CG vector and scalar kernels -------------------------------------
+
+// Start of an inner CG solve with x0 = 0: x = 0, p = 0, r = b (masked), and
+// per-CTA partials of ||b||^2; inactive problems (st->done) do nothing.
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) kb_cg_start(const BVecArgs<T>* __restrict__ args,
+                                                          const int* __restrict__ off, int nprob) {
+  __shared__ double red[32];
+  const int i = batch_problem(off, nprob);
+  const BVecArgs<T> a = args[i];
+  const int bx = blockIdx.x - off[i];
+  const int gx = off[i + 1] - off[i];
+  if (a.gate && a.gate->done) return;
+  double v = 0.0;
+  for (long long k = (long long)bx * blockDim.x + threadIdx.x; k < a.N;
+       k += (long long)gx * blockDim.x) {
+    const T bv = (a.mask && !a.mask[k]) ? (T)0 : a.b[k];
+    a.r[k] = bv;
+    a.x[k] = (T)0;
+    a.p[k] = (T)0;
+    v += (double)bv * (double)bv;
+  }
+  const double s = cta_sum(v, red);
+  if (threadIdx.x == 0) a.part[bx] = s;
+}
+
+// CG update without preconditioner: alpha = rz / pq, x += alpha p,
+// r -= alpha q, partials of ||r||^2 (z aliases r).
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) kb_noprec_update(const BVecArgs<T>* __restrict__ args,
+                                                               const int* __restrict__ off, int nprob) {
+  __shared__ double red[32];
+  __shared__ double s_alpha;
+  const int i = batch_problem(off, nprob);
+  const BVecArgs<T> a = args[i];
+  const int bx = blockIdx.x - off[i];
+  const int gx = off[i + 1] - off[i];
+  if (a.st->done) return;
+  const double pq = cta_sum_partials(a.pq_part, a.pq_count, red);
+  if (threadIdx.x == 0) {
+    s_alpha = a.st->rz / pq;
+    if (bx == 0) {
+      a.st->pq = pq;
+      a.st->alpha = s_alpha;
+    }
+  }
+  __syncthreads();
+  const T al = (T)s_alpha;
+  double rr = 0.0;
+  for (long long k = (long long)bx * blockDim.x + threadIdx.x; k < a.N;
+       k += (long long)gx * blockDim.x) {
+    a.x[k] += al * a.p[k];
+    const T rn = a.r[k] - al * a.q[k];
+    a.r[k] = rn;
+    rr += (double)rn * (double)rn;
+  }
+  const double s = cta_sum(rr, red);
+  if (threadIdx.x == 0) a.part[bx] = s;
+}
+
+// FP64 right-hand side to the FP32 inner right-hand side (masked), with
+// partials of ||b||^2 -- the residual of the zero initial guess.
+__global__ void __launch_bounds__(kVecThreads) kb_cast_rhs(const BVecArgs<double>* __restrict__ args,
+                                                          float* const* __restrict__ out32,
+                                                          const int* __restrict__ off, int nprob) {
+  __shared__ double red[32];
+  const int i = batch_problem(off, nprob);
+  const BVecArgs<double> a = args[i];
+  float* o = out32[i];
+  const int bx = blockIdx.x - off[i];
+  const int gx = off[i + 1] - off[i];
+  double v = 0.0;
+  for (long long k = (long long)bx * blockDim.x + threadIdx.x; k < a.N;
+       k += (long long)gx * blockDim.x) {
+    const double bv = (a.mask && !a.mask[k]) ? 0.0 : a.b[k];
+    o[k] = (float)bv;
+    a.x[k] = 0.0;
+    v += bv * bv;
+  }
+  const double s = cta_sum(v, red);
+  if (threadIdx.x == 0) a.part[bx] = s;
+}
+
+// One CTA per problem: CG start-up scalars (as k_pcg_init).  Problems whose
+// gate is done start done.
+__global__ void kb_pcg_init(const BScalarArgs* __restrict__ args, int nprob) {
+  __shared__ double red[32];
+  const BScalarArgs a = args[blockIdx.x];
+  const double bb = cta_sum_partials(a.bb_part, a.bb_count, red);
+  const double rz = cta_sum_partials(a.rz_part, a.rz_count, red);
+  if (threadIdx.x == 0) {
+    PcgState* st = a.st;
+    st->bb = bb;
+    st->rr = bb;
+    st->rz = rz;
+    st->tol2 = a.tol[0] * a.tol[0] * bb;
+    st->beta = 0.0;
+    st->alpha = 0.0;
+    st->pq = 0.0;
+    st->it = 0;
+    st->maxit = a.maxit;
+    st->status = 0;
+    st->done = (bb == 0.0 || (a.gate && a.gate->done)) ? 1 : 0;
+    if (!(rz > 0.0) && !st->done) { st->done = 1; st->status = 3; }
+  }
+}
+
+// One CTA per problem: the CG scalar step (as k_pcg_scalar).
+__global__ void kb_pcg_scalar(const BScalarArgs* __restrict__ args, int nprob) {
+  __shared__ double red[32];
+  const BScalarArgs a = args[blockIdx.x];
+  PcgState* st = a.st;
+  if (st->done) return;
+  const double rr = cta_sum_partials(a.rr_part, a.rr_count, red);
+  const double rz = cta_sum_partials(a.rz_part, a.rz_count, red);
+  if (threadIdx.x == 0) {
+    st->it += 1;
+    st->rr = rr;
+    const double pq = st->pq;
+    if (!(pq > 0.0) || rr != rr || rz != rz) {
+      st->done = 1;
+      st->status = 3;
+    } else if (rr <= st->tol2) {
+      st->done = 1;
+      st->status = 0;
+    } else if (st->it >= st->maxit) {
+      st->done = 1;
+      st->status = 2;
+    } else if (!(rz > 0.0)) {
+      st->done = 1;
+      st->status = 3;
+    } else {
+      st->beta = rz / st->rz;
+      st->rz = rz;
+    }
+  }
+}
+
+// One CTA per problem: sum of partials into out[i] (skips done gates).
+__global__ void kb_sum(const BScalarArgs* __restrict__ args, double* out, int nprob) {
+  __shared__ double red[32];
+  const BScalarArgs a = args[blockIdx.x];
+  if (a.gate && a.gate->done) return;
+  const double s = cta_sum_partials(a.rr_part, a.rr_count, red);
+  if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+// --- launchers --------------------------------------------------------------
+
+template <typename T>
+cudaError_t launch_batched(const BatchPass& bp, cudaStream_t s) {
+  typedef Cfg<T> K;
+  if (bp.nprob == 0 || bp.blocks == 0) return cudaSuccess;
+  switch (bp.kind) {
+    case BK_ROWS_FWD:
+      FL_KERNEL(sizeof(T) == 4 ? "b_rows_fwd<f32>" : "b_rows_fwd<f64>", s,
+                kb_rows_fwd<T, K::RT, K::RV><<<bp.blocks, K::RT, bp.smem, s>>>(
+                    (const RowsFwdArgs<T>*)bp.args, bp.off, bp.gx, bp.nprob));
+      break;
+    case BK_COLS:
+      FL_KERNEL(sizeof(T) == 4 ? "b_cols<f32>" : "b_cols<f64>", s,
+                kb_cols<T, K::CT, K::CV><<<bp.blocks, K::CT, bp.smem, s>>>(
+                    (const ColsArgs<T>*)bp.args, bp.off, bp.gx, bp.nprob));
+      break;
+    case BK_ROWS_INV:
+      FL_KERNEL(sizeof(T) == 4 ? "b_rows_inv<f32>" : "b_rows_inv<f64>", s,
+                kb_rows_inv<T, K::RT, K::RV><<<bp.blocks, K::RT, bp.smem, s>>>(
+                    (const RowsInvArgs<T>*)bp.args, bp.off, bp.gx, bp.nprob));
+      break;
+    case BK_DST_ROWS:
+      FL_KERNEL(sizeof(T) == 4 ? "b_dst_rows<f32>" : "b_dst_rows<f64>", s,
+                kb_dst_rows<T, K::RT, K::RV><<<bp.blocks, K::RT, bp.smem, s>>>(
+                    (const DstRowsArgs<T>*)bp.args, bp.off, bp.gx, bp.nprob));
+      break;
+    case BK_DST_COLS:
+      FL_KERNEL(sizeof(T) == 4 ? "b_dst_cols<f32>" : "b_dst_cols<f64>", s,
+                kb_dst_cols<T, K::CT, K::CV><<<bp.blocks, K::CT, bp.smem, s>>>(
+                    (const DstColsArgs<T>*)bp.args, bp.off, bp.gx, bp.nprob));
+      break;
+    case BK_CG_START:
+      FL_KERNEL(sizeof(T) == 4 ? "b_cg_start<f32>" : "b_cg_start<f64>", s,
+                kb_cg_start<T><<<bp.blocks, kVecThreads, 0, s>>>((const BVecArgs<T>*)bp.args,
+                                                                  bp.off, bp.nprob));
+      break;
+    case BK_NOPREC:
+      FL_KERNEL(sizeof(T) == 4 ? "b_noprec_update<f32>" : "b_noprec_update<f64>", s,
+                kb_noprec_update<T><<<bp.blocks, kVecThreads, 0, s>>>((const BVecArgs<T>*)bp.args,
+                                                                       bp.off, bp.nprob));
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cast_rhs(const BatchPass& bp, float* const* out32, cudaStream_t s) {
+  if (bp.nprob == 0) return cudaSuccess;
+  FL_KERNEL("b_cast_rhs", s,
+            kb_cast_rhs<<<bp.blocks, kVecThreads, 0, s>>>((const BVecArgs<double>*)bp.args, out32,
+                                                           bp.off, bp.nprob));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batched_scalar(int which, const BScalarArgs* args, double* out, int nprob,
+                                  cudaStream_t s) {
+  if (nprob == 0) return cudaSuccess;
+  if (which == 0)
+    FL_KERNEL("b_pcg_init", s, kb_pcg_init<<<nprob, 256, 0, s>>>(args, nprob));
+  else if (which == 1)
+    FL_KERNEL("b_pcg_scalar", s, kb_pcg_scalar<<<nprob, 256, 0, s>>>(args, nprob));
+  else
+    FL_KERNEL("b_sum", s, kb_sum<<<nprob, 256, 0, s>>>(args, out, nprob));
+  return cudaGetLastError();
+}
+
+cudaError_t configure_batched_kernels() {
+  cudaError_t e = cudaSuccess;
+  auto set = [&](const void* f) {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+  };
+  set(reinterpret_cast<const void*>(&kb_rows_fwd<float, Cfg<float>::RT, Cfg<float>::RV>));
+  set(reinterpret_cast<const void*>(&kb_rows_fwd<double, Cfg<double>::RT, Cfg<double>::RV>));
+  set(reinterpret_cast<const void*>(&kb_rows_inv<float, Cfg<float>::RT, Cfg<float>::RV>));
+  set(reinterpret_cast<const void*>(&kb_rows_inv<double, Cfg<double>::RT, Cfg<double>::RV>));
+  set(reinterpret_cast<const void*>(&kb_cols<float, Cfg<float>::CT, Cfg<float>::CV>));
+  set(reinterpret_cast<const void*>(&kb_cols<double, Cfg<double>::CT, Cfg<double>::CV>));
+  set(reinterpret_cast<const void*>(&kb_dst_rows<float, Cfg<float>::RT, Cfg<float>::RV>));
+  set(reinterpret_cast<const void*>(&kb_dst_cols<float, Cfg<float>::CT, Cfg<float>::CV>));
+  return e;
+}
+
+template cudaError_t launch_batched<float>(const BatchPass&, cudaStream_t);
+template cudaError_t launch_batched<double>(const BatchPass&, cudaStream_t);
+
+}  // namespace fl

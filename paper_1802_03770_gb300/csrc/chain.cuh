@@ -1,0 +1,138 @@
+// Launch shapes and argument chains shared by the single-problem launchers
+// (ops.cu), the batched launchers (batch.cu) and the host drivers (plan.cu).
+#pragma once
+
+#include <algorithm>
+
+#include "internal.h"
+#include "kernels.cuh"
+
+namespace fl {
+
+// Launch shapes.  A CTA keeps VPT * THREADS complex values in shared memory:
+// row passes one or two lines of L = 2048 (many small CTAs, up to eight per
+// SM, so that a 1024-line pass fills all 152 SMs several times over);
+// strided passes a tile of 4 (FP32) or 2 (FP64) columns of L = 2048, i.e. at
+// least 32 contiguous bytes per line element.
+template <typename T> struct Cfg;
+template <> struct Cfg<float> {
+  static constexpr int RT = 256, RV = 8;    // rows: threads, values per thread
+  static constexpr int CT = 512, CV = 16;   // strided passes
+};
+template <> struct Cfg<double> {
+  static constexpr int RT = 256, RV = 16;
+  static constexpr int CT = 512, CV = 8;
+};
+
+constexpr int kVecBlocks = 608;   // 4 x 152 SMs, fixed for deterministic partials
+constexpr int kVecThreads = 256;
+constexpr int kMaxTx = 64;
+constexpr int kSmemLimit = 200 * 1024;
+
+template <typename T> inline int row_lines(int L) { return (Cfg<T>::RT * Cfg<T>::RV) / L; }
+template <typename T> inline int col_tx(int L) {
+  return std::min(kMaxTx, (Cfg<T>::CT * Cfg<T>::CV) / L);
+}
+template <typename T> inline size_t smem_bytes(int lines, int L) {
+  return (size_t)lines * (L + 2) * sizeof(typename Cplx<T>::type);
+}
+// interleaved tiles (strided passes) carry no padding
+template <typename T> inline size_t tile_bytes(int tx, int L) {
+  return (size_t)tx * L * sizeof(typename Cplx<T>::type);
+}
+inline int ilog2i(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+// One operator apply: the row pass, one (2D) or three (3D) strided passes
+// and the last row pass, with their launch shapes.
+template <typename T>
+struct ApplyChain {
+  RowsFwdArgs<T> fwd;
+  ColsArgs<T> cols[3];
+  dim3 cols_grid[3];
+  size_t cols_smem[3];
+  int ncols;
+  RowsInvArgs<T> inv;
+  int row_blocks;
+  size_t row_smem;
+};
+
+// One preconditioner solve: DST rows, one or three strided DST passes, DST rows.
+template <typename T>
+struct PrecChain {
+  DstRowsArgs<T> first;
+  DstColsArgs<T> cols[3];
+  dim3 cols_grid[3];
+  size_t cols_smem[3];
+  int ncols;
+  DstRowsArgs<T> last;
+  int row_blocks;
+  size_t row_smem;
+};
+
+// --- batched passes (batch.cu) ----------------------------------------------
+
+// Per-problem arguments of the batched CG vector kernels.
+template <typename T>
+struct BVecArgs {
+  const PcgState* gate;      // nullable: skip the problem when gate->done
+  PcgState* st;              // inner CG state
+  const T* b;
+  T* x;
+  T* r;
+  T* p;
+  const T* q;
+  const uint8_t* mask;
+  const double* pq_part;
+  int pq_count;
+  double* part;              // per-CTA partials written by the kernel
+  long long N;
+};
+
+// Per-problem arguments of the batched scalar kernels (one CTA each).
+struct BScalarArgs {
+  PcgState* st;
+  const PcgState* gate;
+  const double* bb_part;
+  int bb_count;
+  const double* rr_part;
+  int rr_count;
+  const double* rz_part;
+  int rz_count;
+  const double* tol;         // device pointer to the problem's tolerance
+  int maxit;
+};
+
+enum { BK_ROWS_FWD = 0, BK_COLS, BK_ROWS_INV, BK_DST_ROWS, BK_DST_COLS, BK_CG_START, BK_NOPREC,
+       BK_CAST };
+
+// One batched launch: device arrays of per-problem arguments and of block
+// offsets (nprob + 1 entries) and grid x-extents.
+struct BatchPass {
+  int kind = 0;
+  const void* args = nullptr;
+  const int* off = nullptr;
+  const int* gx = nullptr;
+  int nprob = 0;
+  int blocks = 0;
+  size_t smem = 0;
+};
+
+template <typename T>
+cudaError_t launch_batched(const BatchPass& bp, cudaStream_t s);
+cudaError_t launch_cast_rhs(const BatchPass& bp, float* const* out32, cudaStream_t s);
+// which: 0 = CG start-up scalars, 1 = CG scalar step, 2 = sums into out
+cudaError_t launch_batched_scalar(int which, const BScalarArgs* args, double* out, int nprob,
+                                  cudaStream_t s);
+cudaError_t configure_batched_kernels();
+
+template <typename T>
+ApplyChain<T> build_apply(const Geo& g, const Tables<T>& tb, const ApplyIO<T>& io);
+template <typename T>
+PrecChain<T> build_precond(const Geo& g, const Tables<T>& tb, const double* const* mu,
+                           const PrecIO<T>& io);
+
+}  // namespace fl

@@ -132,6 +132,68 @@ __device__ __forceinline__ void stockham_stage(C* buf, int lg, int ls, int nline
   __syncthreads();
 }
 
+// The same stage for 2^ltx lines stored interleaved: element j of line c is
+// buf[j * tx + c] (the natural layout of a tile of tx consecutive columns).
+// Consecutive threads take consecutive lines, so the leg reads are
+// contiguous.
+template <int R, int VPT, typename C>
+__device__ __forceinline__ void stockham_stage_il(C* buf, int lg, int ltx, int Ns,
+                                                  const C* __restrict__ tw, int lgmax, bool inv) {
+  constexpr int NB = VPT / R;
+  const int L = 1 << lg;
+  const int LR = L / R;
+  const int tx = 1 << ltx;
+  const int total = LR << ltx;
+  C v[NB][R];
+  int dst[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int g = threadIdx.x + b * blockDim.x;
+    dst[b] = -1;
+    if (g < total) {
+      const int c = g & (tx - 1);
+      const int j = g >> ltx;
+      const int k = j & (Ns - 1);
+      const int step = k << (lgmax - __ffs(Ns * R) + 1);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        C x = buf[((j + r * LR) << ltx) + c];
+        if (r > 0 && k != 0) {
+          C w = tw[r * step];
+          if (inv) w.y = -w.y;
+          x = cmul(x, w);
+        }
+        v[b][r] = x;
+      }
+      dftR<R>(v[b], inv);
+      dst[b] = (((j - k) * R + k) << ltx) + c;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    if (dst[b] >= 0) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[dst[b] + ((r * Ns) << ltx)] = v[b][r];
+    }
+  }
+  __syncthreads();
+}
+
+template <int VPT, typename C>
+__device__ __forceinline__ void fft_lines_il(C* buf, int lg, int ltx, const C* __restrict__ tw,
+                                             int lgmax, bool inv) {
+  int Ns = 1;
+  int rem = lg;
+  while (rem >= 3) {
+    stockham_stage_il<8, VPT>(buf, lg, ltx, Ns, tw, lgmax, inv);
+    Ns <<= 3;
+    rem -= 3;
+  }
+  if (rem == 2) stockham_stage_il<4, VPT>(buf, lg, ltx, Ns, tw, lgmax, inv);
+  else if (rem == 1) stockham_stage_il<2, VPT>(buf, lg, ltx, Ns, tw, lgmax, inv);
+}
+
 // Full FFT (unnormalised) of `nlines` lines of length 2^lg in shared memory.
 // Forward: X_k = sum_j x_j exp(-2 pi i jk / L); inverse uses +.
 // The caller must __syncthreads() before (data ready); on return the data is

@@ -101,7 +101,7 @@ struct RowsFwdArgs {
 };
 
 template <typename T, int THREADS, int VPT>
-__global__ void __launch_bounds__(THREADS) k_rows_fwd(RowsFwdArgs<T> a) {
+__device__ __forceinline__ void body_rows_fwd(const RowsFwdArgs<T>& a, int bx, int by) {
   typedef typename Cplx<T>::type C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
@@ -109,37 +109,62 @@ __global__ void __launch_bounds__(THREADS) k_rows_fwd(RowsFwdArgs<T> a) {
   const int L = 1 << a.lg;
   const int ls = L + 2;
   const int NL = (VPT * THREADS) / L;       // complex lines (row pairs) per CTA
-  const int pair0 = blockIdx.x * NL;
+  const int pair0 = bx * NL;
   const int npairs = (a.rows + 1) / 2;
   const int nl = min(NL, npairs - pair0);
   const T beta = (a.pre == PRE_PUPDATE) ? (T)a.st->beta : (T)0;
-  for (int e = threadIdx.x; e < nl * L; e += THREADS) {
-    const int q = e / L, j = e - q * L;
-    const int ra = 2 * (pair0 + q), rb = ra + 1;
-    T va = 0, vb = 0;
-    if (j < a.n) {
-      const size_t ia = (size_t)ra * a.n + j, ib = (size_t)rb * a.n + j;
-      const bool hb = rb < a.rows;
-      if (a.pre == PRE_PUPDATE) {
-        // beta == 0 (first iteration): p = z, without reading the old p
-        va = beta != (T)0 ? a.u[ia] + beta * a.p[ia] : a.u[ia];
-        a.p[ia] = va;
-        if (hb) { vb = beta != (T)0 ? a.u[ib] + beta * a.p[ib] : a.u[ib]; a.p[ib] = vb; }
-      } else if (a.pre == PRE_ACCUM) {
-        double da = a.acc[ia] + (double)a.x32[ia];
-        a.acc[ia] = da;
-        va = (T)da;
-        if (hb) { double db = a.acc[ib] + (double)a.x32[ib]; a.acc[ib] = db; vb = (T)db; }
-      } else {
-        va = a.u[ia];
-        if (hb) vb = a.u[ib];
-      }
-      if (a.mask) {
-        if (!a.mask[ia]) va = 0;
-        if (hb && !a.mask[ib]) vb = 0;
+  // loads first (U elements per thread in flight), then the stores
+  constexpr int U = 4;
+  const int tot = nl * L;
+  for (int e0 = threadIdx.x; e0 < tot; e0 += THREADS * U) {
+    T va[U], vb[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * THREADS;
+      const int q = e / L, j = e - q * L;
+      const int ra = 2 * (pair0 + q), rb = ra + 1;
+      va[u] = 0;
+      vb[u] = 0;
+      if (e < tot && j < a.n) {
+        const size_t ia = (size_t)ra * a.n + j, ib = (size_t)rb * a.n + j;
+        const bool hb = rb < a.rows;
+        if (a.pre == PRE_PUPDATE) {
+          // beta == 0 (first iteration): p = z, without reading the old p
+          va[u] = beta != (T)0 ? a.u[ia] + beta * a.p[ia] : a.u[ia];
+          if (hb) vb[u] = beta != (T)0 ? a.u[ib] + beta * a.p[ib] : a.u[ib];
+        } else if (a.pre == PRE_ACCUM) {
+          va[u] = (T)(a.acc[ia] + (double)a.x32[ia]);
+          if (hb) vb[u] = (T)(a.acc[ib] + (double)a.x32[ib]);
+        } else {
+          va[u] = a.u[ia];
+          if (hb) vb[u] = a.u[ib];
+        }
       }
     }
-    buf[q * ls + j] = cmake<C>(va, vb);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * THREADS;
+      if (e >= tot) continue;
+      const int q = e / L, j = e - q * L;
+      const int ra = 2 * (pair0 + q), rb = ra + 1;
+      T xa = va[u], xb = vb[u];
+      if (j < a.n) {
+        const size_t ia = (size_t)ra * a.n + j, ib = (size_t)rb * a.n + j;
+        const bool hb = rb < a.rows;
+        if (a.pre == PRE_PUPDATE) {
+          a.p[ia] = xa;
+          if (hb) a.p[ib] = xb;
+        } else if (a.pre == PRE_ACCUM) {
+          a.acc[ia] = (double)xa;
+          if (hb) a.acc[ib] = (double)xb;
+        }
+        if (a.mask) {
+          if (!a.mask[ia]) xa = 0;
+          if (hb && !a.mask[ib]) xb = 0;
+        }
+      }
+      buf[q * ls + j] = cmake<C>(xa, xb);
+    }
   }
   __syncthreads();
   fft_lines<VPT>(buf, a.lg, ls, nl, a.tw, a.lgmax, false);
@@ -157,6 +182,11 @@ __global__ void __launch_bounds__(THREADS) k_rows_fwd(RowsFwdArgs<T> a) {
       a.S[sb + k] = xb;
     }
   }
+}
+
+template <typename T, int THREADS, int VPT>
+__global__ void __launch_bounds__(THREADS) k_rows_fwd(RowsFwdArgs<T> a) {
+  body_rows_fwd<T, THREADS, VPT>(a, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -177,48 +207,67 @@ struct ColsArgs {
   // symbol index = kk * sig_line + min(o, Lo - o) * sig_outer + kx, kk = min(k, L-k)
   long long sig_line, sig_outer;
   int Lo;                  // length of the outer axis in the spectrum (3D: L_1), 0 if unused
-  int tx;                  // columns per CTA
+  int ltx;                 // log2 of the columns per CTA
 };
 
+// The tile is kept in its natural layout, buf[r * TX + c] (row r of the line,
+// column c), and transformed with the interleaved-line FFT; global loads are
+// issued U at a time so that several are in flight per thread.
 template <typename T, int THREADS, int VPT>
-__global__ void __launch_bounds__(THREADS) k_cols(ColsArgs<T> a) {
+__device__ __forceinline__ void body_cols(const ColsArgs<T>& a, int bx, int by) {
   typedef typename Cplx<T>::type C;
+  constexpr int U = 8;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   if (a.st && a.st->done) return;
   const int L = 1 << a.lg;
-  const int ls = L + 2;
-  const int TX = a.tx;
-  const int kx0 = blockIdx.x * TX;
-  const int o = blockIdx.y;
+  const int ltx = a.ltx;
+  const int TX = 1 << ltx;
+  const int kx0 = bx * TX;
+  const int o = by;
   const int ncol = min(TX, a.H - kx0);
   C* base = a.S + (size_t)o * a.ostride + kx0;
-  for (int e = threadIdx.x; e < TX * L; e += THREADS) {
-    const int r = e / TX, c = e - r * TX;
-    C v = cmake<C>((T)0, (T)0);
-    if (r < a.rows_in && c < ncol) v = base[(size_t)r * a.lstride + c];
-    buf[c * ls + r] = v;
+  const int total = TX * L;
+  for (int e0 = threadIdx.x; e0 < total; e0 += THREADS * U) {
+    C v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * THREADS;
+      const int r = e >> ltx, c = e & (TX - 1);
+      v[u] = cmake<C>((T)0, (T)0);
+      if (e < total && r < a.rows_in && c < ncol) v[u] = base[(size_t)r * a.lstride + c];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * THREADS;
+      if (e < total) buf[e] = v[u];
+    }
   }
   __syncthreads();
   const bool inv_only = (a.mode == COLS_INV);
-  fft_lines<VPT>(buf, a.lg, ls, TX, a.tw, a.lgmax, inv_only);
+  fft_lines_il<VPT>(buf, a.lg, ltx, a.tw, a.lgmax, inv_only);
   if (a.mode == COLS_CONV) {
     const size_t soff = a.Lo ? (size_t)min(o, a.Lo - o) * a.sig_outer : 0;
-    for (int e = threadIdx.x; e < TX * L; e += THREADS) {
-      const int c = e / L, k = e - c * L;
+    for (int e = threadIdx.x; e < total; e += THREADS) {
+      const int k = e >> ltx, c = e & (TX - 1);
       if (c < ncol) {
         const int kk = min(k, L - k);
-        const T s = a.sig[(size_t)kk * a.sig_line + soff + kx0 + c];
-        buf[c * ls + k] = cscale(buf[c * ls + k], s);
+        buf[e] = cscale(buf[e], a.sig[(size_t)kk * a.sig_line + soff + kx0 + c]);
       }
     }
     __syncthreads();
-    fft_lines<VPT>(buf, a.lg, ls, TX, a.tw, a.lgmax, true);
+    fft_lines_il<VPT>(buf, a.lg, ltx, a.tw, a.lgmax, true);
   }
-  for (int e = threadIdx.x; e < TX * a.rows_out; e += THREADS) {
-    const int r = e / TX, c = e - r * TX;
-    if (c < ncol) base[(size_t)r * a.lstride + c] = buf[c * ls + r];
+  const int tout = TX * a.rows_out;
+  for (int e = threadIdx.x; e < tout; e += THREADS) {
+    const int r = e >> ltx, c = e & (TX - 1);
+    if (c < ncol) base[(size_t)r * a.lstride + c] = buf[e];
   }
+}
+
+template <typename T, int THREADS, int VPT>
+__global__ void __launch_bounds__(THREADS) k_cols(ColsArgs<T> a) {
+  body_cols<T, THREADS, VPT>(a, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -246,7 +295,7 @@ struct RowsInvArgs {
 };
 
 template <typename T, int THREADS, int VPT>
-__global__ void __launch_bounds__(THREADS) k_rows_inv(RowsInvArgs<T> a) {
+__device__ __forceinline__ void body_rows_inv(const RowsInvArgs<T>& a, int bx, int by) {
   typedef typename Cplx<T>::type C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
@@ -255,9 +304,10 @@ __global__ void __launch_bounds__(THREADS) k_rows_inv(RowsInvArgs<T> a) {
   const int L = 1 << a.lg;
   const int ls = L + 2;
   const int NL = (VPT * THREADS) / L;
-  const int pair0 = blockIdx.x * NL;
+  const int pair0 = bx * NL;
   const int npairs = (a.rows + 1) / 2;
   const int nl = min(NL, npairs - pair0);
+#pragma unroll 4
   for (int e = threadIdx.x; e < nl * a.H; e += THREADS) {
     const int q = e / a.H, k = e - q * a.H;
     const int ra = 2 * (pair0 + q), rb = ra + 1;
@@ -275,6 +325,12 @@ __global__ void __launch_bounds__(THREADS) k_rows_inv(RowsInvArgs<T> a) {
   __syncthreads();
   fft_lines<VPT>(buf, a.lg, ls, nl, a.tw, a.lgmax, true);
   double part = 0.0;
+  const T* __restrict__ xin = (a.cx != 0.0) ? a.x : nullptr;
+  const T* __restrict__ bin = (a.cb != 0.0) ? a.b : nullptr;
+  const T* __restrict__ win = a.dot_self ? nullptr : a.dotw;
+  T* __restrict__ out = a.out;
+  float* __restrict__ out32 = a.out32;
+#pragma unroll 4
   for (int e = threadIdx.x; e < nl * 2 * a.n; e += THREADS) {
     const int q = e / (2 * a.n), rem = e - q * 2 * a.n;
     const int half = rem / a.n, j = rem - half * a.n;
@@ -283,18 +339,23 @@ __global__ void __launch_bounds__(THREADS) k_rows_inv(RowsInvArgs<T> a) {
     const size_t idx = (size_t)row * a.n + j;
     const C z = buf[q * ls + j];
     double v = (double)(half ? z.y : z.x) * a.cm;
-    if (a.x && a.cx != 0.0) v += a.cx * (double)a.x[idx];
-    if (a.b && a.cb != 0.0) v += a.cb * (double)a.b[idx];
+    if (xin) v += a.cx * (double)xin[idx];
+    if (bin) v += a.cb * (double)bin[idx];
     if (a.mask && !a.mask[idx]) v = 0.0;
     const T tv = (T)v;
-    if (a.out) a.out[idx] = tv;
-    if (a.out32) a.out32[idx] = (float)v;
-    if (a.partials) part += a.dot_self ? (double)tv * (double)tv : (double)tv * (double)a.dotw[idx];
+    if (out) out[idx] = tv;
+    if (out32) out32[idx] = (float)v;
+    if (a.partials) part += win ? (double)tv * (double)win[idx] : (double)tv * (double)tv;
   }
   if (a.partials) {
     const double s = cta_sum(part, red);
-    if (threadIdx.x == 0) a.partials[blockIdx.x] = s;
+    if (threadIdx.x == 0) a.partials[bx] = s;
   }
+}
+
+template <typename T, int THREADS, int VPT>
+__global__ void __launch_bounds__(THREADS) k_rows_inv(RowsInvArgs<T> a) {
+  body_rows_inv<T, THREADS, VPT>(a, blockIdx.x, blockIdx.y);
 }
 
 // In place on `nl` lines of length L in shared memory: y = IFFT(FFT(v) * bhat),
@@ -311,6 +372,17 @@ __device__ __forceinline__ void chirp_conv(C* buf, int ls, int nl, int L, int lg
   fft_lines<VPT>(buf, lg, ls, nl, tw, lgmax, true);
 }
 
+// Interleaved-line version of chirp_conv (element j of line c at j * TX + c).
+template <int VPT, typename C>
+__device__ __forceinline__ void chirp_conv_il(C* buf, int ltx, int L, int lg, int lgmax,
+                                              const C* __restrict__ tw, const C* __restrict__ bhat) {
+  fft_lines_il<VPT>(buf, lg, ltx, tw, lgmax, false);
+  const int total = L << ltx;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) buf[e] = cmul(buf[e], bhat[e >> ltx]);
+  __syncthreads();
+  fft_lines_il<VPT>(buf, lg, ltx, tw, lgmax, true);
+}
+
 // ---------------------------------------------------------------------------
 // Preconditioner: DST-I along the last axis (rows of length n), by chirp-z.
 // DPRE_UPDATE fuses the CG update before the transform:
@@ -325,7 +397,7 @@ struct DstRowsArgs {
   const typename Cplx<T>::type* tw;
   const typename Cplx<T>::type* chirp;   // c_{j+1}, j = 0..n-1
   const typename Cplx<T>::type* bhat;    // FFT_L of conj(c_m) embedded circularly, / L
-  const PcgState* st;
+  PcgState* st;            // DPRE_UPDATE: CTA 0 records pq and alpha
   // DPRE_UPDATE
   T* x; T* r; const T* p; const T* q;
   const double* pq_part; int pq_count;
@@ -337,7 +409,7 @@ struct DstRowsArgs {
 };
 
 template <typename T, int THREADS, int VPT>
-__global__ void __launch_bounds__(THREADS) k_dst_rows(DstRowsArgs<T> a) {
+__device__ __forceinline__ void body_dst_rows(const DstRowsArgs<T>& a, int bx, int by) {
   typedef typename Cplx<T>::type C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
@@ -347,29 +419,41 @@ __global__ void __launch_bounds__(THREADS) k_dst_rows(DstRowsArgs<T> a) {
   const int L = 1 << a.lg;
   const int ls = L + 2;
   const int NL = (VPT * THREADS) / L;
-  const int row0 = blockIdx.x * NL;
+  const int row0 = bx * NL;
   const int nl = min(NL, a.rows - row0);
   double rr = 0.0;
   if (a.pre == DPRE_UPDATE) {
     const double pq = cta_sum_partials(a.pq_part, a.pq_count, red);
-    if (threadIdx.x == 0) s_alpha = a.st->rz / pq;
+    if (threadIdx.x == 0) {
+      s_alpha = a.st->rz / pq;
+      if (bx == 0) {   // for the scalar kernel's breakdown test
+        a.st->pq = pq;
+        a.st->alpha = s_alpha;
+      }
+    }
     __syncthreads();
     const T al = (T)s_alpha;
+    T* __restrict__ xv = a.x;
+    T* __restrict__ rv = a.r;
+    const T* __restrict__ pv = a.p;
+    const T* __restrict__ qv = a.q;
+#pragma unroll 4
     for (int e = threadIdx.x; e < nl * L; e += THREADS) {
       const int q = e / L, j = e - q * L;
       C v = cmake<C>((T)0, (T)0);
       if (j < a.n) {
         const size_t idx = (size_t)(row0 + q) * a.n + j;
-        const T xn = a.x[idx] + al * a.p[idx];
-        const T rn = a.r[idx] - al * a.q[idx];
-        a.x[idx] = xn;
-        a.r[idx] = rn;
+        const T xn = xv[idx] + al * pv[idx];
+        const T rn = rv[idx] - al * qv[idx];
+        xv[idx] = xn;
+        rv[idx] = rn;
         rr += (double)rn * (double)rn;
         v = cscale(a.chirp[j], rn);
       }
       buf[q * ls + j] = v;
     }
   } else {
+#pragma unroll 4
     for (int e = threadIdx.x; e < nl * L; e += THREADS) {
       const int q = e / L, j = e - q * L;
       C v = cmake<C>((T)0, (T)0);
@@ -386,6 +470,7 @@ __global__ void __launch_bounds__(THREADS) k_dst_rows(DstRowsArgs<T> a) {
   __syncthreads();
   fft_lines<VPT>(buf, a.lg, ls, nl, a.tw, a.lgmax, true);
   double dp = 0.0;
+#pragma unroll 4
   for (int e = threadIdx.x; e < nl * a.n; e += THREADS) {
     const int q = e / a.n, k = e - q * a.n;
     const C y = cmul(a.chirp[k], buf[q * ls + k]);
@@ -396,12 +481,17 @@ __global__ void __launch_bounds__(THREADS) k_dst_rows(DstRowsArgs<T> a) {
   }
   if (a.pre == DPRE_UPDATE) {
     const double s = cta_sum(rr, red);
-    if (threadIdx.x == 0) a.rr_part[blockIdx.x] = s;
+    if (threadIdx.x == 0) a.rr_part[bx] = s;
   }
   if (a.dotw) {
     const double s = cta_sum(dp, red);
-    if (threadIdx.x == 0) a.dot_part[blockIdx.x] = s;
+    if (threadIdx.x == 0) a.dot_part[bx] = s;
   }
+}
+
+template <typename T, int THREADS, int VPT>
+__global__ void __launch_bounds__(THREADS) k_dst_rows(DstRowsArgs<T> a) {
+  body_dst_rows<T, THREADS, VPT>(a, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -424,53 +514,71 @@ struct DstColsArgs {
   double shift, scale, post;
   int n, ncols, lg, lgmax;
   long long ostride, lstride;
-  int mode, tx;
+  int mode, ltx;
 };
 
 template <typename T, int THREADS, int VPT>
-__global__ void __launch_bounds__(THREADS) k_dst_cols(DstColsArgs<T> a) {
+__device__ __forceinline__ void body_dst_cols(const DstColsArgs<T>& a, int bx, int by) {
   typedef typename Cplx<T>::type C;
+  constexpr int U = 8;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   if (a.st && a.st->done) return;
   const int L = 1 << a.lg;
-  const int ls = L + 2;
-  const int TX = a.tx;
-  const int c0 = blockIdx.x * TX;
-  const int o = blockIdx.y;
+  const int ltx = a.ltx;
+  const int TX = 1 << ltx;
+  const int c0 = bx * TX;
+  const int o = by;
   const int ncol = min(TX, a.ncols - c0);
   T* base = a.v + (size_t)o * a.ostride + c0;
-  for (int e = threadIdx.x; e < TX * L; e += THREADS) {
-    const int r = e / TX, c = e - r * TX;
-    C val = cmake<C>((T)0, (T)0);
-    if (r < a.n && c < ncol) val = cscale(a.chirp[r], base[(size_t)r * a.lstride + c]);
-    buf[c * ls + r] = val;
+  const int total = TX * L;
+  for (int e0 = threadIdx.x; e0 < total; e0 += THREADS * U) {
+    T v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * THREADS;
+      const int r = e >> ltx, c = e & (TX - 1);
+      v[u] = (T)0;
+      if (e < total && r < a.n && c < ncol) v[u] = base[(size_t)r * a.lstride + c];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * THREADS;
+      const int r = e >> ltx;
+      if (e < total) buf[e] = r < a.n ? cscale(a.chirp[r], v[u]) : cmake<C>((T)0, (T)0);
+    }
   }
   __syncthreads();
-  chirp_conv<VPT>(buf, ls, TX, L, a.lg, a.lgmax, a.tw, a.bhat);
+  chirp_conv_il<VPT>(buf, ltx, L, a.lg, a.lgmax, a.tw, a.bhat);
   if (a.mode == DST_DIV_DST) {
     // X_k = Im(c_k y_k); divide by the eigenvalue; re-chirp for the second DST
     const double muo = a.mu_outer ? a.mu_outer[o] : 0.0;
-    for (int e = threadIdx.x; e < TX * L; e += THREADS) {
-      const int c = e / L, k = e - c * L;
+    for (int e = threadIdx.x; e < total; e += THREADS) {
+      const int k = e >> ltx, c = e & (TX - 1);
       C val = cmake<C>((T)0, (T)0);
       if (k < a.n && c < ncol) {
-        const C y = cmul(a.chirp[k], buf[c * ls + k]);
+        const C y = cmul(a.chirp[k], buf[e]);
         const double lam = a.shift + a.scale * (a.mu_line[k] + a.mu_col[c0 + c] + muo);
         val = cscale(a.chirp[k], (T)((double)y.y / lam));
       }
-      buf[c * ls + k] = val;
+      buf[e] = val;
     }
     __syncthreads();
-    chirp_conv<VPT>(buf, ls, TX, L, a.lg, a.lgmax, a.tw, a.bhat);
+    chirp_conv_il<VPT>(buf, ltx, L, a.lg, a.lgmax, a.tw, a.bhat);
   }
-  for (int e = threadIdx.x; e < TX * a.n; e += THREADS) {
-    const int r = e / TX, c = e - r * TX;
+  const int tout = TX * a.n;
+  for (int e = threadIdx.x; e < tout; e += THREADS) {
+    const int r = e >> ltx, c = e & (TX - 1);
     if (c < ncol) {
-      const C y = cmul(a.chirp[r], buf[c * ls + r]);
+      const C y = cmul(a.chirp[r], buf[e]);
       base[(size_t)r * a.lstride + c] = (T)((double)y.y * a.post);
     }
   }
+}
+
+template <typename T, int THREADS, int VPT>
+__global__ void __launch_bounds__(THREADS) k_dst_cols(DstColsArgs<T> a) {
+  body_dst_cols<T, THREADS, VPT>(a, blockIdx.x, blockIdx.y);
 }
 
 }  // namespace fl

@@ -2,36 +2,9 @@
 // vector and scalar kernels, and the plan-time symbol build.
 #include <algorithm>
 
-#include "internal.h"
-#include "kernels.cuh"
+#include "chain.cuh"
 
 namespace fl {
-
-// Launch shapes.  Row passes keep VPT * THREADS complex values of a CTA in
-// shared memory (FP32: 8192, FP64: 4096); strided passes twice that, so a
-// tile of columns reads at least 64 contiguous bytes per line element.
-template <typename T> struct Cfg;
-template <> struct Cfg<float> {
-  static constexpr int RT = 512, RV = 16;   // rows: threads, values per thread
-  static constexpr int CT = 512, CV = 32;   // strided passes
-};
-template <> struct Cfg<double> {
-  static constexpr int RT = 512, RV = 8;
-  static constexpr int CT = 512, CV = 16;
-};
-
-static constexpr int kVecBlocks = 608;   // 4 x 152 SMs, fixed for deterministic partials
-static constexpr int kVecThreads = 256;
-static constexpr int kMaxTx = 64;
-static constexpr int kSmemLimit = 200 * 1024;
-
-template <typename T> static inline int row_lines(int L) { return (Cfg<T>::RT * Cfg<T>::RV) / L; }
-template <typename T> static inline int col_tx(int L) {
-  return std::min(kMaxTx, (Cfg<T>::CT * Cfg<T>::CV) / L);
-}
-template <typename T> static inline size_t smem_bytes(int lines, int L) {
-  return (size_t)lines * (L + 2) * sizeof(typename Cplx<T>::type);
-}
 
 // ---------------------------------------------------------------------------
 // CG vector kernels (grid-stride, kVecBlocks CTAs, one partial per CTA).
@@ -169,16 +142,6 @@ __global__ void k_sum(const double* part, int count, double* out) {
   if (threadIdx.x == 0) *out = s;
 }
 
-// The DST-rows kernel computes alpha from the pq partials but only CTA 0 of
-// k_noprec_update stores it; this small kernel stores pq for the scalar
-// kernel's breakdown test when the preconditioned path runs.
-__global__ void k_store_pq(PcgState* st, const double* pq_part, int pq_count) {
-  __shared__ double red[32];
-  if (st->done) return;
-  const double pq = cta_sum_partials(pq_part, pq_count, red);
-  if (threadIdx.x == 0) st->pq = pq;
-}
-
 // ---------------------------------------------------------------------------
 // Plan-time symbol: fill the circular embedding of k(m) (FP64, complex),
 // FFT along every axis, keep the real part on [0, L_i/2]^d / prod L.
@@ -306,38 +269,37 @@ int precond_partials(const Geo& g) {
 }
 
 template <typename T>
-cudaError_t launch_apply(const Geo& g, const Tables<T>& tb, cudaStream_t s, const ApplyIO<T>& io) {
-  typedef Cfg<T> K;
+ApplyChain<T> build_apply(const Geo& g, const Tables<T>& tb, const ApplyIO<T>& io) {
+  ApplyChain<T> ch;
   const int d = g.d;
   const int Lx = g.L[d - 1];
   const long long rows = g.N / g.n[d - 1];
   const int NL = row_lines<T>(Lx);
-  const int rblocks = (int)(((rows + 1) / 2 + NL - 1) / NL);
+  ch.row_blocks = (int)(((rows + 1) / 2 + NL - 1) / NL);
+  ch.row_smem = smem_bytes<T>(NL, Lx);
   const int rpp = d == 3 ? g.n[1] : (int)rows;
   const int pstride = d == 3 ? g.L[1] : 0;
   {
-    RowsFwdArgs<T> a;
+    RowsFwdArgs<T>& a = ch.fwd;
     a.u = io.u; a.p = io.p; a.acc = io.acc; a.x32 = io.x32; a.mask = io.mask;
     a.S = tb.S; a.tw = tb.tw; a.st = io.st;
     a.rows = (int)rows; a.n = g.n[d - 1]; a.H = g.H; a.lg = g.lg[d - 1]; a.lgmax = g.lgmax;
     a.rows_per_plane = rpp; a.plane_stride = pstride; a.pre = io.pre;
-    FL_KERNEL((sizeof(T) == 4 ? "rows_fwd" "<f32>" : "rows_fwd" "<f64>"), s,
-              k_rows_fwd<T, K::RT, K::RV><<<rblocks, K::RT, smem_bytes<T>(NL, Lx), s>>>(a));
   }
+  ch.ncols = 0;
   auto cols = [&](int axis, int mode, int rows_in, int rows_out, long long lstride,
                   long long ostride, int nouter, long long sig_line, long long sig_outer, int Lo) {
-    ColsArgs<T> a;
+    ColsArgs<T>& a = ch.cols[ch.ncols];
     a.S = tb.S; a.tw = tb.tw; a.sig = tb.sig; a.st = io.st;
     a.H = g.H; a.lg = g.lg[axis]; a.lgmax = g.lgmax;
     a.rows_in = rows_in; a.rows_out = rows_out; a.lstride = lstride; a.ostride = ostride;
     a.nouter = nouter; a.mode = mode; a.sig_line = sig_line; a.sig_outer = sig_outer; a.Lo = Lo;
     const int L = g.L[axis];
-    a.tx = col_tx<T>(L);
-    dim3 grid((g.H + a.tx - 1) / a.tx, nouter);
-    static const char* const kn[2][4] = {{"cols_fwd<f64>", "cols_conv<f64>", "cols_inv<f64>", "cols_full<f64>"},
-                                         {"cols_fwd<f32>", "cols_conv<f32>", "cols_inv<f32>", "cols_full<f32>"}};
-    FL_KERNEL(kn[sizeof(T) == 4][mode], s,
-              k_cols<T, K::CT, K::CV><<<grid, K::CT, smem_bytes<T>(a.tx, L), s>>>(a));
+    const int tx = col_tx<T>(L);
+    a.ltx = ilog2i(tx);
+    ch.cols_grid[ch.ncols] = dim3((g.H + tx - 1) / tx, nouter);
+    ch.cols_smem[ch.ncols] = tile_bytes<T>(tx, L);
+    ch.ncols++;
   };
   if (d == 2) {
     cols(0, COLS_CONV, g.n[0], g.n[0], g.H, 0, 1, g.H, 0, 0);
@@ -348,7 +310,7 @@ cudaError_t launch_apply(const Geo& g, const Tables<T>& tb, cudaStream_t s, cons
     cols(1, COLS_INV, g.L[1], g.n[1], H, L1 * H, g.n[0], 0, 0, 0);
   }
   {
-    RowsInvArgs<T> a;
+    RowsInvArgs<T>& a = ch.inv;
     a.S = tb.S; a.tw = tb.tw; a.mask = io.mask; a.st = io.st;
     a.out = io.out; a.out32 = io.out32;
     // the epilogue's x is the apply input (after any pre-op)
@@ -356,48 +318,61 @@ cudaError_t launch_apply(const Geo& g, const Tables<T>& tb, cudaStream_t s, cons
     a.cm = io.cm; a.cx = io.cx; a.cb = io.cb;
     a.rows = (int)rows; a.n = g.n[d - 1]; a.H = g.H; a.lg = g.lg[d - 1]; a.lgmax = g.lgmax;
     a.rows_per_plane = rpp; a.plane_stride = pstride; a.dot_self = io.dot_self;
-    FL_KERNEL((sizeof(T) == 4 ? "rows_inv" "<f32>" : "rows_inv" "<f64>"), s,
-              k_rows_inv<T, K::RT, K::RV><<<rblocks, K::RT, smem_bytes<T>(NL, Lx), s>>>(a));
   }
+  return ch;
+}
+
+template <typename T>
+cudaError_t launch_apply(const Geo& g, const Tables<T>& tb, cudaStream_t s, const ApplyIO<T>& io) {
+  typedef Cfg<T> K;
+  const ApplyChain<T> ch = build_apply<T>(g, tb, io);
+  FL_KERNEL((sizeof(T) == 4 ? "rows_fwd" "<f32>" : "rows_fwd" "<f64>"), s,
+            k_rows_fwd<T, K::RT, K::RV><<<ch.row_blocks, K::RT, ch.row_smem, s>>>(ch.fwd));
+  static const char* const kn[2][4] = {{"cols_fwd<f64>", "cols_conv<f64>", "cols_inv<f64>", "cols_full<f64>"},
+                                       {"cols_fwd<f32>", "cols_conv<f32>", "cols_inv<f32>", "cols_full<f32>"}};
+  for (int j = 0; j < ch.ncols; ++j)
+    FL_KERNEL(kn[sizeof(T) == 4][ch.cols[j].mode], s,
+              k_cols<T, K::CT, K::CV><<<ch.cols_grid[j], K::CT, ch.cols_smem[j], s>>>(ch.cols[j]));
+  FL_KERNEL((sizeof(T) == 4 ? "rows_inv" "<f32>" : "rows_inv" "<f64>"), s,
+            k_rows_inv<T, K::RT, K::RV><<<ch.row_blocks, K::RT, ch.row_smem, s>>>(ch.inv));
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_precond(const Geo& g, const Tables<T>& tb, const double* const* mu,
-                           cudaStream_t s, const PrecIO<T>& io) {
-  typedef Cfg<T> K;
+PrecChain<T> build_precond(const Geo& g, const Tables<T>& tb, const double* const* mu,
+                           const PrecIO<T>& io) {
+  PrecChain<T> ch;
   const int d = g.d;
   const int nx = g.n[d - 1], Lx = g.L[d - 1];
   const long long rows = g.N / nx;
   const int NL = row_lines<T>(Lx);
-  const int rblocks = (int)((rows + NL - 1) / NL);
+  ch.row_blocks = (int)((rows + NL - 1) / NL);
+  ch.row_smem = smem_bytes<T>(NL, Lx);
   double post = 1.0;
   for (int i = 0; i < d; ++i) post *= 2.0 / (g.n[i] + 1.0);
   {
-    DstRowsArgs<T> a;
+    DstRowsArgs<T>& a = ch.first;
     a.in = io.in; a.out = tb.t; a.tw = tb.tw; a.chirp = tb.chirp[d - 1]; a.bhat = tb.bhat[d - 1];
     a.st = io.st; a.x = io.x; a.r = io.r; a.p = io.p; a.q = io.q;
     a.pq_part = io.pq_part; a.pq_count = io.pq_count; a.rr_part = io.rr_part;
     a.dotw = nullptr; a.dot_part = nullptr; a.post = 1.0;
     a.rows = (int)rows; a.n = nx; a.lg = g.lg[d - 1]; a.lgmax = g.lgmax; a.pre = io.pre;
-    FL_KERNEL((sizeof(T) == 4 ? "dst_rows" "<f32>" : "dst_rows" "<f64>"), s,
-              k_dst_rows<T, K::RT, K::RV><<<rblocks, K::RT, smem_bytes<T>(NL, Lx), s>>>(a));
   }
+  ch.ncols = 0;
   auto cols = [&](int axis, int mode, long long lstride, long long ostride, int nouter,
                   const double* mu_line, const double* mu_col, const double* mu_outer) {
-    DstColsArgs<T> a;
+    DstColsArgs<T>& a = ch.cols[ch.ncols];
     a.v = tb.t; a.tw = tb.tw; a.chirp = tb.chirp[axis]; a.bhat = tb.bhat[axis]; a.st = io.st;
     a.mu_line = mu_line; a.mu_col = mu_col; a.mu_outer = mu_outer;
     a.shift = io.shift; a.scale = io.scale; a.post = 1.0;
     a.n = g.n[axis]; a.ncols = nx; a.lg = g.lg[axis]; a.lgmax = g.lgmax;
     a.ostride = ostride; a.lstride = lstride; a.mode = mode;
     const int L = g.L[axis];
-    a.tx = col_tx<T>(L);
-    dim3 grid((nx + a.tx - 1) / a.tx, nouter);
-    static const char* const kn[2][2] = {{"dst_cols<f64>", "dst_cols_div<f64>"},
-                                         {"dst_cols<f32>", "dst_cols_div<f32>"}};
-    FL_KERNEL(kn[sizeof(T) == 4][mode], s,
-              k_dst_cols<T, K::CT, K::CV><<<grid, K::CT, smem_bytes<T>(a.tx, L), s>>>(a));
+    const int tx = col_tx<T>(L);
+    a.ltx = ilog2i(tx);
+    ch.cols_grid[ch.ncols] = dim3((nx + tx - 1) / tx, nouter);
+    ch.cols_smem[ch.ncols] = tile_bytes<T>(tx, L);
+    ch.ncols++;
   };
   if (d == 2) {
     cols(0, DST_DIV_DST, nx, 0, 1, mu[0], mu[1], nullptr);
@@ -408,15 +383,30 @@ cudaError_t launch_precond(const Geo& g, const Tables<T>& tb, const double* cons
     cols(1, DST_ONE, n2, n1 * n2, g.n[0], nullptr, nullptr, nullptr);
   }
   {
-    DstRowsArgs<T> a;
+    DstRowsArgs<T>& a = ch.last;
     a.in = tb.t; a.out = io.out; a.tw = tb.tw; a.chirp = tb.chirp[d - 1]; a.bhat = tb.bhat[d - 1];
-    a.st = io.st; a.dotw = io.dotw; a.dot_part = io.dot_part; a.post = post;
+    a.st = io.st; a.x = nullptr; a.r = nullptr; a.p = nullptr; a.q = nullptr;
+    a.pq_part = nullptr; a.pq_count = 0; a.rr_part = nullptr;
+    a.dotw = io.dotw; a.dot_part = io.dot_part; a.post = post;
     a.rows = (int)rows; a.n = nx; a.lg = g.lg[d - 1]; a.lgmax = g.lgmax; a.pre = DPRE_NONE;
-    FL_KERNEL((sizeof(T) == 4 ? "dst_rows" "<f32>" : "dst_rows" "<f64>"), s,
-              k_dst_rows<T, K::RT, K::RV><<<rblocks, K::RT, smem_bytes<T>(NL, Lx), s>>>(a));
   }
-  if (io.pre == DPRE_UPDATE)
-    FL_KERNEL("store_pq", s, k_store_pq<<<1, 256, 0, s>>>(io.st, io.pq_part, io.pq_count));
+  return ch;
+}
+
+template <typename T>
+cudaError_t launch_precond(const Geo& g, const Tables<T>& tb, const double* const* mu,
+                           cudaStream_t s, const PrecIO<T>& io) {
+  typedef Cfg<T> K;
+  const PrecChain<T> ch = build_precond<T>(g, tb, mu, io);
+  FL_KERNEL((sizeof(T) == 4 ? "dst_rows" "<f32>" : "dst_rows" "<f64>"), s,
+            k_dst_rows<T, K::RT, K::RV><<<ch.row_blocks, K::RT, ch.row_smem, s>>>(ch.first));
+  static const char* const kn[2][2] = {{"dst_cols<f64>", "dst_cols_div<f64>"},
+                                       {"dst_cols<f32>", "dst_cols_div<f32>"}};
+  for (int j = 0; j < ch.ncols; ++j)
+    FL_KERNEL(kn[sizeof(T) == 4][ch.cols[j].mode], s,
+              k_dst_cols<T, K::CT, K::CV><<<ch.cols_grid[j], K::CT, ch.cols_smem[j], s>>>(ch.cols[j]));
+  FL_KERNEL((sizeof(T) == 4 ? "dst_rows" "<f32>" : "dst_rows" "<f64>"), s,
+            k_dst_rows<T, K::RT, K::RV><<<ch.row_blocks, K::RT, ch.row_smem, s>>>(ch.last));
   return cudaGetLastError();
 }
 
@@ -528,10 +518,11 @@ cudaError_t build_symbol(const Geo& g, double c, double Z, double a, double expo
     if (d == 2) { ca.lstride = Ls[1]; ca.ostride = 0; ca.nouter = 1; }
     else if (axis == 1) { ca.lstride = Ls[2]; ca.ostride = (long long)Ls[1] * Ls[2]; ca.nouter = Ls[0]; }
     else { ca.lstride = (long long)Ls[1] * Ls[2]; ca.ostride = Ls[2]; ca.nouter = Ls[1]; }
-    ca.tx = col_tx<double>(Ls[axis]);
-    dim3 grid((ca.H + ca.tx - 1) / ca.tx, ca.nouter);
+    const int tx = col_tx<double>(Ls[axis]);
+    ca.ltx = ilog2i(tx);
+    dim3 grid((ca.H + tx - 1) / tx, ca.nouter);
     FL_KERNEL("cols_symbol", s,
-              k_cols<double, K::CT, K::CV><<<grid, K::CT, smem_bytes<double>(ca.tx, Ls[axis]), s>>>(ca));
+              k_cols<double, K::CT, K::CV><<<grid, K::CT, tile_bytes<double>(tx, Ls[axis]), s>>>(ca));
   }
   double inv = 1.0;
   for (int i = 0; i < d; ++i) inv /= (double)g.L[i];
@@ -546,6 +537,10 @@ cudaError_t build_symbol(const Geo& g, double c, double Z, double a, double expo
 // explicit instantiations
 template cudaError_t launch_apply<float>(const Geo&, const Tables<float>&, cudaStream_t, const ApplyIO<float>&);
 template cudaError_t launch_apply<double>(const Geo&, const Tables<double>&, cudaStream_t, const ApplyIO<double>&);
+template ApplyChain<float> build_apply<float>(const Geo&, const Tables<float>&, const ApplyIO<float>&);
+template ApplyChain<double> build_apply<double>(const Geo&, const Tables<double>&, const ApplyIO<double>&);
+template PrecChain<float> build_precond<float>(const Geo&, const Tables<float>&, const double* const*, const PrecIO<float>&);
+template PrecChain<double> build_precond<double>(const Geo&, const Tables<double>&, const double* const*, const PrecIO<double>&);
 template int apply_partials<float>(const Geo&);
 template int apply_partials<double>(const Geo&);
 template int precond_partials<float>(const Geo&);

@@ -12,7 +12,7 @@
 
 #include "../../include/fraclap.h"
 #include "internal.h"
-#include "kernels.cuh"
+#include "chain.cuh"
 
 using namespace fl;
 
@@ -403,8 +403,13 @@ fl_status solve_system(fl_plan* p, double* u, bool x0_nonzero, double shift, dou
         if (loc.rel_residual <= tol) { result = FL_OK; break; }
         if (!(rr == rr)) { result = fail(FL_BREAKDOWN, "NaN in the FP64 residual"); break; }
         if (outer >= p->max_outer) { result = fail(FL_NOT_CONVERGED, "refinement step cap reached"); break; }
+        // Inner target: reduce by inner_tol per step; when the remaining
+        // reduction tol / rel is within FP32 reach (>= 1e-6), aim at half of
+        // it so that this correction is the last one.
+        const double need = tol / loc.rel_residual;
+        const double eta = need >= 1e-6 ? std::min(p->inner_tol, 0.5 * need) : p->inner_tol;
         int its = 0;
-        fl_status in = run_pcg<float>(p, false, shift, scale, use_prec, p->inner_tol, maxit, &its);
+        fl_status in = run_pcg<float>(p, false, shift, scale, use_prec, eta, maxit, &its);
         total += its;
         if (in != FL_OK && in != FL_NOT_CONVERGED) { result = in; break; }
       }
@@ -741,6 +746,397 @@ fl_status fl_sync(fl_plan* p) {
   if (!check_plan(p)) return fail(FL_INVALID_ARG, "NULL plan");
   FL_CUDA(cudaStreamSynchronize(p->stream));
   return FL_OK;
+}
+
+}  // extern "C"
+
+// --- batched solves ------------------------------------------------------------
+// Many independent elliptic problems (different sizes and orders) advance in
+// lockstep: every pass of the FP64 residual, of the FP32 CG start-up and of a
+// CG iteration is ONE launch over all problems (batch.cu).  The CG iteration
+// chunk is captured once into a CUDA graph and replayed until every
+// problem's device state reports done; problems that are done leave at the
+// entry of each kernel.
+namespace {
+
+struct DevArena {
+  std::vector<void*> ptrs;
+  cudaError_t err = cudaSuccess;
+  ~DevArena() {
+    for (void* q : ptrs) cudaFree(q);
+  }
+  template <typename X>
+  X* upload(const std::vector<X>& v) {
+    if (v.empty() || err != cudaSuccess) return nullptr;
+    void* d = nullptr;
+    err = cudaMalloc(&d, v.size() * sizeof(X));
+    if (err != cudaSuccess) return nullptr;
+    ptrs.push_back(d);
+    err = cudaMemcpy(d, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice);
+    return reinterpret_cast<X*>(d);
+  }
+  template <typename X>
+  X* alloc(size_t n) {
+    if (err != cudaSuccess) return nullptr;
+    void* d = nullptr;
+    err = cudaMalloc(&d, n * sizeof(X));
+    if (err == cudaSuccess) ptrs.push_back(d);
+    return reinterpret_cast<X*>(d);
+  }
+};
+
+template <typename A>
+struct PassSet {
+  std::vector<A> args;
+  std::vector<int> off{0};
+  std::vector<int> gx;
+  size_t smem = 0;
+  void add(const A& a, int blocks, int gxv, size_t sm) {
+    args.push_back(a);
+    off.push_back(off.back() + blocks);
+    gx.push_back(gxv);
+    smem = std::max(smem, sm);
+  }
+  BatchPass upload(DevArena& ar, int kind) {
+    BatchPass bp;
+    bp.kind = kind;
+    bp.nprob = (int)args.size();
+    bp.blocks = off.back();
+    bp.smem = smem;
+    bp.args = ar.upload(args);
+    bp.off = ar.upload(off);
+    bp.gx = ar.upload(gx);
+    return bp;
+  }
+};
+
+inline int vec_blocks(long long N) {
+  return (int)std::min<long long>(kVecBlocks, std::max<long long>(1, (N + 1023) / 1024));
+}
+
+template <typename T>
+struct ChainSets {
+  PassSet<RowsFwdArgs<T>> fwd;
+  PassSet<ColsArgs<T>> cols[3];
+  PassSet<RowsInvArgs<T>> inv;
+  void add(const ApplyChain<T>& ch) {
+    fwd.add(ch.fwd, ch.row_blocks, ch.row_blocks, ch.row_smem);
+    for (int j = 0; j < ch.ncols; ++j)
+      cols[j].add(ch.cols[j], (int)(ch.cols_grid[j].x * ch.cols_grid[j].y), (int)ch.cols_grid[j].x,
+                  ch.cols_smem[j]);
+    inv.add(ch.inv, ch.row_blocks, ch.row_blocks, ch.row_smem);
+  }
+};
+
+template <typename T>
+struct PrecSets {
+  PassSet<DstRowsArgs<T>> first;
+  PassSet<DstColsArgs<T>> cols[3];
+  PassSet<DstRowsArgs<T>> last;
+  void add(const PrecChain<T>& ch) {
+    first.add(ch.first, ch.row_blocks, ch.row_blocks, ch.row_smem);
+    for (int j = 0; j < ch.ncols; ++j)
+      cols[j].add(ch.cols[j], (int)(ch.cols_grid[j].x * ch.cols_grid[j].y), (int)ch.cols_grid[j].x,
+                  ch.cols_smem[j]);
+    last.add(ch.last, ch.row_blocks, ch.row_blocks, ch.row_smem);
+  }
+};
+
+template <typename T>
+struct ChainPasses {
+  BatchPass fwd, cols[3], inv;
+  int ncols = 0;
+  void upload(DevArena& ar, ChainSets<T>& cs, int ncols_) {
+    ncols = ncols_;
+    fwd = cs.fwd.upload(ar, BK_ROWS_FWD);
+    for (int j = 0; j < ncols; ++j) cols[j] = cs.cols[j].upload(ar, BK_COLS);
+    inv = cs.inv.upload(ar, BK_ROWS_INV);
+  }
+  cudaError_t launch(cudaStream_t s) const {
+    cudaError_t e = launch_batched<T>(fwd, s);
+    for (int j = 0; j < ncols && e == cudaSuccess; ++j) e = launch_batched<T>(cols[j], s);
+    if (e == cudaSuccess) e = launch_batched<T>(inv, s);
+    return e;
+  }
+};
+
+template <typename T>
+struct PrecPasses {
+  BatchPass first, cols[3], last;
+  int ncols = 0;
+  void upload(DevArena& ar, PrecSets<T>& ps, int ncols_) {
+    ncols = ncols_;
+    first = ps.first.upload(ar, BK_DST_ROWS);
+    for (int j = 0; j < ncols; ++j) cols[j] = ps.cols[j].upload(ar, BK_DST_COLS);
+    last = ps.last.upload(ar, BK_DST_ROWS);
+  }
+  cudaError_t launch(cudaStream_t s) const {
+    cudaError_t e = launch_batched<T>(first, s);
+    for (int j = 0; j < ncols && e == cudaSuccess; ++j) e = launch_batched<T>(cols[j], s);
+    if (e == cudaSuccess) e = launch_batched<T>(last, s);
+    return e;
+  }
+};
+
+fl_status solve_batched_mixed(fl_plan* const* plans, int count, const double* const* f,
+                              double* const* u, double tol, int maxit, int prec_mode,
+                              fl_solve_info* infos) {
+  const int d = plans[0]->g.d;
+  const int ncols = d == 2 ? 1 : 3;
+  DevArena ar;
+  PcgState* gates = ar.alloc<PcgState>(count);
+  double* tol_dev = ar.alloc<double>(count);
+  double* sums = ar.alloc<double>(count);
+  if (ar.err != cudaSuccess) return cuda_fail(ar.err, "batched workspace");
+  std::vector<int> prec(count);
+  ChainSets<double> res64;
+  PassSet<BVecArgs<double>> cast;
+  std::vector<float*> out32(count);
+  std::vector<BScalarArgs> sum_cast(count), sum_res(count), init(count), step(count);
+  PassSet<BVecArgs<float>> start, noprec;
+  PrecSets<float> pinit, pstep;
+  ChainSets<float> apply32;
+  for (int i = 0; i < count; ++i) {
+    fl_plan* p = plans[i];
+    const Geo& g = p->g;
+    const int vb = vec_blocks(g.N);
+    prec[i] = prec_mode == FL_PRECOND_FD || (prec_mode == FL_PRECOND_AUTO && p->alpha >= 1.0);
+    if (prec[i] && p->has_mask)
+      return fail(FL_INVALID_ARG, "the sine-transform preconditioner needs plans without mask");
+    PcgState* st = p->st;
+    const PcgState* gate = gates + i;
+    // FP64: right-hand side of the zero guess, then residuals with u += x32
+    BVecArgs<double> c = {};
+    c.b = f[i]; c.x = u[i]; c.mask = p->mask; c.part = p->part[P_RES]; c.N = g.N;
+    cast.add(c, vb, vb, 0);
+    out32[i] = p->v32.b;
+    sum_cast[i] = BScalarArgs{nullptr, gate, nullptr, 0, p->part[P_RES], vb, nullptr, 0, nullptr, 0};
+    ApplyIO<double> io64;
+    io64.pre = PRE_ACCUM; io64.u = u[i]; io64.acc = u[i]; io64.x32 = p->v32.x; io64.mask = p->mask;
+    io64.st = const_cast<PcgState*>(gate); io64.out32 = p->v32.b; io64.x = u[i]; io64.b = f[i];
+    io64.cm = -1.0; io64.cx = 0.0; io64.cb = 1.0; io64.partials = p->part[P_RES]; io64.dot_self = 1;
+    res64.add(build_apply<double>(g, p->t64, io64));
+    sum_res[i] = BScalarArgs{nullptr, gate, nullptr, 0, p->part[P_RES], apply_partials<double>(g),
+                             nullptr, 0, nullptr, 0};
+    // FP32 CG start-up (x0 = 0)
+    BVecArgs<float> sa = {};
+    sa.gate = gate; sa.st = st; sa.b = p->v32.b; sa.x = p->v32.x; sa.r = p->v32.r; sa.p = p->v32.p;
+    sa.mask = p->mask; sa.part = p->part[P_BB]; sa.N = g.N;
+    start.add(sa, vb, vb, 0);
+    const int pcount = precond_partials<float>(g);
+    if (prec[i]) {
+      PrecIO<float> pi;
+      pi.in = p->v32.r; pi.out = p->v32.z; pi.dotw = p->v32.r; pi.dot_part = p->part[P_RZ];
+      pi.st = const_cast<PcgState*>(gate);
+      pinit.add(build_precond<float>(g, p->t32, p->mu, pi));
+    }
+    init[i] = BScalarArgs{st, gate, p->part[P_BB], vb, nullptr, 0,
+                          prec[i] ? p->part[P_RZ] : p->part[P_BB], prec[i] ? pcount : vb,
+                          tol_dev + i, maxit};
+    // one CG iteration
+    ApplyIO<float> ioa;
+    ioa.pre = PRE_PUPDATE; ioa.u = prec[i] ? p->v32.z : p->v32.r; ioa.p = p->v32.p;
+    ioa.mask = p->mask; ioa.st = st; ioa.out = p->v32.q; ioa.x = p->v32.p; ioa.cm = 1.0;
+    ioa.dotw = p->v32.p; ioa.partials = p->part[P_PQ];
+    apply32.add(build_apply<float>(g, p->t32, ioa));
+    const int pq_count = apply_partials<float>(g);
+    if (prec[i]) {
+      PrecIO<float> pu;
+      pu.pre = DPRE_UPDATE; pu.out = p->v32.z; pu.x = p->v32.x; pu.r = p->v32.r; pu.p = p->v32.p;
+      pu.q = p->v32.q; pu.pq_part = p->part[P_PQ]; pu.pq_count = pq_count;
+      pu.rr_part = p->part[P_RR]; pu.dotw = p->v32.r; pu.dot_part = p->part[P_RZ]; pu.st = st;
+      pstep.add(build_precond<float>(g, p->t32, p->mu, pu));
+      step[i] = BScalarArgs{st, gate, nullptr, 0, p->part[P_RR], pcount, p->part[P_RZ], pcount,
+                            tol_dev + i, maxit};
+    } else {
+      BVecArgs<float> nu = {};
+      nu.st = st; nu.x = p->v32.x; nu.r = p->v32.r; nu.p = p->v32.p; nu.q = p->v32.q;
+      nu.mask = p->mask; nu.pq_part = p->part[P_PQ]; nu.pq_count = pq_count;
+      nu.part = p->part[P_RR]; nu.N = g.N;
+      noprec.add(nu, vb, vb, 0);
+      step[i] = BScalarArgs{st, gate, nullptr, 0, p->part[P_RR], vb, p->part[P_RR], vb,
+                            tol_dev + i, maxit};
+    }
+  }
+  // upload every argument array once
+  ChainPasses<double> R64;
+  R64.upload(ar, res64, ncols);
+  BatchPass CAST = cast.upload(ar, BK_CAST);
+  float* const* out32_dev = ar.upload(out32);
+  BScalarArgs* SUMC = ar.upload(sum_cast);
+  BScalarArgs* SUMR = ar.upload(sum_res);
+  BScalarArgs* INIT = ar.upload(init);
+  BScalarArgs* STEP = ar.upload(step);
+  BatchPass START = start.upload(ar, BK_CG_START);
+  BatchPass NOPREC = noprec.upload(ar, BK_NOPREC);
+  PrecPasses<float> PI, PS;
+  PI.upload(ar, pinit, ncols);
+  PS.upload(ar, pstep, ncols);
+  ChainPasses<float> A32;
+  A32.upload(ar, apply32, ncols);
+  if (ar.err != cudaSuccess) return cuda_fail(ar.err, "batched argument upload");
+
+  // a private stream (capturable), ordered after and before the plans' streams
+  cudaStream_t bs = nullptr;
+  cudaEvent_t ev = nullptr;
+  FL_CUDA(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+  struct StreamGuard {
+    cudaStream_t s;
+    cudaEvent_t e;
+    ~StreamGuard() {
+      if (e) cudaEventDestroy(e);
+      if (s) cudaStreamDestroy(s);
+    }
+  } guard{bs, nullptr};
+  FL_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  guard.e = ev;
+  for (int i = 0; i < count; ++i) {
+    FL_CUDA(cudaEventRecord(ev, plans[i]->stream));
+    FL_CUDA(cudaStreamWaitEvent(bs, ev, 0));
+  }
+  std::vector<PcgState> gh(count), sh(count);
+  std::vector<double> rr(count), bb(count), tolh(count);
+  std::vector<int> its(count, 0), outers(count, 0), conv(count, 0);
+  memset(gh.data(), 0, count * sizeof(PcgState));
+  FL_CUDA(cudaMemcpyAsync(gates, gh.data(), count * sizeof(PcgState), cudaMemcpyHostToDevice, bs));
+  auto read_sums = [&](std::vector<double>& out) -> fl_status {
+    FL_CUDA(cudaMemcpyAsync(out.data(), sums, count * sizeof(double), cudaMemcpyDeviceToHost, bs));
+    FL_CUDA(cudaStreamSynchronize(bs));
+    return FL_OK;
+  };
+  // outer 0: the residual of u = 0 is f
+  FL_CUDA(launch_cast_rhs(CAST, out32_dev, bs));
+  FL_CUDA(launch_batched_scalar(2, SUMC, sums, count, bs));
+  fl_status st = read_sums(bb);
+  if (st != FL_OK) return st;
+  rr = bb;
+  // graph of a chunk of CG iterations, captured on first use
+  const int kChunk = 8;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  struct GraphGuard {
+    cudaGraph_t* g;
+    cudaGraphExec_t* x;
+    ~GraphGuard() {
+      if (*x) cudaGraphExecDestroy(*x);
+      if (*g) cudaGraphDestroy(*g);
+    }
+  } gguard{&graph, &exec};
+  long long kernels_per_chunk = 0;
+  fl_status result = FL_OK;
+  fl_plan* p0 = plans[0];
+  for (int outer = 0;; ++outer) {
+    bool all = true;
+    for (int i = 0; i < count; ++i) {
+      const double rel = bb[i] > 0 ? std::sqrt(rr[i] / bb[i]) : 0.0;
+      conv[i] = rel <= tol;
+      all = all && conv[i];
+      const double need = rel > 0 ? tol / rel : 1.0;
+      tolh[i] = need >= 1e-6 ? std::min(plans[i]->inner_tol, 0.5 * need) : plans[i]->inner_tol;
+      gh[i].done = conv[i];
+      if (!conv[i]) outers[i] = outer;
+    }
+    if (all) break;
+    if (outer >= p0->max_outer) {
+      result = fail(FL_NOT_CONVERGED, "refinement step cap reached");
+      break;
+    }
+    FL_CUDA(cudaMemcpyAsync(gates, gh.data(), count * sizeof(PcgState), cudaMemcpyHostToDevice, bs));
+    FL_CUDA(cudaMemcpyAsync(tol_dev, tolh.data(), count * sizeof(double), cudaMemcpyHostToDevice, bs));
+    // inner FP32 CG start-up
+    FL_CUDA(launch_batched<float>(START, bs));
+    FL_CUDA(PI.launch(bs));
+    FL_CUDA(launch_batched_scalar(0, INIT, nullptr, count, bs));
+    if (!exec) {
+      const long long before = fl_launch_count();
+      ProfScope off(nullptr);
+      FL_CUDA(cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal));
+      cudaError_t ce = cudaSuccess;
+      for (int k = 0; k < kChunk && ce == cudaSuccess; ++k) {
+        ce = A32.launch(bs);
+        if (ce == cudaSuccess) ce = PS.launch(bs);
+        if (ce == cudaSuccess) ce = launch_batched<float>(NOPREC, bs);
+        if (ce == cudaSuccess) ce = launch_batched_scalar(1, STEP, nullptr, count, bs);
+      }
+      cudaError_t ee = cudaStreamEndCapture(bs, &graph);
+      if (ce != cudaSuccess) return cuda_fail(ce, "batched CG capture");
+      if (ee != cudaSuccess) return cuda_fail(ee, "cudaStreamEndCapture");
+      FL_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+      kernels_per_chunk = fl_launch_count() - before;
+      g_launches.fetch_sub(kernels_per_chunk);   // counted when the graph runs
+    }
+    for (;;) {
+      FL_CUDA(cudaGraphLaunch(exec, bs));
+      g_launches.fetch_add(kernels_per_chunk);
+      bool alldone = true;
+      for (int i = 0; i < count; ++i) {
+        FL_CUDA(cudaMemcpyAsync(&sh[i], plans[i]->st, sizeof(PcgState), cudaMemcpyDeviceToHost, bs));
+      }
+      FL_CUDA(cudaStreamSynchronize(bs));
+      for (int i = 0; i < count; ++i) alldone = alldone && sh[i].done;
+      if (alldone) break;
+    }
+    for (int i = 0; i < count; ++i)
+      if (!conv[i]) its[i] += sh[i].it;
+    // FP64 residual with u += x32 (skips converged problems)
+    FL_CUDA(R64.launch(bs));
+    FL_CUDA(launch_batched_scalar(2, SUMR, sums, count, bs));
+    std::vector<double> fresh(count);
+    st = read_sums(fresh);
+    if (st != FL_OK) return st;
+    for (int i = 0; i < count; ++i)
+      if (!conv[i]) rr[i] = fresh[i];
+  }
+  FL_CUDA(cudaEventRecord(ev, bs));
+  for (int i = 0; i < count; ++i) FL_CUDA(cudaStreamWaitEvent(plans[i]->stream, ev, 0));
+  FL_CUDA(cudaStreamSynchronize(bs));
+  if (infos) {
+    for (int i = 0; i < count; ++i) {
+      fl_solve_info& in = infos[i];
+      memset(&in, 0, sizeof(in));
+      in.iterations = its[i];
+      in.outer_iterations = outers[i] + (conv[i] && its[i] > 0 ? 1 : 0);
+      in.rel_residual = bb[i] > 0 ? std::sqrt(rr[i] / bb[i]) : 0.0;
+      in.converged = conv[i];
+      in.status = conv[i] ? FL_OK : FL_NOT_CONVERGED;
+    }
+  }
+  return result;
+}
+
+}  // namespace
+
+extern "C" {
+
+fl_status fl_solve_elliptic_batched(fl_plan* const* plans, int count, const double* const* f_dev,
+                                    double* const* u_dev, double tol, int maxit, int mode,
+                                    fl_solve_info* infos) {
+  if (!plans || !f_dev || !u_dev || count < 1) return fail(FL_INVALID_ARG, "NULL argument or count < 1");
+  for (int i = 0; i < count; ++i) {
+    if (!plans[i] || !f_dev[i] || !u_dev[i]) return fail(FL_INVALID_ARG, "NULL plan or array");
+    if (plans[i]->g.d != plans[0]->g.d) return fail(FL_INVALID_ARG, "all plans must have the same d");
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == plans[i]) return fail(FL_INVALID_ARG, "a plan appears twice in the batch");
+  }
+  if (!(tol > 0.0) || maxit < 1) return fail(FL_INVALID_ARG, "tol must be > 0 and maxit >= 1");
+  const int precision = mode & 0x0F, prec_mode = mode & 0xF0;
+  if (prec_mode != FL_PRECOND_FD && prec_mode != FL_PRECOND_NONE && prec_mode != FL_PRECOND_AUTO)
+    return fail(FL_INVALID_ARG, "unknown preconditioner mode");
+  if (precision == FL_MODE_F64) {
+    // plain FP64 CG: the problems one after another
+    fl_status worst = FL_OK;
+    for (int i = 0; i < count; ++i) {
+      fl_status s = fl_solve_elliptic(plans[i], f_dev[i], u_dev[i], 0, tol, maxit, mode,
+                                      infos ? infos + i : nullptr);
+      if (s != FL_OK && s != FL_NOT_CONVERGED) return s;
+      if (s != FL_OK) worst = s;
+    }
+    return worst;
+  }
+  if (precision != FL_MODE_MIXED) return fail(FL_INVALID_ARG, "unknown precision mode");
+  cudaError_t e = configure_batched_kernels();
+  if (e != cudaSuccess) return cuda_fail(e, "configure_batched_kernels");
+  return solve_batched_mixed(plans, count, f_dev, u_dev, tol, maxit, prec_mode, infos);
 }
 
 }  // extern "C"
