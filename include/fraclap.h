@@ -213,6 +213,42 @@ fl_status fl_solve_elliptic_batched(fl_plan* const* plans, int count, const doub
                                     double* const* u_dev, double tol, int maxit, int mode,
                                     fl_solve_info* infos);
 
+/* --- learned preconditioner (not in the paper) ---------------------------
+ * A 3-level U-Net (channels 16/32/64, 3 x 3 convolutions, BF16 weights,
+ * FP32 accumulation) maps features [r / s_r, z0 / s_z, alpha] of a residual
+ * r (z0 = the base preconditioner applied to r, s = root mean square) on an
+ * H x W grid to a correction y; the learned preconditioner is
+ * z = z0 + s_z y, used inside flexible CG.  Activations and features are
+ * device float arrays [channel][y][x].
+ *
+ * Parameter layout (fl_net_get_params / fl_net_set_params, checkpoints): per
+ * layer in the order e0a, e0b, e1a, e1b, ba, bb, d1a, d1b, d0a, d0b, head,
+ * the weights W[cout][cin][k][k] then the biases b[cout], as float. */
+typedef struct fl_net fl_net;
+
+/* H, W: multiples of 64 (two 2 x 2 poolings on 16 x 16 tiles); seed of the
+ * He-normal initialisation; stream: cudaStream_t (NULL = default). */
+fl_status fl_net_create(int H, int W, uint64_t seed, void* stream, fl_net** out);
+fl_status fl_net_destroy(fl_net* net);
+long long fl_net_num_params(const fl_net* net);
+/* Copy the FP32 parameters and/or the last gradients to host (nullable). */
+fl_status fl_net_get_params(fl_net* net, float* params_host, float* grads_host);
+/* Set the parameters from host; resets the Adam state. */
+fl_status fl_net_set_params(fl_net* net, const float* params_host);
+/* y_dev[H*W] = N(x_dev[3*H*W]). */
+fl_status fl_net_forward(fl_net* net, const float* x_dev, float* y_dev);
+/* Mean squared error over a batch (xs_dev[batch][3][H][W], ts_dev[batch][H][W])
+ * and its gradient (kept in the net, see fl_net_get_params). */
+fl_status fl_net_loss_grad(fl_net* net, const float* xs_dev, const float* ts_dev, int batch,
+                           double* loss);
+/* fl_net_loss_grad followed by one Adam step with learning rate lr. */
+fl_status fl_net_train_step(fl_net* net, const float* xs_dev, const float* ts_dev, int batch,
+                            float lr, double* loss);
+/* Checkpoint file: header (magic, version, parameter count, Adam step),
+ * FNV-1a checksum, FP32 parameters. */
+fl_status fl_net_save(fl_net* net, const char* path);
+fl_status fl_net_load(fl_net* net, const char* path);
+
 /* Wait for all work on the plan's stream. */
 fl_status fl_sync(fl_plan* plan);
 

@@ -80,6 +80,16 @@ SIGNATURES = {
     "fl_launch_count": (ctypes.c_longlong, []),
     "fl_profile_enable": (_I, [_P, _I]),
     "fl_profile_read": (_I, [_P, ctypes.POINTER(FlKernelStat), _I]),
+    "fl_net_create": (_I, [_I, _I, ctypes.c_uint64, _P, ctypes.POINTER(_P)]),
+    "fl_net_destroy": (_I, [_P]),
+    "fl_net_num_params": (ctypes.c_longlong, [_P]),
+    "fl_net_get_params": (_I, [_P, _P, _P]),
+    "fl_net_set_params": (_I, [_P, _P]),
+    "fl_net_forward": (_I, [_P, _P, _P]),
+    "fl_net_loss_grad": (_I, [_P, _P, _P, _I, ctypes.POINTER(_D)]),
+    "fl_net_train_step": (_I, [_P, _P, _P, _I, ctypes.c_float, ctypes.POINTER(_D)]),
+    "fl_net_save": (_I, [_P, ctypes.c_char_p]),
+    "fl_net_load": (_I, [_P, ctypes.c_char_p]),
     "fl_last_error_string": (ctypes.c_char_p, []),
 }
 

@@ -31,6 +31,80 @@ def launch_count():
     return int(L.load().fl_launch_count())
 
 
+class Net:
+    """The U-Net of the learned preconditioner (fl_net_*); H, W multiples of 64."""
+
+    def __init__(self, H, W, seed=0, stream=None):
+        import torch
+        self._lib = L.load()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        L.check(self._lib.fl_net_create(int(H), int(W), int(seed), ctypes.c_void_p(stream.cuda_stream),
+                                        ctypes.byref(h)), "fl_net_create")
+        self._h, self.H, self.W = h, int(H), int(W)
+        self.nparams = int(self._lib.fl_net_num_params(h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fl_net_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self, grads=False):
+        p = np.empty(self.nparams, np.float32)
+        g = np.empty(self.nparams, np.float32) if grads else None
+        L.check(self._lib.fl_net_get_params(self._h, p.ctypes.data_as(ctypes.c_void_p),
+                                            g.ctypes.data_as(ctypes.c_void_p) if grads else None),
+                "fl_net_get_params")
+        return (p, g) if grads else p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        if p.size != self.nparams:
+            raise ValueError("wrong parameter count")
+        L.check(self._lib.fl_net_set_params(self._h, p.ctypes.data_as(ctypes.c_void_p)),
+                "fl_net_set_params")
+
+    def forward(self, x):
+        import torch
+        _check_tensor(x, torch.float32, 3 * self.H * self.W, "x")
+        y = torch.empty(self.H * self.W, dtype=torch.float32, device=x.device)
+        L.check(self._lib.fl_net_forward(self._h, _ptr(x), _ptr(y)), "fl_net_forward")
+        return y
+
+    def loss_grad(self, xs, ts):
+        import torch
+        b = xs.shape[0]
+        _check_tensor(xs, torch.float32, b * 3 * self.H * self.W, "xs")
+        _check_tensor(ts, torch.float32, b * self.H * self.W, "ts")
+        loss = ctypes.c_double()
+        L.check(self._lib.fl_net_loss_grad(self._h, _ptr(xs), _ptr(ts), int(b), ctypes.byref(loss)),
+                "fl_net_loss_grad")
+        return loss.value
+
+    def train_step(self, xs, ts, lr=1e-3):
+        import torch
+        b = xs.shape[0]
+        _check_tensor(xs, torch.float32, b * 3 * self.H * self.W, "xs")
+        _check_tensor(ts, torch.float32, b * self.H * self.W, "ts")
+        loss = ctypes.c_double()
+        L.check(self._lib.fl_net_train_step(self._h, _ptr(xs), _ptr(ts), int(b), float(lr),
+                                            ctypes.byref(loss)), "fl_net_train_step")
+        return loss.value
+
+    def save(self, path):
+        L.check(self._lib.fl_net_save(self._h, str(path).encode()), "fl_net_save")
+
+    def load(self, path):
+        L.check(self._lib.fl_net_load(self._h, str(path).encode()), "fl_net_load")
+
+
 def solve_batched(plans, fs, tol=1e-8, maxit=1000, mode=L.FL_MODE_MIXED | L.FL_PRECOND_AUTO,
                   raise_on_fail=True):
     """fl_solve_elliptic_batched over lists of plans and float64 CUDA tensors;

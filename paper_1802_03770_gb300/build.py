@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 OUT = os.path.join(HERE, "libfraclap.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SOURCES = ["ops.cu", "plan.cu", "batch.cu"]
+CUDA_SOURCES = ["ops.cu", "plan.cu", "batch.cu", "unet.cu", "learned.cu"]
 CXX_SOURCES = ["consts.cpp"]
 
 

@@ -91,9 +91,10 @@ template <int R, int VPT, typename C>
 __device__ __forceinline__ void stockham_stage(C* buf, int lg, int ls, int nlines, int Ns,
                                                const C* __restrict__ tw, int lgmax, bool inv) {
   constexpr int NB = VPT / R;  // butterflies per thread
-  const int L = 1 << lg;
-  const int LR = L / R;
-  const int total = nlines * LR;
+  constexpr int LGR = R == 8 ? 3 : (R == 4 ? 2 : 1);
+  const int lglr = lg - LGR;
+  const int LR = 1 << lglr;
+  const int total = nlines << lglr;
   C v[NB][R];
   int dst[NB];
 #pragma unroll
@@ -101,8 +102,8 @@ __device__ __forceinline__ void stockham_stage(C* buf, int lg, int ls, int nline
     const int g = threadIdx.x + b * blockDim.x;
     dst[b] = -1;
     if (g < total) {
-      const int line = g / LR;
-      const int j = g - line * LR;
+      const int line = g >> lglr;
+      const int j = g & (LR - 1);
       const int k = j & (Ns - 1);
       C* base = buf + (size_t)line * ls;
       // twiddle index for leg r: r * k * (Lmax / (Ns * R))

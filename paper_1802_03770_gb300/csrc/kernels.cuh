@@ -121,7 +121,7 @@ __device__ __forceinline__ void body_rows_fwd(const RowsFwdArgs<T>& a, int bx, i
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int e = e0 + u * THREADS;
-      const int q = e / L, j = e - q * L;
+      const int q = e >> a.lg, j = e & (L - 1);
       const int ra = 2 * (pair0 + q), rb = ra + 1;
       va[u] = 0;
       vb[u] = 0;
@@ -145,7 +145,7 @@ __device__ __forceinline__ void body_rows_fwd(const RowsFwdArgs<T>& a, int bx, i
     for (int u = 0; u < U; ++u) {
       const int e = e0 + u * THREADS;
       if (e >= tot) continue;
-      const int q = e / L, j = e - q * L;
+      const int q = e >> a.lg, j = e & (L - 1);
       const int ra = 2 * (pair0 + q), rb = ra + 1;
       T xa = va[u], xb = vb[u];
       if (j < a.n) {
@@ -168,18 +168,20 @@ __device__ __forceinline__ void body_rows_fwd(const RowsFwdArgs<T>& a, int bx, i
   }
   __syncthreads();
   fft_lines<VPT>(buf, a.lg, ls, nl, a.tw, a.lgmax, false);
-  for (int e = threadIdx.x; e < nl * a.H; e += THREADS) {
-    const int q = e / a.H, k = e - q * a.H;
+  for (int q = 0; q < nl; ++q) {
     const int ra = 2 * (pair0 + q), rb = ra + 1;
-    const C z = buf[q * ls + k];
-    const C w = cconj(buf[q * ls + ((L - k) & (L - 1))]);
-    const C xa = cmake<C>((z.x + w.x) * (T)0.5, (z.y + w.y) * (T)0.5);
-    const C xb = cmake<C>((z.y - w.y) * (T)0.5, (w.x - z.x) * (T)0.5);
-    const size_t sa = ((size_t)(ra / a.rows_per_plane) * a.plane_stride + ra % a.rows_per_plane) * a.H;
-    a.S[sa + k] = xa;
-    if (rb < a.rows) {
-      const size_t sb = ((size_t)(rb / a.rows_per_plane) * a.plane_stride + rb % a.rows_per_plane) * a.H;
-      a.S[sb + k] = xb;
+    const bool hb = rb < a.rows;
+    typename Cplx<T>::type* __restrict__ Sa =
+        a.S + ((size_t)(ra / a.rows_per_plane) * a.plane_stride + ra % a.rows_per_plane) * a.H;
+    typename Cplx<T>::type* __restrict__ Sb =
+        hb ? a.S + ((size_t)(rb / a.rows_per_plane) * a.plane_stride + rb % a.rows_per_plane) * a.H
+           : nullptr;
+    const C* lb = buf + q * ls;
+    for (int k = threadIdx.x; k < a.H; k += THREADS) {
+      const C z = lb[k];
+      const C w = cconj(lb[(L - k) & (L - 1)]);
+      Sa[k] = cmake<C>((z.x + w.x) * (T)0.5, (z.y + w.y) * (T)0.5);
+      if (hb) Sb[k] = cmake<C>((z.y - w.y) * (T)0.5, (w.x - z.x) * (T)0.5);
     }
   }
 }
@@ -307,20 +309,23 @@ __device__ __forceinline__ void body_rows_inv(const RowsInvArgs<T>& a, int bx, i
   const int pair0 = bx * NL;
   const int npairs = (a.rows + 1) / 2;
   const int nl = min(NL, npairs - pair0);
-#pragma unroll 4
-  for (int e = threadIdx.x; e < nl * a.H; e += THREADS) {
-    const int q = e / a.H, k = e - q * a.H;
+  for (int q = 0; q < nl; ++q) {
     const int ra = 2 * (pair0 + q), rb = ra + 1;
-    const size_t sa = ((size_t)(ra / a.rows_per_plane) * a.plane_stride + ra % a.rows_per_plane) * a.H;
-    const C xa = a.S[sa + k];
-    C xb = cmake<C>((T)0, (T)0);
-    if (rb < a.rows) {
-      const size_t sb = ((size_t)(rb / a.rows_per_plane) * a.plane_stride + rb % a.rows_per_plane) * a.H;
-      xb = a.S[sb + k];
+    const bool hb = rb < a.rows;
+    const typename Cplx<T>::type* __restrict__ Sa =
+        a.S + ((size_t)(ra / a.rows_per_plane) * a.plane_stride + ra % a.rows_per_plane) * a.H;
+    const typename Cplx<T>::type* __restrict__ Sb =
+        hb ? a.S + ((size_t)(rb / a.rows_per_plane) * a.plane_stride + rb % a.rows_per_plane) * a.H
+           : nullptr;
+    C* lb = buf + q * ls;
+#pragma unroll 4
+    for (int k = threadIdx.x; k < a.H; k += THREADS) {
+      const C xa = Sa[k];
+      const C xb = hb ? Sb[k] : cmake<C>((T)0, (T)0);
+      // Z[k] = Xa[k] + i Xb[k];  Z[L-k] = conj(Xa[k]) + i conj(Xb[k])
+      lb[k] = cmake<C>(xa.x - xb.y, xa.y + xb.x);
+      if (k > 0 && k < a.H - 1) lb[L - k] = cmake<C>(xa.x + xb.y, xb.x - xa.y);
     }
-    // Z[k] = Xa[k] + i Xb[k];  Z[L-k] = conj(Xa[k]) + i conj(Xb[k])
-    buf[q * ls + k] = cmake<C>(xa.x - xb.y, xa.y + xb.x);
-    if (k > 0 && k < a.H - 1) buf[q * ls + (L - k)] = cmake<C>(xa.x + xb.y, xb.x - xa.y);
   }
   __syncthreads();
   fft_lines<VPT>(buf, a.lg, ls, nl, a.tw, a.lgmax, true);
@@ -330,22 +335,25 @@ __device__ __forceinline__ void body_rows_inv(const RowsInvArgs<T>& a, int bx, i
   const T* __restrict__ win = a.dot_self ? nullptr : a.dotw;
   T* __restrict__ out = a.out;
   float* __restrict__ out32 = a.out32;
+  for (int q = 0; q < 2 * nl; ++q) {
+    const int row = 2 * pair0 + q;
+    if (row >= a.rows) break;
+    const int half = q & 1;
+    const C* lb = buf + (q >> 1) * ls;
+    const size_t base = (size_t)row * a.n;
 #pragma unroll 4
-  for (int e = threadIdx.x; e < nl * 2 * a.n; e += THREADS) {
-    const int q = e / (2 * a.n), rem = e - q * 2 * a.n;
-    const int half = rem / a.n, j = rem - half * a.n;
-    const int row = 2 * (pair0 + q) + half;
-    if (row >= a.rows) continue;
-    const size_t idx = (size_t)row * a.n + j;
-    const C z = buf[q * ls + j];
-    double v = (double)(half ? z.y : z.x) * a.cm;
-    if (xin) v += a.cx * (double)xin[idx];
-    if (bin) v += a.cb * (double)bin[idx];
-    if (a.mask && !a.mask[idx]) v = 0.0;
-    const T tv = (T)v;
-    if (out) out[idx] = tv;
-    if (out32) out32[idx] = (float)v;
-    if (a.partials) part += win ? (double)tv * (double)win[idx] : (double)tv * (double)tv;
+    for (int j = threadIdx.x; j < a.n; j += THREADS) {
+      const size_t idx = base + j;
+      const C z = lb[j];
+      double v = (double)(half ? z.y : z.x) * a.cm;
+      if (xin) v += a.cx * (double)xin[idx];
+      if (bin) v += a.cb * (double)bin[idx];
+      if (a.mask && !a.mask[idx]) v = 0.0;
+      const T tv = (T)v;
+      if (out) out[idx] = tv;
+      if (out32) out32[idx] = (float)v;
+      if (a.partials) part += win ? (double)tv * (double)win[idx] : (double)tv * (double)tv;
+    }
   }
   if (a.partials) {
     const double s = cta_sum(part, red);
@@ -365,7 +373,7 @@ __device__ __forceinline__ void chirp_conv(C* buf, int ls, int nl, int L, int lg
                                            const C* __restrict__ tw, const C* __restrict__ bhat) {
   fft_lines<VPT>(buf, lg, ls, nl, tw, lgmax, false);
   for (int e = threadIdx.x; e < nl * L; e += blockDim.x) {
-    const int q = e / L, k = e - q * L;
+    const int q = e >> lg, k = e & (L - 1);
     buf[q * ls + k] = cmul(buf[q * ls + k], bhat[k]);
   }
   __syncthreads();
@@ -439,7 +447,7 @@ __device__ __forceinline__ void body_dst_rows(const DstRowsArgs<T>& a, int bx, i
     const T* __restrict__ qv = a.q;
 #pragma unroll 4
     for (int e = threadIdx.x; e < nl * L; e += THREADS) {
-      const int q = e / L, j = e - q * L;
+      const int q = e >> a.lg, j = e & (L - 1);
       C v = cmake<C>((T)0, (T)0);
       if (j < a.n) {
         const size_t idx = (size_t)(row0 + q) * a.n + j;
@@ -455,7 +463,7 @@ __device__ __forceinline__ void body_dst_rows(const DstRowsArgs<T>& a, int bx, i
   } else {
 #pragma unroll 4
     for (int e = threadIdx.x; e < nl * L; e += THREADS) {
-      const int q = e / L, j = e - q * L;
+      const int q = e >> a.lg, j = e & (L - 1);
       C v = cmake<C>((T)0, (T)0);
       if (j < a.n) v = cscale(a.chirp[j], a.in[(size_t)(row0 + q) * a.n + j]);
       buf[q * ls + j] = v;
@@ -464,20 +472,22 @@ __device__ __forceinline__ void body_dst_rows(const DstRowsArgs<T>& a, int bx, i
   __syncthreads();
   fft_lines<VPT>(buf, a.lg, ls, nl, a.tw, a.lgmax, false);
   for (int e = threadIdx.x; e < nl * L; e += THREADS) {
-    const int q = e / L, k = e - q * L;
+    const int q = e >> a.lg, k = e & (L - 1);
     buf[q * ls + k] = cmul(buf[q * ls + k], a.bhat[k]);
   }
   __syncthreads();
   fft_lines<VPT>(buf, a.lg, ls, nl, a.tw, a.lgmax, true);
   double dp = 0.0;
+  for (int q = 0; q < nl; ++q) {
+    const C* lb = buf + q * ls;
+    const size_t base = (size_t)(row0 + q) * a.n;
 #pragma unroll 4
-  for (int e = threadIdx.x; e < nl * a.n; e += THREADS) {
-    const int q = e / a.n, k = e - q * a.n;
-    const C y = cmul(a.chirp[k], buf[q * ls + k]);
-    const size_t idx = (size_t)(row0 + q) * a.n + k;
-    const T v = (T)((double)y.y * a.post);
-    a.out[idx] = v;
-    if (a.dotw) dp += (double)v * (double)a.dotw[idx];
+    for (int k = threadIdx.x; k < a.n; k += THREADS) {
+      const C y = cmul(a.chirp[k], lb[k]);
+      const T v = (T)((double)y.y * a.post);
+      a.out[base + k] = v;
+      if (a.dotw) dp += (double)v * (double)a.dotw[base + k];
+    }
   }
   if (a.pre == DPRE_UPDATE) {
     const double s = cta_sum(rr, red);

@@ -1,0 +1,377 @@
+// The network object of the learned preconditioner: parameters (FP32
+// master, BF16 copy, Adam moments), activations and gradients, forward,
+// backward, training step, checkpoint files.  The architecture is described
+// in unet.cu.
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/fraclap.h"
+#include "chain.cuh"
+#include "learned.h"
+#include "unet.h"
+
+namespace fl {
+
+namespace {
+
+// layer table: name, input sources (tensor id, mode), cout, k, level
+enum { T_X = 0, T_E0A, T_E0B, T_E1A, T_E1B, T_BA, T_BB, T_D1A, T_D1B, T_D0A, T_D0B, T_Y, T_COUNT };
+
+struct LayerSpec {
+  int out;          // output tensor id
+  int src[2];       // source tensor ids (-1 unused)
+  int mode[2];
+  int k;
+  int relu;
+};
+
+const LayerSpec kLayers[kNetLayers] = {
+    {T_E0A, {T_X, -1}, {SRC_DIRECT, 0}, 3, 1},
+    {T_E0B, {T_E0A, -1}, {SRC_DIRECT, 0}, 3, 1},
+    {T_E1A, {T_E0B, -1}, {SRC_POOL, 0}, 3, 1},
+    {T_E1B, {T_E1A, -1}, {SRC_DIRECT, 0}, 3, 1},
+    {T_BA, {T_E1B, -1}, {SRC_POOL, 0}, 3, 1},
+    {T_BB, {T_BA, -1}, {SRC_DIRECT, 0}, 3, 1},
+    {T_D1A, {T_BB, T_E1B}, {SRC_UP, SRC_DIRECT}, 3, 1},
+    {T_D1B, {T_D1A, -1}, {SRC_DIRECT, 0}, 3, 1},
+    {T_D0A, {T_D1B, T_E0B}, {SRC_UP, SRC_DIRECT}, 3, 1},
+    {T_D0B, {T_D0A, -1}, {SRC_DIRECT, 0}, 3, 1},
+    {T_Y, {T_D0B, -1}, {SRC_DIRECT, 0}, 1, 0},
+};
+
+// 64-bit mixer (splitmix64) and Box-Muller, for the He-normal initialisation.
+uint64_t splitmix(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ULL);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+double uniform01(uint64_t& s) { return ((splitmix(s) >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
+
+}  // namespace
+
+int NetState::channels(int t) const {
+  switch (t) {
+    case T_X: return kNetInputs;
+    case T_E0A: case T_E0B: case T_D0A: case T_D0B: return c[0];
+    case T_E1A: case T_E1B: case T_D1A: case T_D1B: return c[1];
+    case T_BA: case T_BB: return c[2];
+    default: return 1;
+  }
+}
+
+int NetState::level(int t) const {
+  switch (t) {
+    case T_E1A: case T_E1B: case T_D1A: case T_D1B: return 1;
+    case T_BA: case T_BB: return 2;
+    default: return 0;
+  }
+}
+
+cudaError_t NetState::init(int h, int wd, uint64_t seed, cudaStream_t s) {
+  H = h;
+  W = wd;
+  stream = s;
+  nparams = 0;
+  for (int l = 0; l < kNetLayers; ++l) {
+    const LayerSpec& L = kLayers[l];
+    int cin = 0;
+    for (int j = 0; j < 2; ++j)
+      if (L.src[j] >= 0) cin += channels(L.src[j]);
+    cin_[l] = cin;
+    cout_[l] = channels(L.out);
+    woff[l] = nparams;
+    nparams += (long long)cout_[l] * cin * L.k * L.k;
+    boff[l] = nparams;
+    nparams += cout_[l];
+  }
+  // He-normal weights, zero biases
+  std::vector<float> host(nparams, 0.f);
+  uint64_t st = seed;
+  for (int l = 0; l < kNetLayers; ++l) {
+    const int k = kLayers[l].k;
+    const double stdv = std::sqrt(2.0 / (cin_[l] * k * k));
+    for (long long i = woff[l]; i < boff[l]; ++i) {
+      const double u1 = uniform01(st), u2 = uniform01(st);
+      host[i] = (float)(stdv * std::sqrt(-2.0 * std::log(u1)) * std::cos(2.0 * M_PI * u2));
+    }
+  }
+  cudaError_t e = cudaSuccess;
+  auto al = [&](void** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) allocs.push_back(*p);
+  };
+  al((void**)&w, nparams * sizeof(float));
+  al((void**)&wb, nparams * sizeof(__nv_bfloat16));
+  al((void**)&g, nparams * sizeof(float));
+  al((void**)&m, nparams * sizeof(float));
+  al((void**)&v, nparams * sizeof(float));
+  size_t maxg = 0, maxgx = 0, maxpart = 0;
+  for (int t = 0; t < T_COUNT; ++t) {
+    const size_t n = (size_t)channels(t) * (H >> level(t)) * (W >> level(t));
+    al((void**)&act[t], n * sizeof(float));
+    al((void**)&grad[t], n * sizeof(float));
+    maxg = std::max(maxg, n);
+  }
+  for (int l = 0; l < kNetLayers; ++l) {
+    const int lev = level(kLayers[l].out);
+    maxgx = std::max(maxgx, (size_t)cin_[l] * (H >> lev) * (W >> lev));
+    ConvArgs a = conv_args(l, false);
+    maxpart = std::max(maxpart, conv_wgrad_partials(a));
+  }
+  al((void**)&gz, maxg * sizeof(float));
+  al((void**)&gx, maxgx * sizeof(float));
+  al((void**)&part, maxpart * sizeof(float));
+  al((void**)&bpart, (size_t)(H / 16) * (W / 16) * 64 * sizeof(float));
+  al((void**)&lpart, kLossBlocks * sizeof(double));
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(w, host.data(), nparams * sizeof(float), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m, 0, nparams * sizeof(float), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(v, 0, nparams * sizeof(float), s);
+  if (e == cudaSuccess) e = launch_to_bf16(w, wb, nparams, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  step = 0;
+  return e;
+}
+
+NetState::~NetState() {
+  for (void* p : allocs) cudaFree(p);
+}
+
+ConvArgs NetState::conv_args(int l, bool input_grad) const {
+  const LayerSpec& L = kLayers[l];
+  const int lev = level(L.out);
+  ConvArgs a;
+  memset(&a, 0, sizeof(a));
+  a.H = H >> lev;
+  a.W = W >> lev;
+  a.k = L.k;
+  a.w = wb + woff[l];
+  if (!input_grad) {
+    for (int j = 0; j < 2; ++j) {
+      a.src[j].p = L.src[j] >= 0 ? act[L.src[j]] : nullptr;
+      a.src[j].nc = L.src[j] >= 0 ? channels(L.src[j]) : 0;
+      a.src[j].mode = L.mode[j];
+    }
+    a.cin = cin_[l];
+    a.cout = cout_[l];
+    a.bias = w + boff[l];
+    a.out = act[L.out];
+    a.relu = L.relu;
+    a.transposed = 0;
+  } else {
+    a.src[0].p = gz;
+    a.src[0].nc = cout_[l];
+    a.src[0].mode = SRC_DIRECT;
+    a.src[1].nc = 0;
+    a.cin = cout_[l];
+    a.cout = cin_[l];
+    a.bias = nullptr;
+    a.out = gx;
+    a.relu = 0;
+    a.transposed = 1;
+  }
+  return a;
+}
+
+cudaError_t NetState::forward(const float* x, float* y) {
+  cudaError_t e = cudaMemcpyAsync(act[T_X], x, (size_t)kNetInputs * H * W * sizeof(float),
+                                  cudaMemcpyDeviceToDevice, stream);
+  for (int l = 0; l < kNetLayers && e == cudaSuccess; ++l) e = launch_conv(conv_args(l, false), stream);
+  if (e == cudaSuccess && y)
+    e = cudaMemcpyAsync(y, act[T_Y], (size_t)H * W * sizeof(float), cudaMemcpyDeviceToDevice, stream);
+  return e;
+}
+
+// Accumulates the parameter gradients of one sample into g, given the
+// gradient of the loss with respect to the output, already in grad[T_Y].
+cudaError_t NetState::backward() {
+  cudaError_t e = cudaSuccess;
+  for (int t = 0; t < T_COUNT - 1 && e == cudaSuccess; ++t) {
+    const size_t n = (size_t)channels(t) * (H >> level(t)) * (W >> level(t));
+    e = cudaMemsetAsync(grad[t], 0, n * sizeof(float), stream);
+  }
+  for (int l = kNetLayers - 1; l >= 0 && e == cudaSuccess; --l) {
+    const LayerSpec& L = kLayers[l];
+    const int lev = level(L.out);
+    const int h = H >> lev, wd = W >> lev;
+    const long long n = (long long)cout_[l] * h * wd;
+    if (L.relu) e = launch_relu_mask(grad[L.out], act[L.out], gz, n, stream);
+    else e = cudaMemcpyAsync(gz, grad[L.out], n * sizeof(float), cudaMemcpyDeviceToDevice, stream);
+    if (e != cudaSuccess) break;
+    e = launch_conv_wgrad(conv_args(l, false), gz, part, bpart, g + woff[l], g + boff[l], 1, stream);
+    if (e != cudaSuccess || l == 0) continue;   // the input features need no gradient
+    e = launch_conv(conv_args(l, true), stream);
+    int c_off = 0;
+    for (int j = 0; j < 2 && e == cudaSuccess; ++j) {
+      if (L.src[j] < 0) continue;
+      const int nc = channels(L.src[j]);
+      e = launch_scatter(gx, c_off, nc, L.mode[j], h, wd, grad[L.src[j]], stream);
+      c_off += nc;
+    }
+  }
+  return e;
+}
+
+cudaError_t NetState::loss_grad(const float* xs, const float* ts, int batch, double* loss) {
+  cudaError_t e = cudaMemsetAsync(g, 0, nparams * sizeof(float), stream);
+  const long long npix = (long long)H * W;
+  double total = 0.0;
+  std::vector<double> lp(kLossBlocks);
+  for (int b = 0; b < batch && e == cudaSuccess; ++b) {
+    e = forward(xs + (size_t)b * kNetInputs * npix, nullptr);
+    if (e == cudaSuccess)
+      e = launch_mse(act[T_Y], ts + (size_t)b * npix, grad[T_Y], npix, 1.f / (float)(npix * batch),
+                     lpart, kLossBlocks, stream);
+    if (e == cudaSuccess) e = backward();
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(lp.data(), lpart, kLossBlocks * sizeof(double), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    for (double x : lp) total += x;
+  }
+  if (loss) *loss = total / ((double)npix * batch);
+  return e;
+}
+
+cudaError_t NetState::train_step(const float* xs, const float* ts, int batch, float lr, double* loss) {
+  cudaError_t e = loss_grad(xs, ts, batch, loss);
+  if (e == cudaSuccess) e = launch_adam(w, wb, g, m, v, nparams, lr, ++step, stream);
+  return e;
+}
+
+}  // namespace fl
+
+// --- C ABI ---------------------------------------------------------------------
+
+struct fl_net : public fl::NetState {};
+
+namespace {
+thread_local std::string g_net_err;
+fl_status net_fail(fl_status s, const std::string& m) {
+  g_net_err = m;
+  fl_set_error_string(m.c_str());
+  return s;
+}
+fl_status net_cuda(cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return FL_OK;
+  return net_fail(e == cudaErrorMemoryAllocation ? FL_OOM : FL_CUDA_ERROR,
+                  std::string(where) + ": " + cudaGetErrorString(e));
+}
+const uint32_t kMagic = 0x464c4e54;  // "FLNT"
+uint64_t fnv1a(const void* p, size_t n) {
+  const unsigned char* c = (const unsigned char*)p;
+  uint64_t h = 1469598103934665603ULL;
+  for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ULL;
+  return h;
+}
+}  // namespace
+
+extern "C" {
+
+fl_status fl_net_create(int H, int W, uint64_t seed, void* stream, fl_net** out) {
+  if (!out) return net_fail(FL_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (H < 64 || W < 64 || H % 64 || W % 64 || H > 4096 || W > 4096)
+    return net_fail(FL_INVALID_ARG, "H and W must be multiples of 64 in [64, 4096]");
+  fl_net* n = new fl_net();
+  cudaError_t e = n->init(H, W, seed, (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    delete n;
+    return net_cuda(e, "fl_net_create");
+  }
+  *out = n;
+  return FL_OK;
+}
+
+fl_status fl_net_destroy(fl_net* n) {
+  if (n) {
+    cudaStreamSynchronize(n->stream);
+    delete n;
+  }
+  return FL_OK;
+}
+
+long long fl_net_num_params(const fl_net* n) { return n ? n->nparams : 0; }
+
+fl_status fl_net_get_params(fl_net* n, float* host, float* grads_host) {
+  if (!n || (!host && !grads_host)) return net_fail(FL_INVALID_ARG, "NULL argument");
+  if (host) {
+    fl_status s = net_cuda(cudaMemcpyAsync(host, n->w, n->nparams * sizeof(float),
+                                           cudaMemcpyDeviceToHost, n->stream), "get params");
+    if (s != FL_OK) return s;
+  }
+  if (grads_host) {
+    fl_status s = net_cuda(cudaMemcpyAsync(grads_host, n->g, n->nparams * sizeof(float),
+                                           cudaMemcpyDeviceToHost, n->stream), "get grads");
+    if (s != FL_OK) return s;
+  }
+  return net_cuda(cudaStreamSynchronize(n->stream), "sync");
+}
+
+fl_status fl_net_set_params(fl_net* n, const float* host) {
+  if (!n || !host) return net_fail(FL_INVALID_ARG, "NULL argument");
+  cudaError_t e = cudaMemcpyAsync(n->w, host, n->nparams * sizeof(float), cudaMemcpyHostToDevice, n->stream);
+  if (e == cudaSuccess) e = fl::launch_to_bf16(n->w, n->wb, n->nparams, n->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(n->m, 0, n->nparams * sizeof(float), n->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(n->v, 0, n->nparams * sizeof(float), n->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
+  n->step = 0;
+  return net_cuda(e, "fl_net_set_params");
+}
+
+fl_status fl_net_forward(fl_net* n, const float* x_dev, float* y_dev) {
+  if (!n || !x_dev || !y_dev) return net_fail(FL_INVALID_ARG, "NULL argument");
+  return net_cuda(n->forward(x_dev, y_dev), "fl_net_forward");
+}
+
+fl_status fl_net_loss_grad(fl_net* n, const float* xs_dev, const float* ts_dev, int batch,
+                           double* loss) {
+  if (!n || !xs_dev || !ts_dev || batch < 1) return net_fail(FL_INVALID_ARG, "bad argument");
+  return net_cuda(n->loss_grad(xs_dev, ts_dev, batch, loss), "fl_net_loss_grad");
+}
+
+fl_status fl_net_train_step(fl_net* n, const float* xs_dev, const float* ts_dev, int batch, float lr,
+                            double* loss) {
+  if (!n || !xs_dev || !ts_dev || batch < 1 || !(lr > 0.f)) return net_fail(FL_INVALID_ARG, "bad argument");
+  return net_cuda(n->train_step(xs_dev, ts_dev, batch, lr, loss), "fl_net_train_step");
+}
+
+fl_status fl_net_save(fl_net* n, const char* path) {
+  if (!n || !path) return net_fail(FL_INVALID_ARG, "NULL argument");
+  std::vector<float> host(n->nparams);
+  fl_status s = fl_net_get_params(n, host.data(), nullptr);
+  if (s != FL_OK) return s;
+  FILE* f = fopen(path, "wb");
+  if (!f) return net_fail(FL_INVALID_ARG, std::string("cannot open ") + path);
+  const uint32_t hdr[4] = {kMagic, 1u, (uint32_t)n->nparams, (uint32_t)n->step};
+  const uint64_t sum = fnv1a(host.data(), host.size() * sizeof(float));
+  bool ok = fwrite(hdr, sizeof(hdr), 1, f) == 1 && fwrite(&sum, sizeof(sum), 1, f) == 1 &&
+            fwrite(host.data(), sizeof(float), host.size(), f) == host.size();
+  ok = (fclose(f) == 0) && ok;
+  return ok ? FL_OK : net_fail(FL_INVALID_ARG, "write failed");
+}
+
+fl_status fl_net_load(fl_net* n, const char* path) {
+  if (!n || !path) return net_fail(FL_INVALID_ARG, "NULL argument");
+  FILE* f = fopen(path, "rb");
+  if (!f) return net_fail(FL_INVALID_ARG, std::string("cannot open ") + path);
+  uint32_t hdr[4];
+  uint64_t sum = 0;
+  std::vector<float> host(n->nparams);
+  bool ok = fread(hdr, sizeof(hdr), 1, f) == 1 && fread(&sum, sizeof(sum), 1, f) == 1;
+  ok = ok && hdr[0] == kMagic && hdr[1] == 1u && hdr[2] == (uint32_t)n->nparams;
+  ok = ok && fread(host.data(), sizeof(float), host.size(), f) == host.size();
+  fclose(f);
+  if (!ok) return net_fail(FL_INVALID_ARG, "not a network file of this architecture");
+  if (fnv1a(host.data(), host.size() * sizeof(float)) != sum)
+    return net_fail(FL_INVALID_ARG, "network file checksum mismatch");
+  fl_status s = fl_net_set_params(n, host.data());
+  if (s == FL_OK) n->step = (int)hdr[3];
+  return s;
+}
+
+}  // extern "C"

@@ -1,0 +1,55 @@
+// The network object of the learned preconditioner (learned.cu).
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "unet.h"
+
+// Sets the thread's fl_last_error_string() text (defined in plan.cu).
+void fl_set_error_string(const char* msg);
+
+namespace fl {
+
+constexpr int kNetLayers = 11;
+constexpr int kNetTensors = 12;  // input, ten hidden activations, output
+constexpr int kNetInputs = 3;    // r / s_r, z0 / s_z, alpha
+constexpr int kLossBlocks = 256;
+
+struct NetState {
+  int H = 0, W = 0;
+  int c[3] = {16, 32, 64};
+  cudaStream_t stream = nullptr;
+  long long nparams = 0;
+  long long woff[kNetLayers] = {}, boff[kNetLayers] = {};
+  int cin_[kNetLayers] = {}, cout_[kNetLayers] = {};
+  float* w = nullptr;          // FP32 master parameters (weights and biases, flat)
+  __nv_bfloat16* wb = nullptr; // BF16 copy read by the convolutions
+  float* g = nullptr;          // gradients
+  float* m = nullptr;          // Adam moments
+  float* v = nullptr;
+  float* act[kNetTensors] = {};
+  float* grad[kNetTensors] = {};
+  float* gz = nullptr;
+  float* gx = nullptr;
+  float* part = nullptr;
+  float* bpart = nullptr;
+  double* lpart = nullptr;
+  int step = 0;
+  std::vector<void*> allocs;
+
+  int channels(int t) const;
+  int level(int t) const;
+  cudaError_t init(int h, int w, uint64_t seed, cudaStream_t s);
+  ConvArgs conv_args(int l, bool input_grad) const;
+  cudaError_t forward(const float* x, float* y);
+  cudaError_t backward();
+  cudaError_t loss_grad(const float* xs, const float* ts, int batch, double* loss);
+  cudaError_t train_step(const float* xs, const float* ts, int batch, float lr, double* loss);
+  ~NetState();
+};
+
+}  // namespace fl

@@ -345,6 +345,8 @@ fl_status true_residual(fl_plan* p, const double* u, double shift, double scale,
 }
 
 // Solve (shift I + scale M) u = b, b already in v64.b; u in/out (device).
+bool trace_enabled();
+
 fl_status solve_system(fl_plan* p, double* u, bool x0_nonzero, double shift, double scale,
                        double tol, int maxit, int mode, fl_solve_info* info) {
   const Geo& g = p->g;
@@ -411,6 +413,9 @@ fl_status solve_system(fl_plan* p, double* u, bool x0_nonzero, double shift, dou
         int its = 0;
         fl_status in = run_pcg<float>(p, false, shift, scale, use_prec, eta, maxit, &its);
         total += its;
+        if (trace_enabled())
+          fprintf(stderr, "fraclap: refinement %d: rel %.3e -> inner eta %.2e, %d its, status %d\n",
+                  outer, loc.rel_residual, eta, its, (int)in);
         if (in != FL_OK && in != FL_NOT_CONVERGED) { result = in; break; }
       }
       loc.iterations = total;
@@ -433,6 +438,15 @@ fl_status solve_system(fl_plan* p, double* u, bool x0_nonzero, double shift, dou
 }
 
 bool check_plan(const fl_plan* p) { return p != nullptr; }
+
+// FRACLAP_TRACE=1 in the environment prints one line per refinement step.
+bool trace_enabled() {
+  static const bool on = [] {
+    const char* v = getenv("FRACLAP_TRACE");
+    return v && v[0] == '1';
+  }();
+  return on;
+}
 
 }  // namespace
 
@@ -470,6 +484,12 @@ ProfScope::ProfScope(fl_plan* p) : saved(t_prof) { t_prof = p ? p->prof : nullpt
 extern "C" {
 
 const char* fl_last_error_string(void) { return g_err.c_str(); }
+
+}  // extern "C"
+
+void fl_set_error_string(const char* msg) { g_err = msg ? msg : ""; }
+
+extern "C" {
 
 fl_status fl_plan_create(int d, const int64_t* n, double h, double alpha, const uint8_t* mask,
                          const fl_opts* opts, fl_plan** out) {

@@ -1,0 +1,297 @@
+// U-Net of the learned preconditioner: forward, backward and Adam kernels.
+//
+// The network (3-level U-Net, channels 16/32/64, 3 x 3 convolutions with
+// zero padding and bias, ReLU, 2 x 2 average pooling, 2 x 2 nearest
+// upsampling, skip concatenation, 1 x 1 head) maps the features
+// [r / s_r, z0 / s_z, alpha] of a residual r to a correction of the base
+// preconditioner z0 = B r.  Weights are kept as an FP32 master copy for
+// Adam and a BF16 copy that the convolutions read; products are
+// accumulated in FP32.  Activations are FP32, layout [channel][y][x].
+//
+// Pooling, upsampling and concatenation are not materialised: a
+// convolution reads its input through up to two sources, each either
+// direct, a 2 x 2 average of a twice finer tensor, or the nearest value of a
+// twice coarser one.  The backward pass reuses the forward kernel with the
+// weights read transposed and flipped (input gradient), a tiled weight
+// gradient with per-tile partials reduced in a fixed order (deterministic),
+// and a scatter that routes the input gradient back through the sources.
+#include <cuda_bf16.h>
+
+#include "chain.cuh"
+#include "unet.h"
+
+namespace fl {
+
+namespace {
+
+constexpr int TILE = 16;   // output pixels per CTA side
+constexpr int CO = 16;     // output channels per CTA
+constexpr int CI = 8;      // input channels per shared-memory chunk
+
+// Value of input channel c (of the virtual concatenated input) at (y, x)
+// of the output resolution H x W; zero outside the image.
+__device__ __forceinline__ float src_value(const ConvArgs& a, int c, int y, int x) {
+  if (y < 0 || y >= a.H || x < 0 || x >= a.W) return 0.f;
+  const ConvSrc& s = (c < a.src[0].nc) ? a.src[0] : a.src[1];
+  const int cc = (c < a.src[0].nc) ? c : c - a.src[0].nc;
+  if (s.mode == SRC_DIRECT) return s.p[((size_t)cc * a.H + y) * a.W + x];
+  if (s.mode == SRC_POOL) {
+    const int W2 = 2 * a.W;
+    const float* q = s.p + ((size_t)cc * 2 * a.H + 2 * y) * W2 + 2 * x;
+    return 0.25f * (q[0] + q[1] + q[W2] + q[W2 + 1]);
+  }
+  // SRC_UP: twice coarser source
+  return s.p[((size_t)cc * (a.H / 2) + (y >> 1)) * (a.W / 2) + (x >> 1)];
+}
+
+// Weight (output channel o, input channel i, tap t) of the layer as this
+// launch reads it: w[o][i][t], or for the input-gradient pass of a layer
+// w_f[cout_f][cin_f][k][k], w[i][o][k*k-1-t] (transposed and flipped).
+__device__ __forceinline__ float weight(const ConvArgs& a, int o, int i, int t) {
+  const int kk = a.k * a.k;
+  if (!a.transposed) return __bfloat162float(a.w[((size_t)o * a.cin + i) * kk + t]);
+  return __bfloat162float(a.w[((size_t)i * a.cout + o) * kk + (kk - 1 - t)]);
+}
+
+template <int K>
+__global__ void __launch_bounds__(TILE * TILE) k_conv(ConvArgs a) {
+  constexpr int R = K / 2;
+  constexpr int S = TILE + 2 * R;
+  __shared__ float tile[CI][S][S];
+  __shared__ float ws[CO][CI][K * K];
+  const int tx = threadIdx.x % TILE, ty = threadIdx.x / TILE;
+  const int x0 = blockIdx.x * TILE, y0 = blockIdx.y * TILE;
+  const int co0 = blockIdx.z * CO;
+  float acc[CO];
+#pragma unroll
+  for (int o = 0; o < CO; ++o) acc[o] = 0.f;
+  for (int c0 = 0; c0 < a.cin; c0 += CI) {
+    for (int e = threadIdx.x; e < CI * S * S; e += TILE * TILE) {
+      const int c = e / (S * S), rem = e - c * S * S;
+      const int yy = rem / S, xx = rem - yy * S;
+      tile[c][yy][xx] = (c0 + c < a.cin) ? src_value(a, c0 + c, y0 + yy - R, x0 + xx - R) : 0.f;
+    }
+    for (int e = threadIdx.x; e < CO * CI * K * K; e += TILE * TILE) {
+      const int o = e / (CI * K * K), rem = e - o * CI * K * K;
+      const int i = rem / (K * K), t = rem - i * K * K;
+      ws[o][i][t] = (co0 + o < a.cout && c0 + i < a.cin) ? weight(a, co0 + o, c0 + i, t) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < CI; ++i) {
+#pragma unroll
+      for (int t = 0; t < K * K; ++t) {
+        const float v = tile[i][ty + t / K][tx + t % K];
+#pragma unroll
+        for (int o = 0; o < CO; ++o) acc[o] = fmaf(v, ws[o][i][t], acc[o]);
+      }
+    }
+    __syncthreads();
+  }
+  const int y = y0 + ty, x = x0 + tx;
+#pragma unroll
+  for (int o = 0; o < CO; ++o) {
+    const int co = co0 + o;
+    if (co < a.cout) {
+      float z = acc[o] + (a.bias ? a.bias[co] : 0.f);
+      if (a.relu) z = fmaxf(z, 0.f);
+      a.out[((size_t)co * a.H + y) * a.W + x] = z;
+    }
+  }
+}
+
+// Weight and bias gradient partials of one 16 x 16 tile for 16 output and 8
+// input channels: part[tile][co][ci][t] = sum_p gz[co][p] in[ci][p + t],
+// bpart[tile][co] = sum_p gz[co][p] (written by the ci-chunk-0 CTAs).
+template <int K>
+__global__ void __launch_bounds__(TILE * TILE) k_conv_wgrad(ConvArgs a, const float* __restrict__ gz,
+                                                           float* __restrict__ part,
+                                                           float* __restrict__ bpart) {
+  constexpr int R = K / 2;
+  constexpr int S = TILE + 2 * R;
+  __shared__ float tile[CI][S][S];
+  __shared__ float g[CO][TILE * TILE];
+  const int ntx = a.W / TILE;
+  const int tile_id = blockIdx.y * ntx + blockIdx.x;
+  const int x0 = blockIdx.x * TILE, y0 = blockIdx.y * TILE;
+  const int nci = (a.cin + CI - 1) / CI;
+  const int co0 = (blockIdx.z / nci) * CO;
+  const int c0 = (blockIdx.z % nci) * CI;
+  for (int e = threadIdx.x; e < CI * S * S; e += TILE * TILE) {
+    const int c = e / (S * S), rem = e - c * S * S;
+    const int yy = rem / S, xx = rem - yy * S;
+    tile[c][yy][xx] = (c0 + c < a.cin) ? src_value(a, c0 + c, y0 + yy - R, x0 + xx - R) : 0.f;
+  }
+  for (int e = threadIdx.x; e < CO * TILE * TILE; e += TILE * TILE) {
+    const int o = e / (TILE * TILE), p = e - o * TILE * TILE;
+    const int yy = p / TILE, xx = p - yy * TILE;
+    g[o][p] = (co0 + o < a.cout) ? gz[((size_t)(co0 + o) * a.H + y0 + yy) * a.W + x0 + xx] : 0.f;
+  }
+  __syncthreads();
+  const size_t wsz = (size_t)a.cout * a.cin * K * K;
+  for (int e = threadIdx.x; e < CO * CI * K * K; e += TILE * TILE) {
+    const int o = e / (CI * K * K), rem = e - o * CI * K * K;
+    const int i = rem / (K * K), t = rem - i * K * K;
+    const int dy = t / K, dx = t % K;
+    float s = 0.f;
+    for (int p = 0; p < TILE * TILE; ++p) {
+      const int yy = p / TILE, xx = p - yy * TILE;
+      s = fmaf(g[o][p], tile[i][yy + dy][xx + dx], s);
+    }
+    if (co0 + o < a.cout && c0 + i < a.cin)
+      part[(size_t)tile_id * wsz + ((size_t)(co0 + o) * a.cin + c0 + i) * K * K + t] = s;
+  }
+  if (c0 == 0) {
+    for (int o = threadIdx.x; o < CO; o += TILE * TILE) {
+      float s = 0.f;
+      for (int p = 0; p < TILE * TILE; ++p) s += g[o][p];
+      if (co0 + o < a.cout) bpart[(size_t)tile_id * a.cout + co0 + o] = s;
+    }
+  }
+}
+
+// out[i] (+)= sum over tiles of part[tile][i] (fixed order).
+__global__ void k_reduce_tiles(const float* __restrict__ part, int ntiles, long long n,
+                               float* __restrict__ out, int accumulate) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float s = 0.f;
+  for (int t = 0; t < ntiles; ++t) s += part[(size_t)t * n + i];
+  out[i] = accumulate ? out[i] + s : s;
+}
+
+// gz = g where the layer's ReLU output is positive, else 0.
+__global__ void k_relu_mask(const float* __restrict__ g, const float* __restrict__ act,
+                            float* __restrict__ gz, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) gz[i] = act[i] > 0.f ? g[i] : 0.f;
+}
+
+// Route the input gradient gx[cin][H][W] of a convolution to its sources
+// (accumulating): direct +=, pooled source (2H x 2W) gets 0.25 gx in each
+// of its 2 x 2 cells, upsampled source (H/2 x W/2) the sum of a 2 x 2 block.
+__global__ void k_scatter(const float* __restrict__ gx, int c_off, int nc, int mode, int H, int W,
+                          float* __restrict__ gsrc) {
+  const long long n = (long long)nc * (mode == SRC_POOL ? 4 * H * W : (mode == SRC_UP ? H * W / 4 : H * W));
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (mode == SRC_DIRECT) {
+    gsrc[i] += gx[(size_t)c_off * H * W + i];
+  } else if (mode == SRC_POOL) {
+    const int W2 = 2 * W;
+    const long long c = i / (4LL * H * W), rem = i - c * 4LL * H * W;
+    const int y = (int)(rem / W2), x = (int)(rem % W2);
+    gsrc[i] += 0.25f * gx[((size_t)(c_off + c) * H + y / 2) * W + x / 2];
+  } else {
+    const int Wh = W / 2, Hh = H / 2;
+    const long long c = i / ((long long)Hh * Wh), rem = i - c * Hh * Wh;
+    const int y = (int)(rem / Wh), x = (int)(rem % Wh);
+    const float* q = gx + ((size_t)(c_off + c) * H + 2 * y) * W + 2 * x;
+    gsrc[i] += q[0] + q[1] + q[W] + q[W + 1];
+  }
+}
+
+// MSE loss: gy = 2 (y - t) / (npix * batch), per-CTA partials of (y - t)^2.
+__global__ void k_mse(const float* __restrict__ y, const float* __restrict__ t, float* __restrict__ gy,
+                      long long n, float scale, double* __restrict__ part) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float r = y[i] - t[i];
+    gy[i] = 2.f * r * scale;
+    s += (double)r * r;
+  }
+  const double v = cta_sum(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = v;
+}
+
+// Adam (Kingma & Ba) on the FP32 master weights; refreshes the BF16 copy.
+__global__ void k_adam(float* __restrict__ w, __nv_bfloat16* __restrict__ wb, const float* __restrict__ g,
+                       float* __restrict__ m, float* __restrict__ v, long long n, float lr, float b1,
+                       float b2, float eps, float c1, float c2) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  w[i] = wi;
+  if (wb) wb[i] = __float2bfloat16(wi);
+}
+
+__global__ void k_to_bf16(const float* __restrict__ w, __nv_bfloat16* __restrict__ wb, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) wb[i] = __float2bfloat16(w[i]);
+}
+
+}  // namespace
+
+cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s) {
+  dim3 grid(a.W / TILE, a.H / TILE, (a.cout + CO - 1) / CO);
+  if (a.k == 3)
+    FL_KERNEL("unet_conv3", s, k_conv<3><<<grid, TILE * TILE, 0, s>>>(a));
+  else
+    FL_KERNEL("unet_conv1", s, k_conv<1><<<grid, TILE * TILE, 0, s>>>(a));
+  return cudaGetLastError();
+}
+
+size_t conv_wgrad_partials(const ConvArgs& a) {
+  return (size_t)(a.W / TILE) * (a.H / TILE) * a.cout * a.cin * a.k * a.k;
+}
+
+cudaError_t launch_conv_wgrad(const ConvArgs& a, const float* gz, float* part, float* bpart,
+                              float* dw, float* db, int accumulate, cudaStream_t s) {
+  const int nci = (a.cin + CI - 1) / CI, nco = (a.cout + CO - 1) / CO;
+  dim3 grid(a.W / TILE, a.H / TILE, nci * nco);
+  if (a.k == 3)
+    FL_KERNEL("unet_wgrad3", s, k_conv_wgrad<3><<<grid, TILE * TILE, 0, s>>>(a, gz, part, bpart));
+  else
+    FL_KERNEL("unet_wgrad1", s, k_conv_wgrad<1><<<grid, TILE * TILE, 0, s>>>(a, gz, part, bpart));
+  const int ntiles = (a.W / TILE) * (a.H / TILE);
+  const long long nw = (long long)a.cout * a.cin * a.k * a.k;
+  FL_KERNEL("unet_reduce", s,
+            k_reduce_tiles<<<(unsigned)((nw + 255) / 256), 256, 0, s>>>(part, ntiles, nw, dw, accumulate));
+  FL_KERNEL("unet_reduce", s,
+            k_reduce_tiles<<<(unsigned)((a.cout + 255) / 256), 256, 0, s>>>(bpart, ntiles, a.cout, db,
+                                                                            accumulate));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_relu_mask(const float* g, const float* act, float* gz, long long n, cudaStream_t s) {
+  FL_KERNEL("unet_mask", s, k_relu_mask<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, act, gz, n));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const float* gx, int c_off, int nc, int mode, int H, int W, float* gsrc,
+                           cudaStream_t s) {
+  const long long n = (long long)nc * (mode == SRC_POOL ? 4LL * H * W : (mode == SRC_UP ? (long long)H * W / 4 : (long long)H * W));
+  FL_KERNEL("unet_scatter", s,
+            k_scatter<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(gx, c_off, nc, mode, H, W, gsrc));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mse(const float* y, const float* t, float* gy, long long n, float scale,
+                       double* part, int nblocks, cudaStream_t s) {
+  FL_KERNEL("unet_mse", s, k_mse<<<nblocks, 256, 0, s>>>(y, t, gy, n, scale, part));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* w, __nv_bfloat16* wb, const float* g, float* m, float* v, long long n,
+                        float lr, int step, cudaStream_t s) {
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+  FL_KERNEL("unet_adam", s,
+            k_adam<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w, wb, g, m, v, n, lr, b1, b2, 1e-8f,
+                                                                c1, c2));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_bf16(const float* w, __nv_bfloat16* wb, long long n, cudaStream_t s) {
+  FL_KERNEL("unet_to_bf16", s, k_to_bf16<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w, wb, n));
+  return cudaGetLastError();
+}
+
+}  // namespace fl

@@ -1,0 +1,110 @@
+"""The U-Net kernels (forward, backward, Adam, checkpoints) against the NumPy
+reference network of the oracle."""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import unet  # noqa: E402
+from paper_1802_03770_gb300 import _lib  # noqa: E402
+from paper_1802_03770_gb300.api import Net  # noqa: E402
+
+
+def bf16_round(a):
+    """Round float32 values to bfloat16 (nearest, ties to even), as float32."""
+    u = np.ascontiguousarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def flatten(params):
+    out = []
+    for name in unet.LAYERS:
+        w, b = params[name]
+        out += [np.ravel(w), np.ravel(b)]
+    return np.concatenate(out).astype(np.float32)
+
+
+def unflatten(flat, dtype=np.float64):
+    shapes = unet.layer_shapes()
+    params, i = {}, 0
+    for name in unet.LAYERS:
+        co, ci, k = shapes[name]
+        nw = co * ci * k * k
+        params[name] = (flat[i:i + nw].reshape(co, ci, k, k).astype(dtype),
+                        flat[i + nw:i + nw + co].astype(dtype))
+        i += nw + co
+    return params
+
+
+def setup_net(H=64, seed=1):
+    net = Net(H, H, seed=0)
+    p = unet.init_params(seed, dtype=np.float64)
+    rng = np.random.default_rng(seed + 1)
+    p = {k: (w, rng.standard_normal(b.shape) * 0.05) for k, (w, b) in p.items()}
+    flat = flatten(p)
+    # weights as the kernels see them (BF16), biases FP32
+    shapes = unet.layer_shapes()
+    i = 0
+    for name in unet.LAYERS:
+        co, ci, k = shapes[name]
+        nw = co * ci * k * k
+        flat[i:i + nw] = bf16_round(flat[i:i + nw])
+        i += nw + co
+    net.set_params(flat)
+    return net, unflatten(flat)
+
+
+def test_forward_matches_oracle():
+    net, params = setup_net()
+    x = np.random.default_rng(3).standard_normal((3, 64, 64)).astype(np.float32)
+    y = net.forward(torch.tensor(x, device="cuda:0").view(-1)).cpu().numpy()
+    ref = unet.forward(params, x.astype(np.float64))[0]
+    assert np.linalg.norm(y - ref.ravel()) <= 2e-5 * np.linalg.norm(ref)
+
+
+def test_loss_and_gradients_match_oracle():
+    net, params = setup_net(seed=5)
+    rng = np.random.default_rng(6)
+    xs = rng.standard_normal((2, 3, 64, 64)).astype(np.float32)
+    ts = rng.standard_normal((2, 1, 64, 64)).astype(np.float32)
+    loss = net.loss_grad(torch.tensor(xs, device="cuda:0"), torch.tensor(ts, device="cuda:0"))
+    ref_loss, ref_grads = unet.loss_and_grads(params, xs.astype(np.float64), ts.astype(np.float64))
+    assert loss == pytest.approx(ref_loss, rel=1e-5)
+    _, g = net.get_params(grads=True)
+    gref = flatten(ref_grads)
+    shapes = unet.layer_shapes()
+    i = 0
+    for name in unet.LAYERS:
+        co, ci, k = shapes[name]
+        n = co * ci * k * k + co
+        a, b = g[i:i + n], gref[i:i + n]
+        assert np.linalg.norm(a - b) <= 1e-4 * np.linalg.norm(b) + 1e-12, name
+        i += n
+
+
+def test_adam_training_reduces_loss():
+    net, _ = setup_net(seed=7)
+    rng = np.random.default_rng(8)
+    xs = torch.tensor(rng.standard_normal((2, 3, 64, 64)), dtype=torch.float32, device="cuda:0")
+    ts = torch.tensor(rng.standard_normal((2, 1, 64, 64)) * 0.1, dtype=torch.float32, device="cuda:0")
+    first = net.train_step(xs, ts, lr=1e-3)
+    for _ in range(30):
+        last = net.train_step(xs, ts, lr=1e-3)
+    assert last < 0.5 * first
+
+
+def test_checkpoint_roundtrip(tmp_path):
+    net, _ = setup_net(seed=9)
+    path = tmp_path / "net.bin"
+    net.save(path)
+    other = Net(64, 64, seed=123)
+    other.load(path)
+    assert np.array_equal(other.get_params(), net.get_params())
+    raw = bytearray(path.read_bytes())
+    raw[-1] ^= 0xFF
+    path.write_bytes(bytes(raw))
+    with pytest.raises(_lib.FracLapError, match="checksum"):
+        other.load(path)
