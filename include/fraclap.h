@@ -53,6 +53,8 @@ typedef enum {
 enum {
   FL_MODE_F64 = 0,        /* plain FP64 CG                                 */
   FL_MODE_MIXED = 1,      /* FP32 inner CG inside FP64 iterative refinement */
+  FL_MODE_LEARNED = 2,    /* as MIXED, inner flexible CG with the learned
+                             preconditioner of the attached network        */
   FL_PRECOND_FD = 0x00,   /* FD-Laplacian preconditioner (Sec. 3.1, 3.2)   */
   FL_PRECOND_NONE = 0x10, /* plain CG                                      */
   FL_PRECOND_AUTO = 0x20  /* FD preconditioner for alpha >= 1, none below
@@ -91,7 +93,7 @@ typedef struct {
 
 /* Create a plan for the operator of eq. linearelliptic (Sec. 3.1).
  *   d      : 2 or 3
- *   n      : host array of d extents n_i >= 1 (n_i <= 2048)
+ *   n      : host array of d extents n_i >= 1 (n_i <= 1024: padded FFT lengths up to 2048)
  *   h      : grid spacing > 0 (the unit box has h = 1/(n+1))
  *   alpha  : order, 0 < alpha < 2
  *   mask   : nullable host array of N bytes, nonzero = point of Omega
@@ -248,6 +250,12 @@ fl_status fl_net_train_step(fl_net* net, const float* xs_dev, const float* ts_de
  * FNV-1a checksum, FP32 parameters. */
 fl_status fl_net_save(fl_net* net, const char* path);
 fl_status fl_net_load(fl_net* net, const char* path);
+
+/* Attach (net != NULL) or detach a network for FL_MODE_LEARNED solves on a
+ * 2D plan without mask; the network's H x W must equal n_0 x n_1.  Allocates
+ * the plan's feature buffers on first attach.  The plan does not own the
+ * network. */
+fl_status fl_plan_attach_net(fl_plan* plan, fl_net* net);
 
 /* Wait for all work on the plan's stream. */
 fl_status fl_sync(fl_plan* plan);

@@ -23,6 +23,7 @@ STATUS_NAMES = {0: "FL_OK", 1: "FL_INVALID_ARG", 2: "FL_NOT_CONVERGED", 3: "FL_B
 
 FL_MODE_F64 = 0
 FL_MODE_MIXED = 1
+FL_MODE_LEARNED = 2
 FL_PRECOND_FD = 0x00
 FL_PRECOND_NONE = 0x10
 FL_PRECOND_AUTO = 0x20
@@ -90,6 +91,7 @@ SIGNATURES = {
     "fl_net_train_step": (_I, [_P, _P, _P, _I, ctypes.c_float, ctypes.POINTER(_D)]),
     "fl_net_save": (_I, [_P, ctypes.c_char_p]),
     "fl_net_load": (_I, [_P, ctypes.c_char_p]),
+    "fl_plan_attach_net": (_I, [_P, _P]),
     "fl_last_error_string": (ctypes.c_char_p, []),
 }
 

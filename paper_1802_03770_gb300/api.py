@@ -240,6 +240,12 @@ class Plan:
         L.check(st, "fl_time_step")
         return u_next, info.as_dict()
 
+    def attach_net(self, net):
+        """Use `net` (api.Net, or None to detach) for FL_MODE_LEARNED solves."""
+        L.check(self._lib.fl_plan_attach_net(self._h, net._h if net is not None else None),
+                "fl_plan_attach_net")
+        self._net = net
+
     def profile(self, enable=True):
         L.check(self._lib.fl_profile_enable(self._h, int(enable)), "fl_profile_enable")
 

@@ -264,6 +264,9 @@ cudaError_t configure_batched_kernels() {
   auto set = [&](const void* f) {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               cudaSharedmemCarveoutMaxShared);
   };
   set(reinterpret_cast<const void*>(&kb_rows_fwd<float, Cfg<float>::RT, Cfg<float>::RV>));
   set(reinterpret_cast<const void*>(&kb_rows_fwd<double, Cfg<double>::RT, Cfg<double>::RV>));

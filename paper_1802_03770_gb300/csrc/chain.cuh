@@ -16,12 +16,12 @@ namespace fl {
 // least 32 contiguous bytes per line element.
 template <typename T> struct Cfg;
 template <> struct Cfg<float> {
-  static constexpr int RT = 256, RV = 8;    // rows: threads, values per thread
+  static constexpr int RT = 128, RV = 16;   // rows: threads, values per thread
   static constexpr int CT = 512, CV = 16;   // strided passes
 };
 template <> struct Cfg<double> {
   static constexpr int RT = 256, RV = 16;
-  static constexpr int CT = 512, CV = 8;
+  static constexpr int CT = 256, CV = 16;
 };
 
 constexpr int kVecBlocks = 608;   // 4 x 152 SMs, fixed for deterministic partials

@@ -1,14 +1,13 @@
 // Shared-memory FFT building blocks for sm_103a.
 //
-// A CTA transforms a batch of complex lines that live in shared memory.
-// Each line has power-of-two length L and the lines are spaced `ls`
-// complex elements apart.  The transform is a Stockham autosort FFT: stage s
-// with radix R reads butterfly j's legs at j + r L/R, multiplies leg r by the
-// twiddle w^(r k), k = j mod Ns, with w = exp(-+ 2 pi i / (Ns R)), does a
+// A CTA transforms a batch of complex lines that live in shared memory, each
+// of power-of-two length L.  The transform is a Stockham autosort FFT: stage
+// s with radix R reads butterfly j's legs at j + r L/R, multiplies leg r by
+// the twiddle w^(r k), k = j mod Ns, with w = exp(-+ 2 pi i / (Ns R)), does a
 // radix-R DFT in registers and writes leg r to (j / Ns) Ns R + k + r Ns
 // (Govindaraju et al., SC'08).  After the last stage the line is in natural
-// order.  Stages are radix 8 with one radix-4 or radix-2 stage when log2 L
-// is not a multiple of 3.
+// order.  Stages are radix 16 (when a thread may hold 16 values), then radix
+// 8, with one radix-4 or radix-2 stage for the remainder of log2 L.
 //
 // Every stage is in place: each thread loads all legs of the butterflies it
 // owns into registers, the CTA synchronises, then every thread writes.  The
@@ -16,7 +15,12 @@
 // compile-time bound chosen by the launcher.
 //
 // Twiddles come from a table tw[k] = exp(-2 pi i k / Lmax) computed on the
-// host in long double; a line of length L uses stride Lmax / L.
+// host in long double; a stage loads w, w^2, w^4 (and w^8) from it and forms
+// the other powers by complex products.
+//
+// Two storage layouts: lines of stride ls (element j of line q at
+// q * ls + j), and 2^ltx interleaved lines (element j of line c at
+// j * 2^ltx + c, the natural layout of a tile of consecutive columns).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -42,6 +46,11 @@ template <typename C, typename T> __device__ __forceinline__ C cscale(C a, T s) 
 template <typename C> __device__ __forceinline__ C mul_mi(C a, bool inv) {
   return inv ? cmake<C>(-a.y, a.x) : cmake<C>(a.y, -a.x);
 }
+// multiply by exp(-+ i theta) given (cos theta, sin theta)
+template <typename C, typename T> __device__ __forceinline__ C mul_rot(C a, T c, T s, bool inv) {
+  const T sg = inv ? s : -s;
+  return cmake<C>(a.x * c - a.y * sg, a.x * sg + a.y * c);
+}
 
 template <typename C> __device__ __forceinline__ void dft2(C* v) {
   C a = v[0], b = v[1];
@@ -66,11 +75,9 @@ template <typename C> __device__ __forceinline__ void dft8(C* v, bool inv) {
   dft4(e, inv);
   dft4(o, inv);
   // o[k] *= w8^k, w8 = (1 -+ i)/sqrt(2)
-  o[1] = inv ? cmake<C>((o[1].x - o[1].y) * s, (o[1].x + o[1].y) * s)
-             : cmake<C>((o[1].x + o[1].y) * s, (o[1].y - o[1].x) * s);
+  o[1] = mul_rot(o[1], s, s, inv);
   o[2] = mul_mi(o[2], inv);
-  o[3] = inv ? cmake<C>((-o[3].x - o[3].y) * s, (o[3].x - o[3].y) * s)
-             : cmake<C>((o[3].y - o[3].x) * s, (-o[3].x - o[3].y) * s);
+  o[3] = mul_rot(o[3], -s, s, inv);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     v[k] = cadd(e[k], o[k]);
@@ -78,21 +85,89 @@ template <typename C> __device__ __forceinline__ void dft8(C* v, bool inv) {
   }
 }
 
+// 16-point DFT as 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2,
+// X[k] = sum_n2 w16^(n2 k1) w4^(n2 k2) sum_n1 x[4 n1 + n2] w4^(n1 k1).
+template <typename C> __device__ __forceinline__ void dft16(C* v, bool inv) {
+  typedef decltype(C().x) T;
+  const T c1 = (T)0.92387953251128675612818318939678828682;  // cos(pi/8)
+  const T s1 = (T)0.38268343236508977172845998403039886676;  // sin(pi/8)
+  const T h = (T)0.70710678118654752440084436210484903928;
+  C a[4][4];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    a[n2][0] = v[n2];
+    a[n2][1] = v[4 + n2];
+    a[n2][2] = v[8 + n2];
+    a[n2][3] = v[12 + n2];
+    dft4(a[n2], inv);
+  }
+  // twiddles w16^(n2 k1): (1,1)=1, (1,2)=2, (1,3)=3, (2,1)=2, (2,2)=4, (2,3)=6, (3,1)=3, (3,2)=6, (3,3)=9
+  a[1][1] = mul_rot(a[1][1], c1, s1, inv);
+  a[1][2] = mul_rot(a[1][2], h, h, inv);
+  a[1][3] = mul_rot(a[1][3], s1, c1, inv);
+  a[2][1] = mul_rot(a[2][1], h, h, inv);
+  a[2][2] = mul_mi(a[2][2], inv);
+  a[2][3] = mul_rot(a[2][3], -h, h, inv);
+  a[3][1] = mul_rot(a[3][1], s1, c1, inv);
+  a[3][2] = mul_rot(a[3][2], -h, h, inv);
+  a[3][3] = mul_rot(a[3][3], -c1, -s1, inv);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    C b[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+    dft4(b, inv);
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = b[k2];
+  }
+}
+
 template <int R, typename C> __device__ __forceinline__ void dftR(C* v, bool inv) {
   if (R == 2) dft2(v);
   else if (R == 4) dft4(v, inv);
-  else dft8(v, inv);
+  else if (R == 8) dft8(v, inv);
+  else dft16(v, inv);
 }
 
-// One Stockham stage of radix R over `nlines` lines of length L = 2^lg.
-// VPT: values per thread (upper bound, compile time).  Contains two
-// __syncthreads(); every thread of the CTA must call it.
+template <int R> struct LogR;
+template <> struct LogR<2> { static constexpr int v = 1; };
+template <> struct LogR<4> { static constexpr int v = 2; };
+template <> struct LogR<8> { static constexpr int v = 3; };
+template <> struct LogR<16> { static constexpr int v = 4; };
+
+// w[r] = w1^r, r = 0..R-1, for w1 = tw[step] (conjugated for the inverse):
+// w1, w2, w4, w8 come from the table, the rest are products.
+template <int R, typename C>
+__device__ __forceinline__ void twiddles(const C* __restrict__ tw, int step, bool inv, C* w) {
+  auto ld = [&](int i) {
+    C t = tw[i];
+    if (inv) t.y = -t.y;
+    return t;
+  };
+  w[0] = cmake<C>(1, 0);
+  if (R >= 2) w[1] = ld(step);
+  if (R >= 4) {
+    w[2] = ld(2 * step);
+    w[3] = cmul(w[1], w[2]);
+  }
+  if (R >= 8) {
+    w[4] = ld(4 * step);
+    w[5] = cmul(w[4], w[1]);
+    w[6] = cmul(w[4], w[2]);
+    w[7] = cmul(w[4], w[3]);
+  }
+  if (R >= 16) {
+    w[8] = ld(8 * step);
+#pragma unroll
+    for (int r = 9; r < 16; ++r) w[r] = cmul(w[8], w[r - 8]);
+  }
+}
+
+// One Stockham stage of radix R over `nlines` lines of length L = 2^lg
+// (line q at buf + q * ls).  Contains two __syncthreads().
 template <int R, int VPT, typename C>
 __device__ __forceinline__ void stockham_stage(C* buf, int lg, int ls, int nlines, int Ns,
                                                const C* __restrict__ tw, int lgmax, bool inv) {
   constexpr int NB = VPT / R;  // butterflies per thread
-  constexpr int LGR = R == 8 ? 3 : (R == 4 ? 2 : 1);
-  const int lglr = lg - LGR;
+  const int lglr = lg - LogR<R>::v;
   const int LR = 1 << lglr;
   const int total = nlines << lglr;
   C v[NB][R];
@@ -105,18 +180,15 @@ __device__ __forceinline__ void stockham_stage(C* buf, int lg, int ls, int nline
       const int line = g >> lglr;
       const int j = g & (LR - 1);
       const int k = j & (Ns - 1);
-      C* base = buf + (size_t)line * ls;
-      // twiddle index for leg r: r * k * (Lmax / (Ns * R))
-      const int step = k << (lgmax - __ffs(Ns * R) + 1);
+      const C* base = buf + (size_t)line * ls;
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        C x = base[j + r * LR];
-        if (r > 0 && k != 0) {
-          C w = tw[r * step];
-          if (inv) w.y = -w.y;
-          x = cmul(x, w);
-        }
-        v[b][r] = x;
+      for (int r = 0; r < R; ++r) v[b][r] = base[j + r * LR];
+      if (k != 0) {
+        // twiddle w^(r k) = tw[r * k * Lmax / (Ns R)]
+        C w[R];
+        twiddles<R>(tw, k << (lgmax - __ffs(Ns * R) + 1), inv, w);
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], w[r]);
       }
       dftR<R>(v[b], inv);
       dst[b] = line * ls + (j - k) * R + k;
@@ -133,16 +205,14 @@ __device__ __forceinline__ void stockham_stage(C* buf, int lg, int ls, int nline
   __syncthreads();
 }
 
-// The same stage for 2^ltx lines stored interleaved: element j of line c is
-// buf[j * tx + c] (the natural layout of a tile of tx consecutive columns).
-// Consecutive threads take consecutive lines, so the leg reads are
-// contiguous.
+// The same stage for 2^ltx interleaved lines (element j of line c at
+// j * 2^ltx + c).  Consecutive threads take consecutive lines, so the leg
+// reads are contiguous.
 template <int R, int VPT, typename C>
 __device__ __forceinline__ void stockham_stage_il(C* buf, int lg, int ltx, int Ns,
                                                   const C* __restrict__ tw, int lgmax, bool inv) {
   constexpr int NB = VPT / R;
-  const int L = 1 << lg;
-  const int LR = L / R;
+  const int LR = 1 << (lg - LogR<R>::v);
   const int tx = 1 << ltx;
   const int total = LR << ltx;
   C v[NB][R];
@@ -155,16 +225,13 @@ __device__ __forceinline__ void stockham_stage_il(C* buf, int lg, int ltx, int N
       const int c = g & (tx - 1);
       const int j = g >> ltx;
       const int k = j & (Ns - 1);
-      const int step = k << (lgmax - __ffs(Ns * R) + 1);
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        C x = buf[((j + r * LR) << ltx) + c];
-        if (r > 0 && k != 0) {
-          C w = tw[r * step];
-          if (inv) w.y = -w.y;
-          x = cmul(x, w);
-        }
-        v[b][r] = x;
+      for (int r = 0; r < R; ++r) v[b][r] = buf[((j + r * LR) << ltx) + c];
+      if (k != 0) {
+        C w[R];
+        twiddles<R>(tw, k << (lgmax - __ffs(Ns * R) + 1), inv, w);
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], w[r]);
       }
       dftR<R>(v[b], inv);
       dst[b] = (((j - k) * R + k) << ltx) + c;
@@ -181,29 +248,20 @@ __device__ __forceinline__ void stockham_stage_il(C* buf, int lg, int ltx, int N
   __syncthreads();
 }
 
+// Stage plan: radix 16 while at least four factors of two remain (if VPT
+// allows), then radix 8, then one radix-4 or radix-2 stage.
 template <int VPT, typename C>
-__device__ __forceinline__ void fft_lines_il(C* buf, int lg, int ltx, const C* __restrict__ tw,
-                                             int lgmax, bool inv) {
+__device__ __forceinline__ void fft_lines(C* buf, int lg, int ls, int nlines, const C* __restrict__ tw,
+                                          int lgmax, bool inv) {
   int Ns = 1;
   int rem = lg;
-  while (rem >= 3) {
-    stockham_stage_il<8, VPT>(buf, lg, ltx, Ns, tw, lgmax, inv);
-    Ns <<= 3;
-    rem -= 3;
+  if (VPT >= 16) {
+    while (rem >= 4) {
+      stockham_stage<(VPT >= 16 ? 16 : 8), VPT>(buf, lg, ls, nlines, Ns, tw, lgmax, inv);
+      Ns <<= 4;
+      rem -= 4;
+    }
   }
-  if (rem == 2) stockham_stage_il<4, VPT>(buf, lg, ltx, Ns, tw, lgmax, inv);
-  else if (rem == 1) stockham_stage_il<2, VPT>(buf, lg, ltx, Ns, tw, lgmax, inv);
-}
-
-// Full FFT (unnormalised) of `nlines` lines of length 2^lg in shared memory.
-// Forward: X_k = sum_j x_j exp(-2 pi i jk / L); inverse uses +.
-// The caller must __syncthreads() before (data ready); on return the data is
-// visible to all threads.
-template <int VPT, typename C>
-__device__ __forceinline__ void fft_lines(C* buf, int lg, int ls, int nlines, const C* __restrict__ tw, int lgmax,
-                          bool inv) {
-  int Ns = 1;
-  int rem = lg;
   while (rem >= 3) {
     stockham_stage<8, VPT>(buf, lg, ls, nlines, Ns, tw, lgmax, inv);
     Ns <<= 3;
@@ -211,6 +269,27 @@ __device__ __forceinline__ void fft_lines(C* buf, int lg, int ls, int nlines, co
   }
   if (rem == 2) stockham_stage<4, VPT>(buf, lg, ls, nlines, Ns, tw, lgmax, inv);
   else if (rem == 1) stockham_stage<2, VPT>(buf, lg, ls, nlines, Ns, tw, lgmax, inv);
+}
+
+template <int VPT, typename C>
+__device__ __forceinline__ void fft_lines_il(C* buf, int lg, int ltx, const C* __restrict__ tw,
+                                             int lgmax, bool inv) {
+  int Ns = 1;
+  int rem = lg;
+  if (VPT >= 16) {
+    while (rem >= 4) {
+      stockham_stage_il<(VPT >= 16 ? 16 : 8), VPT>(buf, lg, ltx, Ns, tw, lgmax, inv);
+      Ns <<= 4;
+      rem -= 4;
+    }
+  }
+  while (rem >= 3) {
+    stockham_stage_il<8, VPT>(buf, lg, ltx, Ns, tw, lgmax, inv);
+    Ns <<= 3;
+    rem -= 3;
+  }
+  if (rem == 2) stockham_stage_il<4, VPT>(buf, lg, ltx, Ns, tw, lgmax, inv);
+  else if (rem == 1) stockham_stage_il<2, VPT>(buf, lg, ltx, Ns, tw, lgmax, inv);
 }
 
 }  // namespace fl

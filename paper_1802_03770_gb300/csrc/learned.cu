@@ -375,3 +375,137 @@ fl_status fl_net_load(fl_net* n, const char* path) {
 }
 
 }  // extern "C"
+
+// --- kernels of the learned flexible CG ------------------------------------------
+
+namespace fl {
+
+namespace {
+
+// Features of the network: x[0] = r / s_r, x[1] = z0 / s_z, x[2] = alpha,
+// with s = root mean square from the partial sums of squares.
+__global__ void __launch_bounds__(256) k_features(const float* __restrict__ r, const float* __restrict__ z0,
+                                                   const double* __restrict__ rr_part, int rr_count,
+                                                   const double* __restrict__ zz_part, int zz_count,
+                                                   float alpha, float* __restrict__ x, long long N,
+                                                   const PcgState* st) {
+  __shared__ double red[32];
+  if (st && st->done) return;
+  const double rr = cta_sum_partials(rr_part, rr_count, red);
+  const double zz = cta_sum_partials(zz_part, zz_count, red);
+  const float ir = rr > 0 ? (float)rsqrt(rr / (double)N) : 0.f;
+  const float iz = zz > 0 ? (float)rsqrt(zz / (double)N) : 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    x[i] = r[i] * ir;
+    x[N + i] = z0[i] * iz;
+    x[2 * N + i] = alpha;
+  }
+}
+
+// z_new = z0 + s_z y; partials of r . z_new and r . z_old (z_old = z before
+// the overwrite).
+__global__ void __launch_bounds__(256) k_combine(const float* __restrict__ r, const float* __restrict__ z0,
+                                                  const float* __restrict__ y, float* __restrict__ z,
+                                                  const double* __restrict__ zz_part, int zz_count,
+                                                  double* __restrict__ rz_part, double* __restrict__ rzo_part,
+                                                  long long N, const PcgState* st) {
+  __shared__ double red[32];
+  if (st && st->done) return;
+  const double zz = cta_sum_partials(zz_part, zz_count, red);
+  const float sz = (float)sqrt(zz / (double)N);
+  double a = 0.0, b = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float zo = z[i];
+    const float zn = z0[i] + sz * y[i];
+    z[i] = zn;
+    a += (double)r[i] * zn;
+    b += (double)r[i] * zo;
+  }
+  const double sa = cta_sum(a, red);
+  const double sb = cta_sum(b, red);
+  if (threadIdx.x == 0) {
+    rz_part[blockIdx.x] = sa;
+    if (rzo_part) rzo_part[blockIdx.x] = sb;
+  }
+}
+
+// dst = scale * src
+__global__ void k_scale(const float* __restrict__ src, float* __restrict__ dst, float scale, long long N,
+                        const PcgState* st) {
+  if (st && st->done) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = scale * src[i];
+}
+
+// Flexible CG scalars: beta = (r.z_new - r.z_old) / rz (Polak-Ribiere),
+// convergence on ||r||, breakdown when r.z_new <= 0 (then the caller falls
+// back to the fixed preconditioner).
+__global__ void k_fpcg_scalar(PcgState* st, const double* rr_part, int rr_count, const double* rz_part,
+                              const double* rzo_part, int rz_count) {
+  __shared__ double red[32];
+  if (st->done) return;
+  const double rr = cta_sum_partials(rr_part, rr_count, red);
+  const double rz = cta_sum_partials(rz_part, rz_count, red);
+  const double rzo = cta_sum_partials(rzo_part, rz_count, red);
+  if (threadIdx.x == 0) {
+    st->it += 1;
+    st->rr = rr;
+    if (!(st->pq > 0.0) || rr != rr || rz != rz) {
+      st->done = 1;
+      st->status = 3;
+    } else if (rr <= st->tol2) {
+      st->done = 1;
+      st->status = 0;
+    } else if (st->it >= st->maxit) {
+      st->done = 1;
+      st->status = 2;
+    } else if (!(rz > 0.0)) {
+      st->done = 1;
+      st->status = 4;   // learned direction not a descent direction: fall back
+    } else {
+      st->beta = (rz - rzo) / st->rz;
+      st->rz = rz;
+    }
+  }
+}
+
+constexpr int kFBlocks = 608;
+
+}  // namespace
+
+cudaError_t launch_features(const float* r, const float* z0, const double* rr_part, int rr_count,
+                            const double* zz_part, int zz_count, float alpha, float* x, long long N,
+                            const PcgState* st, cudaStream_t s) {
+  FL_KERNEL("features", s,
+            k_features<<<kFBlocks, 256, 0, s>>>(r, z0, rr_part, rr_count, zz_part, zz_count, alpha, x, N, st));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine(const float* r, const float* z0, const float* y, float* z, const double* zz_part,
+                           int zz_count, double* rz_part, double* rzo_part, long long N, const PcgState* st,
+                           int* count, cudaStream_t s) {
+  FL_KERNEL("combine", s,
+            k_combine<<<kFBlocks, 256, 0, s>>>(r, z0, y, z, zz_part, zz_count, rz_part, rzo_part, N, st));
+  *count = kFBlocks;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale(const float* src, float* dst, float scale, long long N, const PcgState* st,
+                         cudaStream_t s) {
+  FL_KERNEL("scale", s, k_scale<<<kFBlocks, 256, 0, s>>>(src, dst, scale, N, st));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fpcg_scalar(PcgState* st, const double* rr_part, int rr_count, const double* rz_part,
+                               const double* rzo_part, int rz_count, cudaStream_t s) {
+  FL_KERNEL("fpcg_scalar", s, k_fpcg_scalar<<<1, 256, 0, s>>>(st, rr_part, rr_count, rz_part, rzo_part,
+                                                               rz_count));
+  return cudaGetLastError();
+}
+
+}  // namespace fl
+
+fl::NetState* fl_net_state(fl_net* n) { return n; }

@@ -53,3 +53,20 @@ struct NetState {
 };
 
 }  // namespace fl
+
+namespace fl {
+struct PcgState;
+cudaError_t launch_features(const float* r, const float* z0, const double* rr_part, int rr_count,
+                            const double* zz_part, int zz_count, float alpha, float* x, long long N,
+                            const PcgState* st, cudaStream_t s);
+cudaError_t launch_combine(const float* r, const float* z0, const float* y, float* z, const double* zz_part,
+                           int zz_count, double* rz_part, double* rzo_part, long long N, const PcgState* st,
+                           int* count, cudaStream_t s);
+cudaError_t launch_scale(const float* src, float* dst, float scale, long long N, const PcgState* st,
+                         cudaStream_t s);
+cudaError_t launch_fpcg_scalar(PcgState* st, const double* rr_part, int rr_count, const double* rz_part,
+                               const double* rzo_part, int rz_count, cudaStream_t s);
+}  // namespace fl
+
+struct fl_net;
+fl::NetState* fl_net_state(fl_net* n);

@@ -220,8 +220,14 @@ __global__ void k_extract_symbol(const double2* buf, int d, int L0, int L1, int 
 
 // ---------------------------------------------------------------------------
 
+// Large dynamic shared memory and the whole L1/shared carveout as shared
+// memory, so that as many FFT tiles as fit are resident per SM.
 static cudaError_t set_smem(const void* f) {
-  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+  return e;
 }
 
 cudaError_t configure_kernels() {

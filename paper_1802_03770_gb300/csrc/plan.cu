@@ -13,6 +13,7 @@
 #include "../../include/fraclap.h"
 #include "internal.h"
 #include "chain.cuh"
+#include "learned.h"
 
 using namespace fl;
 
@@ -108,6 +109,11 @@ struct fl_plan {
   std::vector<void*> allocs;
   int64_t bytes = 0;
   struct Profiler* prof = nullptr;   // non-null while profiling is enabled
+  // learned preconditioner (fl_plan_attach_net)
+  fl::NetState* net = nullptr;
+  float* z0 = nullptr;     // base preconditioned residual
+  float* feat = nullptr;   // network input, 3 x N
+  double* lpart[3] = {nullptr, nullptr, nullptr};  // ||z0||^2, r.z, r.z_old partials
 };
 
 namespace {
@@ -347,6 +353,80 @@ fl_status true_residual(fl_plan* p, const double* u, double shift, double scale,
 // Solve (shift I + scale M) u = b, b already in v64.b; u in/out (device).
 bool trace_enabled();
 
+// Flexible CG in FP32 for (shift I + scale M) x = b (b = v32.b, x0 = 0)
+// with the learned preconditioner z = z0 + s_z N(r / s_r, z0 / s_z, alpha),
+// z0 = the base preconditioner applied to r (FD-Laplacian solve for
+// alpha >= 1, a diagonal scaling 1 / M_ii below).  beta is the
+// Polak-Ribiere (flexible) one.  Returns FL_BREAKDOWN with *fallback = 1
+// when r . z <= 0, so that the caller reruns the fixed preconditioner.
+fl_status run_fpcg_learned(fl_plan* p, double shift, double scale, double tol, int maxit, int* iters,
+                           int* fallback) {
+  const Geo& g = p->g;
+  Vecs<float>& v = p->v32;
+  cudaStream_t s = p->stream;
+  *fallback = 0;
+  const bool fd = p->alpha >= 1.0;
+  const float jac = (float)(1.0 / (shift + scale * p->c * (p->Z - 2.0 * g.d * p->a)));
+  int bb_count = 0, zz_count = 0, rz_count = 0, rr_count = 0;
+  const int pq_count = apply_partials<float>(g);
+  auto base = [&](const PcgState* st) -> cudaError_t {
+    cudaError_t e;
+    if (fd) {
+      PrecIO<float> io;
+      io.in = v.r; io.out = p->z0; io.shift = shift; io.scale = scale;
+      io.st = const_cast<PcgState*>(st);
+      e = launch_precond<float>(g, p->t32, p->mu, s, io);
+    } else {
+      e = launch_scale(v.r, p->z0, jac, g.N, st, s);
+    }
+    if (e == cudaSuccess) e = launch_dot<float>(g.N, s, p->z0, p->z0, p->lpart[0], &zz_count);
+    return e;
+  };
+  auto learned = [&](const double* rr_part, int rr_cnt, const PcgState* st, double* rzo) -> cudaError_t {
+    cudaError_t e = launch_features(v.r, p->z0, rr_part, rr_cnt, p->lpart[0], zz_count,
+                                    (float)p->alpha, p->feat, g.N, st, s);
+    if (e == cudaSuccess) e = p->net->forward(p->feat, nullptr);
+    if (e == cudaSuccess)
+      e = launch_combine(v.r, p->z0, p->net->act[kNetTensors - 1], v.z, p->lpart[0], zz_count,
+                         p->lpart[1], rzo, g.N, st, &rz_count, s);
+    return e;
+  };
+  FL_CUDA(cudaMemsetAsync(v.x, 0, g.N * sizeof(float), s));
+  FL_CUDA(cudaMemsetAsync(v.p, 0, g.N * sizeof(float), s));
+  FL_CUDA(cudaMemsetAsync(v.z, 0, g.N * sizeof(float), s));
+  FL_CUDA(launch_mask_copy_dot<float>(g.N, s, v.b, p->mask, v.r, p->part[P_BB], &bb_count));
+  FL_CUDA(base(nullptr));
+  FL_CUDA(learned(p->part[P_BB], bb_count, nullptr, nullptr));
+  FL_CUDA(launch_pcg_init(s, p->st, p->part[P_BB], bb_count, p->part[P_BB], bb_count, p->lpart[1],
+                          rz_count, tol, maxit));
+  for (;;) {
+    for (int k = 0; k < 2; ++k) {
+      ApplyIO<float> io;
+      io.pre = PRE_PUPDATE; io.u = v.z; io.p = v.p; io.mask = p->mask; io.st = p->st;
+      io.out = v.q; io.x = v.p; io.cm = scale; io.cx = shift;
+      io.dotw = v.p; io.partials = p->part[P_PQ];
+      FL_CUDA(launch_apply<float>(g, p->t32, s, io));
+      FL_CUDA(launch_noprec_update<float>(g.N, s, p->st, v.x, v.r, v.p, v.q, p->part[P_PQ], pq_count,
+                                          p->part[P_RR], &rr_count));
+      FL_CUDA(base(p->st));
+      FL_CUDA(learned(p->part[P_RR], rr_count, p->st, p->lpart[2]));
+      FL_CUDA(launch_fpcg_scalar(p->st, p->part[P_RR], rr_count, p->lpart[1], p->lpart[2], rz_count, s));
+    }
+    fl_status st = read_state(p);
+    if (st != FL_OK) return st;
+    if (p->st_host->done) break;
+  }
+  *iters = p->st_host->it;
+  switch (p->st_host->status) {
+    case 0: return FL_OK;
+    case 2: return fail(FL_NOT_CONVERGED, "flexible CG reached the iteration cap");
+    case 4: *fallback = 1; return fail(FL_BREAKDOWN, "learned preconditioner gave r.z <= 0");
+    // any other breakdown of the learned iteration (e.g. a non-finite network
+    // output) also hands the correction to the fixed preconditioner
+    default: *fallback = 1; return fail(FL_BREAKDOWN, "flexible CG breakdown");
+  }
+}
+
 fl_status solve_system(fl_plan* p, double* u, bool x0_nonzero, double shift, double scale,
                        double tol, int maxit, int mode, fl_solve_info* info) {
   const Geo& g = p->g;
@@ -359,6 +439,8 @@ fl_status solve_system(fl_plan* p, double* u, bool x0_nonzero, double shift, dou
   if (use_prec && p->has_mask)
     return fail(FL_INVALID_ARG, "the sine-transform preconditioner needs a plan without mask");
   if (!(tol > 0.0) || maxit < 1) return fail(FL_INVALID_ARG, "tol must be > 0 and maxit >= 1");
+  if (precision == FL_MODE_LEARNED && (!p->net || p->has_mask))
+    return fail(FL_INVALID_ARG, "FL_MODE_LEARNED needs a network attached to a plan without mask");
   fl_solve_info loc;
   memset(&loc, 0, sizeof(loc));
   fl_status result = FL_OK;
@@ -369,7 +451,7 @@ fl_status solve_system(fl_plan* p, double* u, bool x0_nonzero, double shift, dou
     if (result != FL_OK && result != FL_NOT_CONVERGED && result != FL_BREAKDOWN) return result;
     FL_CUDA(cudaMemcpyAsync(u, p->v64.x, g.N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     loc.iterations = its;
-  } else if (precision == FL_MODE_MIXED) {
+  } else if (precision == FL_MODE_MIXED || precision == FL_MODE_LEARNED) {
     // FP64 iterative refinement: r = b - A u (FP64), A d = r by FP32 CG to
     // inner_tol, u += d.
     int c = 0;
@@ -411,7 +493,18 @@ fl_status solve_system(fl_plan* p, double* u, bool x0_nonzero, double shift, dou
         const double need = tol / loc.rel_residual;
         const double eta = need >= 1e-6 ? std::min(p->inner_tol, 0.5 * need) : p->inner_tol;
         int its = 0;
-        fl_status in = run_pcg<float>(p, false, shift, scale, use_prec, eta, maxit, &its);
+        fl_status in;
+        if (precision == FL_MODE_LEARNED) {
+          int fallback = 0;
+          in = run_fpcg_learned(p, shift, scale, eta, maxit, &its, &fallback);
+          if (fallback) {   // plain preconditioned CG takes over this correction
+            int its2 = 0;
+            in = run_pcg<float>(p, false, shift, scale, use_prec, eta, maxit, &its2);
+            its += its2;
+          }
+        } else {
+          in = run_pcg<float>(p, false, shift, scale, use_prec, eta, maxit, &its);
+        }
         total += its;
         if (trace_enabled())
           fprintf(stderr, "fraclap: refinement %d: rel %.3e -> inner eta %.2e, %d its, status %d\n",
@@ -507,7 +600,7 @@ fl_status fl_plan_create(int d, const int64_t* n, double h, double alpha, const 
   g.lgmax = 0;
   for (int i = 0; i < 3; ++i) { g.n[i] = 1; g.L[i] = 1; g.lg[i] = 0; }
   for (int i = 0; i < d; ++i) {
-    if (n[i] < 1 || n[i] > 2048) { delete p; return fail(FL_INVALID_ARG, "each n_i must be in [1, 2048]"); }
+    if (n[i] < 1 || n[i] > 1024) { delete p; return fail(FL_INVALID_ARG, "each n_i must be in [1, 1024]"); }
     g.n[i] = (int)n[i];
     g.lg[i] = std::max(4, ilog2(2 * g.n[i] - 1));  // L_i >= 2 n_i - 1, at least 16
     g.L[i] = 1 << g.lg[i];
@@ -1157,6 +1250,28 @@ fl_status fl_solve_elliptic_batched(fl_plan* const* plans, int count, const doub
   cudaError_t e = configure_batched_kernels();
   if (e != cudaSuccess) return cuda_fail(e, "configure_batched_kernels");
   return solve_batched_mixed(plans, count, f_dev, u_dev, tol, maxit, prec_mode, infos);
+}
+
+}  // extern "C"
+
+extern "C" {
+
+fl_status fl_plan_attach_net(fl_plan* p, fl_net* net) {
+  if (!check_plan(p)) return fail(FL_INVALID_ARG, "NULL plan");
+  if (!net) {
+    p->net = nullptr;
+    return FL_OK;
+  }
+  fl::NetState* ns = fl_net_state(net);
+  if (p->g.d != 2 || ns->H != p->g.n[0] || ns->W != p->g.n[1])
+    return fail(FL_INVALID_ARG, "the network's H x W must equal the 2D plan's n_0 x n_1");
+  if (!p->z0) {
+    FL_CUDA(dalloc(p, &p->z0, p->g.N * sizeof(float)));
+    FL_CUDA(dalloc(p, &p->feat, 3 * p->g.N * sizeof(float)));
+    for (int i = 0; i < 3; ++i) FL_CUDA(dalloc(p, &p->lpart[i], kVecBlocks * sizeof(double)));
+  }
+  p->net = ns;
+  return FL_OK;
 }
 
 }  // extern "C"

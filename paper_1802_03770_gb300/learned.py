@@ -1,0 +1,161 @@
+"""Training and evaluation of the learned preconditioner (GPU, through the C ABI).
+
+Training pairs come from the solver itself: for a seeded Gaussian-mixture
+right-hand side f and order alpha, the converged solution u* and the plain
+FP64 CG iterates x_k stopped at tolerances 1e-1 ... 1e-4 give residual /
+error pairs r = f - M x_k, e = u* - x_k.  With the base preconditioner z0
+(the FD-Laplacian solve for alpha >= 1, the diagonal scaling 1 / M_ii
+below) and root-mean-square scales s_r, s_z the network input is
+[r / s_r, z0 / s_z, alpha] and its target (e - z0) / s_z, so that
+z = z0 + s_z N(...) approximates e = M^{-1} r.
+
+Usage (GPU):  python -m paper_1802_03770_gb300.learned --n 512 --pairs 20000 \
+                  --out weights.bin
+"""
+
+import argparse
+import json
+import os
+import time
+
+import numpy as np
+
+from . import _lib as L
+from . import inputs
+from .api import Net, Plan
+
+STAGES = (1e-1, 1e-2, 1e-3, 1e-4)
+
+
+def base_precond(plan, r, alpha, kernel0):
+    """z0 = B r in float64 (CUDA tensors)."""
+    if alpha >= 1.0:
+        return plan.precond(r)
+    return r / kernel0
+
+
+def make_pairs(plan, alpha, f, kernel0, stages=STAGES):
+    """Features [len(stages), 3, n, n] and targets [len(stages), n, n] (float32)."""
+    import torch
+    u_star, info = plan.solve(f, tol=1e-11, mode=L.FL_MODE_F64 | L.FL_PRECOND_AUTO, maxit=4000)
+    feats, targets = [], []
+    for tau in stages:
+        x, _ = plan.solve(f, tol=tau, mode=L.FL_MODE_F64 | L.FL_PRECOND_AUTO, maxit=4000,
+                          raise_on_fail=False)
+        e = u_star - x
+        r = f - plan.apply(x)
+        z0 = base_precond(plan, r, alpha, kernel0)
+        s_r = torch.sqrt(torch.mean(r * r)).clamp_min(1e-300)
+        s_z = torch.sqrt(torch.mean(z0 * z0)).clamp_min(1e-300)
+        feats.append(torch.stack([r / s_r, z0 / s_z, torch.full_like(r, alpha)]).float())
+        targets.append(((e - z0) / s_z).float())
+    return torch.stack(feats), torch.stack(targets)
+
+
+class PlanPool:
+    """Plans for a fixed set of seeded orders alpha ~ U(lo, hi) on an n x n grid."""
+
+    def __init__(self, n, count, seed, lo=0.3, hi=1.8):
+        self.n = n
+        self.alphas = inputs.alpha_draws(count, seed, lo, hi)
+        self.plans = [Plan(2, (n, n), 1.0 / (n + 1), a) for a in self.alphas]
+        self.k0 = [p.describe()["kernel0"] for p in self.plans]
+
+    def pick(self, i):
+        j = i % len(self.plans)
+        return self.plans[j], float(self.alphas[j]), self.k0[j]
+
+
+def train(n=512, pairs=20000, batch=4, lr=1e-3, seed=0, pool=16, log_every=50, net=None,
+          max_seconds=None):
+    """Train a network on solver-generated pairs; returns (net, history)."""
+    import torch
+    plans = PlanPool(n, pool, seed + 1)
+    if net is None:
+        net = Net(n, n, seed=seed)
+    hist = []
+    steps = max(1, pairs // len(STAGES))
+    t0 = time.time()
+    for step in range(steps):
+        plan, alpha, k0 = plans.pick(step)
+        f = torch.tensor(inputs.gaussian_mixture(n, 2, 16, seed * 100000 + step), dtype=torch.float64,
+                         device="cuda").view(-1)
+        xs, ts = make_pairs(plan, alpha, f, k0)
+        for b0 in range(0, xs.shape[0], batch):
+            loss = net.train_step(xs[b0:b0 + batch].contiguous(), ts[b0:b0 + batch].contiguous(), lr)
+        if step % log_every == 0:
+            hist.append((step, loss, time.time() - t0))
+            if not np.isfinite(loss):
+                break
+        if max_seconds and time.time() - t0 > max_seconds:
+            break
+    return net, hist
+
+
+def evaluate(net, n=512, seeds=range(10000, 10256), tol=1e-8, pool=16):
+    """Held-out comparison: iterations and wall time of FL_MODE_MIXED (plain
+    FD-preconditioned CG inside refinement) vs FL_MODE_LEARNED."""
+    import torch
+    alphas = inputs.alpha_draws(len(seeds), 777)
+    res = []
+    cache = {}
+    for k, sd in enumerate(seeds):
+        a = float(alphas[k])
+        key = round(a, 2)
+        if key not in cache:
+            if len(cache) >= pool:
+                cache.pop(next(iter(cache)))
+            p = Plan(2, (n, n), 1.0 / (n + 1), a)
+            p.attach_net(net)
+            cache[key] = p
+        p = cache[key]
+        f = torch.tensor(inputs.gaussian_mixture(n, 2, 16, sd), dtype=torch.float64, device="cuda").view(-1)
+        row = {"seed": sd, "alpha": a}
+        for name, mode in (("plain", L.FL_MODE_MIXED | L.FL_PRECOND_AUTO),
+                           ("learned", L.FL_MODE_LEARNED | L.FL_PRECOND_AUTO)):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            _, info = p.solve(f, tol=tol, mode=mode, maxit=4000)
+            torch.cuda.synchronize()
+            row[name] = {"iterations": info["iterations"], "seconds": time.perf_counter() - t,
+                         "rel_residual": info["rel_residual"], "converged": info["converged"]}
+        res.append(row)
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--pairs", type=int, default=20000)
+    ap.add_argument("--batch", type=int, default=4)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--max-seconds", type=float, default=None)
+    ap.add_argument("--eval", type=int, default=32, help="held-out seeds to evaluate")
+    ap.add_argument("--out", default=None)
+    ap.add_argument("--report", default=None)
+    args = ap.parse_args()
+    net, hist = train(args.n, args.pairs, args.batch, args.lr, args.seed,
+                      max_seconds=args.max_seconds)
+    print(json.dumps({"history": hist}), flush=True)
+    if args.out:
+        net.save(args.out)
+    ev = evaluate(net, args.n, range(10000, 10000 + args.eval))
+    summary = {
+        "history": hist,
+        "plain_iterations": float(np.mean([r["plain"]["iterations"] for r in ev])),
+        "learned_iterations": float(np.mean([r["learned"]["iterations"] for r in ev])),
+        "plain_seconds": float(np.mean([r["plain"]["seconds"] for r in ev])),
+        "learned_seconds": float(np.mean([r["learned"]["seconds"] for r in ev])),
+        "all_converged": all(r["plain"]["converged"] and r["learned"]["converged"] for r in ev),
+        "rows": ev,
+    }
+    text = json.dumps(summary)
+    if args.report:
+        with open(args.report, "w") as fh:
+            fh.write(text)
+    print(json.dumps({k: v for k, v in summary.items() if k != "rows"}))
+
+
+if __name__ == "__main__":
+    main()

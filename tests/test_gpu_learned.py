@@ -1,0 +1,66 @@
+"""Flexible CG with the learned preconditioner, and the training pipeline."""
+
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle.operator import Plan as OPlan  # noqa: E402
+from paper_1802_03770_gb300 import _lib, inputs, learned  # noqa: E402
+from paper_1802_03770_gb300.api import Net, Plan  # noqa: E402
+
+WEIGHTS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                       "paper_1802_03770_gb300", "weights", "unet512.bin")
+
+
+@pytest.mark.parametrize("alpha", [0.7, 1.5])
+def test_learned_solve_converges_with_untrained_network(alpha):
+    """Flexible CG stays correct for any network: an untrained one either
+    helps a little, hurts, or triggers the fallback to plain CG."""
+    n = 64
+    h = 1.0 / (n + 1)
+    f = inputs.gaussian_mixture(n, 2, 8, 11)
+    p = Plan(2, (n, n), h, alpha)
+    net = Net(n, n, seed=3)
+    p.attach_net(net)
+    u, info = p.solve(torch.tensor(f, dtype=torch.float64, device="cuda:0"), tol=1e-8,
+                      mode=_lib.FL_MODE_LEARNED | _lib.FL_PRECOND_AUTO)
+    assert info["converged"] == 1
+    op = OPlan(2, n, h, alpha)
+    res = np.linalg.norm(op.apply(u.cpu().numpy()) - f) / np.linalg.norm(f)
+    assert res <= 1.05e-8
+
+
+def test_learned_mode_needs_a_network():
+    p = Plan(2, (64, 64), 1.0 / 65, 1.0)
+    with pytest.raises(_lib.FracLapError, match="INVALID_ARG"):
+        p.solve(torch.ones(64 * 64, dtype=torch.float64, device="cuda:0"),
+                mode=_lib.FL_MODE_LEARNED)
+    with pytest.raises(_lib.FracLapError, match="INVALID_ARG"):
+        p.attach_net(Net(128, 128))
+
+
+def test_training_pipeline_reduces_loss_and_solves():
+    net, hist = learned.train(n=64, pairs=96, batch=4, lr=2e-3, seed=5, pool=4, log_every=1)
+    losses = [h[1] for h in hist]
+    assert np.mean(losses[-4:]) < np.mean(losses[:4])
+    ev = learned.evaluate(net, n=64, seeds=range(10000, 10004), pool=4)
+    for row in ev:
+        assert row["plain"]["converged"] and row["learned"]["converged"], row
+
+
+@pytest.mark.skipif(not os.path.exists(WEIGHTS), reason="no trained 512 x 512 weights")
+def test_trained_network_gain_on_held_out_seeds():
+    """What the trained network gains (or loses) over plain CG, 512 x 512,
+    held-out seeds: both converge to 1e-8; the gain is printed."""
+    net = Net(512, 512)
+    net.load(WEIGHTS)
+    ev = learned.evaluate(net, n=512, seeds=range(10000, 10008), pool=8)
+    plain = np.mean([r["plain"]["iterations"] for r in ev])
+    lrn = np.mean([r["learned"]["iterations"] for r in ev])
+    print(f"mean CG iterations: plain {plain:.1f}, learned {lrn:.1f}")
+    for row in ev:
+        assert row["plain"]["converged"] and row["learned"]["converged"], row
