@@ -251,6 +251,14 @@ fl_status fl_net_train_step(fl_net* net, const float* xs_dev, const float* ts_de
 fl_status fl_net_save(fl_net* net, const char* path);
 fl_status fl_net_load(fl_net* net, const char* path);
 
+/* Run the 3 x 3 convolutions on the tcgen05 tensor cores (enable = 1, the
+ * default: BF16 activations and weights, FP32 accumulation in TMEM) or on
+ * the CUDA cores (enable = 0: FP32 activations, BF16 weights). */
+fl_status fl_net_set_tensor_cores(fl_net* net, int enable);
+/* FL_DEVICE_TIMEOUT if a bounded tensor-core wait of an earlier call gave up
+ * (its outputs were zeroed), else FL_OK; waits for the net's stream. */
+fl_status fl_net_check(fl_net* net);
+
 /* Attach (net != NULL) or detach a network for FL_MODE_LEARNED solves on a
  * 2D plan without mask; the network's H x W must equal n_0 x n_1.  Allocates
  * the plan's feature buffers on first attach.  The plan does not own the

@@ -92,6 +92,8 @@ SIGNATURES = {
     "fl_net_save": (_I, [_P, ctypes.c_char_p]),
     "fl_net_load": (_I, [_P, ctypes.c_char_p]),
     "fl_plan_attach_net": (_I, [_P, _P]),
+    "fl_net_set_tensor_cores": (_I, [_P, _I]),
+    "fl_net_check": (_I, [_P]),
     "fl_last_error_string": (ctypes.c_char_p, []),
 }
 

@@ -56,6 +56,12 @@ class Net:
         except Exception:
             pass
 
+    def tensor_cores(self, enable=True):
+        L.check(self._lib.fl_net_set_tensor_cores(self._h, int(enable)), "fl_net_set_tensor_cores")
+
+    def check(self):
+        L.check(self._lib.fl_net_check(self._h), "fl_net_check")
+
     def get_params(self, grads=False):
         p = np.empty(self.nparams, np.float32)
         g = np.empty(self.nparams, np.float32) if grads else None

@@ -128,11 +128,14 @@ cudaError_t NetState::init(int h, int wd, uint64_t seed, cudaStream_t s) {
   al((void**)&part, maxpart * sizeof(float));
   al((void**)&bpart, (size_t)(H / 16) * (W / 16) * 64 * sizeof(float));
   al((void**)&lpart, kLossBlocks * sizeof(double));
+  al((void**)&err, sizeof(int));
   if (e != cudaSuccess) return e;
   e = cudaMemcpyAsync(w, host.data(), nparams * sizeof(float), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(m, 0, nparams * sizeof(float), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(v, 0, nparams * sizeof(float), s);
   if (e == cudaSuccess) e = launch_to_bf16(w, wb, nparams, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = configure_unet_kernels();
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   step = 0;
   return e;
@@ -151,6 +154,8 @@ ConvArgs NetState::conv_args(int l, bool input_grad) const {
   a.W = W >> lev;
   a.k = L.k;
   a.w = wb + woff[l];
+  a.tensor_cores = use_tc;
+  a.err = err;
   if (!input_grad) {
     for (int j = 0; j < 2; ++j) {
       a.src[j].p = L.src[j] >= 0 ? act[L.src[j]] : nullptr;
@@ -509,3 +514,23 @@ cudaError_t launch_fpcg_scalar(PcgState* st, const double* rr_part, int rr_count
 }  // namespace fl
 
 fl::NetState* fl_net_state(fl_net* n) { return n; }
+
+extern "C" {
+
+fl_status fl_net_set_tensor_cores(fl_net* n, int enable) {
+  if (!n) return net_fail(FL_INVALID_ARG, "NULL net");
+  n->use_tc = enable ? 1 : 0;
+  return FL_OK;
+}
+
+fl_status fl_net_check(fl_net* n) {
+  if (!n) return net_fail(FL_INVALID_ARG, "NULL net");
+  int flag = 0;
+  fl_status s = net_cuda(cudaMemcpyAsync(&flag, n->err, sizeof(int), cudaMemcpyDeviceToHost, n->stream),
+                         "fl_net_check");
+  if (s == FL_OK) s = net_cuda(cudaStreamSynchronize(n->stream), "fl_net_check");
+  if (s == FL_OK && flag) return net_fail(FL_DEVICE_TIMEOUT, "a tensor-core wait gave up");
+  return s;
+}
+
+}  // extern "C"

@@ -39,6 +39,8 @@ struct NetState {
   float* bpart = nullptr;
   double* lpart = nullptr;
   int step = 0;
+  int use_tc = 1;              // 3 x 3 convolutions on tcgen05 (BF16 operands)
+  int* err = nullptr;          // device flag of the bounded tensor-core waits
   std::vector<void*> allocs;
 
   int channels(int t) const;

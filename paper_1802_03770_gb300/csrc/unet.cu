@@ -229,7 +229,165 @@ __global__ void k_to_bf16(const float* __restrict__ w, __nv_bfloat16* __restrict
 
 }  // namespace
 
+// --- 3 x 3 convolution on the tensor cores (tcgen05, kind::f16) ----------------
+//
+// Implicit GEMM: D[128 pixels][N = cout] += A[128][K] B[N][K]^T with
+// K = 9 cin (k = 9 ci + 3 dy + dx) in chunks of 64.  A (the im2col tile of
+// 8 x 16 output pixels) and B (the weights) are converted to BF16 by the
+// CTA's threads and stored K-major in the canonical no-swizzle layout (core
+// matrices of 8 rows x 8 elements, 128 contiguous bytes; adjacent along K:
+// 128 B, adjacent along rows: 1024 B).  One thread issues four 128 x N x 16
+// MMAs per chunk into a TMEM accumulator; completion is signalled through an
+// mbarrier (bounded wait).  The epilogue reads TMEM lane p (= pixel p) with
+// tcgen05.ld, adds the bias and applies the ReLU.
+namespace {
+
+constexpr int TC_M = 128, TC_KC = 64, TC_NMAX = 96;
+constexpr int TC_SMEM = TC_M * TC_KC * 2 + TC_NMAX * TC_KC * 2 + 64;
+constexpr int kWaitLimit = 1 << 24;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor: start, leading (K) and stride (row-group)
+// byte offsets, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// canonical K-major offset of element (row, k) for a 64-wide K chunk
+__device__ __forceinline__ int canon64(int row, int k) {
+  return (((row >> 3) * 8 + (k >> 3)) << 6) + ((row & 7) << 3) + (k & 7);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+  for (int it = 0; it < kWaitLimit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(mbar), "r"(phase) : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(TC_M) k_conv_tc(ConvArgs a, int tmem_cols) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  __nv_bfloat16* sa = reinterpret_cast<__nv_bfloat16*>(tc_smem);
+  __nv_bfloat16* sb = sa + TC_M * TC_KC;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sb + TC_NMAX * TC_KC);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int x0 = blockIdx.x * 16, y0 = blockIdx.y * 8;
+  const int N = a.cout;
+  const int K = a.cin * 9;
+  const int nchunks = (K + TC_KC - 1) / TC_KC;
+  const uint32_t mb = smem_addr(mbar);
+  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb));
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_addr(tmem_slot)), "r"(tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+                         ((uint32_t)(TC_M >> 4) << 24);
+  bool ok = true;
+  for (int ch = 0; ch < nchunks; ++ch) {
+    const int k0 = ch * TC_KC;
+    // A: im2col of the 8 x 16 pixel tile
+    for (int e = tid; e < TC_M * TC_KC; e += TC_M) {
+      const int p = e >> 6, kl = e & 63;
+      const int k = k0 + kl;
+      float v = 0.f;
+      if (k < K) {
+        const int ci = k / 9, t = k - ci * 9;
+        const int dy = t / 3, dx = t - dy * 3;
+        v = src_value(a, ci, y0 + (p >> 4) + dy - 1, x0 + (p & 15) + dx - 1);
+      }
+      sa[canon64(p, kl)] = __float2bfloat16(v);
+    }
+    // B: weights of the chunk
+    for (int e = tid; e < N * TC_KC; e += TC_M) {
+      const int o = e >> 6, kl = e & 63;
+      const int k = k0 + kl;
+      float v = 0.f;
+      if (k < K) {
+        const int ci = k / 9, t = k - ci * 9;
+        v = weight(a, o, ci, t);
+      }
+      sb[canon64(o, kl)] = __float2bfloat16(v);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int kk = 0; kk < TC_KC / 16; ++kk) {
+        const uint64_t ad = umma_desc(smem_addr(sa) + kk * 256, 128, 1024);
+        const uint64_t bd = umma_desc(smem_addr(sb) + kk * 256, 128, 1024);
+        const uint32_t acc = (ch > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+            :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   :: "r"(mb) : "memory");
+    }
+    // the MMAs read sa / sb: wait before the next chunk overwrites them
+    ok = mbar_wait(mb, (uint32_t)(ch & 1)) && ok;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  if (!ok && a.err) atomicExch(a.err, 1);
+  // epilogue: lane p of TMEM holds pixel p
+  const int p = warp * 32 + (tid & 31);
+  const int y = y0 + (p >> 4), x = x0 + (p & 15);
+  for (int c0 = 0; c0 < N; c0 += 16) {
+    uint32_t v[16];
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int co = c0 + j;
+      float z = __uint_as_float(v[j]) + (a.bias ? a.bias[co] : 0.f);
+      if (a.relu) z = fmaxf(z, 0.f);
+      a.out[((size_t)co * a.H + y) * a.W + x] = ok ? z : 0.f;
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(tmem_cols));
+}
+
+}  // namespace
+
+cudaError_t configure_unet_kernels() {
+  return cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_conv_tc),
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+}
+
 cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s) {
+  if (a.tensor_cores && a.k == 3 && a.cout % 16 == 0 && a.cout <= TC_NMAX && a.H % 8 == 0 &&
+      a.W % 16 == 0) {
+    const int cols = a.cout <= 32 ? 32 : (a.cout <= 64 ? 64 : 128);
+    dim3 grid(a.W / 16, a.H / 8);
+    FL_KERNEL("unet_conv3_tc", s, k_conv_tc<<<grid, TC_M, TC_SMEM, s>>>(a, cols));
+    return cudaGetLastError();
+  }
   dim3 grid(a.W / TILE, a.H / TILE, (a.cout + CO - 1) / CO);
   if (a.k == 3)
     FL_KERNEL("unet_conv3", s, k_conv<3><<<grid, TILE * TILE, 0, s>>>(a));

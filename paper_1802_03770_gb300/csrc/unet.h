@@ -28,9 +28,12 @@ struct ConvArgs {
   const float* bias; // nullable
   float* out;        // [cout][H][W]
   int relu;
+  int tensor_cores;  // 1: 3 x 3 layers with cout % 16 == 0 run on tcgen05 (BF16 operands)
+  int* err;          // device flag set when a bounded tensor-core wait gives up
 };
 
 cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s);
+cudaError_t configure_unet_kernels();
 size_t conv_wgrad_partials(const ConvArgs& a);
 cudaError_t launch_conv_wgrad(const ConvArgs& a, const float* gz, float* part, float* bpart, float* dw,
                               float* db, int accumulate, cudaStream_t s);

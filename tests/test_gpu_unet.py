@@ -39,8 +39,9 @@ def unflatten(flat, dtype=np.float64):
     return params
 
 
-def setup_net(H=64, seed=1):
+def setup_net(H=64, seed=1, tensor_cores=False):
     net = Net(H, H, seed=0)
+    net.tensor_cores(tensor_cores)
     p = unet.init_params(seed, dtype=np.float64)
     rng = np.random.default_rng(seed + 1)
     p = {k: (w, rng.standard_normal(b.shape) * 0.05) for k, (w, b) in p.items()}
@@ -108,3 +109,26 @@ def test_checkpoint_roundtrip(tmp_path):
     path.write_bytes(bytes(raw))
     with pytest.raises(_lib.FracLapError, match="checksum"):
         other.load(path)
+
+
+def test_tensor_core_forward_matches_cuda_core_forward():
+    """tcgen05 path (BF16 activations): within 2e-2 of the FP32-activation
+    path; the bound is BF16's 2^-9 unit roundoff on both GEMM operands,
+    accumulated over ten 3 x 3 layers."""
+    net, _ = setup_net(H=128, seed=11)
+    x = torch.tensor(np.random.default_rng(12).standard_normal((3, 128, 128)), dtype=torch.float32,
+                     device="cuda:0").view(-1)
+    y32 = net.forward(x).cpu().numpy()
+    net.tensor_cores(True)
+    ytc = net.forward(x).cpu().numpy()
+    net.check()
+    assert np.linalg.norm(ytc - y32) <= 2e-2 * np.linalg.norm(y32)
+    # and the training step runs on the tensor cores too
+    xs = torch.tensor(np.random.default_rng(13).standard_normal((2, 3, 128, 128)), dtype=torch.float32,
+                      device="cuda:0")
+    ts = torch.zeros((2, 1, 128, 128), dtype=torch.float32, device="cuda:0")
+    l0 = net.train_step(xs, ts, lr=1e-3)
+    for _ in range(10):
+        l1 = net.train_step(xs, ts, lr=1e-3)
+    net.check()
+    assert l1 < l0
