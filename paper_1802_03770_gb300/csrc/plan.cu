@@ -86,6 +86,22 @@ struct Profiler {
   }
 };
 
+// A captured chunk of CG iterations of one precision, valid for one
+// (preconditioner, shift, scale) configuration.
+struct GraphCache {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool use_prec = false;
+  double shift = 0.0, scale = 0.0;
+  long long kernels = 0;
+  void release() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+  }
+};
+
 struct fl_plan {
   Geo g;
   double h, alpha, rho;
@@ -109,6 +125,7 @@ struct fl_plan {
   std::vector<void*> allocs;
   int64_t bytes = 0;
   struct Profiler* prof = nullptr;   // non-null while profiling is enabled
+  GraphCache gcache[2];              // [0] FP64, [1] FP32 CG iteration graphs
   // learned preconditioner (fl_plan_attach_net)
   fl::NetState* net = nullptr;
   float* z0 = nullptr;     // base preconditioned residual
@@ -117,8 +134,33 @@ struct fl_plan {
 };
 
 namespace {
+std::atomic<long long> g_launches{0};
+thread_local Profiler* t_prof = nullptr;
+
+// Makes the plan's profiler the active one for the duration of an API call.
+struct ProfScope {
+  Profiler* saved;
+  explicit ProfScope(fl_plan* p);
+  ~ProfScope() { t_prof = saved; }
+};
+}  // namespace
+
+ProfScope::ProfScope(fl_plan* p) : saved(t_prof) { t_prof = p ? p->prof : nullptr; }
+
+namespace {
 
 enum { P_PQ = 0, P_RR = 1, P_RZ = 2, P_BB = 3, P_RES = 4, P_AUX = 5 };
+
+constexpr int kGraphIters = 4;
+
+// FRACLAP_GRAPHS=0 in the environment launches CG iterations one by one.
+bool graphs_enabled() {
+  static const bool on = [] {
+    const char* v = getenv("FRACLAP_GRAPHS");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
 
 template <typename P>
 cudaError_t dalloc(fl_plan* p, P** ptr, size_t bytes) {
@@ -134,6 +176,7 @@ cudaError_t dalloc(fl_plan* p, P** ptr, size_t bytes) {
 
 void free_plan(fl_plan* p) {
   if (!p) return;
+  for (auto& gc : p->gcache) gc.release();
   if (p->prof) {
     cudaStreamSynchronize(p->stream);
     delete p->prof;
@@ -289,32 +332,64 @@ fl_status run_pcg(fl_plan* p, bool x0_nonzero, double shift, double scale, bool 
   }
   FL_CUDA(launch_pcg_init(s, p->st, p->part[P_BB], bb_count, rr0_part, rr0_count, p->part[P_RZ],
                           rz_count, tol, maxit));
+  // one CG iteration: q = A p (p = z + beta p fused), x/r update fused into
+  // the first preconditioner pass (or the plain update), scalars
+  const int it_rr = use_prec ? precond_partials<T>(g) : kVecBlocks;
+  auto enqueue = [&](cudaStream_t qs) -> cudaError_t {
+    ApplyIO<T> io;
+    io.pre = PRE_PUPDATE; io.u = z; io.p = v.p; io.mask = p->mask; io.st = p->st;
+    io.out = v.q; io.x = v.p; io.cm = scale; io.cx = shift;
+    io.dotw = v.p; io.partials = p->part[P_PQ];
+    cudaError_t e = launch_apply<T>(g, tb, qs, io);
+    if (e != cudaSuccess) return e;
+    int cnt = 0;
+    if (use_prec) {
+      PrecIO<T> pi;
+      pi.pre = DPRE_UPDATE; pi.out = v.z; pi.shift = shift; pi.scale = scale;
+      pi.x = v.x; pi.r = v.r; pi.p = v.p; pi.q = v.q;
+      pi.pq_part = p->part[P_PQ]; pi.pq_count = pq_count; pi.rr_part = p->part[P_RR];
+      pi.dotw = v.r; pi.dot_part = p->part[P_RZ]; pi.st = p->st;
+      e = launch_precond<T>(g, tb, p->mu, qs, pi);
+      if (e != cudaSuccess) return e;
+      return launch_pcg_scalar(qs, p->st, p->part[P_RR], it_rr, p->part[P_RZ], it_rr);
+    }
+    e = launch_noprec_update<T>(g.N, qs, p->st, v.x, v.r, v.p, v.q, p->part[P_PQ], pq_count,
+                                p->part[P_RR], &cnt);
+    if (e != cudaSuccess) return e;
+    return launch_pcg_scalar(qs, p->st, p->part[P_RR], it_rr, p->part[P_RR], it_rr);
+  };
+  // Iterations run in chunks of 4, 8, 16, 32 between reads of the device
+  // state; a chunk is replays of a captured 4-iteration CUDA graph (not
+  // while the per-kernel profiler is on).
+  GraphCache& gc = p->gcache[sizeof(T) == 4 ? 1 : 0];
+  const bool use_graph = p->prof == nullptr && graphs_enabled();
+  if (use_graph && !(gc.exec && gc.use_prec == use_prec && gc.shift == shift && gc.scale == scale)) {
+    gc.release();
+    cudaStream_t cs = nullptr;
+    FL_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    const long long before = g_launches.load();
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    for (int k = 0; k < kGraphIters && e == cudaSuccess; ++k) e = enqueue(cs);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &gc.graph);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return cuda_fail(e, "CG iteration capture");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+    FL_CUDA(cudaGraphInstantiate(&gc.exec, gc.graph, 0));
+    gc.kernels = g_launches.load() - before;
+    g_launches.fetch_sub(gc.kernels);   // counted when the graph runs
+    gc.use_prec = use_prec;
+    gc.shift = shift;
+    gc.scale = scale;
+  }
   int chunk = 4;
   for (;;) {
-    for (int k = 0; k < chunk; ++k) {
-      ApplyIO<T> io;
-      io.pre = PRE_PUPDATE; io.u = z; io.p = v.p; io.mask = p->mask; io.st = p->st;
-      io.out = v.q; io.x = v.p; io.cm = scale; io.cx = shift;
-      io.dotw = v.p; io.partials = p->part[P_PQ];
-      FL_CUDA(launch_apply<T>(g, tb, s, io));
-      const double* rz_part;
-      if (use_prec) {
-        PrecIO<T> pi;
-        pi.pre = DPRE_UPDATE; pi.out = v.z; pi.shift = shift; pi.scale = scale;
-        pi.x = v.x; pi.r = v.r; pi.p = v.p; pi.q = v.q;
-        pi.pq_part = p->part[P_PQ]; pi.pq_count = pq_count; pi.rr_part = p->part[P_RR];
-        pi.dotw = v.r; pi.dot_part = p->part[P_RZ]; pi.st = p->st;
-        FL_CUDA(launch_precond<T>(g, tb, p->mu, s, pi));
-        rr_count = precond_partials<T>(g);
-        rz_count = rr_count;
-        rz_part = p->part[P_RZ];
-      } else {
-        FL_CUDA(launch_noprec_update<T>(g.N, s, p->st, v.x, v.r, v.p, v.q, p->part[P_PQ], pq_count,
-                                        p->part[P_RR], &rr_count));
-        rz_count = rr_count;
-        rz_part = p->part[P_RR];
+    if (use_graph) {
+      for (int c = 0; c < chunk / kGraphIters; ++c) {
+        FL_CUDA(cudaGraphLaunch(gc.exec, s));
+        g_launches.fetch_add(gc.kernels);
       }
-      FL_CUDA(launch_pcg_scalar(s, p->st, p->part[P_RR], rr_count, rz_part, rz_count));
+    } else {
+      for (int k = 0; k < chunk; ++k) FL_CUDA(enqueue(s));
     }
     fl_status st = read_state(p);
     if (st != FL_OK) return st;
@@ -545,17 +620,6 @@ bool trace_enabled() {
 
 // --- launch accounting and the per-kernel profiler -----------------------------
 
-namespace {
-std::atomic<long long> g_launches{0};
-thread_local Profiler* t_prof = nullptr;
-
-// Makes the plan's profiler the active one for the duration of an API call.
-struct ProfScope {
-  Profiler* saved;
-  explicit ProfScope(fl_plan* p);
-  ~ProfScope() { t_prof = saved; }
-};
-}  // namespace
 
 namespace fl {
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -572,7 +636,6 @@ void prof_end(const char* name, cudaEvent_t e0, cudaStream_t s) {
 }
 }  // namespace fl
 
-ProfScope::ProfScope(fl_plan* p) : saved(t_prof) { t_prof = p ? p->prof : nullptr; }
 
 extern "C" {
 
