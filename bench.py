@@ -122,6 +122,62 @@ def algorithmic_bytes(name, n, L, elem):
     return table.get(base)
 
 
+def apply_bytes(n, L, elem):
+    """Streamed bytes of one 2D apply (three passes, each reading and writing
+    its working array once, the compact symbol read once)."""
+    H = L // 2 + 1
+    real = n * n * elem
+    spec = n * H * 2 * elem
+    return real + spec + (2 * spec + H * H * elem) + spec + real
+
+
+def time_apply(plan, dev, reps=50):
+    """Operator apply y = M u on the workload grid: ours (FP32 and FP64) and,
+    beside it as a reference only, a cuFFT (torch.fft) zero-padded
+    convolution of the same shape with a stand-in symbol.  Inputs are
+    L2-resident, as inside the CG loop."""
+    import torch
+    L = 2 * N_SIDE
+    out = {}
+    for dt, tag in ((torch.float32, "f32"), (torch.float64, "f64")):
+        u = torch.randn(N_SIDE * N_SIDE, dtype=dt, device=dev)
+        y = torch.empty_like(u)
+        for _ in range(5):
+            plan.apply(u, y)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            plan.apply(u, y)
+        e1.record()
+        torch.cuda.synchronize()
+        t_ours = e0.elapsed_time(e1) / reps * 1e3
+        sym = torch.rand(L, L // 2 + 1, dtype=dt, device=dev)
+        pad = torch.zeros(L, L, dtype=dt, device=dev)
+
+        def cufft_apply():
+            pad[:N_SIDE, :N_SIDE] = u.view(N_SIDE, N_SIDE)
+            s = torch.fft.rfft2(pad)
+            s *= sym
+            return torch.fft.irfft2(s, s=(L, L))[:N_SIDE, :N_SIDE].contiguous()
+
+        for _ in range(5):
+            cufft_apply()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            cufft_apply()
+        e1.record()
+        torch.cuda.synchronize()
+        t_ref = e0.elapsed_time(e1) / reps * 1e3
+        ab = apply_bytes(N_SIDE, L, 4 if tag == "f32" else 8)
+        out[tag] = {"us": round(t_ours, 2), "streamed_bytes": ab,
+                    "gbs": round(ab / (t_ours * 1e-6) / 1e9, 1),
+                    "cufft_reference_us": round(t_ref, 2)}
+    return out
+
+
 def run_ours(args, rank, world, local):
     import torch
     from paper_1802_03770_gb300 import _lib
@@ -210,6 +266,8 @@ def run_ours(args, rank, world, local):
            "h2d_bytes_per_step": solves_per_step * N_SIDE * N_SIDE * 8,
            "d2h_bytes_per_step": solves_per_step * N_SIDE * N_SIDE * 8}
 
+    apply = time_apply(plans[-1], dev)
+
     # per-kernel device time over profiled steps (CUDA events around each launch)
     for p in plans:
         p.profile(True)
@@ -252,7 +310,7 @@ def run_ours(args, rank, world, local):
         "speedup_vs_fp64_pcg": value / value_f64,
         "iterations_mixed": its_mixed,
         "refinements": [i["outer_iterations"] for i in infos_mixed[: len(ALPHAS)]],
-        "kernels": kernel_shares,
+        "kernels": kernel_shares, "apply": apply,
     }
 
 
@@ -371,7 +429,7 @@ def main():
                 "roofline": res["roofline"], "cpu_baseline": cpu,
                 "fp64_pcg": res["fp64_pcg"], "speedup_vs_fp64_pcg": res["speedup_vs_fp64_pcg"],
                 "iterations_mixed": res["iterations_mixed"], "refinements": res["refinements"],
-                "t_con_s": res["t_con_s"], "kernels": res["kernels"]}
+                "t_con_s": res["t_con_s"], "apply": res["apply"], "kernels": res["kernels"]}
         print(json.dumps(line))
     if world > 1:
         import torch
