@@ -122,7 +122,8 @@ fl_status fl_apply_f32(fl_plan* plan, const float* u_dev, float* y_dev);
 
 /* z = (shift I + scale C h^d L)^{-1} r on the full box (Sec. 3.1 with
  * shift = 0, scale = 1; Sec. 3.2 with shift = 1, scale = theta dt).
- * Requires a plan without mask.  r_dev, z_dev: N doubles, may not alias. */
+ * Requires a plan without mask, shift >= 0 and scale > 0 (FL_INVALID_ARG
+ * otherwise).  r_dev, z_dev: N doubles, may not alias. */
 fl_status fl_precond(fl_plan* plan, double shift, double scale, const double* r_dev,
                      double* z_dev);
 fl_status fl_precond_f32(fl_plan* plan, double shift, double scale, const float* r_dev,

@@ -44,6 +44,14 @@ FL_BATCHED_KERNEL(dst_cols, DstColsArgs)
 
 #undef FL_BATCHED_KERNEL
 
+template <typename T>
+__global__ void __launch_bounds__(kTriCols * kTriSeg)
+    kb_tri_cols(const TriArgs<T>* __restrict__ args, const int* __restrict__ off, int nprob) {
+  const int i = batch_problem(off, nprob);
+  const TriArgs<T> a = args[i];
+  body_tri_cols<T>(a, blockIdx.x - off[i]);
+}
+
 // --- batched CG vector and scalar kernels -------------------------------------
 
 // Start of an inner CG solve with x0 = 0: x = 0, p = 0, r = b (masked), and
@@ -57,16 +65,16 @@ __global__ void __launch_bounds__(kVecThreads) kb_cg_start(const BVecArgs<T>* __
   const int bx = blockIdx.x - off[i];
   const int gx = off[i + 1] - off[i];
   if (a.gate && a.gate->done) return;
-  double v = 0.0;
+  DotAcc<T> v;
   for (long long k = (long long)bx * blockDim.x + threadIdx.x; k < a.N;
        k += (long long)gx * blockDim.x) {
     const T bv = (a.mask && !a.mask[k]) ? (T)0 : a.b[k];
     a.r[k] = bv;
     a.x[k] = (T)0;
     a.p[k] = (T)0;
-    v += (double)bv * (double)bv;
+    v.add(bv * bv);
   }
-  const double s = cta_sum(v, red);
+  const double s = cta_sum(v.value(), red);
   if (threadIdx.x == 0) a.part[bx] = s;
 }
 
@@ -92,15 +100,15 @@ __global__ void __launch_bounds__(kVecThreads) kb_noprec_update(const BVecArgs<T
   }
   __syncthreads();
   const T al = (T)s_alpha;
-  double rr = 0.0;
+  DotAcc<T> rr;
   for (long long k = (long long)bx * blockDim.x + threadIdx.x; k < a.N;
        k += (long long)gx * blockDim.x) {
     a.x[k] += al * a.p[k];
     const T rn = a.r[k] - al * a.q[k];
     a.r[k] = rn;
-    rr += (double)rn * (double)rn;
+    rr.add(rn * rn);
   }
-  const double s = cta_sum(rr, red);
+  const double s = cta_sum(rr.value(), red);
   if (threadIdx.x == 0) a.part[bx] = s;
 }
 
@@ -222,6 +230,11 @@ cudaError_t launch_batched(const BatchPass& bp, cudaStream_t s) {
       FL_KERNEL(sizeof(T) == 4 ? "b_dst_cols<f32>" : "b_dst_cols<f64>", s,
                 kb_dst_cols<T, K::CT, K::CV><<<bp.blocks, K::CT, bp.smem, s>>>(
                     (const DstColsArgs<T>*)bp.args, bp.off, bp.gx, bp.nprob));
+      break;
+    case BK_TRI_COLS:
+      FL_KERNEL(sizeof(T) == 4 ? "b_tri_cols<f32>" : "b_tri_cols<f64>", s,
+                kb_tri_cols<T><<<bp.blocks, kTriCols * kTriSeg, 0, s>>>(
+                    (const TriArgs<T>*)bp.args, bp.off, bp.nprob));
       break;
     case BK_CG_START:
       FL_KERNEL(sizeof(T) == 4 ? "b_cg_start<f32>" : "b_cg_start<f64>", s,

@@ -33,12 +33,13 @@ template <typename T> inline int row_lines(int L) { return (Cfg<T>::RT * Cfg<T>:
 template <typename T> inline int col_tx(int L) {
   return std::min(kMaxTx, (Cfg<T>::CT * Cfg<T>::CV) / L);
 }
+// shared-memory bytes of `lines` lines of L complex values (padded, SBuf)
 template <typename T> inline size_t smem_bytes(int lines, int L) {
-  return (size_t)lines * (L + 2) * sizeof(typename Cplx<T>::type);
+  return (size_t)sbuf_elems((long long)lines * L) * sizeof(typename Cplx<T>::type);
 }
-// interleaved tiles (strided passes) carry no padding
+// interleaved tile of tx columns of length L (padded, SBuf)
 template <typename T> inline size_t tile_bytes(int tx, int L) {
-  return (size_t)tx * L * sizeof(typename Cplx<T>::type);
+  return (size_t)sbuf_elems((long long)tx * L) * sizeof(typename Cplx<T>::type);
 }
 inline int ilog2i(int v) {
   int l = 0;
@@ -60,7 +61,10 @@ struct ApplyChain {
   size_t row_smem;
 };
 
-// One preconditioner solve: DST rows, one or three strided DST passes, DST rows.
+// One preconditioner solve: DST rows; in 3D a strided DST pass along the
+// middle axis; the tridiagonal solve along axis 0; in 3D the middle-axis DST
+// again; DST rows.  The tridiagonal pass runs after the first `tri_after`
+// strided passes.
 template <typename T>
 struct PrecChain {
   DstRowsArgs<T> first;
@@ -68,6 +72,9 @@ struct PrecChain {
   dim3 cols_grid[3];
   size_t cols_smem[3];
   int ncols;
+  TriArgs<T> tri;
+  int tri_after;
+  int tri_blocks;
   DstRowsArgs<T> last;
   int row_blocks;
   size_t row_smem;
@@ -107,7 +114,7 @@ struct BScalarArgs {
 };
 
 enum { BK_ROWS_FWD = 0, BK_COLS, BK_ROWS_INV, BK_DST_ROWS, BK_DST_COLS, BK_CG_START, BK_NOPREC,
-       BK_CAST };
+       BK_CAST, BK_TRI_COLS };
 
 // One batched launch: device arrays of per-problem arguments and of block
 // offsets (nprob + 1 entries) and grid x-extents.
@@ -132,7 +139,6 @@ cudaError_t configure_batched_kernels();
 template <typename T>
 ApplyChain<T> build_apply(const Geo& g, const Tables<T>& tb, const ApplyIO<T>& io);
 template <typename T>
-PrecChain<T> build_precond(const Geo& g, const Tables<T>& tb, const double* const* mu,
-                           const PrecIO<T>& io);
+PrecChain<T> build_precond(const Geo& g, const Tables<T>& tb, const PrecIO<T>& io);
 
 }  // namespace fl

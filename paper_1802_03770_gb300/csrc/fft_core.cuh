@@ -19,8 +19,9 @@
 // the other powers by complex products.
 //
 // Two storage layouts: lines of stride ls (element j of line q at
-// q * ls + j), and 2^ltx interleaved lines (element j of line c at
-// j * 2^ltx + c, the natural layout of a tile of consecutive columns).
+// q * ls + j, ls a multiple of 16), and 2^ltx interleaved lines (element j
+// of line c at j * 2^ltx + c, the natural layout of a tile of consecutive
+// columns).  Indices are logical (see SBuf).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -31,6 +32,21 @@ namespace fl {
 template <typename T> struct Cplx;
 template <> struct Cplx<float> { typedef float2 type; };
 template <> struct Cplx<double> { typedef double2 type; };
+
+// Complex buffer in shared memory with one pad element after every 16: the
+// logical index i is stored at i + i/16.  The first Stockham stage writes the
+// R legs of a butterfly to R consecutive logical places (a stride of R
+// complex values across threads), which without the pad puts every thread of
+// a warp on the same banks.
+template <typename C>
+struct SBuf {
+  C* p;
+  __device__ __forceinline__ C& operator[](int i) const { return p[i + (i >> 4)]; }
+  // view starting at logical offset `off` (a multiple of 16)
+  __device__ __forceinline__ SBuf at(int off) const { return SBuf{p + off + (off >> 4)}; }
+};
+// complex elements to allocate for `logical` logical ones
+inline constexpr long long sbuf_elems(long long logical) { return logical + logical / 16 + 1; }
 
 template <typename C> __device__ __forceinline__ C cmake(decltype(C().x) a, decltype(C().x) b) {
   C r; r.x = a; r.y = b; return r;
@@ -164,7 +180,7 @@ __device__ __forceinline__ void twiddles(const C* __restrict__ tw, int step, boo
 // One Stockham stage of radix R over `nlines` lines of length L = 2^lg
 // (line q at buf + q * ls).  Contains two __syncthreads().
 template <int R, int VPT, typename C>
-__device__ __forceinline__ void stockham_stage(C* buf, int lg, int ls, int nlines, int Ns,
+__device__ __forceinline__ void stockham_stage(SBuf<C> buf, int lg, int ls, int nlines, int Ns,
                                                const C* __restrict__ tw, int lgmax, bool inv) {
   constexpr int NB = VPT / R;  // butterflies per thread
   const int lglr = lg - LogR<R>::v;
@@ -180,7 +196,7 @@ __device__ __forceinline__ void stockham_stage(C* buf, int lg, int ls, int nline
       const int line = g >> lglr;
       const int j = g & (LR - 1);
       const int k = j & (Ns - 1);
-      const C* base = buf + (size_t)line * ls;
+      const SBuf<C> base = buf.at(line * ls);
 #pragma unroll
       for (int r = 0; r < R; ++r) v[b][r] = base[j + r * LR];
       if (k != 0) {
@@ -209,7 +225,7 @@ __device__ __forceinline__ void stockham_stage(C* buf, int lg, int ls, int nline
 // j * 2^ltx + c).  Consecutive threads take consecutive lines, so the leg
 // reads are contiguous.
 template <int R, int VPT, typename C>
-__device__ __forceinline__ void stockham_stage_il(C* buf, int lg, int ltx, int Ns,
+__device__ __forceinline__ void stockham_stage_il(SBuf<C> buf, int lg, int ltx, int Ns,
                                                   const C* __restrict__ tw, int lgmax, bool inv) {
   constexpr int NB = VPT / R;
   const int LR = 1 << (lg - LogR<R>::v);
@@ -251,7 +267,7 @@ __device__ __forceinline__ void stockham_stage_il(C* buf, int lg, int ltx, int N
 // Stage plan: radix 16 while at least four factors of two remain (if VPT
 // allows), then radix 8, then one radix-4 or radix-2 stage.
 template <int VPT, typename C>
-__device__ __forceinline__ void fft_lines(C* buf, int lg, int ls, int nlines, const C* __restrict__ tw,
+__device__ __forceinline__ void fft_lines(SBuf<C> buf, int lg, int ls, int nlines, const C* __restrict__ tw,
                                           int lgmax, bool inv) {
   int Ns = 1;
   int rem = lg;
@@ -272,7 +288,7 @@ __device__ __forceinline__ void fft_lines(C* buf, int lg, int ls, int nlines, co
 }
 
 template <int VPT, typename C>
-__device__ __forceinline__ void fft_lines_il(C* buf, int lg, int ltx, const C* __restrict__ tw,
+__device__ __forceinline__ void fft_lines_il(SBuf<C> buf, int lg, int ltx, const C* __restrict__ tw,
                                              int lgmax, bool inv) {
   int Ns = 1;
   int rem = lg;

@@ -27,6 +27,7 @@ struct Geo {
   int H;          // L[d-1]/2 + 1
   long long N;    // prod n
   long long spec; // complex entries of the operator spectrum workspace
+  double cA;      // c (-a): weight of the finite-difference stencil in C h^d L
 };
 
 struct PcgState;
@@ -41,6 +42,7 @@ struct Tables {
   C* bhat[3] = {nullptr, nullptr, nullptr};
   C* S = nullptr;             // operator spectrum workspace
   T* t = nullptr;             // preconditioner workspace (N)
+  T* mu[3] = {nullptr, nullptr, nullptr};  // eigenvalues of C h^d L per axis
 };
 
 // Inputs and outputs of one operator apply.
@@ -84,8 +86,7 @@ cudaError_t launch_apply(const Geo& g, const Tables<T>& tb, cudaStream_t s, cons
 template <typename T>
 int apply_partials(const Geo& g);  // partials written by the apply epilogue
 template <typename T>
-cudaError_t launch_precond(const Geo& g, const Tables<T>& tb, const double* const* mu,
-                           cudaStream_t s, const PrecIO<T>& io);
+cudaError_t launch_precond(const Geo& g, const Tables<T>& tb, cudaStream_t s, const PrecIO<T>& io);
 template <typename T>
 int precond_partials(const Geo& g);  // partials of the first / last DST pass
 template <typename T>

@@ -66,6 +66,27 @@ __device__ __forceinline__ double cta_sum_partials(const double* __restrict__ pa
   return t;
 }
 
+// Per-thread accumulator of a CG dot product.  Products and runs of up to
+// 16 terms are summed in the working precision T (GB300 issues FP64 at a
+// small fraction of the FP32 rate, so per-element FP64 work would dominate
+// the FP32 passes); every run is then added into an FP64 sum, and the
+// reduction across threads and CTAs (cta_sum, cta_sum_partials) is FP64.
+template <typename T>
+struct DotAcc {
+  double hi = 0.0;
+  T lo = (T)0;
+  int cnt = 0;
+  __device__ __forceinline__ void add(T v) {
+    lo += v;
+    if (++cnt == 16) {
+      hi += (double)lo;
+      lo = (T)0;
+      cnt = 0;
+    }
+  }
+  __device__ __forceinline__ double value() const { return hi + (double)lo; }
+};
+
 // CTA-wide sum of one value per thread; result valid in thread 0.
 __device__ __forceinline__ double cta_sum(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -104,10 +125,10 @@ template <typename T, int THREADS, int VPT>
 __device__ __forceinline__ void body_rows_fwd(const RowsFwdArgs<T>& a, int bx, int by) {
   typedef typename Cplx<T>::type C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
+  const SBuf<C> buf{reinterpret_cast<C*>(smem_raw)};
   if (a.st && a.st->done) return;
   const int L = 1 << a.lg;
-  const int ls = L + 2;
+  const int ls = L;
   const int NL = (VPT * THREADS) / L;       // complex lines (row pairs) per CTA
   const int pair0 = bx * NL;
   const int npairs = (a.rows + 1) / 2;
@@ -176,7 +197,7 @@ __device__ __forceinline__ void body_rows_fwd(const RowsFwdArgs<T>& a, int bx, i
     typename Cplx<T>::type* __restrict__ Sb =
         hb ? a.S + ((size_t)(rb / a.rows_per_plane) * a.plane_stride + rb % a.rows_per_plane) * a.H
            : nullptr;
-    const C* lb = buf + q * ls;
+    const SBuf<C> lb = buf.at(q * ls);
     for (int k = threadIdx.x; k < a.H; k += THREADS) {
       const C z = lb[k];
       const C w = cconj(lb[(L - k) & (L - 1)]);
@@ -220,7 +241,7 @@ __device__ __forceinline__ void body_cols(const ColsArgs<T>& a, int bx, int by) 
   typedef typename Cplx<T>::type C;
   constexpr int U = 8;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
+  const SBuf<C> buf{reinterpret_cast<C*>(smem_raw)};
   if (a.st && a.st->done) return;
   const int L = 1 << a.lg;
   const int ltx = a.ltx;
@@ -300,11 +321,11 @@ template <typename T, int THREADS, int VPT>
 __device__ __forceinline__ void body_rows_inv(const RowsInvArgs<T>& a, int bx, int by) {
   typedef typename Cplx<T>::type C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
+  const SBuf<C> buf{reinterpret_cast<C*>(smem_raw)};
   __shared__ double red[32];
   if (a.st && a.st->done) return;
   const int L = 1 << a.lg;
-  const int ls = L + 2;
+  const int ls = L;
   const int NL = (VPT * THREADS) / L;
   const int pair0 = bx * NL;
   const int npairs = (a.rows + 1) / 2;
@@ -317,7 +338,7 @@ __device__ __forceinline__ void body_rows_inv(const RowsInvArgs<T>& a, int bx, i
     const typename Cplx<T>::type* __restrict__ Sb =
         hb ? a.S + ((size_t)(rb / a.rows_per_plane) * a.plane_stride + rb % a.rows_per_plane) * a.H
            : nullptr;
-    C* lb = buf + q * ls;
+    const SBuf<C> lb = buf.at(q * ls);
 #pragma unroll 4
     for (int k = threadIdx.x; k < a.H; k += THREADS) {
       const C xa = Sa[k];
@@ -329,34 +350,34 @@ __device__ __forceinline__ void body_rows_inv(const RowsInvArgs<T>& a, int bx, i
   }
   __syncthreads();
   fft_lines<VPT>(buf, a.lg, ls, nl, a.tw, a.lgmax, true);
-  double part = 0.0;
+  DotAcc<T> part;
   const T* __restrict__ xin = (a.cx != 0.0) ? a.x : nullptr;
   const T* __restrict__ bin = (a.cb != 0.0) ? a.b : nullptr;
   const T* __restrict__ win = a.dot_self ? nullptr : a.dotw;
   T* __restrict__ out = a.out;
   float* __restrict__ out32 = a.out32;
+  const T cm = (T)a.cm, cx = (T)a.cx, cb = (T)a.cb;
   for (int q = 0; q < 2 * nl; ++q) {
     const int row = 2 * pair0 + q;
     if (row >= a.rows) break;
     const int half = q & 1;
-    const C* lb = buf + (q >> 1) * ls;
+    const SBuf<C> lb = buf.at((q >> 1) * ls);
     const size_t base = (size_t)row * a.n;
 #pragma unroll 4
     for (int j = threadIdx.x; j < a.n; j += THREADS) {
       const size_t idx = base + j;
       const C z = lb[j];
-      double v = (double)(half ? z.y : z.x) * a.cm;
-      if (xin) v += a.cx * (double)xin[idx];
-      if (bin) v += a.cb * (double)bin[idx];
-      if (a.mask && !a.mask[idx]) v = 0.0;
-      const T tv = (T)v;
-      if (out) out[idx] = tv;
+      T v = (half ? z.y : z.x) * cm;
+      if (xin) v += cx * xin[idx];
+      if (bin) v += cb * bin[idx];
+      if (a.mask && !a.mask[idx]) v = (T)0;
+      if (out) out[idx] = v;
       if (out32) out32[idx] = (float)v;
-      if (a.partials) part += win ? (double)tv * (double)win[idx] : (double)tv * (double)tv;
+      if (a.partials) part.add(win ? v * win[idx] : v * v);
     }
   }
   if (a.partials) {
-    const double s = cta_sum(part, red);
+    const double s = cta_sum(part.value(), red);
     if (threadIdx.x == 0) a.partials[bx] = s;
   }
 }
@@ -369,7 +390,7 @@ __global__ void __launch_bounds__(THREADS) k_rows_inv(RowsInvArgs<T> a) {
 // In place on `nl` lines of length L in shared memory: y = IFFT(FFT(v) * bhat),
 // the chirp-z convolution of the DST-I (bhat already holds the 1/L).
 template <int VPT, typename C>
-__device__ __forceinline__ void chirp_conv(C* buf, int ls, int nl, int L, int lg, int lgmax,
+__device__ __forceinline__ void chirp_conv(SBuf<C> buf, int ls, int nl, int L, int lg, int lgmax,
                                            const C* __restrict__ tw, const C* __restrict__ bhat) {
   fft_lines<VPT>(buf, lg, ls, nl, tw, lgmax, false);
   for (int e = threadIdx.x; e < nl * L; e += blockDim.x) {
@@ -382,7 +403,7 @@ __device__ __forceinline__ void chirp_conv(C* buf, int ls, int nl, int L, int lg
 
 // Interleaved-line version of chirp_conv (element j of line c at j * TX + c).
 template <int VPT, typename C>
-__device__ __forceinline__ void chirp_conv_il(C* buf, int ltx, int L, int lg, int lgmax,
+__device__ __forceinline__ void chirp_conv_il(SBuf<C> buf, int ltx, int L, int lg, int lgmax,
                                               const C* __restrict__ tw, const C* __restrict__ bhat) {
   fft_lines_il<VPT>(buf, lg, ltx, tw, lgmax, false);
   const int total = L << ltx;
@@ -420,16 +441,16 @@ template <typename T, int THREADS, int VPT>
 __device__ __forceinline__ void body_dst_rows(const DstRowsArgs<T>& a, int bx, int by) {
   typedef typename Cplx<T>::type C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
+  const SBuf<C> buf{reinterpret_cast<C*>(smem_raw)};
   __shared__ double red[32];
   __shared__ double s_alpha;
   if (a.st && a.st->done) return;
   const int L = 1 << a.lg;
-  const int ls = L + 2;
+  const int ls = L;
   const int NL = (VPT * THREADS) / L;
   const int row0 = bx * NL;
   const int nl = min(NL, a.rows - row0);
-  double rr = 0.0;
+  DotAcc<T> rr;
   if (a.pre == DPRE_UPDATE) {
     const double pq = cta_sum_partials(a.pq_part, a.pq_count, red);
     if (threadIdx.x == 0) {
@@ -455,7 +476,7 @@ __device__ __forceinline__ void body_dst_rows(const DstRowsArgs<T>& a, int bx, i
         const T rn = rv[idx] - al * qv[idx];
         xv[idx] = xn;
         rv[idx] = rn;
-        rr += (double)rn * (double)rn;
+        rr.add(rn * rn);
         v = cscale(a.chirp[j], rn);
       }
       buf[q * ls + j] = v;
@@ -477,24 +498,25 @@ __device__ __forceinline__ void body_dst_rows(const DstRowsArgs<T>& a, int bx, i
   }
   __syncthreads();
   fft_lines<VPT>(buf, a.lg, ls, nl, a.tw, a.lgmax, true);
-  double dp = 0.0;
+  DotAcc<T> dp;
+  const T post = (T)a.post;
   for (int q = 0; q < nl; ++q) {
-    const C* lb = buf + q * ls;
+    const SBuf<C> lb = buf.at(q * ls);
     const size_t base = (size_t)(row0 + q) * a.n;
 #pragma unroll 4
     for (int k = threadIdx.x; k < a.n; k += THREADS) {
       const C y = cmul(a.chirp[k], lb[k]);
-      const T v = (T)((double)y.y * a.post);
+      const T v = y.y * post;
       a.out[base + k] = v;
-      if (a.dotw) dp += (double)v * (double)a.dotw[base + k];
+      if (a.dotw) dp.add(v * a.dotw[base + k]);
     }
   }
   if (a.pre == DPRE_UPDATE) {
-    const double s = cta_sum(rr, red);
+    const double s = cta_sum(rr.value(), red);
     if (threadIdx.x == 0) a.rr_part[bx] = s;
   }
   if (a.dotw) {
-    const double s = cta_sum(dp, red);
+    const double s = cta_sum(dp.value(), red);
     if (threadIdx.x == 0) a.dot_part[bx] = s;
   }
 }
@@ -518,9 +540,9 @@ struct DstColsArgs {
   const typename Cplx<T>::type* chirp;
   const typename Cplx<T>::type* bhat;
   const PcgState* st;
-  const double* mu_line;   // eigen table of this axis (length n)
-  const double* mu_col;    // eigen table of the column axis
-  const double* mu_outer;  // nullable (2D): eigen table of the outer axis
+  const T* mu_line;        // eigen table of this axis (length n)
+  const T* mu_col;         // eigen table of the column axis
+  const T* mu_outer;       // nullable (2D): eigen table of the outer axis
   double shift, scale, post;
   int n, ncols, lg, lgmax;
   long long ostride, lstride;
@@ -532,7 +554,7 @@ __device__ __forceinline__ void body_dst_cols(const DstColsArgs<T>& a, int bx, i
   typedef typename Cplx<T>::type C;
   constexpr int U = 8;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
+  const SBuf<C> buf{reinterpret_cast<C*>(smem_raw)};
   if (a.st && a.st->done) return;
   const int L = 1 << a.lg;
   const int ltx = a.ltx;
@@ -562,14 +584,15 @@ __device__ __forceinline__ void body_dst_cols(const DstColsArgs<T>& a, int bx, i
   chirp_conv_il<VPT>(buf, ltx, L, a.lg, a.lgmax, a.tw, a.bhat);
   if (a.mode == DST_DIV_DST) {
     // X_k = Im(c_k y_k); divide by the eigenvalue; re-chirp for the second DST
-    const double muo = a.mu_outer ? a.mu_outer[o] : 0.0;
+    const T muo = a.mu_outer ? a.mu_outer[o] : (T)0;
+    const T shift = (T)a.shift, scale = (T)a.scale;
     for (int e = threadIdx.x; e < total; e += THREADS) {
       const int k = e >> ltx, c = e & (TX - 1);
       C val = cmake<C>((T)0, (T)0);
       if (k < a.n && c < ncol) {
         const C y = cmul(a.chirp[k], buf[e]);
-        const double lam = a.shift + a.scale * (a.mu_line[k] + a.mu_col[c0 + c] + muo);
-        val = cscale(a.chirp[k], (T)((double)y.y / lam));
+        const T lam = shift + scale * (a.mu_line[k] + a.mu_col[c0 + c] + muo);
+        val = cscale(a.chirp[k], y.y / lam);
       }
       buf[e] = val;
     }
@@ -577,11 +600,12 @@ __device__ __forceinline__ void body_dst_cols(const DstColsArgs<T>& a, int bx, i
     chirp_conv_il<VPT>(buf, ltx, L, a.lg, a.lgmax, a.tw, a.bhat);
   }
   const int tout = TX * a.n;
+  const T post = (T)a.post;
   for (int e = threadIdx.x; e < tout; e += THREADS) {
     const int r = e >> ltx, c = e & (TX - 1);
     if (c < ncol) {
       const C y = cmul(a.chirp[r], buf[e]);
-      base[(size_t)r * a.lstride + c] = (T)((double)y.y * a.post);
+      base[(size_t)r * a.lstride + c] = y.y * post;
     }
   }
 }
@@ -589,6 +613,192 @@ __device__ __forceinline__ void body_dst_cols(const DstColsArgs<T>& a, int bx, i
 template <typename T, int THREADS, int VPT>
 __global__ void __launch_bounds__(THREADS) k_dst_cols(DstColsArgs<T> a) {
   body_dst_cols<T, THREADS, VPT>(a, blockIdx.x, blockIdx.y);
+}
+
+}  // namespace fl
+
+namespace fl {
+
+// ---------------------------------------------------------------------------
+// Preconditioner solve along axis 0, after the DST-I along the other axes.
+// Mode c of the other axes leaves, along axis 0, the tridiagonal system
+//   (shift + scale mu_c) z_i + scale cA (2 z_i - z_{i-1} - z_{i+1}) = t_i,
+// z_{-1} = z_n = 0 (mu_c: eigenvalue of C h^d L over the other axes, cA =
+// c (-a) the stencil weight), i.e. scale cA T_d z = t with
+// T_d = tridiag(-1, d, -1), d = 2 + e, e = (shift + scale mu_c)/(scale cA).
+// With r = 2 / (d + sqrt(d^2 - 4)) in (0, 1), the root of r^2 - d r + 1 = 0,
+// and S the down-shift,
+//   T_d = (1/r) (I - r S)(I - r S^T) + r e_0 e_0^T,
+// so T_d^{-1} t is two first-order recurrences and a rank-one
+// (Sherman-Morrison) correction:
+//   y_i = t_i + r y_{i-1},  w_i = y_i + r w_{i+1},  x = r w,
+//   z = x - gamma v,  v_i = (r^{i+1} - r^{2n+1-i}) / (1 - r^2),
+//   gamma = r x_0 / (1 + r v_0).
+// This is the same solve the DST-I along axis 0 would give, in O(n) work.
+// Each column runs as kTriSeg segments of m <= kTriM rows, one thread each;
+// the segment carries (factor R = r^m) are chained through shared memory.
+// Per-column constants are formed in FP64 from the working-precision r, so
+// that the correction is consistent with the recurrences actually run.
+constexpr int kTriCols = 8;    // columns per CTA: 32-byte row pieces in FP32
+constexpr int kTriSeg = 32;    // segments per column
+constexpr int kTriM = 32;      // max rows per segment: n <= 1024
+
+template <typename T>
+struct TriArgs {
+  T* v;                  // in: coefficients t; out: z (in place); row stride ncols
+  const PcgState* st;
+  const T* mu_col;       // eigen table of the innermost other axis
+  const T* mu_outer;     // nullable (2D): eigen table of the middle axis
+  double shift, scale, cA;
+  int n;                 // rows along axis 0
+  int ncols;             // columns: product of the other axes
+  int n_inner;           // column c: inner index c % n_inner, outer c / n_inner
+  int m;                 // rows per segment, ceil(n / kTriSeg)
+};
+
+template <typename T>
+__device__ __forceinline__ void body_tri_cols(const TriArgs<T>& a, int bx) {
+  __shared__ T s_e[kTriSeg][kTriCols];    // segment end values, then carries in
+  __shared__ T s_cf[kTriSeg][kTriCols];   // forward carry into each segment
+  __shared__ T s_cb[kTriSeg][kTriCols];   // backward carry into each segment
+  __shared__ T s_p0[kTriSeg][kTriCols];   // r^{s m + 1}
+  __shared__ T s_qe[kTriSeg][kTriCols];   // r^{2n + 2 - (s+1) m}
+  __shared__ T s_r[kTriCols], s_R[kTriCols], s_g[kTriCols];
+  __shared__ double s_d[kTriCols][3];     // FP64: r, log r, 1 - r^2
+  if (a.st && a.st->done) return;
+  const int c = threadIdx.x % kTriCols, s = threadIdx.x / kTriCols;
+  const int col = bx * kTriCols + c;
+  const bool act = col < a.ncols;
+  const int n = a.n, m = a.m, i0 = s * m;
+  const int P = (n + m - 1) / m;
+  T* __restrict__ vc = a.v + col;
+  const size_t ld = (size_t)a.ncols;
+  T y[kTriM];
+#pragma unroll
+  for (int j = 0; j < kTriM; ++j)
+    y[j] = (act && j < m && i0 + j < n) ? vc[(size_t)(i0 + j) * ld] : (T)0;
+  if (s == 0 && act) {
+    const int ci = col % a.n_inner, co = col / a.n_inner;
+    const double mu = (double)a.mu_col[ci] + (a.mu_outer ? (double)a.mu_outer[co] : 0.0);
+    const double e = (a.shift + a.scale * mu) / (a.scale * a.cA);
+    const double dd = 2.0 + e;
+    const T rt = (T)(2.0 / (dd + sqrt(e * (e + 4.0))));
+    const double r = (double)rt;
+    const double lr = log1p(-(1.0 - r));
+    s_r[c] = rt;
+    s_R[c] = (T)exp((double)m * lr);
+    s_d[c][0] = r;
+    s_d[c][1] = lr;
+    s_d[c][2] = (1.0 - r) * (1.0 + r);
+  }
+  __syncthreads();
+  const T r = act ? s_r[c] : (T)0;
+  // forward recurrence within the segment
+  {
+    T acc = (T)0;
+#pragma unroll
+    for (int j = 0; j < kTriM; ++j)
+      if (j < m) {
+        acc = y[j] + r * acc;
+        y[j] = acc;
+      }
+    s_e[s][c] = acc;
+  }
+  __syncthreads();
+  if (s == 0 && act) {
+    const T R = s_R[c];
+    T carry = (T)0;
+    for (int q = 0; q < kTriSeg; ++q) {
+      s_cf[q][c] = carry;
+      carry = s_e[q][c] + R * carry;
+    }
+  }
+  __syncthreads();
+  {
+    const T cin = act ? s_cf[s][c] : (T)0;
+    T pw = r;
+#pragma unroll
+    for (int j = 0; j < kTriM; ++j)
+      if (j < m) {
+        y[j] = (i0 + j < n) ? y[j] + pw * cin : (T)0;
+        pw *= r;
+      }
+  }
+  // backward recurrence within the segment
+  {
+    T acc = (T)0;
+#pragma unroll
+    for (int j = kTriM - 1; j >= 0; --j)
+      if (j < m) {
+        acc = y[j] + r * acc;
+        y[j] = acc;
+      }
+    s_e[s][c] = acc;
+  }
+  __syncthreads();
+  if (s == 0 && act) {
+    const T R = s_R[c];
+    T carry = (T)0;
+    for (int q = kTriSeg - 1; q >= 0; --q) {
+      s_cb[q][c] = carry;
+      carry = s_e[q][c] + R * carry;
+    }
+    // carry = w_0; rank-one correction and the powers of r per segment
+    const double rd = s_d[c][0], lr = s_d[c][1], omr2 = s_d[c][2];
+    const double Rd = exp((double)m * lr);
+    const double v0 = (rd - exp((2.0 * n + 1.0) * lr)) / omr2;
+    const double x0 = rd * (double)carry;
+    const double gam = rd * x0 / (1.0 + rd * v0);
+    s_g[c] = (T)(gam / omr2);
+    double pw = rd;
+    for (int q = 0; q < kTriSeg; ++q) {
+      s_p0[q][c] = (T)pw;
+      pw *= Rd;
+    }
+    double qe = exp((2.0 * n + 2.0 - (double)P * m) * lr);
+    for (int q = kTriSeg - 1; q >= 0; --q) {
+      if (q < P) {
+        s_qe[q][c] = (T)qe;
+        qe *= Rd;
+      } else {
+        s_qe[q][c] = (T)0;
+      }
+    }
+  }
+  __syncthreads();
+  if (!act || i0 >= n) return;
+  const T g = s_g[c];
+  const T inv_sc = (T)(1.0 / (a.scale * a.cA));
+  // z_i = (r w_i - g (r^{i+1} - r^{2n+1-i})) / (scale cA), w_i = w_local + r^{m-j} cin
+  {
+    T p = s_p0[s][c];
+#pragma unroll
+    for (int j = 0; j < kTriM; ++j)
+      if (j < m) {
+        y[j] = r * y[j] - g * p;
+        p *= r;
+      }
+  }
+  {
+    const T cin = s_cb[s][c];
+    T pw = r * r;
+    T qv = s_qe[s][c];
+#pragma unroll
+    for (int j = kTriM - 1; j >= 0; --j)
+      if (j < m) {
+        y[j] = (y[j] + pw * cin + g * qv) * inv_sc;
+        pw *= r;
+        qv *= r;
+      }
+  }
+#pragma unroll
+  for (int j = 0; j < kTriM; ++j)
+    if (j < m && i0 + j < n) vc[(size_t)(i0 + j) * ld] = y[j];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTriCols * kTriSeg) k_tri_cols(TriArgs<T> a) {
+  body_tri_cols<T>(a, blockIdx.x);
 }
 
 }  // namespace fl

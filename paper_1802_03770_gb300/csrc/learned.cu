@@ -419,17 +419,17 @@ __global__ void __launch_bounds__(256) k_combine(const float* __restrict__ r, co
   if (st && st->done) return;
   const double zz = cta_sum_partials(zz_part, zz_count, red);
   const float sz = (float)sqrt(zz / (double)N);
-  double a = 0.0, b = 0.0;
+  DotAcc<float> a, b;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
     const float zo = z[i];
     const float zn = z0[i] + sz * y[i];
     z[i] = zn;
-    a += (double)r[i] * zn;
-    b += (double)r[i] * zo;
+    a.add(r[i] * zn);
+    b.add(r[i] * zo);
   }
-  const double sa = cta_sum(a, red);
-  const double sb = cta_sum(b, red);
+  const double sa = cta_sum(a.value(), red);
+  const double sb = cta_sum(b.value(), red);
   if (threadIdx.x == 0) {
     rz_part[blockIdx.x] = sa;
     if (rzo_part) rzo_part[blockIdx.x] = sb;

@@ -24,15 +24,15 @@ __global__ void __launch_bounds__(kVecThreads) k_noprec_update(PcgState* st, T* 
   }
   __syncthreads();
   const T al = (T)s_alpha;
-  double rr = 0.0;
+  DotAcc<T> rr;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
     x[i] += al * p[i];
     const T rn = r[i] - al * q[i];
     r[i] = rn;
-    rr += (double)rn * (double)rn;
+    rr.add(rn * rn);
   }
-  const double s = cta_sum(rr, red);
+  const double s = cta_sum(rr.value(), red);
   if (threadIdx.x == 0) rr_part[blockIdx.x] = s;
 }
 
@@ -40,11 +40,11 @@ template <typename T>
 __global__ void __launch_bounds__(kVecThreads) k_dot(const T* a, const T* b, double* part,
                                                     long long N) {
   __shared__ double red[32];
-  double v = 0.0;
+  DotAcc<T> v;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x)
-    v += (double)a[i] * (double)b[i];
-  const double s = cta_sum(v, red);
+    v.add(a[i] * b[i]);
+  const double s = cta_sum(v.value(), red);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
@@ -67,14 +67,14 @@ template <typename T>
 __global__ void __launch_bounds__(kVecThreads) k_mask_copy_dot(const T* src, const uint8_t* mask, T* dst,
                                                               double* part, long long N) {
   __shared__ double red[32];
-  double v = 0.0;
+  DotAcc<T> v;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
     const T x = (mask && !mask[i]) ? (T)0 : src[i];
     if (dst) dst[i] = x;
-    v += (double)x * (double)x;
+    v.add(x * x);
   }
-  const double s = cta_sum(v, red);
+  const double s = cta_sum(v.value(), red);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
@@ -183,8 +183,8 @@ template <int THREADS, int VPT>
 __global__ void __launch_bounds__(THREADS) k_rows_c2c(double2* buf, int rows, int lg, int lgmax,
                                                      const double2* tw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* sb = reinterpret_cast<double2*>(smem_raw);
-  const int L = 1 << lg, ls = L + 2;
+  const SBuf<double2> sb{reinterpret_cast<double2*>(smem_raw)};
+  const int L = 1 << lg, ls = L;
   const int NL = (VPT * THREADS) / L;
   const int r0 = blockIdx.x * NL;
   const int nl = min(NL, rows - r0);
@@ -345,17 +345,18 @@ cudaError_t launch_apply(const Geo& g, const Tables<T>& tb, cudaStream_t s, cons
 }
 
 template <typename T>
-PrecChain<T> build_precond(const Geo& g, const Tables<T>& tb, const double* const* mu,
-                           const PrecIO<T>& io) {
+PrecChain<T> build_precond(const Geo& g, const Tables<T>& tb, const PrecIO<T>& io) {
   PrecChain<T> ch;
+  T* const* mu = tb.mu;
   const int d = g.d;
   const int nx = g.n[d - 1], Lx = g.L[d - 1];
   const long long rows = g.N / nx;
   const int NL = row_lines<T>(Lx);
   ch.row_blocks = (int)((rows + NL - 1) / NL);
   ch.row_smem = smem_bytes<T>(NL, Lx);
+  // DST normalisation of every axis but 0 (solved by the tridiagonal pass)
   double post = 1.0;
-  for (int i = 0; i < d; ++i) post *= 2.0 / (g.n[i] + 1.0);
+  for (int i = 1; i < d; ++i) post *= 2.0 / (g.n[i] + 1.0);
   {
     DstRowsArgs<T>& a = ch.first;
     a.in = io.in; a.out = tb.t; a.tw = tb.tw; a.chirp = tb.chirp[d - 1]; a.bhat = tb.bhat[d - 1];
@@ -366,7 +367,7 @@ PrecChain<T> build_precond(const Geo& g, const Tables<T>& tb, const double* cons
   }
   ch.ncols = 0;
   auto cols = [&](int axis, int mode, long long lstride, long long ostride, int nouter,
-                  const double* mu_line, const double* mu_col, const double* mu_outer) {
+                  const T* mu_line, const T* mu_col, const T* mu_outer) {
     DstColsArgs<T>& a = ch.cols[ch.ncols];
     a.v = tb.t; a.tw = tb.tw; a.chirp = tb.chirp[axis]; a.bhat = tb.bhat[axis]; a.st = io.st;
     a.mu_line = mu_line; a.mu_col = mu_col; a.mu_outer = mu_outer;
@@ -380,12 +381,23 @@ PrecChain<T> build_precond(const Geo& g, const Tables<T>& tb, const double* cons
     ch.cols_smem[ch.ncols] = tile_bytes<T>(tx, L);
     ch.ncols++;
   };
+  {
+    TriArgs<T>& a = ch.tri;
+    a.v = tb.t; a.st = io.st;
+    a.mu_col = mu[d - 1]; a.mu_outer = d == 3 ? mu[1] : nullptr;
+    a.shift = io.shift; a.scale = io.scale; a.cA = g.cA;
+    a.n = g.n[0];
+    a.ncols = (int)(g.N / g.n[0]);
+    a.n_inner = nx;
+    a.m = (g.n[0] + kTriSeg - 1) / kTriSeg;
+    ch.tri_blocks = (a.ncols + kTriCols - 1) / kTriCols;
+  }
   if (d == 2) {
-    cols(0, DST_DIV_DST, nx, 0, 1, mu[0], mu[1], nullptr);
+    ch.tri_after = 0;
   } else {
     const long long n1 = g.n[1], n2 = g.n[2];
     cols(1, DST_ONE, n2, n1 * n2, g.n[0], nullptr, nullptr, nullptr);
-    cols(0, DST_DIV_DST, n1 * n2, n2, g.n[1], mu[0], mu[2], mu[1]);
+    ch.tri_after = 1;
     cols(1, DST_ONE, n2, n1 * n2, g.n[0], nullptr, nullptr, nullptr);
   }
   {
@@ -400,17 +412,21 @@ PrecChain<T> build_precond(const Geo& g, const Tables<T>& tb, const double* cons
 }
 
 template <typename T>
-cudaError_t launch_precond(const Geo& g, const Tables<T>& tb, const double* const* mu,
-                           cudaStream_t s, const PrecIO<T>& io) {
+cudaError_t launch_precond(const Geo& g, const Tables<T>& tb, cudaStream_t s, const PrecIO<T>& io) {
   typedef Cfg<T> K;
-  const PrecChain<T> ch = build_precond<T>(g, tb, mu, io);
+  const PrecChain<T> ch = build_precond<T>(g, tb, io);
   FL_KERNEL((sizeof(T) == 4 ? "dst_rows" "<f32>" : "dst_rows" "<f64>"), s,
             k_dst_rows<T, K::RT, K::RV><<<ch.row_blocks, K::RT, ch.row_smem, s>>>(ch.first));
   static const char* const kn[2][2] = {{"dst_cols<f64>", "dst_cols_div<f64>"},
                                        {"dst_cols<f32>", "dst_cols_div<f32>"}};
-  for (int j = 0; j < ch.ncols; ++j)
-    FL_KERNEL(kn[sizeof(T) == 4][ch.cols[j].mode], s,
-              k_dst_cols<T, K::CT, K::CV><<<ch.cols_grid[j], K::CT, ch.cols_smem[j], s>>>(ch.cols[j]));
+  for (int j = 0; j <= ch.ncols; ++j) {
+    if (j == ch.tri_after)
+      FL_KERNEL((sizeof(T) == 4 ? "tri_cols" "<f32>" : "tri_cols" "<f64>"), s,
+                k_tri_cols<T><<<ch.tri_blocks, kTriCols * kTriSeg, 0, s>>>(ch.tri));
+    if (j < ch.ncols)
+      FL_KERNEL(kn[sizeof(T) == 4][ch.cols[j].mode], s,
+                k_dst_cols<T, K::CT, K::CV><<<ch.cols_grid[j], K::CT, ch.cols_smem[j], s>>>(ch.cols[j]));
+  }
   FL_KERNEL((sizeof(T) == 4 ? "dst_rows" "<f32>" : "dst_rows" "<f64>"), s,
             k_dst_rows<T, K::RT, K::RV><<<ch.row_blocks, K::RT, ch.row_smem, s>>>(ch.last));
   return cudaGetLastError();
@@ -545,14 +561,14 @@ template cudaError_t launch_apply<float>(const Geo&, const Tables<float>&, cudaS
 template cudaError_t launch_apply<double>(const Geo&, const Tables<double>&, cudaStream_t, const ApplyIO<double>&);
 template ApplyChain<float> build_apply<float>(const Geo&, const Tables<float>&, const ApplyIO<float>&);
 template ApplyChain<double> build_apply<double>(const Geo&, const Tables<double>&, const ApplyIO<double>&);
-template PrecChain<float> build_precond<float>(const Geo&, const Tables<float>&, const double* const*, const PrecIO<float>&);
-template PrecChain<double> build_precond<double>(const Geo&, const Tables<double>&, const double* const*, const PrecIO<double>&);
+template PrecChain<float> build_precond<float>(const Geo&, const Tables<float>&, const PrecIO<float>&);
+template PrecChain<double> build_precond<double>(const Geo&, const Tables<double>&, const PrecIO<double>&);
 template int apply_partials<float>(const Geo&);
 template int apply_partials<double>(const Geo&);
 template int precond_partials<float>(const Geo&);
 template int precond_partials<double>(const Geo&);
-template cudaError_t launch_precond<float>(const Geo&, const Tables<float>&, const double* const*, cudaStream_t, const PrecIO<float>&);
-template cudaError_t launch_precond<double>(const Geo&, const Tables<double>&, const double* const*, cudaStream_t, const PrecIO<double>&);
+template cudaError_t launch_precond<float>(const Geo&, const Tables<float>&, cudaStream_t, const PrecIO<float>&);
+template cudaError_t launch_precond<double>(const Geo&, const Tables<double>&, cudaStream_t, const PrecIO<double>&);
 template cudaError_t launch_noprec_update<float>(long long, cudaStream_t, PcgState*, float*, float*, const float*, const float*, const double*, int, double*, int*);
 template cudaError_t launch_noprec_update<double>(long long, cudaStream_t, PcgState*, double*, double*, const double*, const double*, const double*, int, double*, int*);
 template cudaError_t launch_dot<float>(long long, cudaStream_t, const float*, const float*, double*, int*);

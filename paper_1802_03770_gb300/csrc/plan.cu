@@ -113,7 +113,6 @@ struct fl_plan {
   uint8_t* mask = nullptr;
   Tables<float> t32;
   Tables<double> t64;
-  double* mu[3] = {nullptr, nullptr, nullptr};
   Vecs<float> v32;
   Vecs<double> v64;
   double* part[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -250,8 +249,11 @@ fl_status build_tables(fl_plan* p) {
       const long double s = sinl(pi * (long double)(k + 1) / (2.0L * (long double)N1));
       mu[k] = (double)((long double)p->c * (long double)(-p->a) * 4.0L * s * s);
     }
-    FL_CUDA(dalloc(p, &p->mu[ax], n * sizeof(double)));
-    FL_CUDA(cudaMemcpy(p->mu[ax], mu.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    std::vector<float> mu32(mu.begin(), mu.end());
+    FL_CUDA(dalloc(p, &p->t64.mu[ax], n * sizeof(double)));
+    FL_CUDA(dalloc(p, &p->t32.mu[ax], n * sizeof(float)));
+    FL_CUDA(cudaMemcpy(p->t64.mu[ax], mu.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    FL_CUDA(cudaMemcpy(p->t32.mu[ax], mu32.data(), n * sizeof(float), cudaMemcpyHostToDevice));
   }
   return FL_OK;
 }
@@ -318,7 +320,7 @@ fl_status run_pcg(fl_plan* p, bool x0_nonzero, double shift, double scale, bool 
     PrecIO<T> io;
     io.in = v.r; io.out = v.z; io.shift = shift; io.scale = scale;
     io.dotw = v.r; io.dot_part = p->part[P_RZ];
-    FL_CUDA(launch_precond<T>(g, tb, p->mu, s, io));
+    FL_CUDA(launch_precond<T>(g, tb, s, io));
     rz_count = precond_partials<T>(g);
   } else {
     FL_CUDA(launch_dot<T>(g.N, s, v.r, v.r, p->part[P_RZ], &rz_count));
@@ -349,7 +351,7 @@ fl_status run_pcg(fl_plan* p, bool x0_nonzero, double shift, double scale, bool 
       pi.x = v.x; pi.r = v.r; pi.p = v.p; pi.q = v.q;
       pi.pq_part = p->part[P_PQ]; pi.pq_count = pq_count; pi.rr_part = p->part[P_RR];
       pi.dotw = v.r; pi.dot_part = p->part[P_RZ]; pi.st = p->st;
-      e = launch_precond<T>(g, tb, p->mu, qs, pi);
+      e = launch_precond<T>(g, tb, qs, pi);
       if (e != cudaSuccess) return e;
       return launch_pcg_scalar(qs, p->st, p->part[P_RR], it_rr, p->part[P_RZ], it_rr);
     }
@@ -450,7 +452,7 @@ fl_status run_fpcg_learned(fl_plan* p, double shift, double scale, double tol, i
       PrecIO<float> io;
       io.in = v.r; io.out = p->z0; io.shift = shift; io.scale = scale;
       io.st = const_cast<PcgState*>(st);
-      e = launch_precond<float>(g, p->t32, p->mu, s, io);
+      e = launch_precond<float>(g, p->t32, s, io);
     } else {
       e = launch_scale(v.r, p->z0, jac, g.N, st, s);
     }
@@ -682,6 +684,7 @@ fl_status fl_plan_create(int d, const int64_t* n, double h, double alpha, const 
   p->Z = lattice_zeta(d, alpha);
   p->a = window_corr(d, alpha, p->rho);
   p->c = p->C * std::pow(h, -alpha);
+  g.cA = p->c * (-p->a);
   fl_status st = FL_OK;
   cudaError_t e = configure_kernels();
   if (e != cudaSuccess) { free_plan(p); return cuda_fail(e, "configure_kernels"); }
@@ -777,9 +780,11 @@ fl_status fl_precond(fl_plan* p, double shift, double scale, const double* r, do
   if (!check_plan(p) || !r || !z) return fail(FL_INVALID_ARG, "NULL argument");
   if (r == z) return fail(FL_INVALID_ARG, "r and z may not alias");
   if (p->has_mask) return fail(FL_INVALID_ARG, "the sine-transform preconditioner needs a plan without mask");
+  if (!(scale > 0.0) || !(shift >= 0.0) || !std::isfinite(scale) || !std::isfinite(shift))
+    return fail(FL_INVALID_ARG, "the preconditioner needs shift >= 0 and scale > 0");
   PrecIO<double> io;
   io.in = r; io.out = z; io.shift = shift; io.scale = scale;
-  FL_CUDA(launch_precond<double>(p->g, p->t64, p->mu, p->stream, io));
+  FL_CUDA(launch_precond<double>(p->g, p->t64, p->stream, io));
   return FL_OK;
 }
 
@@ -788,9 +793,11 @@ fl_status fl_precond_f32(fl_plan* p, double shift, double scale, const float* r,
   if (!check_plan(p) || !r || !z) return fail(FL_INVALID_ARG, "NULL argument");
   if (r == z) return fail(FL_INVALID_ARG, "r and z may not alias");
   if (p->has_mask) return fail(FL_INVALID_ARG, "the sine-transform preconditioner needs a plan without mask");
+  if (!(scale > 0.0) || !(shift >= 0.0) || !std::isfinite(scale) || !std::isfinite(shift))
+    return fail(FL_INVALID_ARG, "the preconditioner needs shift >= 0 and scale > 0");
   PrecIO<float> io;
   io.in = r; io.out = z; io.shift = shift; io.scale = scale;
-  FL_CUDA(launch_precond<float>(p->g, p->t32, p->mu, p->stream, io));
+  FL_CUDA(launch_precond<float>(p->g, p->t32, p->stream, io));
   return FL_OK;
 }
 
@@ -1008,13 +1015,18 @@ template <typename T>
 struct PrecSets {
   PassSet<DstRowsArgs<T>> first;
   PassSet<DstColsArgs<T>> cols[3];
+  PassSet<TriArgs<T>> tri;
   PassSet<DstRowsArgs<T>> last;
+  int ncols = 0, tri_after = 0;
   void add(const PrecChain<T>& ch) {
     first.add(ch.first, ch.row_blocks, ch.row_blocks, ch.row_smem);
     for (int j = 0; j < ch.ncols; ++j)
       cols[j].add(ch.cols[j], (int)(ch.cols_grid[j].x * ch.cols_grid[j].y), (int)ch.cols_grid[j].x,
                   ch.cols_smem[j]);
+    tri.add(ch.tri, ch.tri_blocks, ch.tri_blocks, 0);
     last.add(ch.last, ch.row_blocks, ch.row_blocks, ch.row_smem);
+    ncols = ch.ncols;          // the same for every problem of one dimension
+    tri_after = ch.tri_after;
   }
 };
 
@@ -1038,17 +1050,22 @@ struct ChainPasses {
 
 template <typename T>
 struct PrecPasses {
-  BatchPass first, cols[3], last;
-  int ncols = 0;
-  void upload(DevArena& ar, PrecSets<T>& ps, int ncols_) {
-    ncols = ncols_;
+  BatchPass first, cols[3], tri, last;
+  int ncols = 0, tri_after = 0;
+  void upload(DevArena& ar, PrecSets<T>& ps) {
+    ncols = ps.ncols;
+    tri_after = ps.tri_after;
     first = ps.first.upload(ar, BK_DST_ROWS);
     for (int j = 0; j < ncols; ++j) cols[j] = ps.cols[j].upload(ar, BK_DST_COLS);
+    tri = ps.tri.upload(ar, BK_TRI_COLS);
     last = ps.last.upload(ar, BK_DST_ROWS);
   }
   cudaError_t launch(cudaStream_t s) const {
     cudaError_t e = launch_batched<T>(first, s);
-    for (int j = 0; j < ncols && e == cudaSuccess; ++j) e = launch_batched<T>(cols[j], s);
+    for (int j = 0; j <= ncols && e == cudaSuccess; ++j) {
+      if (j == tri_after) e = launch_batched<T>(tri, s);
+      if (j < ncols && e == cudaSuccess) e = launch_batched<T>(cols[j], s);
+    }
     if (e == cudaSuccess) e = launch_batched<T>(last, s);
     return e;
   }
@@ -1104,7 +1121,7 @@ fl_status solve_batched_mixed(fl_plan* const* plans, int count, const double* co
       PrecIO<float> pi;
       pi.in = p->v32.r; pi.out = p->v32.z; pi.dotw = p->v32.r; pi.dot_part = p->part[P_RZ];
       pi.st = const_cast<PcgState*>(gate);
-      pinit.add(build_precond<float>(g, p->t32, p->mu, pi));
+      pinit.add(build_precond<float>(g, p->t32, pi));
     }
     init[i] = BScalarArgs{st, gate, p->part[P_BB], vb, nullptr, 0,
                           prec[i] ? p->part[P_RZ] : p->part[P_BB], prec[i] ? pcount : vb,
@@ -1121,7 +1138,7 @@ fl_status solve_batched_mixed(fl_plan* const* plans, int count, const double* co
       pu.pre = DPRE_UPDATE; pu.out = p->v32.z; pu.x = p->v32.x; pu.r = p->v32.r; pu.p = p->v32.p;
       pu.q = p->v32.q; pu.pq_part = p->part[P_PQ]; pu.pq_count = pq_count;
       pu.rr_part = p->part[P_RR]; pu.dotw = p->v32.r; pu.dot_part = p->part[P_RZ]; pu.st = st;
-      pstep.add(build_precond<float>(g, p->t32, p->mu, pu));
+      pstep.add(build_precond<float>(g, p->t32, pu));
       step[i] = BScalarArgs{st, gate, nullptr, 0, p->part[P_RR], pcount, p->part[P_RZ], pcount,
                             tol_dev + i, maxit};
     } else {
@@ -1146,8 +1163,8 @@ fl_status solve_batched_mixed(fl_plan* const* plans, int count, const double* co
   BatchPass START = start.upload(ar, BK_CG_START);
   BatchPass NOPREC = noprec.upload(ar, BK_NOPREC);
   PrecPasses<float> PI, PS;
-  PI.upload(ar, pinit, ncols);
-  PS.upload(ar, pstep, ncols);
+  PI.upload(ar, pinit);
+  PS.upload(ar, pstep);
   ChainPasses<float> A32;
   A32.upload(ar, apply32, ncols);
   if (ar.err != cudaSuccess) return cuda_fail(ar.err, "batched argument upload");

@@ -115,7 +115,8 @@ def test_plan_constants_match_oracle():
 
 
 @pytest.mark.parametrize("d,n", [(2, (64, 64)), (2, (37, 53)), (2, (1, 6)), (3, (12, 9, 17)),
-                                 (3, (33, 20, 31))])
+                                 (3, (33, 20, 31)), (2, (1024, 1024)), (2, (1000, 333)),
+                                 (3, (97, 8, 40))])
 @pytest.mark.parametrize("shift,scale", [(0.0, 1.0), (1.0, 2e-3)])
 def test_precond_matches_oracle(d, n, shift, scale):
     h = 1.0 / (max(n) + 1)
@@ -183,6 +184,14 @@ def test_solve_masked_plain_cg():
     u = host(u)
     assert np.all(u[~mask] == 0.0)
     assert rel(op.apply(u), f) <= 1.05e-9
+
+
+def test_precond_rejects_nonpositive_scale():
+    p = Plan(2, (16, 16), 0.05, 1.5)
+    r = gpu(np.ones((16, 16)))
+    for shift, scale in [(1.0, 0.0), (0.0, -1.0), (-1.0, 1.0)]:
+        with pytest.raises(_lib.FracLapError, match="INVALID_ARG"):
+            p.precond(r, shift, scale)
 
 
 def test_preconditioned_solve_on_masked_plan_is_rejected():
