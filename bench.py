@@ -114,8 +114,10 @@ def algorithmic_bytes(name, n, L, elem):
         "rows_fwd": 3 * real + spec,             # z, p in; p out; spectrum out
         "cols_conv": 2 * spec + (L // 2 + 1) * H * elem,
         "rows_inv": spec + 2 * real,             # spectrum, p in; q out
-        "dst_rows": 7 * real,                    # x, r, p, q in; x, r, t out
-        "dst_cols_div": 2 * real,
+        # one CG iteration launches it twice: x, r, p, q in and x, r, t out
+        # (with the CG update), then t, r in and z out: 10 N values per pair
+        "dst_rows": 5 * real,
+        "tri_cols": 2 * real,                    # t in, z out
         "dst_cols": 2 * real,
     }
     base = name.split("<")[0]

@@ -27,7 +27,7 @@ __device__ __forceinline__ int batch_problem(const int* __restrict__ off, int np
 
 #define FL_BATCHED_KERNEL(NAME, ARGS)                                                          \
   template <typename T, int THREADS, int VPT>                                                  \
-  __global__ void __launch_bounds__(THREADS)                                                   \
+  __global__ void __launch_bounds__(THREADS, min_ctas(THREADS))                               \
       kb_##NAME(const ARGS<T>* __restrict__ args, const int* __restrict__ off,                 \
                 const int* __restrict__ gx, int nprob) {                                       \
     const int i = batch_problem(off, nprob);                                                   \
@@ -74,32 +74,23 @@ __global__ void __launch_bounds__(kVecThreads) kb_cg_start(const BVecArgs<T>* __
     a.p[k] = (T)0;
     v.add(bv * bv);
   }
-  const double s = cta_sum(v.value(), red);
+  const double s = v.cta_total(red);
   if (threadIdx.x == 0) a.part[bx] = s;
 }
 
-// CG update without preconditioner: alpha = rz / pq, x += alpha p,
-// r -= alpha q, partials of ||r||^2 (z aliases r).
+// CG update without preconditioner (z aliases r): x += alpha p, r -= alpha q
+// with alpha from the state (set by the apply's last CTA), partials of
+// ||r||^2; the last CTA of the problem takes the CG scalar step.
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads) kb_noprec_update(const BVecArgs<T>* __restrict__ args,
                                                                const int* __restrict__ off, int nprob) {
   __shared__ double red[32];
-  __shared__ double s_alpha;
   const int i = batch_problem(off, nprob);
   const BVecArgs<T> a = args[i];
   const int bx = blockIdx.x - off[i];
   const int gx = off[i + 1] - off[i];
   if (a.st->done) return;
-  const double pq = cta_sum_partials(a.pq_part, a.pq_count, red);
-  if (threadIdx.x == 0) {
-    s_alpha = a.st->rz / pq;
-    if (bx == 0) {
-      a.st->pq = pq;
-      a.st->alpha = s_alpha;
-    }
-  }
-  __syncthreads();
-  const T al = (T)s_alpha;
+  const T al = (T)a.st->alpha;
   DotAcc<T> rr;
   for (long long k = (long long)bx * blockDim.x + threadIdx.x; k < a.N;
        k += (long long)gx * blockDim.x) {
@@ -108,8 +99,12 @@ __global__ void __launch_bounds__(kVecThreads) kb_noprec_update(const BVecArgs<T
     a.r[k] = rn;
     rr.add(rn * rn);
   }
-  const double s = cta_sum(rr.value(), red);
+  const double s = rr.cta_total(red);
   if (threadIdx.x == 0) a.part[bx] = s;
+  if (arrive_last(&a.st->arrive, gx)) {
+    const double rrv = cta_sum_partials(a.part, gx, red);
+    if (threadIdx.x == 0) pcg_step(a.st, rrv, rrv);
+  }
 }
 
 // FP64 right-hand side to the FP32 inner right-hand side (masked), with
@@ -154,39 +149,9 @@ __global__ void kb_pcg_init(const BScalarArgs* __restrict__ args, int nprob) {
     st->it = 0;
     st->maxit = a.maxit;
     st->status = 0;
+    st->arrive = 0u;
     st->done = (bb == 0.0 || (a.gate && a.gate->done)) ? 1 : 0;
     if (!(rz > 0.0) && !st->done) { st->done = 1; st->status = 3; }
-  }
-}
-
-// One CTA per problem: the CG scalar step (as k_pcg_scalar).
-__global__ void kb_pcg_scalar(const BScalarArgs* __restrict__ args, int nprob) {
-  __shared__ double red[32];
-  const BScalarArgs a = args[blockIdx.x];
-  PcgState* st = a.st;
-  if (st->done) return;
-  const double rr = cta_sum_partials(a.rr_part, a.rr_count, red);
-  const double rz = cta_sum_partials(a.rz_part, a.rz_count, red);
-  if (threadIdx.x == 0) {
-    st->it += 1;
-    st->rr = rr;
-    const double pq = st->pq;
-    if (!(pq > 0.0) || rr != rr || rz != rz) {
-      st->done = 1;
-      st->status = 3;
-    } else if (rr <= st->tol2) {
-      st->done = 1;
-      st->status = 0;
-    } else if (st->it >= st->maxit) {
-      st->done = 1;
-      st->status = 2;
-    } else if (!(rz > 0.0)) {
-      st->done = 1;
-      st->status = 3;
-    } else {
-      st->beta = rz / st->rz;
-      st->rz = rz;
-    }
   }
 }
 
@@ -265,8 +230,6 @@ cudaError_t launch_batched_scalar(int which, const BScalarArgs* args, double* ou
   if (nprob == 0) return cudaSuccess;
   if (which == 0)
     FL_KERNEL("b_pcg_init", s, kb_pcg_init<<<nprob, 256, 0, s>>>(args, nprob));
-  else if (which == 1)
-    FL_KERNEL("b_pcg_scalar", s, kb_pcg_scalar<<<nprob, 256, 0, s>>>(args, nprob));
   else
     FL_KERNEL("b_sum", s, kb_sum<<<nprob, 256, 0, s>>>(args, out, nprob));
   return cudaGetLastError();

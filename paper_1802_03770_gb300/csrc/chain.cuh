@@ -93,8 +93,6 @@ struct BVecArgs {
   T* p;
   const T* q;
   const uint8_t* mask;
-  const double* pq_part;
-  int pq_count;
   double* part;              // per-CTA partials written by the kernel
   long long N;
 };
@@ -131,7 +129,7 @@ struct BatchPass {
 template <typename T>
 cudaError_t launch_batched(const BatchPass& bp, cudaStream_t s);
 cudaError_t launch_cast_rhs(const BatchPass& bp, float* const* out32, cudaStream_t s);
-// which: 0 = CG start-up scalars, 1 = CG scalar step, 2 = sums into out
+// which: 0 = CG start-up scalars, 2 = sums into out
 cudaError_t launch_batched_scalar(int which, const BScalarArgs* args, double* out, int nprob,
                                   cudaStream_t s);
 cudaError_t configure_batched_kernels();

@@ -64,6 +64,7 @@ struct ApplyIO {
   const T* dotw = nullptr;
   double* partials = nullptr;
   int dot_self = 0;
+  int fin = 0;                // FIN_PQ: the last CTA sets st->pq and st->alpha
 };
 
 // Inputs and outputs of one preconditioner solve.
@@ -74,10 +75,10 @@ struct PrecIO {
   T* out = nullptr;
   double shift = 0.0, scale = 1.0;
   T* x = nullptr; T* r = nullptr; const T* p = nullptr; const T* q = nullptr;
-  const double* pq_part = nullptr; int pq_count = 0;
   double* rr_part = nullptr;
   const T* dotw = nullptr; double* dot_part = nullptr;
   PcgState* st = nullptr;
+  int fin = 0;                // FIN_STEP: the last pass ends with the CG scalar step
 };
 
 // --- ops.cu: launchers (return the first CUDA error) --------------------------
@@ -91,8 +92,7 @@ template <typename T>
 int precond_partials(const Geo& g);  // partials of the first / last DST pass
 template <typename T>
 cudaError_t launch_noprec_update(long long N, cudaStream_t s, PcgState* st, T* x, T* r,
-                                 const T* p, const T* q, const double* pq_part, int pq_count,
-                                 double* rr_part, int* count);
+                                 const T* p, const T* q, double* rr_part, int step, int* count);
 template <typename T>
 cudaError_t launch_dot(long long N, cudaStream_t s, const T* a, const T* b, double* part,
                        int* count);

@@ -26,6 +26,10 @@
 
 #include "fft_core.cuh"
 
+#ifndef FL_ROW_MIN_CTAS
+#define FL_ROW_MIN_CTAS 7
+#endif
+
 namespace fl {
 
 // Device-resident state of one CG solve (all reductions in FP64).
@@ -35,26 +39,45 @@ struct PcgState {
   double tol2;     // tol^2 ||b||^2
   double rr;       // ||r||^2 of the current iterate
   double beta;     // p = z + beta p for the next iteration
-  double alpha;    // last step length
-  double pq;       // last p^T A p
+  double alpha;    // step length of the current iteration, rz / pq
+  double pq;       // p^T A p of the current iteration
   int it;          // iterations done
   int maxit;
   int done;        // 1: stop (converged, failed or hit maxit)
   int status;      // 0 ok/converged, 2 not converged, 3 breakdown
+  unsigned int arrive;  // CTAs of the current pass that stored their partial
 };
 
 enum { PRE_NONE = 0, PRE_PUPDATE = 1, PRE_ACCUM = 2 };
 enum { COLS_FWD = 0, COLS_CONV = 1, COLS_INV = 2, COLS_FULL = 3 };
-enum { DST_ONE = 0, DST_DIV_DST = 1 };
 enum { DPRE_NONE = 0, DPRE_UPDATE = 1 };
+// What the last CTA of a pass does with the pass's partial sums:
+// FIN_PQ: pq = sum, alpha = rz / pq; FIN_STEP: the CG scalar step.
+enum { FIN_NONE = 0, FIN_PQ = 1, FIN_STEP = 2 };
 
 // Sum `count` per-CTA partials in a fixed order (deterministic); every
-// thread of the CTA gets the result.  Uses `red` (>= 32 doubles) of shared
-// memory.
+// thread of the CTA gets the result.  The loads bypass L1, so partials
+// stored by other CTAs of the running grid are seen (after arrive_last).
+// Uses `red` (>= 32 doubles) of shared memory.
+__device__ __forceinline__ double thread_sum_partials(const double* __restrict__ part, int count) {
+  // eight loads in flight per thread, then the adds (fixed order)
+  double s = 0.0;
+  const int nt = blockDim.x;
+  int i = threadIdx.x;
+  for (; i + 7 * nt < count; i += 8 * nt) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = __ldcg(part + i + u * nt);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s += v[u];
+  }
+  for (; i < count; i += nt) s += __ldcg(part + i);
+  return s;
+}
+
 __device__ __forceinline__ double cta_sum_partials(const double* __restrict__ part, int count,
                                                    double* red) {
-  double s = 0.0;
-  for (int i = threadIdx.x; i < count; i += blockDim.x) s += part[i];
+  double s = thread_sum_partials(part, count);
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   __syncthreads();
@@ -66,26 +89,11 @@ __device__ __forceinline__ double cta_sum_partials(const double* __restrict__ pa
   return t;
 }
 
-// Per-thread accumulator of a CG dot product.  Products and runs of up to
-// 16 terms are summed in the working precision T (GB300 issues FP64 at a
-// small fraction of the FP32 rate, so per-element FP64 work would dominate
-// the FP32 passes); every run is then added into an FP64 sum, and the
-// reduction across threads and CTAs (cta_sum, cta_sum_partials) is FP64.
-template <typename T>
-struct DotAcc {
-  double hi = 0.0;
-  T lo = (T)0;
-  int cnt = 0;
-  __device__ __forceinline__ void add(T v) {
-    lo += v;
-    if (++cnt == 16) {
-      hi += (double)lo;
-      lo = (T)0;
-      cnt = 0;
-    }
-  }
-  __device__ __forceinline__ double value() const { return hi + (double)lo; }
-};
+// Minimum resident CTAs per SM asked of the compiler for a pass kernel of
+// THREADS threads.  The passes are latency-bound: the 128-thread FP32 row
+// passes keep at least 7 CTAs (28 warps) per SM (<= 73 registers), the
+// 256- and 512-thread passes at least 2 CTAs.
+constexpr int min_ctas(int threads) { return threads <= 128 ? FL_ROW_MIN_CTAS : 2; }
 
 // CTA-wide sum of one value per thread; result valid in thread 0.
 __device__ __forceinline__ double cta_sum(double v, double* red) {
@@ -99,6 +107,113 @@ __device__ __forceinline__ double cta_sum(double v, double* red) {
     for (int i = 0; i < nw; ++i) t += red[i];
   __syncthreads();
   return t;
+}
+
+// s + e == a + b exactly (Knuth's two-sum, round-to-nearest adds).
+__device__ __forceinline__ float two_sum(float a, float b, float& e) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return s;
+}
+
+// CTA-wide sum of one float-float value (hi + lo) per thread: the warp tree
+// in float-float arithmetic, then FP64 across warps; valid in thread 0.
+__device__ __forceinline__ double cta_sum_ff(float hi, float lo, double* red) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    float e;
+    const float s = two_sum(hi, h2, e);
+    const float t = __fadd_rn(__fadd_rn(lo, l2), e);
+    hi = __fadd_rn(s, t);
+    lo = __fsub_rn(t, __fsub_rn(hi, s));
+  }
+  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[w] = (double)hi + (double)lo;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < nw; ++i) t += red[i];
+  __syncthreads();
+  return t;
+}
+
+// Per-thread accumulator of a CG dot product.  GB300 issues FP64 at a small
+// fraction of the FP32 rate, so the FP32 passes keep FP64 off the per-element
+// path: products and runs of up to 16 terms are summed in FP32, each run is
+// added into a float-float (two-sum) total, the warp tree is float-float
+// and the sums across warps and CTAs are FP64.  FP64 passes accumulate in
+// FP64 throughout.
+template <typename T>
+struct DotAcc {
+  double acc = 0.0;
+  __device__ __forceinline__ void add(double v) { acc += v; }
+  // CTA total, valid in thread 0
+  __device__ __forceinline__ double cta_total(double* red) const { return cta_sum(acc, red); }
+};
+template <>
+struct DotAcc<float> {
+  float hi = 0.f, lo = 0.f, run = 0.f;
+  int cnt = 0;
+  __device__ __forceinline__ void add(float v) {
+    run += v;
+    if (++cnt == 16) flush();
+  }
+  __device__ __forceinline__ void flush() {
+    float e;
+    hi = two_sum(hi, run, e);
+    lo = __fadd_rn(lo, e);
+    run = 0.f;
+    cnt = 0;
+  }
+  __device__ __forceinline__ double cta_total(double* red) {
+    flush();
+    return cta_sum_ff(hi, lo, red);
+  }
+};
+
+// Every CTA of a pass calls this once, after its partial is stored; it
+// returns true (in all threads) in the CTA that arrives last, which may
+// then read every partial of the pass.  That CTA also resets the counter
+// for the next pass.  No CTA waits for another.
+__device__ __forceinline__ bool arrive_last(unsigned int* ctr, int nctas) {
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int t = atomicAdd(ctr, 1u);
+    s_last = (t + 1u == (unsigned int)nctas) ? 1 : 0;
+    if (s_last) *ctr = 0u;
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last != 0;
+}
+
+// The CG scalar step after an iteration (one thread): iteration count,
+// convergence and breakdown tests, beta.
+__device__ __forceinline__ void pcg_step(PcgState* st, double rr, double rz) {
+  st->it += 1;
+  st->rr = rr;
+  const double pq = st->pq;
+  if (!(pq > 0.0) || rr != rr || rz != rz) {
+    st->done = 1;
+    st->status = 3;
+  } else if (rr <= st->tol2) {
+    st->done = 1;
+    st->status = 0;
+  } else if (st->it >= st->maxit) {
+    st->done = 1;
+    st->status = 2;
+  } else if (!(rz > 0.0)) {
+    st->done = 1;
+    st->status = 3;
+  } else {
+    st->beta = rz / st->rz;
+    st->rz = rz;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -208,7 +323,7 @@ __device__ __forceinline__ void body_rows_fwd(const RowsFwdArgs<T>& a, int bx, i
 }
 
 template <typename T, int THREADS, int VPT>
-__global__ void __launch_bounds__(THREADS) k_rows_fwd(RowsFwdArgs<T> a) {
+__global__ void __launch_bounds__(THREADS, min_ctas(THREADS)) k_rows_fwd(RowsFwdArgs<T> a) {
   body_rows_fwd<T, THREADS, VPT>(a, blockIdx.x, blockIdx.y);
 }
 
@@ -289,7 +404,7 @@ __device__ __forceinline__ void body_cols(const ColsArgs<T>& a, int bx, int by) 
 }
 
 template <typename T, int THREADS, int VPT>
-__global__ void __launch_bounds__(THREADS) k_cols(ColsArgs<T> a) {
+__global__ void __launch_bounds__(THREADS, min_ctas(THREADS)) k_cols(ColsArgs<T> a) {
   body_cols<T, THREADS, VPT>(a, blockIdx.x, blockIdx.y);
 }
 
@@ -315,6 +430,9 @@ struct RowsInvArgs {
   int rows, n, H, lg, lgmax;
   int rows_per_plane, plane_stride;
   int dot_self;            // 1: partial = sum out^2
+  int fin;                 // FIN_NONE or FIN_PQ (the last CTA sets fst->pq, fst->alpha)
+  int nparts;              // CTAs of the pass (partials to sum)
+  PcgState* fst;
 };
 
 template <typename T, int THREADS, int VPT>
@@ -377,13 +495,20 @@ __device__ __forceinline__ void body_rows_inv(const RowsInvArgs<T>& a, int bx, i
     }
   }
   if (a.partials) {
-    const double s = cta_sum(part.value(), red);
+    const double s = part.cta_total(red);
     if (threadIdx.x == 0) a.partials[bx] = s;
+    if (a.fin == FIN_PQ && arrive_last(&a.fst->arrive, a.nparts)) {
+      const double pq = cta_sum_partials(a.partials, a.nparts, red);
+      if (threadIdx.x == 0) {
+        a.fst->pq = pq;
+        a.fst->alpha = a.fst->rz / pq;
+      }
+    }
   }
 }
 
 template <typename T, int THREADS, int VPT>
-__global__ void __launch_bounds__(THREADS) k_rows_inv(RowsInvArgs<T> a) {
+__global__ void __launch_bounds__(THREADS, min_ctas(THREADS)) k_rows_inv(RowsInvArgs<T> a) {
   body_rows_inv<T, THREADS, VPT>(a, blockIdx.x, blockIdx.y);
 }
 
@@ -426,15 +551,19 @@ struct DstRowsArgs {
   const typename Cplx<T>::type* tw;
   const typename Cplx<T>::type* chirp;   // c_{j+1}, j = 0..n-1
   const typename Cplx<T>::type* bhat;    // FFT_L of conj(c_m) embedded circularly, / L
-  PcgState* st;            // DPRE_UPDATE: CTA 0 records pq and alpha
+  PcgState* st;            // DPRE_UPDATE: alpha from here; FIN_STEP: updated
   // DPRE_UPDATE
   T* x; T* r; const T* p; const T* q;
-  const double* pq_part; int pq_count;
   double* rr_part;         // per-CTA ||r||^2 (after update)
   const T* dotw; double* dot_part;
   double post;
   int rows, n, lg, lgmax;
   int pre;
+  // FIN_STEP (with dotw = r): the last CTA sums rr_in (rr_count partials of
+  // the DPRE_UPDATE pass) and its own r.z partials and takes the CG step
+  int fin;
+  int nparts;
+  const double* rr_in; int rr_count;
 };
 
 template <typename T, int THREADS, int VPT>
@@ -443,7 +572,6 @@ __device__ __forceinline__ void body_dst_rows(const DstRowsArgs<T>& a, int bx, i
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SBuf<C> buf{reinterpret_cast<C*>(smem_raw)};
   __shared__ double red[32];
-  __shared__ double s_alpha;
   if (a.st && a.st->done) return;
   const int L = 1 << a.lg;
   const int ls = L;
@@ -452,16 +580,7 @@ __device__ __forceinline__ void body_dst_rows(const DstRowsArgs<T>& a, int bx, i
   const int nl = min(NL, a.rows - row0);
   DotAcc<T> rr;
   if (a.pre == DPRE_UPDATE) {
-    const double pq = cta_sum_partials(a.pq_part, a.pq_count, red);
-    if (threadIdx.x == 0) {
-      s_alpha = a.st->rz / pq;
-      if (bx == 0) {   // for the scalar kernel's breakdown test
-        a.st->pq = pq;
-        a.st->alpha = s_alpha;
-      }
-    }
-    __syncthreads();
-    const T al = (T)s_alpha;
+    const T al = (T)a.st->alpha;
     T* __restrict__ xv = a.x;
     T* __restrict__ rv = a.r;
     const T* __restrict__ pv = a.p;
@@ -512,27 +631,29 @@ __device__ __forceinline__ void body_dst_rows(const DstRowsArgs<T>& a, int bx, i
     }
   }
   if (a.pre == DPRE_UPDATE) {
-    const double s = cta_sum(rr.value(), red);
+    const double s = rr.cta_total(red);
     if (threadIdx.x == 0) a.rr_part[bx] = s;
   }
   if (a.dotw) {
-    const double s = cta_sum(dp.value(), red);
+    const double s = dp.cta_total(red);
     if (threadIdx.x == 0) a.dot_part[bx] = s;
+    if (a.fin == FIN_STEP && arrive_last(&a.st->arrive, a.nparts)) {
+      const double rrv = cta_sum_partials(a.rr_in, a.rr_count, red);
+      const double rz = cta_sum_partials(a.dot_part, a.nparts, red);
+      if (threadIdx.x == 0) pcg_step(a.st, rrv, rz);
+    }
   }
 }
 
 template <typename T, int THREADS, int VPT>
-__global__ void __launch_bounds__(THREADS) k_dst_rows(DstRowsArgs<T> a) {
+__global__ void __launch_bounds__(THREADS, min_ctas(THREADS)) k_dst_rows(DstRowsArgs<T> a) {
   body_dst_rows<T, THREADS, VPT>(a, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
 // Preconditioner strided pass: DST-I along a slow axis for a tile of TX
 // consecutive columns of a real field; line element r of column c at outer
-// index o is v[o * ostride + r * lstride + c0 + c].  DST_DIV_DST divides
-// between two transforms by shift + scale * sum_i mu_i(k_i), where
-// mu_i are per-axis eigenvalue tables; the index along this axis is k,
-// along the column axis kx = c0 + c and along the outer axis `o`.
+// index o is v[o * ostride + r * lstride + c0 + c] (3D: the middle axis).
 template <typename T>
 struct DstColsArgs {
   T* v;
@@ -540,13 +661,10 @@ struct DstColsArgs {
   const typename Cplx<T>::type* chirp;
   const typename Cplx<T>::type* bhat;
   const PcgState* st;
-  const T* mu_line;        // eigen table of this axis (length n)
-  const T* mu_col;         // eigen table of the column axis
-  const T* mu_outer;       // nullable (2D): eigen table of the outer axis
-  double shift, scale, post;
+  double post;
   int n, ncols, lg, lgmax;
   long long ostride, lstride;
-  int mode, ltx;
+  int ltx;
 };
 
 template <typename T, int THREADS, int VPT>
@@ -582,23 +700,6 @@ __device__ __forceinline__ void body_dst_cols(const DstColsArgs<T>& a, int bx, i
   }
   __syncthreads();
   chirp_conv_il<VPT>(buf, ltx, L, a.lg, a.lgmax, a.tw, a.bhat);
-  if (a.mode == DST_DIV_DST) {
-    // X_k = Im(c_k y_k); divide by the eigenvalue; re-chirp for the second DST
-    const T muo = a.mu_outer ? a.mu_outer[o] : (T)0;
-    const T shift = (T)a.shift, scale = (T)a.scale;
-    for (int e = threadIdx.x; e < total; e += THREADS) {
-      const int k = e >> ltx, c = e & (TX - 1);
-      C val = cmake<C>((T)0, (T)0);
-      if (k < a.n && c < ncol) {
-        const C y = cmul(a.chirp[k], buf[e]);
-        const T lam = shift + scale * (a.mu_line[k] + a.mu_col[c0 + c] + muo);
-        val = cscale(a.chirp[k], y.y / lam);
-      }
-      buf[e] = val;
-    }
-    __syncthreads();
-    chirp_conv_il<VPT>(buf, ltx, L, a.lg, a.lgmax, a.tw, a.bhat);
-  }
   const int tout = TX * a.n;
   const T post = (T)a.post;
   for (int e = threadIdx.x; e < tout; e += THREADS) {
@@ -611,7 +712,7 @@ __device__ __forceinline__ void body_dst_cols(const DstColsArgs<T>& a, int bx, i
 }
 
 template <typename T, int THREADS, int VPT>
-__global__ void __launch_bounds__(THREADS) k_dst_cols(DstColsArgs<T> a) {
+__global__ void __launch_bounds__(THREADS, min_ctas(THREADS)) k_dst_cols(DstColsArgs<T> a) {
   body_dst_cols<T, THREADS, VPT>(a, blockIdx.x, blockIdx.y);
 }
 

@@ -428,8 +428,8 @@ __global__ void __launch_bounds__(256) k_combine(const float* __restrict__ r, co
     a.add(r[i] * zn);
     b.add(r[i] * zo);
   }
-  const double sa = cta_sum(a.value(), red);
-  const double sb = cta_sum(b.value(), red);
+  const double sa = a.cta_total(red);
+  const double sb = b.cta_total(red);
   if (threadIdx.x == 0) {
     rz_part[blockIdx.x] = sa;
     if (rzo_part) rzo_part[blockIdx.x] = sb;

@@ -9,21 +9,16 @@ namespace fl {
 // ---------------------------------------------------------------------------
 // CG vector kernels (grid-stride, kVecBlocks CTAs, one partial per CTA).
 
+// CG update without preconditioner (z = r): x += alpha p, r -= alpha q with
+// alpha = st->alpha (set by the apply's last CTA), partials of ||r||^2;
+// with `step` the last CTA takes the CG scalar step (r.z = ||r||^2).
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads) k_noprec_update(PcgState* st, T* x, T* r, const T* p,
-                                                              const T* q, const double* pq_part,
-                                                              int pq_count, double* rr_part,
+                                                              const T* q, double* rr_part, int step,
                                                               long long N) {
   __shared__ double red[32];
-  __shared__ double s_alpha;
   if (st->done) return;
-  const double pq = cta_sum_partials(pq_part, pq_count, red);
-  if (threadIdx.x == 0) {
-    s_alpha = st->rz / pq;
-    if (blockIdx.x == 0) { st->pq = pq; st->alpha = s_alpha; }
-  }
-  __syncthreads();
-  const T al = (T)s_alpha;
+  const T al = (T)st->alpha;
   DotAcc<T> rr;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
@@ -32,8 +27,12 @@ __global__ void __launch_bounds__(kVecThreads) k_noprec_update(PcgState* st, T* 
     r[i] = rn;
     rr.add(rn * rn);
   }
-  const double s = cta_sum(rr.value(), red);
+  const double s = rr.cta_total(red);
   if (threadIdx.x == 0) rr_part[blockIdx.x] = s;
+  if (step && arrive_last(&st->arrive, gridDim.x)) {
+    const double rrv = cta_sum_partials(rr_part, gridDim.x, red);
+    if (threadIdx.x == 0) pcg_step(st, rrv, rrv);
+  }
 }
 
 template <typename T>
@@ -44,7 +43,7 @@ __global__ void __launch_bounds__(kVecThreads) k_dot(const T* a, const T* b, dou
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x)
     v.add(a[i] * b[i]);
-  const double s = cta_sum(v.value(), red);
+  const double s = v.cta_total(red);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
@@ -74,7 +73,7 @@ __global__ void __launch_bounds__(kVecThreads) k_mask_copy_dot(const T* src, con
     if (dst) dst[i] = x;
     v.add(x * x);
   }
-  const double s = cta_sum(v.value(), red);
+  const double s = v.cta_total(red);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
@@ -102,6 +101,7 @@ __global__ void k_pcg_init(PcgState* st, const double* bb_part, int bb_count, co
     st->it = 0;
     st->maxit = maxit;
     st->status = 0;
+    st->arrive = 0u;
     st->done = (bb == 0.0 || rr <= st->tol2) ? 1 : 0;
     if (!(rz > 0.0) && !st->done) { st->done = 1; st->status = 3; }
   }
@@ -113,27 +113,7 @@ __global__ void k_pcg_scalar(PcgState* st, const double* rr_part, int rr_count, 
   if (st->done) return;
   const double rr = cta_sum_partials(rr_part, rr_count, red);
   const double rz = cta_sum_partials(rz_part, rz_count, red);
-  if (threadIdx.x == 0) {
-    st->it += 1;
-    st->rr = rr;
-    const double pq = st->pq;
-    if (!(pq > 0.0) || rr != rr || rz != rz) {
-      st->done = 1;
-      st->status = 3;
-    } else if (rr <= st->tol2) {
-      st->done = 1;
-      st->status = 0;
-    } else if (st->it >= st->maxit) {
-      st->done = 1;
-      st->status = 2;
-    } else if (!(rz > 0.0)) {
-      st->done = 1;
-      st->status = 3;
-    } else {
-      st->beta = rz / st->rz;
-      st->rz = rz;
-    }
-  }
+  if (threadIdx.x == 0) pcg_step(st, rr, rz);
 }
 
 __global__ void k_sum(const double* part, int count, double* out) {
@@ -324,6 +304,8 @@ ApplyChain<T> build_apply(const Geo& g, const Tables<T>& tb, const ApplyIO<T>& i
     a.cm = io.cm; a.cx = io.cx; a.cb = io.cb;
     a.rows = (int)rows; a.n = g.n[d - 1]; a.H = g.H; a.lg = g.lg[d - 1]; a.lgmax = g.lgmax;
     a.rows_per_plane = rpp; a.plane_stride = pstride; a.dot_self = io.dot_self;
+    a.fin = (io.partials && io.st) ? io.fin : FIN_NONE;
+    a.nparts = ch.row_blocks; a.fst = io.st;
   }
   return ch;
 }
@@ -361,19 +343,18 @@ PrecChain<T> build_precond(const Geo& g, const Tables<T>& tb, const PrecIO<T>& i
     DstRowsArgs<T>& a = ch.first;
     a.in = io.in; a.out = tb.t; a.tw = tb.tw; a.chirp = tb.chirp[d - 1]; a.bhat = tb.bhat[d - 1];
     a.st = io.st; a.x = io.x; a.r = io.r; a.p = io.p; a.q = io.q;
-    a.pq_part = io.pq_part; a.pq_count = io.pq_count; a.rr_part = io.rr_part;
+    a.rr_part = io.rr_part;
     a.dotw = nullptr; a.dot_part = nullptr; a.post = 1.0;
     a.rows = (int)rows; a.n = nx; a.lg = g.lg[d - 1]; a.lgmax = g.lgmax; a.pre = io.pre;
+    a.fin = FIN_NONE; a.nparts = ch.row_blocks; a.rr_in = nullptr; a.rr_count = 0;
   }
   ch.ncols = 0;
-  auto cols = [&](int axis, int mode, long long lstride, long long ostride, int nouter,
-                  const T* mu_line, const T* mu_col, const T* mu_outer) {
+  auto cols = [&](int axis, long long lstride, long long ostride, int nouter) {
     DstColsArgs<T>& a = ch.cols[ch.ncols];
     a.v = tb.t; a.tw = tb.tw; a.chirp = tb.chirp[axis]; a.bhat = tb.bhat[axis]; a.st = io.st;
-    a.mu_line = mu_line; a.mu_col = mu_col; a.mu_outer = mu_outer;
-    a.shift = io.shift; a.scale = io.scale; a.post = 1.0;
+    a.post = 1.0;
     a.n = g.n[axis]; a.ncols = nx; a.lg = g.lg[axis]; a.lgmax = g.lgmax;
-    a.ostride = ostride; a.lstride = lstride; a.mode = mode;
+    a.ostride = ostride; a.lstride = lstride;
     const int L = g.L[axis];
     const int tx = col_tx<T>(L);
     a.ltx = ilog2i(tx);
@@ -396,17 +377,22 @@ PrecChain<T> build_precond(const Geo& g, const Tables<T>& tb, const PrecIO<T>& i
     ch.tri_after = 0;
   } else {
     const long long n1 = g.n[1], n2 = g.n[2];
-    cols(1, DST_ONE, n2, n1 * n2, g.n[0], nullptr, nullptr, nullptr);
+    cols(1, n2, n1 * n2, g.n[0]);
     ch.tri_after = 1;
-    cols(1, DST_ONE, n2, n1 * n2, g.n[0], nullptr, nullptr, nullptr);
+    cols(1, n2, n1 * n2, g.n[0]);
   }
   {
     DstRowsArgs<T>& a = ch.last;
     a.in = tb.t; a.out = io.out; a.tw = tb.tw; a.chirp = tb.chirp[d - 1]; a.bhat = tb.bhat[d - 1];
     a.st = io.st; a.x = nullptr; a.r = nullptr; a.p = nullptr; a.q = nullptr;
-    a.pq_part = nullptr; a.pq_count = 0; a.rr_part = nullptr;
+    a.rr_part = nullptr;
     a.dotw = io.dotw; a.dot_part = io.dot_part; a.post = post;
     a.rows = (int)rows; a.n = nx; a.lg = g.lg[d - 1]; a.lgmax = g.lgmax; a.pre = DPRE_NONE;
+    // the CG step needs r.z partials (dotw), the update pass's ||r||^2
+    // partials and a state
+    const bool step = io.fin == FIN_STEP && io.dotw && io.dot_part && io.rr_part && io.st;
+    a.fin = step ? FIN_STEP : FIN_NONE;
+    a.nparts = ch.row_blocks; a.rr_in = io.rr_part; a.rr_count = ch.row_blocks;
   }
   return ch;
 }
@@ -417,14 +403,12 @@ cudaError_t launch_precond(const Geo& g, const Tables<T>& tb, cudaStream_t s, co
   const PrecChain<T> ch = build_precond<T>(g, tb, io);
   FL_KERNEL((sizeof(T) == 4 ? "dst_rows" "<f32>" : "dst_rows" "<f64>"), s,
             k_dst_rows<T, K::RT, K::RV><<<ch.row_blocks, K::RT, ch.row_smem, s>>>(ch.first));
-  static const char* const kn[2][2] = {{"dst_cols<f64>", "dst_cols_div<f64>"},
-                                       {"dst_cols<f32>", "dst_cols_div<f32>"}};
   for (int j = 0; j <= ch.ncols; ++j) {
     if (j == ch.tri_after)
       FL_KERNEL((sizeof(T) == 4 ? "tri_cols" "<f32>" : "tri_cols" "<f64>"), s,
                 k_tri_cols<T><<<ch.tri_blocks, kTriCols * kTriSeg, 0, s>>>(ch.tri));
     if (j < ch.ncols)
-      FL_KERNEL(kn[sizeof(T) == 4][ch.cols[j].mode], s,
+      FL_KERNEL((sizeof(T) == 4 ? "dst_cols" "<f32>" : "dst_cols" "<f64>"), s,
                 k_dst_cols<T, K::CT, K::CV><<<ch.cols_grid[j], K::CT, ch.cols_smem[j], s>>>(ch.cols[j]));
   }
   FL_KERNEL((sizeof(T) == 4 ? "dst_rows" "<f32>" : "dst_rows" "<f64>"), s,
@@ -434,10 +418,9 @@ cudaError_t launch_precond(const Geo& g, const Tables<T>& tb, cudaStream_t s, co
 
 template <typename T>
 cudaError_t launch_noprec_update(long long N, cudaStream_t s, PcgState* st, T* x, T* r, const T* p,
-                                 const T* q, const double* pq_part, int pq_count, double* rr_part,
-                                 int* count) {
+                                 const T* q, double* rr_part, int step, int* count) {
   FL_KERNEL((sizeof(T) == 4 ? "noprec_update" "<f32>" : "noprec_update" "<f64>"), s,
-            k_noprec_update<T><<<kVecBlocks, kVecThreads, 0, s>>>(st, x, r, p, q, pq_part, pq_count, rr_part, N));
+            k_noprec_update<T><<<kVecBlocks, kVecThreads, 0, s>>>(st, x, r, p, q, rr_part, step, N));
   *count = kVecBlocks;
   return cudaGetLastError();
 }
@@ -569,8 +552,8 @@ template int precond_partials<float>(const Geo&);
 template int precond_partials<double>(const Geo&);
 template cudaError_t launch_precond<float>(const Geo&, const Tables<float>&, cudaStream_t, const PrecIO<float>&);
 template cudaError_t launch_precond<double>(const Geo&, const Tables<double>&, cudaStream_t, const PrecIO<double>&);
-template cudaError_t launch_noprec_update<float>(long long, cudaStream_t, PcgState*, float*, float*, const float*, const float*, const double*, int, double*, int*);
-template cudaError_t launch_noprec_update<double>(long long, cudaStream_t, PcgState*, double*, double*, const double*, const double*, const double*, int, double*, int*);
+template cudaError_t launch_noprec_update<float>(long long, cudaStream_t, PcgState*, float*, float*, const float*, const float*, double*, int, int*);
+template cudaError_t launch_noprec_update<double>(long long, cudaStream_t, PcgState*, double*, double*, const double*, const double*, double*, int, int*);
 template cudaError_t launch_dot<float>(long long, cudaStream_t, const float*, const float*, double*, int*);
 template cudaError_t launch_dot<double>(long long, cudaStream_t, const double*, const double*, double*, int*);
 template cudaError_t launch_copy_cast<float>(long long, cudaStream_t, const double*, float*);

@@ -302,7 +302,7 @@ fl_status run_pcg(fl_plan* p, bool x0_nonzero, double shift, double scale, bool 
   Vecs<T>& v = vecs<T>(p);
   Tables<T>& tb = tables<T>(p);
   cudaStream_t s = p->stream;
-  int bb_count = 0, rz_count = 0, rr_count = 0, pq_count = apply_partials<T>(g);
+  int bb_count = 0, rz_count = 0;
   // r = b - A x  (or r = b masked)
   if (x0_nonzero) {
     ApplyIO<T> io;
@@ -334,31 +334,26 @@ fl_status run_pcg(fl_plan* p, bool x0_nonzero, double shift, double scale, bool 
   }
   FL_CUDA(launch_pcg_init(s, p->st, p->part[P_BB], bb_count, rr0_part, rr0_count, p->part[P_RZ],
                           rz_count, tol, maxit));
-  // one CG iteration: q = A p (p = z + beta p fused), x/r update fused into
-  // the first preconditioner pass (or the plain update), scalars
-  const int it_rr = use_prec ? precond_partials<T>(g) : kVecBlocks;
+  // One CG iteration: q = A p (p = z + beta p fused; the apply's last CTA
+  // forms pq and alpha), the x/r update fused into the first preconditioner
+  // pass (or the plain update), and the scalar step in the last CTA of the
+  // last pass.
   auto enqueue = [&](cudaStream_t qs) -> cudaError_t {
     ApplyIO<T> io;
     io.pre = PRE_PUPDATE; io.u = z; io.p = v.p; io.mask = p->mask; io.st = p->st;
     io.out = v.q; io.x = v.p; io.cm = scale; io.cx = shift;
-    io.dotw = v.p; io.partials = p->part[P_PQ];
+    io.dotw = v.p; io.partials = p->part[P_PQ]; io.fin = FIN_PQ;
     cudaError_t e = launch_apply<T>(g, tb, qs, io);
     if (e != cudaSuccess) return e;
     int cnt = 0;
     if (use_prec) {
       PrecIO<T> pi;
       pi.pre = DPRE_UPDATE; pi.out = v.z; pi.shift = shift; pi.scale = scale;
-      pi.x = v.x; pi.r = v.r; pi.p = v.p; pi.q = v.q;
-      pi.pq_part = p->part[P_PQ]; pi.pq_count = pq_count; pi.rr_part = p->part[P_RR];
-      pi.dotw = v.r; pi.dot_part = p->part[P_RZ]; pi.st = p->st;
-      e = launch_precond<T>(g, tb, qs, pi);
-      if (e != cudaSuccess) return e;
-      return launch_pcg_scalar(qs, p->st, p->part[P_RR], it_rr, p->part[P_RZ], it_rr);
+      pi.x = v.x; pi.r = v.r; pi.p = v.p; pi.q = v.q; pi.rr_part = p->part[P_RR];
+      pi.dotw = v.r; pi.dot_part = p->part[P_RZ]; pi.st = p->st; pi.fin = FIN_STEP;
+      return launch_precond<T>(g, tb, qs, pi);
     }
-    e = launch_noprec_update<T>(g.N, qs, p->st, v.x, v.r, v.p, v.q, p->part[P_PQ], pq_count,
-                                p->part[P_RR], &cnt);
-    if (e != cudaSuccess) return e;
-    return launch_pcg_scalar(qs, p->st, p->part[P_RR], it_rr, p->part[P_RR], it_rr);
+    return launch_noprec_update<T>(g.N, qs, p->st, v.x, v.r, v.p, v.q, p->part[P_RR], 1, &cnt);
   };
   // Iterations run in chunks of 4, 8, 16, 32 between reads of the device
   // state; a chunk is replays of a captured 4-iteration CUDA graph (not
@@ -445,7 +440,6 @@ fl_status run_fpcg_learned(fl_plan* p, double shift, double scale, double tol, i
   const bool fd = p->alpha >= 1.0;
   const float jac = (float)(1.0 / (shift + scale * p->c * (p->Z - 2.0 * g.d * p->a)));
   int bb_count = 0, zz_count = 0, rz_count = 0, rr_count = 0;
-  const int pq_count = apply_partials<float>(g);
   auto base = [&](const PcgState* st) -> cudaError_t {
     cudaError_t e;
     if (fd) {
@@ -481,10 +475,10 @@ fl_status run_fpcg_learned(fl_plan* p, double shift, double scale, double tol, i
       ApplyIO<float> io;
       io.pre = PRE_PUPDATE; io.u = v.z; io.p = v.p; io.mask = p->mask; io.st = p->st;
       io.out = v.q; io.x = v.p; io.cm = scale; io.cx = shift;
-      io.dotw = v.p; io.partials = p->part[P_PQ];
+      io.dotw = v.p; io.partials = p->part[P_PQ]; io.fin = FIN_PQ;
       FL_CUDA(launch_apply<float>(g, p->t32, s, io));
-      FL_CUDA(launch_noprec_update<float>(g.N, s, p->st, v.x, v.r, v.p, v.q, p->part[P_PQ], pq_count,
-                                          p->part[P_RR], &rr_count));
+      FL_CUDA(launch_noprec_update<float>(g.N, s, p->st, v.x, v.r, v.p, v.q, p->part[P_RR], 0,
+                                          &rr_count));
       FL_CUDA(base(p->st));
       FL_CUDA(learned(p->part[P_RR], rr_count, p->st, p->lpart[2]));
       FL_CUDA(launch_fpcg_scalar(p->st, p->part[P_RR], rr_count, p->lpart[1], p->lpart[2], rz_count, s));
@@ -1085,7 +1079,7 @@ fl_status solve_batched_mixed(fl_plan* const* plans, int count, const double* co
   ChainSets<double> res64;
   PassSet<BVecArgs<double>> cast;
   std::vector<float*> out32(count);
-  std::vector<BScalarArgs> sum_cast(count), sum_res(count), init(count), step(count);
+  std::vector<BScalarArgs> sum_cast(count), sum_res(count), init(count);
   PassSet<BVecArgs<float>> start, noprec;
   PrecSets<float> pinit, pstep;
   ChainSets<float> apply32;
@@ -1130,25 +1124,20 @@ fl_status solve_batched_mixed(fl_plan* const* plans, int count, const double* co
     ApplyIO<float> ioa;
     ioa.pre = PRE_PUPDATE; ioa.u = prec[i] ? p->v32.z : p->v32.r; ioa.p = p->v32.p;
     ioa.mask = p->mask; ioa.st = st; ioa.out = p->v32.q; ioa.x = p->v32.p; ioa.cm = 1.0;
-    ioa.dotw = p->v32.p; ioa.partials = p->part[P_PQ];
+    ioa.dotw = p->v32.p; ioa.partials = p->part[P_PQ]; ioa.fin = FIN_PQ;
     apply32.add(build_apply<float>(g, p->t32, ioa));
-    const int pq_count = apply_partials<float>(g);
+    // the x/r update and the CG scalar step (in the last CTA of the last pass)
     if (prec[i]) {
       PrecIO<float> pu;
       pu.pre = DPRE_UPDATE; pu.out = p->v32.z; pu.x = p->v32.x; pu.r = p->v32.r; pu.p = p->v32.p;
-      pu.q = p->v32.q; pu.pq_part = p->part[P_PQ]; pu.pq_count = pq_count;
-      pu.rr_part = p->part[P_RR]; pu.dotw = p->v32.r; pu.dot_part = p->part[P_RZ]; pu.st = st;
+      pu.q = p->v32.q; pu.rr_part = p->part[P_RR]; pu.dotw = p->v32.r; pu.dot_part = p->part[P_RZ];
+      pu.st = st; pu.fin = FIN_STEP;
       pstep.add(build_precond<float>(g, p->t32, pu));
-      step[i] = BScalarArgs{st, gate, nullptr, 0, p->part[P_RR], pcount, p->part[P_RZ], pcount,
-                            tol_dev + i, maxit};
     } else {
       BVecArgs<float> nu = {};
       nu.st = st; nu.x = p->v32.x; nu.r = p->v32.r; nu.p = p->v32.p; nu.q = p->v32.q;
-      nu.mask = p->mask; nu.pq_part = p->part[P_PQ]; nu.pq_count = pq_count;
-      nu.part = p->part[P_RR]; nu.N = g.N;
+      nu.mask = p->mask; nu.part = p->part[P_RR]; nu.N = g.N;
       noprec.add(nu, vb, vb, 0);
-      step[i] = BScalarArgs{st, gate, nullptr, 0, p->part[P_RR], vb, p->part[P_RR], vb,
-                            tol_dev + i, maxit};
     }
   }
   // upload every argument array once
@@ -1159,7 +1148,6 @@ fl_status solve_batched_mixed(fl_plan* const* plans, int count, const double* co
   BScalarArgs* SUMC = ar.upload(sum_cast);
   BScalarArgs* SUMR = ar.upload(sum_res);
   BScalarArgs* INIT = ar.upload(init);
-  BScalarArgs* STEP = ar.upload(step);
   BatchPass START = start.upload(ar, BK_CG_START);
   BatchPass NOPREC = noprec.upload(ar, BK_NOPREC);
   PrecPasses<float> PI, PS;
@@ -1249,7 +1237,6 @@ fl_status solve_batched_mixed(fl_plan* const* plans, int count, const double* co
         ce = A32.launch(bs);
         if (ce == cudaSuccess) ce = PS.launch(bs);
         if (ce == cudaSuccess) ce = launch_batched<float>(NOPREC, bs);
-        if (ce == cudaSuccess) ce = launch_batched_scalar(1, STEP, nullptr, count, bs);
       }
       cudaError_t ee = cudaStreamEndCapture(bs, &graph);
       if (ce != cudaSuccess) return cuda_fail(ce, "batched CG capture");
