@@ -43,6 +43,8 @@ struct Tables {
   C* S = nullptr;             // operator spectrum workspace
   T* t = nullptr;             // preconditioner workspace (N)
   T* mu[3] = {nullptr, nullptr, nullptr};  // eigenvalues of C h^d L per axis
+  T* tri_tab = nullptr;       // per-column constants of the axis-0 tridiagonal solve
+  double tri_shift = -1.0, tri_scale = -1.0;  // the shift and scale tri_tab holds
 };
 
 // Inputs and outputs of one operator apply.
@@ -90,6 +92,9 @@ template <typename T>
 cudaError_t launch_precond(const Geo& g, const Tables<T>& tb, cudaStream_t s, const PrecIO<T>& io);
 template <typename T>
 int precond_partials(const Geo& g);  // partials of the first / last DST pass
+// Fill tb.tri_tab for (shift, scale) unless it already holds them.
+template <typename T>
+cudaError_t prepare_precond(const Geo& g, Tables<T>& tb, double shift, double scale, cudaStream_t s);
 template <typename T>
 cudaError_t launch_noprec_update(long long N, cudaStream_t s, PcgState* st, T* x, T* r,
                                  const T* p, const T* q, double* rr_part, int step, int* count);

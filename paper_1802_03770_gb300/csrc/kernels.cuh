@@ -737,63 +737,91 @@ namespace fl {
 //   gamma = r x_0 / (1 + r v_0).
 // This is the same solve the DST-I along axis 0 would give, in O(n) work.
 // Each column runs as kTriSeg segments of m <= kTriM rows, one thread each;
-// the segment carries (factor R = r^m) are chained through shared memory.
-// Per-column constants are formed in FP64 from the working-precision r, so
-// that the correction is consistent with the recurrences actually run.
+// the segment carries (factor R = r^m) are a linear-recurrence scan across
+// the 32 lanes of one warp per column.
 constexpr int kTriCols = 8;    // columns per CTA: 32-byte row pieces in FP32
-constexpr int kTriSeg = 32;    // segments per column
+constexpr int kTriSeg = 32;    // segments per column (one warp lane each)
 constexpr int kTriM = 32;      // max rows per segment: n <= 1024
+constexpr int kTriTab = 4;     // table entries per column
+
+// Per-column constants, data-independent (FP64, once per shift and scale):
+// tab[4c] = r (rounded to T; every other entry is formed from this r),
+// tab[4c+1] = r^m, tab[4c+2] = log2(r), tab[4c+3] = K, with
+// gamma / (1 - r^2) = K w_0 (w_0 = r^{-1} x_0).
+template <typename T>
+__global__ void k_tri_table(T* tab, const T* mu_col, const T* mu_outer, int ncols, int n_inner,
+                            double shift, double scale, double cA, int n, int m) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncols) return;
+  const double mu = (double)mu_col[c % n_inner] + (mu_outer ? (double)mu_outer[c / n_inner] : 0.0);
+  const double e = (shift + scale * mu) / (scale * cA);
+  const T rt = (T)(2.0 / (2.0 + e + sqrt(e * (e + 4.0))));
+  const double r = (double)rt;
+  const double lr = log1p(-(1.0 - r));
+  const double omr2 = (1.0 - r) * (1.0 + r);
+  const double v0 = (r - exp((2.0 * n + 1.0) * lr)) / omr2;
+  tab[kTriTab * c + 0] = rt;
+  tab[kTriTab * c + 1] = (T)exp((double)m * lr);
+  tab[kTriTab * c + 2] = (T)(lr * 1.4426950408889634073599246810018921);
+  tab[kTriTab * c + 3] = (T)(r * r / ((1.0 + r * v0) * omr2));
+}
 
 template <typename T>
 struct TriArgs {
   T* v;                  // in: coefficients t; out: z (in place); row stride ncols
   const PcgState* st;
-  const T* mu_col;       // eigen table of the innermost other axis
-  const T* mu_outer;     // nullable (2D): eigen table of the middle axis
-  double shift, scale, cA;
+  const T* tab;          // k_tri_table for this shift and scale
+  double inv_sc;         // 1 / (scale cA)
   int n;                 // rows along axis 0
   int ncols;             // columns: product of the other axes
-  int n_inner;           // column c: inner index c % n_inner, outer c / n_inner
   int m;                 // rows per segment, ceil(n / kTriSeg)
 };
 
+__device__ __forceinline__ float tri_exp2(float x) { return exp2f(x); }
+__device__ __forceinline__ double tri_exp2(double x) { return exp2(x); }
+
+// Inclusive scan of b_s = E_s + R b_{s-1} over the lanes (up: s = lane;
+// down: s counted from lane 31).
+template <typename T>
+__device__ __forceinline__ T lane_scan(T b, T R, bool up) {
+  const int lane = threadIdx.x & 31;
+  T Rd = R;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const T o = up ? __shfl_up_sync(0xffffffffu, b, d) : __shfl_down_sync(0xffffffffu, b, d);
+    if (up ? lane >= d : lane + d < 32) b += Rd * o;
+    Rd *= Rd;
+  }
+  return b;
+}
+
 template <typename T>
 __device__ __forceinline__ void body_tri_cols(const TriArgs<T>& a, int bx) {
-  __shared__ T s_e[kTriSeg][kTriCols];    // segment end values, then carries in
-  __shared__ T s_cf[kTriSeg][kTriCols];   // forward carry into each segment
-  __shared__ T s_cb[kTriSeg][kTriCols];   // backward carry into each segment
-  __shared__ T s_p0[kTriSeg][kTriCols];   // r^{s m + 1}
-  __shared__ T s_qe[kTriSeg][kTriCols];   // r^{2n + 2 - (s+1) m}
-  __shared__ T s_r[kTriCols], s_R[kTriCols], s_g[kTriCols];
-  __shared__ double s_d[kTriCols][3];     // FP64: r, log r, 1 - r^2
+  __shared__ T s_e[kTriSeg][kTriCols + 1];   // segment end values (forward, backward)
+  __shared__ T s_c[kTriSeg][kTriCols + 1];   // carries into each segment
+  __shared__ T s_w0[kTriCols];
   if (a.st && a.st->done) return;
   const int c = threadIdx.x % kTriCols, s = threadIdx.x / kTriCols;
   const int col = bx * kTriCols + c;
   const bool act = col < a.ncols;
   const int n = a.n, m = a.m, i0 = s * m;
-  const int P = (n + m - 1) / m;
   T* __restrict__ vc = a.v + col;
   const size_t ld = (size_t)a.ncols;
   T y[kTriM];
 #pragma unroll
   for (int j = 0; j < kTriM; ++j)
     y[j] = (act && j < m && i0 + j < n) ? vc[(size_t)(i0 + j) * ld] : (T)0;
-  if (s == 0 && act) {
-    const int ci = col % a.n_inner, co = col / a.n_inner;
-    const double mu = (double)a.mu_col[ci] + (a.mu_outer ? (double)a.mu_outer[co] : 0.0);
-    const double e = (a.shift + a.scale * mu) / (a.scale * a.cA);
-    const double dd = 2.0 + e;
-    const T rt = (T)(2.0 / (dd + sqrt(e * (e + 4.0))));
-    const double r = (double)rt;
-    const double lr = log1p(-(1.0 - r));
-    s_r[c] = rt;
-    s_R[c] = (T)exp((double)m * lr);
-    s_d[c][0] = r;
-    s_d[c][1] = lr;
-    s_d[c][2] = (1.0 - r) * (1.0 + r);
+  T r = (T)0, R = (T)0, l2r = (T)0, K = (T)0;
+  if (act) {
+    r = a.tab[kTriTab * col];
+    R = a.tab[kTriTab * col + 1];
+    l2r = a.tab[kTriTab * col + 2];
+    K = a.tab[kTriTab * col + 3];
   }
-  __syncthreads();
-  const T r = act ? s_r[c] : (T)0;
+  // scan lanes: warp w scans column w, lane = segment
+  const int wc = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wcol = bx * kTriCols + wc;
+  const T wR = wcol < a.ncols ? a.tab[kTriTab * wcol + 1] : (T)0;
   // forward recurrence within the segment
   {
     T acc = (T)0;
@@ -806,17 +834,14 @@ __device__ __forceinline__ void body_tri_cols(const TriArgs<T>& a, int bx) {
     s_e[s][c] = acc;
   }
   __syncthreads();
-  if (s == 0 && act) {
-    const T R = s_R[c];
-    T carry = (T)0;
-    for (int q = 0; q < kTriSeg; ++q) {
-      s_cf[q][c] = carry;
-      carry = s_e[q][c] + R * carry;
-    }
+  {
+    const T b = lane_scan(s_e[lane][wc], wR, true);
+    const T ex = __shfl_up_sync(0xffffffffu, b, 1);
+    s_c[lane][wc] = lane > 0 ? ex : (T)0;
   }
   __syncthreads();
   {
-    const T cin = act ? s_cf[s][c] : (T)0;
+    const T cin = s_c[s][c];
     T pw = r;
 #pragma unroll
     for (int j = 0; j < kTriM; ++j)
@@ -837,42 +862,19 @@ __device__ __forceinline__ void body_tri_cols(const TriArgs<T>& a, int bx) {
     s_e[s][c] = acc;
   }
   __syncthreads();
-  if (s == 0 && act) {
-    const T R = s_R[c];
-    T carry = (T)0;
-    for (int q = kTriSeg - 1; q >= 0; --q) {
-      s_cb[q][c] = carry;
-      carry = s_e[q][c] + R * carry;
-    }
-    // carry = w_0; rank-one correction and the powers of r per segment
-    const double rd = s_d[c][0], lr = s_d[c][1], omr2 = s_d[c][2];
-    const double Rd = exp((double)m * lr);
-    const double v0 = (rd - exp((2.0 * n + 1.0) * lr)) / omr2;
-    const double x0 = rd * (double)carry;
-    const double gam = rd * x0 / (1.0 + rd * v0);
-    s_g[c] = (T)(gam / omr2);
-    double pw = rd;
-    for (int q = 0; q < kTriSeg; ++q) {
-      s_p0[q][c] = (T)pw;
-      pw *= Rd;
-    }
-    double qe = exp((2.0 * n + 2.0 - (double)P * m) * lr);
-    for (int q = kTriSeg - 1; q >= 0; --q) {
-      if (q < P) {
-        s_qe[q][c] = (T)qe;
-        qe *= Rd;
-      } else {
-        s_qe[q][c] = (T)0;
-      }
-    }
+  {
+    const T b = lane_scan(s_e[lane][wc], wR, false);
+    const T ex = __shfl_down_sync(0xffffffffu, b, 1);
+    s_c[lane][wc] = lane < 31 ? ex : (T)0;
+    if (lane == 0) s_w0[wc] = b;   // w_0 of the column
   }
   __syncthreads();
   if (!act || i0 >= n) return;
-  const T g = s_g[c];
-  const T inv_sc = (T)(1.0 / (a.scale * a.cA));
+  const T g = K * s_w0[c];
+  const T inv_sc = (T)a.inv_sc;
   // z_i = (r w_i - g (r^{i+1} - r^{2n+1-i})) / (scale cA), w_i = w_local + r^{m-j} cin
   {
-    T p = s_p0[s][c];
+    T p = tri_exp2(l2r * (T)(i0 + 1));
 #pragma unroll
     for (int j = 0; j < kTriM; ++j)
       if (j < m) {
@@ -881,9 +883,9 @@ __device__ __forceinline__ void body_tri_cols(const TriArgs<T>& a, int bx) {
       }
   }
   {
-    const T cin = s_cb[s][c];
+    const T cin = s_c[s][c];
     T pw = r * r;
-    T qv = s_qe[s][c];
+    T qv = tri_exp2(l2r * (T)(2 * n + 2 - i0 - m));
 #pragma unroll
     for (int j = kTriM - 1; j >= 0; --j)
       if (j < m) {

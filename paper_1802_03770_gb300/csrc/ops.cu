@@ -329,7 +329,6 @@ cudaError_t launch_apply(const Geo& g, const Tables<T>& tb, cudaStream_t s, cons
 template <typename T>
 PrecChain<T> build_precond(const Geo& g, const Tables<T>& tb, const PrecIO<T>& io) {
   PrecChain<T> ch;
-  T* const* mu = tb.mu;
   const int d = g.d;
   const int nx = g.n[d - 1], Lx = g.L[d - 1];
   const long long rows = g.N / nx;
@@ -364,12 +363,10 @@ PrecChain<T> build_precond(const Geo& g, const Tables<T>& tb, const PrecIO<T>& i
   };
   {
     TriArgs<T>& a = ch.tri;
-    a.v = tb.t; a.st = io.st;
-    a.mu_col = mu[d - 1]; a.mu_outer = d == 3 ? mu[1] : nullptr;
-    a.shift = io.shift; a.scale = io.scale; a.cA = g.cA;
+    a.v = tb.t; a.st = io.st; a.tab = tb.tri_tab;
+    a.inv_sc = 1.0 / (io.scale * g.cA);
     a.n = g.n[0];
     a.ncols = (int)(g.N / g.n[0]);
-    a.n_inner = nx;
     a.m = (g.n[0] + kTriSeg - 1) / kTriSeg;
     ch.tri_blocks = (a.ncols + kTriCols - 1) / kTriCols;
   }
@@ -398,8 +395,27 @@ PrecChain<T> build_precond(const Geo& g, const Tables<T>& tb, const PrecIO<T>& i
 }
 
 template <typename T>
+cudaError_t prepare_precond(const Geo& g, Tables<T>& tb, double shift, double scale, cudaStream_t s) {
+  if (tb.tri_shift == shift && tb.tri_scale == scale) return cudaSuccess;
+  const int ncols = (int)(g.N / g.n[0]);
+  const int m = (g.n[0] + kTriSeg - 1) / kTriSeg;
+  FL_KERNEL((sizeof(T) == 4 ? "tri_table" "<f32>" : "tri_table" "<f64>"), s,
+            k_tri_table<T><<<(ncols + 255) / 256, 256, 0, s>>>(
+                tb.tri_tab, tb.mu[g.d - 1], g.d == 3 ? tb.mu[1] : nullptr, ncols, g.n[g.d - 1],
+                shift, scale, g.cA, g.n[0], m));
+  const cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    tb.tri_shift = shift;
+    tb.tri_scale = scale;
+  }
+  return e;
+}
+
+template <typename T>
 cudaError_t launch_precond(const Geo& g, const Tables<T>& tb, cudaStream_t s, const PrecIO<T>& io) {
   typedef Cfg<T> K;
+  // the tridiagonal pass's table must hold this shift and scale
+  if (tb.tri_shift != io.shift || tb.tri_scale != io.scale) return cudaErrorInvalidValue;
   const PrecChain<T> ch = build_precond<T>(g, tb, io);
   FL_KERNEL((sizeof(T) == 4 ? "dst_rows" "<f32>" : "dst_rows" "<f64>"), s,
             k_dst_rows<T, K::RT, K::RV><<<ch.row_blocks, K::RT, ch.row_smem, s>>>(ch.first));
@@ -550,6 +566,8 @@ template int apply_partials<float>(const Geo&);
 template int apply_partials<double>(const Geo&);
 template int precond_partials<float>(const Geo&);
 template int precond_partials<double>(const Geo&);
+template cudaError_t prepare_precond<float>(const Geo&, Tables<float>&, double, double, cudaStream_t);
+template cudaError_t prepare_precond<double>(const Geo&, Tables<double>&, double, double, cudaStream_t);
 template cudaError_t launch_precond<float>(const Geo&, const Tables<float>&, cudaStream_t, const PrecIO<float>&);
 template cudaError_t launch_precond<double>(const Geo&, const Tables<double>&, cudaStream_t, const PrecIO<double>&);
 template cudaError_t launch_noprec_update<float>(long long, cudaStream_t, PcgState*, float*, float*, const float*, const float*, double*, int, int*);

@@ -317,6 +317,7 @@ fl_status run_pcg(fl_plan* p, bool x0_nonzero, double shift, double scale, bool 
   FL_CUDA(cudaMemsetAsync(v.p, 0, g.N * sizeof(T), s));
   T* z = use_prec ? v.z : v.r;
   if (use_prec) {
+    FL_CUDA(prepare_precond<T>(g, tb, shift, scale, s));
     PrecIO<T> io;
     io.in = v.r; io.out = v.z; io.shift = shift; io.scale = scale;
     io.dotw = v.r; io.dot_part = p->part[P_RZ];
@@ -440,6 +441,7 @@ fl_status run_fpcg_learned(fl_plan* p, double shift, double scale, double tol, i
   const bool fd = p->alpha >= 1.0;
   const float jac = (float)(1.0 / (shift + scale * p->c * (p->Z - 2.0 * g.d * p->a)));
   int bb_count = 0, zz_count = 0, rz_count = 0, rr_count = 0;
+  if (fd) FL_CUDA(prepare_precond<float>(g, p->t32, shift, scale, s));
   auto base = [&](const PcgState* st) -> cudaError_t {
     cudaError_t e;
     if (fd) {
@@ -708,6 +710,8 @@ fl_status fl_plan_create(int d, const int64_t* n, double h, double alpha, const 
   FL_TRY(dalloc(p, &p->t32.S, g.spec * sizeof(float2)));
   FL_TRY(dalloc(p, &p->t64.t, g.N * sizeof(double)));
   FL_TRY(dalloc(p, &p->t32.t, g.N * sizeof(float)));
+  FL_TRY(dalloc(p, &p->t64.tri_tab, (size_t)kTriTab * (g.N / g.n[0]) * sizeof(double)));
+  FL_TRY(dalloc(p, &p->t32.tri_tab, (size_t)kTriTab * (g.N / g.n[0]) * sizeof(float)));
   st = alloc_vecs(p, p->v32);
   if (st == FL_OK) st = alloc_vecs(p, p->v64);
   if (st != FL_OK) { free_plan(p); return st; }
@@ -776,6 +780,7 @@ fl_status fl_precond(fl_plan* p, double shift, double scale, const double* r, do
   if (p->has_mask) return fail(FL_INVALID_ARG, "the sine-transform preconditioner needs a plan without mask");
   if (!(scale > 0.0) || !(shift >= 0.0) || !std::isfinite(scale) || !std::isfinite(shift))
     return fail(FL_INVALID_ARG, "the preconditioner needs shift >= 0 and scale > 0");
+  FL_CUDA(prepare_precond<double>(p->g, p->t64, shift, scale, p->stream));
   PrecIO<double> io;
   io.in = r; io.out = z; io.shift = shift; io.scale = scale;
   FL_CUDA(launch_precond<double>(p->g, p->t64, p->stream, io));
@@ -789,6 +794,7 @@ fl_status fl_precond_f32(fl_plan* p, double shift, double scale, const float* r,
   if (p->has_mask) return fail(FL_INVALID_ARG, "the sine-transform preconditioner needs a plan without mask");
   if (!(scale > 0.0) || !(shift >= 0.0) || !std::isfinite(scale) || !std::isfinite(shift))
     return fail(FL_INVALID_ARG, "the preconditioner needs shift >= 0 and scale > 0");
+  FL_CUDA(prepare_precond<float>(p->g, p->t32, shift, scale, p->stream));
   PrecIO<float> io;
   io.in = r; io.out = z; io.shift = shift; io.scale = scale;
   FL_CUDA(launch_precond<float>(p->g, p->t32, p->stream, io));
@@ -1112,6 +1118,8 @@ fl_status solve_batched_mixed(fl_plan* const* plans, int count, const double* co
     start.add(sa, vb, vb, 0);
     const int pcount = precond_partials<float>(g);
     if (prec[i]) {
+      // on the plan's stream, before the batched stream waits for it
+      FL_CUDA(prepare_precond<float>(g, p->t32, 0.0, 1.0, p->stream));
       PrecIO<float> pi;
       pi.in = p->v32.r; pi.out = p->v32.z; pi.dotw = p->v32.r; pi.dot_part = p->part[P_RZ];
       pi.st = const_cast<PcgState*>(gate);
