@@ -264,6 +264,156 @@ __device__ __forceinline__ void stockham_stage_il(SBuf<C> buf, int lg, int ltx, 
   __syncthreads();
 }
 
+// --- stages with fused input / output ---------------------------------------
+//
+// The first stage (Ns = 1, no twiddles) can take its legs from a loader
+// functor load(line, index) instead of shared memory, and the last stage can
+// hand its outputs to an epilogue functor epi(line, index, value) instead of
+// writing them back: the global loads and stores of a pass then happen in the
+// first and last stage, which saves two shared-memory passes and their
+// barriers.  `IL` selects the interleaved-line layout (line = column c of a
+// tile of 2^ltx columns).
+
+template <int R, int VPT, bool IL, typename C, typename Load>
+__device__ __forceinline__ void stage_first_io(SBuf<C> buf, int lg, int ls, int ltx, int nlines,
+                                               bool inv, Load& load, bool sync_mid) {
+  constexpr int NB = VPT / R;
+  const int lglr = lg - LogR<R>::v;
+  const int LR = 1 << lglr;
+  const int total = IL ? (LR << ltx) : (nlines << lglr);
+  C v[NB][R];
+  int dst[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int g = threadIdx.x + b * blockDim.x;
+    dst[b] = -1;
+    if (g < total) {
+      const int line = IL ? (g & ((1 << ltx) - 1)) : (g >> lglr);
+      const int j = IL ? (g >> ltx) : (g & (LR - 1));
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[b][r] = load(line, j + r * LR);
+      dftR<R>(v[b], inv);
+      dst[b] = IL ? (((j * R) << ltx) + line) : (line * ls + j * R);
+    }
+  }
+  if (sync_mid) __syncthreads();
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    if (dst[b] >= 0) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[dst[b] + (IL ? (r << ltx) : r)] = v[b][r];
+    }
+  }
+  __syncthreads();
+}
+
+template <int R, int VPT, bool IL, typename C, typename Epi>
+__device__ __forceinline__ void stage_last_io(SBuf<C> buf, int lg, int ls, int ltx, int nlines, int Ns,
+                                              const C* __restrict__ tw, int lgmax, bool inv, Epi& epi,
+                                              bool sync_mid) {
+  constexpr int NB = VPT / R;
+  const int lglr = lg - LogR<R>::v;
+  const int LR = 1 << lglr;
+  const int total = IL ? (LR << ltx) : (nlines << lglr);
+  C v[NB][R];
+  int line_of[NB], out0[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int g = threadIdx.x + b * blockDim.x;
+    out0[b] = -1;
+    line_of[b] = 0;
+    if (g < total) {
+      const int line = IL ? (g & ((1 << ltx) - 1)) : (g >> lglr);
+      const int j = IL ? (g >> ltx) : (g & (LR - 1));
+      const int k = j & (Ns - 1);
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        v[b][r] = IL ? buf[((j + r * LR) << ltx) + line] : buf[line * ls + j + r * LR];
+      if (k != 0) {
+        C w[R];
+        twiddles<R>(tw, k << (lgmax - __ffs(Ns * R) + 1), inv, w);
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], w[r]);
+      }
+      dftR<R>(v[b], inv);
+      line_of[b] = line;
+      out0[b] = (j - k) * R + k;
+    }
+  }
+  if (sync_mid) __syncthreads();
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    if (out0[b] >= 0) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) epi(line_of[b], out0[b] + r * Ns, v[b][r]);
+    }
+  }
+}
+
+// A full transform of `nlines` lines (IL: 2^ltx interleaved lines) of length
+// 2^lg: legs of the first stage from load(line, index), outputs to
+// epi(line, index, value) in natural order.  sync_load: the loader reads the
+// shared buffer (a barrier separates its reads from the first stage's
+// writes); sync_epi: the epilogue writes the shared buffer.  The buffer is
+// free again after a barrier that follows the call.
+template <int VPT, bool IL, typename C, typename Load, typename Epi>
+__device__ __forceinline__ void fft_io(SBuf<C> buf, int lg, int ls, int ltx, int nlines,
+                                       const C* __restrict__ tw, int lgmax, bool inv, Load load,
+                                       bool sync_load, Epi epi, bool sync_epi) {
+  int rad[12];
+  int S = 0, rem = lg;
+  if (VPT >= 16)
+    while (rem >= 4) { rad[S++] = 16; rem -= 4; }
+  while (rem >= 3) { rad[S++] = 8; rem -= 3; }
+  if (rem == 2) rad[S++] = 4;
+  else if (rem == 1) rad[S++] = 2;
+  constexpr int R16 = VPT >= 16 ? 16 : 8;
+  switch (rad[0]) {
+    case 16: stage_first_io<R16, VPT, IL>(buf, lg, ls, ltx, nlines, inv, load, sync_load); break;
+    case 8: stage_first_io<8, VPT, IL>(buf, lg, ls, ltx, nlines, inv, load, sync_load); break;
+    case 4: stage_first_io<4, VPT, IL>(buf, lg, ls, ltx, nlines, inv, load, sync_load); break;
+    default: stage_first_io<2, VPT, IL>(buf, lg, ls, ltx, nlines, inv, load, sync_load); break;
+  }
+  int Ns = rad[0];
+  for (int s = 1; s + 1 < S; ++s) {
+    if (IL) {
+      switch (rad[s]) {
+        case 16: stockham_stage_il<R16, VPT>(buf, lg, ltx, Ns, tw, lgmax, inv); break;
+        case 8: stockham_stage_il<8, VPT>(buf, lg, ltx, Ns, tw, lgmax, inv); break;
+        case 4: stockham_stage_il<4, VPT>(buf, lg, ltx, Ns, tw, lgmax, inv); break;
+        default: stockham_stage_il<2, VPT>(buf, lg, ltx, Ns, tw, lgmax, inv); break;
+      }
+    } else {
+      switch (rad[s]) {
+        case 16: stockham_stage<R16, VPT>(buf, lg, ls, nlines, Ns, tw, lgmax, inv); break;
+        case 8: stockham_stage<8, VPT>(buf, lg, ls, nlines, Ns, tw, lgmax, inv); break;
+        case 4: stockham_stage<4, VPT>(buf, lg, ls, nlines, Ns, tw, lgmax, inv); break;
+        default: stockham_stage<2, VPT>(buf, lg, ls, nlines, Ns, tw, lgmax, inv); break;
+      }
+    }
+    Ns *= rad[s];
+  }
+  if (S >= 2) {
+    switch (rad[S - 1]) {
+      case 16: stage_last_io<R16, VPT, IL>(buf, lg, ls, ltx, nlines, Ns, tw, lgmax, inv, epi, sync_epi); break;
+      case 8: stage_last_io<8, VPT, IL>(buf, lg, ls, ltx, nlines, Ns, tw, lgmax, inv, epi, sync_epi); break;
+      case 4: stage_last_io<4, VPT, IL>(buf, lg, ls, ltx, nlines, Ns, tw, lgmax, inv, epi, sync_epi); break;
+      default: stage_last_io<2, VPT, IL>(buf, lg, ls, ltx, nlines, Ns, tw, lgmax, inv, epi, sync_epi); break;
+    }
+  } else {
+    // one stage: the result is in natural order; each thread reads and hands
+    // on its own elements (an epilogue writing the buffer rewrites the
+    // element it was given)
+    const int L = 1 << lg;
+    const int total = IL ? (L << ltx) : nlines * L;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+      const int line = IL ? (e & ((1 << ltx) - 1)) : e / L;
+      const int j = IL ? (e >> ltx) : e % L;
+      epi(line, j, IL ? buf[e] : buf[line * ls + j]);
+    }
+  }
+}
+
 // Stage plan: radix 16 while at least four factors of two remain (if VPT
 // allows), then radix 8, then one radix-4 or radix-2 stage.
 template <int VPT, typename C>

@@ -589,10 +589,15 @@ fl_status solve_system(fl_plan* p, double* u, bool x0_nonzero, double shift, dou
   } else {
     return fail(FL_INVALID_ARG, "unknown precision mode");
   }
-  // final FP64 residual (also for F64 mode)
-  double rel = 0.0;
-  fl_status st = true_residual(p, u, shift, scale, &rel);
-  if (st != FL_OK) return st;
+  // Final FP64 residual.  A converged refinement loop has just computed it
+  // for the final u (the last FP64 apply accumulated the last correction
+  // into u and formed f - A u from it); otherwise it is formed here.
+  double rel = loc.rel_residual;
+  const bool have_true = precision != FL_MODE_F64 && result == FL_OK;
+  if (!have_true) {
+    fl_status st = true_residual(p, u, shift, scale, &rel);
+    if (st != FL_OK) return st;
+  }
   loc.rel_residual = rel;
   loc.converged = rel <= tol * 1.0000001 ? 1 : 0;
   if (result == FL_OK && !loc.converged && precision == FL_MODE_F64 && rel <= 10 * tol) {
