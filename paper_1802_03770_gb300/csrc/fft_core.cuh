@@ -276,7 +276,7 @@ __device__ __forceinline__ void stockham_stage_il(SBuf<C> buf, int lg, int ltx, 
 
 template <int R, int VPT, bool IL, typename C, typename Load>
 __device__ __forceinline__ void stage_first_io(SBuf<C> buf, int lg, int ls, int ltx, int nlines,
-                                               bool inv, Load& load, bool sync_mid) {
+                                               bool inv, Load load, bool sync_mid) {
   constexpr int NB = VPT / R;
   const int lglr = lg - LogR<R>::v;
   const int LR = 1 << lglr;
@@ -309,7 +309,7 @@ __device__ __forceinline__ void stage_first_io(SBuf<C> buf, int lg, int ls, int 
 
 template <int R, int VPT, bool IL, typename C, typename Epi>
 __device__ __forceinline__ void stage_last_io(SBuf<C> buf, int lg, int ls, int ltx, int nlines, int Ns,
-                                              const C* __restrict__ tw, int lgmax, bool inv, Epi& epi,
+                                              const C* __restrict__ tw, int lgmax, bool inv, Epi epi,
                                               bool sync_mid) {
   constexpr int NB = VPT / R;
   const int lglr = lg - LogR<R>::v;
@@ -350,67 +350,82 @@ __device__ __forceinline__ void stage_last_io(SBuf<C> buf, int lg, int ls, int l
   }
 }
 
+// Stage plan of a length-2^LG transform with VPT values per thread (the
+// same plan as fft_lines): n16 radix-16 stages, n8 radix-8 stages, then one
+// radix-2^tail stage.
+template <int LG, int VPT>
+struct FftPlan {
+  static constexpr int n16 = VPT >= 16 ? LG / 4 : 0;
+  static constexpr int n8 = (LG - 4 * n16) / 3;
+  static constexpr int tail = LG - 4 * n16 - 3 * n8;
+  static constexpr int S = n16 + n8 + (tail > 0 ? 1 : 0);
+  __host__ __device__ static constexpr int radix(int s) {
+    return s < n16 ? 16 : (s < n16 + n8 ? 8 : (1 << tail));
+  }
+  __host__ __device__ static constexpr int ns(int s) { return s == 0 ? 1 : ns(s - 1) * radix(s - 1); }
+};
+
+template <int LG, int VPT, bool IL, int ST, typename C, typename Load, typename Epi>
+__device__ __forceinline__ void fft_io_stage(SBuf<C> buf, int ls, int ltx, int nlines,
+                                             const C* __restrict__ tw, int lgmax, bool inv, Load load,
+                                             bool sync_load, Epi epi, bool sync_epi) {
+  typedef FftPlan<LG, VPT> P;
+  constexpr int R = P::radix(ST);
+  constexpr int Ns = P::ns(ST);
+  if constexpr (ST == 0) {
+    stage_first_io<R, VPT, IL>(buf, LG, ls, ltx, nlines, inv, load, sync_load);
+  } else if constexpr (ST == P::S - 1) {
+    stage_last_io<R, VPT, IL>(buf, LG, ls, ltx, nlines, Ns, tw, lgmax, inv, epi, sync_epi);
+  } else if constexpr (IL) {
+    stockham_stage_il<R, VPT>(buf, LG, ltx, Ns, tw, lgmax, inv);
+  } else {
+    stockham_stage<R, VPT>(buf, LG, ls, nlines, Ns, tw, lgmax, inv);
+  }
+  if constexpr (ST + 1 < P::S)
+    fft_io_stage<LG, VPT, IL, ST + 1>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi);
+}
+
 // A full transform of `nlines` lines (IL: 2^ltx interleaved lines) of length
-// 2^lg: legs of the first stage from load(line, index), outputs to
+// 2^LG: legs of the first stage from load(line, index), outputs to
 // epi(line, index, value) in natural order.  sync_load: the loader reads the
 // shared buffer (a barrier separates its reads from the first stage's
 // writes); sync_epi: the epilogue writes the shared buffer.  The buffer is
 // free again after a barrier that follows the call.
-template <int VPT, bool IL, typename C, typename Load, typename Epi>
-__device__ __forceinline__ void fft_io(SBuf<C> buf, int lg, int ls, int ltx, int nlines,
-                                       const C* __restrict__ tw, int lgmax, bool inv, Load load,
-                                       bool sync_load, Epi epi, bool sync_epi) {
-  int rad[12];
-  int S = 0, rem = lg;
-  if (VPT >= 16)
-    while (rem >= 4) { rad[S++] = 16; rem -= 4; }
-  while (rem >= 3) { rad[S++] = 8; rem -= 3; }
-  if (rem == 2) rad[S++] = 4;
-  else if (rem == 1) rad[S++] = 2;
-  constexpr int R16 = VPT >= 16 ? 16 : 8;
-  switch (rad[0]) {
-    case 16: stage_first_io<R16, VPT, IL>(buf, lg, ls, ltx, nlines, inv, load, sync_load); break;
-    case 8: stage_first_io<8, VPT, IL>(buf, lg, ls, ltx, nlines, inv, load, sync_load); break;
-    case 4: stage_first_io<4, VPT, IL>(buf, lg, ls, ltx, nlines, inv, load, sync_load); break;
-    default: stage_first_io<2, VPT, IL>(buf, lg, ls, ltx, nlines, inv, load, sync_load); break;
-  }
-  int Ns = rad[0];
-  for (int s = 1; s + 1 < S; ++s) {
-    if (IL) {
-      switch (rad[s]) {
-        case 16: stockham_stage_il<R16, VPT>(buf, lg, ltx, Ns, tw, lgmax, inv); break;
-        case 8: stockham_stage_il<8, VPT>(buf, lg, ltx, Ns, tw, lgmax, inv); break;
-        case 4: stockham_stage_il<4, VPT>(buf, lg, ltx, Ns, tw, lgmax, inv); break;
-        default: stockham_stage_il<2, VPT>(buf, lg, ltx, Ns, tw, lgmax, inv); break;
-      }
-    } else {
-      switch (rad[s]) {
-        case 16: stockham_stage<R16, VPT>(buf, lg, ls, nlines, Ns, tw, lgmax, inv); break;
-        case 8: stockham_stage<8, VPT>(buf, lg, ls, nlines, Ns, tw, lgmax, inv); break;
-        case 4: stockham_stage<4, VPT>(buf, lg, ls, nlines, Ns, tw, lgmax, inv); break;
-        default: stockham_stage<2, VPT>(buf, lg, ls, nlines, Ns, tw, lgmax, inv); break;
-      }
-    }
-    Ns *= rad[s];
-  }
-  if (S >= 2) {
-    switch (rad[S - 1]) {
-      case 16: stage_last_io<R16, VPT, IL>(buf, lg, ls, ltx, nlines, Ns, tw, lgmax, inv, epi, sync_epi); break;
-      case 8: stage_last_io<8, VPT, IL>(buf, lg, ls, ltx, nlines, Ns, tw, lgmax, inv, epi, sync_epi); break;
-      case 4: stage_last_io<4, VPT, IL>(buf, lg, ls, ltx, nlines, Ns, tw, lgmax, inv, epi, sync_epi); break;
-      default: stage_last_io<2, VPT, IL>(buf, lg, ls, ltx, nlines, Ns, tw, lgmax, inv, epi, sync_epi); break;
-    }
+template <int LG, int VPT, bool IL, typename C, typename Load, typename Epi>
+__device__ __forceinline__ void fft_io_ct(SBuf<C> buf, int ls, int ltx, int nlines,
+                                          const C* __restrict__ tw, int lgmax, bool inv, Load load,
+                                          bool sync_load, Epi epi, bool sync_epi) {
+  if constexpr (FftPlan<LG, VPT>::S >= 2) {
+    fft_io_stage<LG, VPT, IL, 0>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi);
   } else {
-    // one stage: the result is in natural order; each thread reads and hands
-    // on its own elements (an epilogue writing the buffer rewrites the
-    // element it was given)
-    const int L = 1 << lg;
+    // one stage: natural order in shared memory afterwards; each thread
+    // hands on elements it reads (an epilogue writing the buffer rewrites
+    // the element it was given)
+    stage_first_io<FftPlan<LG, VPT>::radix(0), VPT, IL>(buf, LG, ls, ltx, nlines, inv, load, sync_load);
+    constexpr int L = 1 << LG;
     const int total = IL ? (L << ltx) : nlines * L;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
       const int line = IL ? (e & ((1 << ltx) - 1)) : e / L;
       const int j = IL ? (e >> ltx) : e % L;
       epi(line, j, IL ? buf[e] : buf[line * ls + j]);
     }
+  }
+}
+
+// Runtime length: dispatch to the compile-time plan (2^4 .. 2^11).
+template <int VPT, bool IL, typename C, typename Load, typename Epi>
+__device__ __forceinline__ void fft_io(SBuf<C> buf, int lg, int ls, int ltx, int nlines,
+                                       const C* __restrict__ tw, int lgmax, bool inv, Load load,
+                                       bool sync_load, Epi epi, bool sync_epi) {
+  switch (lg) {
+    case 11: fft_io_ct<11, VPT, IL>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
+    case 10: fft_io_ct<10, VPT, IL>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
+    case 9: fft_io_ct<9, VPT, IL>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
+    case 8: fft_io_ct<8, VPT, IL>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
+    case 7: fft_io_ct<7, VPT, IL>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
+    case 6: fft_io_ct<6, VPT, IL>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
+    case 5: fft_io_ct<5, VPT, IL>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
+    default: fft_io_ct<4, VPT, IL>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
   }
 }
 

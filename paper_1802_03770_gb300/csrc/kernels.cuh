@@ -382,19 +382,21 @@ __device__ __forceinline__ void body_cols(const ColsArgs<T>& a, int bx, int by) 
     }
   }
   __syncthreads();
-  const bool inv_only = (a.mode == COLS_INV);
-  fft_lines_il<VPT>(buf, a.lg, ltx, a.tw, a.lgmax, inv_only);
   if (a.mode == COLS_CONV) {
+    // forward FFT whose last stage multiplies by the symbol on the way out
     const size_t soff = a.Lo ? (size_t)min(o, a.Lo - o) * a.sig_outer : 0;
-    for (int e = threadIdx.x; e < total; e += THREADS) {
-      const int k = e >> ltx, c = e & (TX - 1);
-      if (c < ncol) {
-        const int kk = min(k, L - k);
-        buf[e] = cscale(buf[e], a.sig[(size_t)kk * a.sig_line + soff + kx0 + c]);
-      }
-    }
+    const T* __restrict__ sig = a.sig + soff + kx0;
+    const long long sig_line = a.sig_line;
+    auto ld = [=](int c, int k) -> C { return buf[(k << ltx) + c]; };
+    auto epi = [=](int c, int k, C v) {
+      if (c < ncol) v = cscale(v, sig[(size_t)min(k, L - k) * sig_line + c]);
+      buf[(k << ltx) + c] = v;
+    };
+    fft_io<VPT, true>(buf, a.lg, 0, ltx, TX, a.tw, a.lgmax, false, ld, true, epi, true);
     __syncthreads();
     fft_lines_il<VPT>(buf, a.lg, ltx, a.tw, a.lgmax, true);
+  } else {
+    fft_lines_il<VPT>(buf, a.lg, ltx, a.tw, a.lgmax, a.mode == COLS_INV);
   }
   const int tout = TX * a.rows_out;
   for (int e = threadIdx.x; e < tout; e += THREADS) {
@@ -610,10 +612,12 @@ __device__ __forceinline__ void body_dst_rows(const DstRowsArgs<T>& a, int bx, i
     }
   }
   __syncthreads();
-  fft_lines<VPT>(buf, a.lg, ls, nl, a.tw, a.lgmax, false);
-  for (int e = threadIdx.x; e < nl * L; e += THREADS) {
-    const int q = e >> a.lg, k = e & (L - 1);
-    buf[q * ls + k] = cmul(buf[q * ls + k], a.bhat[k]);
+  {
+    // forward FFT whose last stage multiplies by bhat on the way out
+    const C* __restrict__ bhat = a.bhat;
+    auto ld = [=](int q, int k) -> C { return buf[q * ls + k]; };
+    auto epi = [=](int q, int k, C v) { buf[q * ls + k] = cmul(v, bhat[k]); };
+    fft_io<VPT, false>(buf, a.lg, ls, 0, nl, a.tw, a.lgmax, false, ld, true, epi, true);
   }
   __syncthreads();
   fft_lines<VPT>(buf, a.lg, ls, nl, a.tw, a.lgmax, true);
