@@ -350,9 +350,9 @@ __device__ __forceinline__ void stage_last_io(SBuf<C> buf, int lg, int ls, int l
   }
 }
 
-// Stage plan of a length-2^LG transform with VPT values per thread (the
-// same plan as fft_lines): n16 radix-16 stages, n8 radix-8 stages, then one
-// radix-2^tail stage.
+// Stage plan of a length-2^LG transform with VPT values per thread: radix 16
+// while at least four factors of two remain (if VPT allows), then radix 8,
+// then one radix-4 or radix-2 stage (n16, n8, tail).
 template <int LG, int VPT>
 struct FftPlan {
   static constexpr int n16 = VPT >= 16 ? LG / 4 : 0;
@@ -429,48 +429,18 @@ __device__ __forceinline__ void fft_io(SBuf<C> buf, int lg, int ls, int ltx, int
   }
 }
 
-// Stage plan: radix 16 while at least four factors of two remain (if VPT
-// allows), then radix 8, then one radix-4 or radix-2 stage.
-template <int VPT, typename C>
-__device__ __forceinline__ void fft_lines(SBuf<C> buf, int lg, int ls, int nlines, const C* __restrict__ tw,
-                                          int lgmax, bool inv) {
-  int Ns = 1;
-  int rem = lg;
-  if (VPT >= 16) {
-    while (rem >= 4) {
-      stockham_stage<(VPT >= 16 ? 16 : 8), VPT>(buf, lg, ls, nlines, Ns, tw, lgmax, inv);
-      Ns <<= 4;
-      rem -= 4;
-    }
-  }
-  while (rem >= 3) {
-    stockham_stage<8, VPT>(buf, lg, ls, nlines, Ns, tw, lgmax, inv);
-    Ns <<= 3;
-    rem -= 3;
-  }
-  if (rem == 2) stockham_stage<4, VPT>(buf, lg, ls, nlines, Ns, tw, lgmax, inv);
-  else if (rem == 1) stockham_stage<2, VPT>(buf, lg, ls, nlines, Ns, tw, lgmax, inv);
-}
-
-template <int VPT, typename C>
-__device__ __forceinline__ void fft_lines_il(SBuf<C> buf, int lg, int ltx, const C* __restrict__ tw,
-                                             int lgmax, bool inv) {
-  int Ns = 1;
-  int rem = lg;
-  if (VPT >= 16) {
-    while (rem >= 4) {
-      stockham_stage_il<(VPT >= 16 ? 16 : 8), VPT>(buf, lg, ltx, Ns, tw, lgmax, inv);
-      Ns <<= 4;
-      rem -= 4;
-    }
-  }
-  while (rem >= 3) {
-    stockham_stage_il<8, VPT>(buf, lg, ltx, Ns, tw, lgmax, inv);
-    Ns <<= 3;
-    rem -= 3;
-  }
-  if (rem == 2) stockham_stage_il<4, VPT>(buf, lg, ltx, Ns, tw, lgmax, inv);
-  else if (rem == 1) stockham_stage_il<2, VPT>(buf, lg, ltx, Ns, tw, lgmax, inv);
+// In-place transform of lines in shared memory (natural order in and out)
+// with the compile-time stage plan; ends with a barrier.
+template <int VPT, bool IL, typename C>
+__device__ __forceinline__ void fft_smem(SBuf<C> buf, int lg, int ls, int ltx, int nlines,
+                                         const C* __restrict__ tw, int lgmax, bool inv) {
+  auto ld = [=](int q, int k) -> C { return IL ? buf[(k << ltx) + q] : buf[q * ls + k]; };
+  auto st = [=](int q, int k, C v) {
+    if (IL) buf[(k << ltx) + q] = v;
+    else buf[q * ls + k] = v;
+  };
+  fft_io<VPT, IL>(buf, lg, ls, ltx, nlines, tw, lgmax, inv, ld, true, st, true);
+  __syncthreads();
 }
 
 }  // namespace fl

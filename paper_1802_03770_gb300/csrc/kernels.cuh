@@ -303,7 +303,7 @@ __device__ __forceinline__ void body_rows_fwd(const RowsFwdArgs<T>& a, int bx, i
     }
   }
   __syncthreads();
-  fft_lines<VPT>(buf, a.lg, ls, nl, a.tw, a.lgmax, false);
+  fft_smem<VPT, false>(buf, a.lg, ls, 0, nl, a.tw, a.lgmax, false);
   for (int q = 0; q < nl; ++q) {
     const int ra = 2 * (pair0 + q), rb = ra + 1;
     const bool hb = rb < a.rows;
@@ -394,10 +394,17 @@ __device__ __forceinline__ void body_cols(const ColsArgs<T>& a, int bx, int by) 
     };
     fft_io<VPT, true>(buf, a.lg, 0, ltx, TX, a.tw, a.lgmax, false, ld, true, epi, true);
     __syncthreads();
-    fft_lines_il<VPT>(buf, a.lg, ltx, a.tw, a.lgmax, true);
-  } else {
-    fft_lines_il<VPT>(buf, a.lg, ltx, a.tw, a.lgmax, a.mode == COLS_INV);
+    // inverse FFT whose last stage writes the kept rows to global
+    const int rows_out = a.rows_out;
+    const long long lstride = a.lstride;
+    auto ld2 = [=](int c, int k) -> C { return buf[(k << ltx) + c]; };
+    auto epi2 = [=](int c, int k, C v) {
+      if (c < ncol && k < rows_out) base[(size_t)k * lstride + c] = v;
+    };
+    fft_io<VPT, true>(buf, a.lg, 0, ltx, TX, a.tw, a.lgmax, true, ld2, true, epi2, false);
+    return;
   }
+  fft_smem<VPT, true>(buf, a.lg, 0, ltx, TX, a.tw, a.lgmax, a.mode == COLS_INV);
   const int tout = TX * a.rows_out;
   for (int e = threadIdx.x; e < tout; e += THREADS) {
     const int r = e >> ltx, c = e & (TX - 1);
@@ -469,7 +476,7 @@ __device__ __forceinline__ void body_rows_inv(const RowsInvArgs<T>& a, int bx, i
     }
   }
   __syncthreads();
-  fft_lines<VPT>(buf, a.lg, ls, nl, a.tw, a.lgmax, true);
+  fft_smem<VPT, false>(buf, a.lg, ls, 0, nl, a.tw, a.lgmax, true);
   DotAcc<T> part;
   const T* __restrict__ xin = (a.cx != 0.0) ? a.x : nullptr;
   const T* __restrict__ bin = (a.cb != 0.0) ? a.b : nullptr;
@@ -514,29 +521,18 @@ __global__ void __launch_bounds__(THREADS, min_ctas(THREADS)) k_rows_inv(RowsInv
   body_rows_inv<T, THREADS, VPT>(a, blockIdx.x, blockIdx.y);
 }
 
-// In place on `nl` lines of length L in shared memory: y = IFFT(FFT(v) * bhat),
-// the chirp-z convolution of the DST-I (bhat already holds the 1/L).
-template <int VPT, typename C>
-__device__ __forceinline__ void chirp_conv(SBuf<C> buf, int ls, int nl, int L, int lg, int lgmax,
-                                           const C* __restrict__ tw, const C* __restrict__ bhat) {
-  fft_lines<VPT>(buf, lg, ls, nl, tw, lgmax, false);
-  for (int e = threadIdx.x; e < nl * L; e += blockDim.x) {
-    const int q = e >> lg, k = e & (L - 1);
-    buf[q * ls + k] = cmul(buf[q * ls + k], bhat[k]);
-  }
-  __syncthreads();
-  fft_lines<VPT>(buf, lg, ls, nl, tw, lgmax, true);
-}
-
-// Interleaved-line version of chirp_conv (element j of line c at j * TX + c).
+// In place on 2^ltx interleaved lines of length L = 2^lg in shared memory
+// (element j of line c at j * 2^ltx + c): y = IFFT(FFT(v) * bhat), the
+// chirp-z convolution of the DST-I (bhat already holds the 1/L); the
+// multiply is done by the forward transform's last stage.
 template <int VPT, typename C>
 __device__ __forceinline__ void chirp_conv_il(SBuf<C> buf, int ltx, int L, int lg, int lgmax,
                                               const C* __restrict__ tw, const C* __restrict__ bhat) {
-  fft_lines_il<VPT>(buf, lg, ltx, tw, lgmax, false);
-  const int total = L << ltx;
-  for (int e = threadIdx.x; e < total; e += blockDim.x) buf[e] = cmul(buf[e], bhat[e >> ltx]);
+  auto ld = [=](int c, int k) -> C { return buf[(k << ltx) + c]; };
+  auto epi = [=](int c, int k, C v) { buf[(k << ltx) + c] = cmul(v, bhat[k]); };
+  fft_io<VPT, true>(buf, lg, 0, ltx, 1 << ltx, tw, lgmax, false, ld, true, epi, true);
   __syncthreads();
-  fft_lines_il<VPT>(buf, lg, ltx, tw, lgmax, true);
+  fft_smem<VPT, true>(buf, lg, 0, ltx, 1 << ltx, tw, lgmax, true);
 }
 
 // ---------------------------------------------------------------------------
@@ -620,19 +616,24 @@ __device__ __forceinline__ void body_dst_rows(const DstRowsArgs<T>& a, int bx, i
     fft_io<VPT, false>(buf, a.lg, ls, 0, nl, a.tw, a.lgmax, false, ld, true, epi, true);
   }
   __syncthreads();
-  fft_lines<VPT>(buf, a.lg, ls, nl, a.tw, a.lgmax, true);
   DotAcc<T> dp;
-  const T post = (T)a.post;
-  for (int q = 0; q < nl; ++q) {
-    const SBuf<C> lb = buf.at(q * ls);
-    const size_t base = (size_t)(row0 + q) * a.n;
-#pragma unroll 4
-    for (int k = threadIdx.x; k < a.n; k += THREADS) {
-      const C y = cmul(a.chirp[k], lb[k]);
-      const T v = y.y * post;
-      a.out[base + k] = v;
-      if (a.dotw) dp.add(v * a.dotw[base + k]);
-    }
+  {
+    // inverse FFT whose last stage writes the DST coefficients to global
+    const T post = (T)a.post;
+    const C* __restrict__ chirp = a.chirp;
+    T* __restrict__ outp = a.out;
+    const T* __restrict__ dw = a.dotw;
+    const int n = a.n;
+    auto ld = [=](int q, int k) -> C { return buf[q * ls + k]; };
+    auto epi = [=, &dp](int q, int k, C v) {
+      if (k < n) {
+        const size_t idx = (size_t)(row0 + q) * n + k;
+        const T o = cmul(chirp[k], v).y * post;
+        outp[idx] = o;
+        if (dw) dp.add(o * dw[idx]);
+      }
+    };
+    fft_io<VPT, false>(buf, a.lg, ls, 0, nl, a.tw, a.lgmax, true, ld, true, epi, false);
   }
   if (a.pre == DPRE_UPDATE) {
     const double s = rr.cta_total(red);

@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(THREADS) k_rows_c2c(double2* buf, int rows, in
     sb[q * ls + j] = buf[(size_t)(r0 + q) * L + j];
   }
   __syncthreads();
-  fft_lines<VPT>(sb, lg, ls, nl, tw, lgmax, false);
+  fft_smem<VPT, false>(sb, lg, ls, 0, nl, tw, lgmax, false);
   for (int e = threadIdx.x; e < nl * L; e += THREADS) {
     const int q = e / L, j = e - q * L;
     buf[(size_t)(r0 + q) * L + j] = sb[q * ls + j];
