@@ -177,144 +177,36 @@ __device__ __forceinline__ void twiddles(const C* __restrict__ tw, int step, boo
   }
 }
 
-// One Stockham stage of radix R over `nlines` lines of length L = 2^lg
-// (line q at buf + q * ls).  Contains two __syncthreads().
-template <int R, int VPT, typename C>
-__device__ __forceinline__ void stockham_stage(SBuf<C> buf, int lg, int ls, int nlines, int Ns,
-                                               const C* __restrict__ tw, int lgmax, bool inv) {
-  constexpr int NB = VPT / R;  // butterflies per thread
-  const int lglr = lg - LogR<R>::v;
-  const int LR = 1 << lglr;
-  const int total = nlines << lglr;
-  C v[NB][R];
-  int dst[NB];
-#pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    const int g = threadIdx.x + b * blockDim.x;
-    dst[b] = -1;
-    if (g < total) {
-      const int line = g >> lglr;
-      const int j = g & (LR - 1);
-      const int k = j & (Ns - 1);
-      const SBuf<C> base = buf.at(line * ls);
-#pragma unroll
-      for (int r = 0; r < R; ++r) v[b][r] = base[j + r * LR];
-      if (k != 0) {
-        // twiddle w^(r k) = tw[r * k * Lmax / (Ns R)]
-        C w[R];
-        twiddles<R>(tw, k << (lgmax - __ffs(Ns * R) + 1), inv, w);
-#pragma unroll
-        for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], w[r]);
-      }
-      dftR<R>(v[b], inv);
-      dst[b] = line * ls + (j - k) * R + k;
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    if (dst[b] >= 0) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) buf[dst[b] + r * Ns] = v[b][r];
-    }
-  }
-  __syncthreads();
-}
+// One Stockham stage with a compile-time shape: radix R, length 2^LG,
+// NS = product of the radices of the earlier stages.  MODE selects where the
+// legs come from and where the outputs go:
+//   STAGE_FIRST: legs from load(line, index) (NS = 1, no twiddles), outputs
+//                to shared memory; a barrier between the two when sync_io
+//                (the loader reads the buffer);
+//   STAGE_MID:   shared memory to shared memory (two barriers);
+//   STAGE_LAST:  legs from shared memory, outputs (natural order) to
+//                epi(line, index, value); a barrier before the epilogue when
+//                sync_io (the epilogue writes the buffer), none after.
+// STAGE_FIRST and STAGE_MID end with a barrier.  With the shape known at
+// compile time, leg r of a butterfly sits at a fixed physical offset from
+// leg 0 (the SBuf pad is one element per 16, and the leg stride is a
+// multiple of 16), so only the first leg's address is padded.
+enum { STAGE_FIRST = 0, STAGE_MID = 1, STAGE_LAST = 2 };
 
-// The same stage for 2^ltx interleaved lines (element j of line c at
-// j * 2^ltx + c).  Consecutive threads take consecutive lines, so the leg
-// reads are contiguous.
-template <int R, int VPT, typename C>
-__device__ __forceinline__ void stockham_stage_il(SBuf<C> buf, int lg, int ltx, int Ns,
-                                                  const C* __restrict__ tw, int lgmax, bool inv) {
+__device__ __forceinline__ int sbuf_phys(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int clog2(int x) { return x <= 1 ? 0 : 1 + clog2(x / 2); }
+
+template <int R, int VPT, bool IL, int LG, int NS, int MODE, typename C, typename Load, typename Epi>
+__device__ __forceinline__ void stage_ct(SBuf<C> buf, int ls, int ltx, int nlines,
+                                         const C* __restrict__ tw, int lgmax, bool inv, Load& load,
+                                         Epi& epi, bool sync_io) {
   constexpr int NB = VPT / R;
-  const int LR = 1 << (lg - LogR<R>::v);
-  const int tx = 1 << ltx;
-  const int total = LR << ltx;
-  C v[NB][R];
-  int dst[NB];
-#pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    const int g = threadIdx.x + b * blockDim.x;
-    dst[b] = -1;
-    if (g < total) {
-      const int c = g & (tx - 1);
-      const int j = g >> ltx;
-      const int k = j & (Ns - 1);
-#pragma unroll
-      for (int r = 0; r < R; ++r) v[b][r] = buf[((j + r * LR) << ltx) + c];
-      if (k != 0) {
-        C w[R];
-        twiddles<R>(tw, k << (lgmax - __ffs(Ns * R) + 1), inv, w);
-#pragma unroll
-        for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], w[r]);
-      }
-      dftR<R>(v[b], inv);
-      dst[b] = (((j - k) * R + k) << ltx) + c;
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    if (dst[b] >= 0) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) buf[dst[b] + ((r * Ns) << ltx)] = v[b][r];
-    }
-  }
-  __syncthreads();
-}
-
-// --- stages with fused input / output ---------------------------------------
-//
-// The first stage (Ns = 1, no twiddles) can take its legs from a loader
-// functor load(line, index) instead of shared memory, and the last stage can
-// hand its outputs to an epilogue functor epi(line, index, value) instead of
-// writing them back: the global loads and stores of a pass then happen in the
-// first and last stage, which saves two shared-memory passes and their
-// barriers.  `IL` selects the interleaved-line layout (line = column c of a
-// tile of 2^ltx columns).
-
-template <int R, int VPT, bool IL, typename C, typename Load>
-__device__ __forceinline__ void stage_first_io(SBuf<C> buf, int lg, int ls, int ltx, int nlines,
-                                               bool inv, Load load, bool sync_mid) {
-  constexpr int NB = VPT / R;
-  const int lglr = lg - LogR<R>::v;
-  const int LR = 1 << lglr;
-  const int total = IL ? (LR << ltx) : (nlines << lglr);
-  C v[NB][R];
-  int dst[NB];
-#pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    const int g = threadIdx.x + b * blockDim.x;
-    dst[b] = -1;
-    if (g < total) {
-      const int line = IL ? (g & ((1 << ltx) - 1)) : (g >> lglr);
-      const int j = IL ? (g >> ltx) : (g & (LR - 1));
-#pragma unroll
-      for (int r = 0; r < R; ++r) v[b][r] = load(line, j + r * LR);
-      dftR<R>(v[b], inv);
-      dst[b] = IL ? (((j * R) << ltx) + line) : (line * ls + j * R);
-    }
-  }
-  if (sync_mid) __syncthreads();
-#pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    if (dst[b] >= 0) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) buf[dst[b] + (IL ? (r << ltx) : r)] = v[b][r];
-    }
-  }
-  __syncthreads();
-}
-
-template <int R, int VPT, bool IL, typename C, typename Epi>
-__device__ __forceinline__ void stage_last_io(SBuf<C> buf, int lg, int ls, int ltx, int nlines, int Ns,
-                                              const C* __restrict__ tw, int lgmax, bool inv, Epi epi,
-                                              bool sync_mid) {
-  constexpr int NB = VPT / R;
-  const int lglr = lg - LogR<R>::v;
-  const int LR = 1 << lglr;
-  const int total = IL ? (LR << ltx) : (nlines << lglr);
+  constexpr int LGLR = LG - LogR<R>::v;
+  constexpr int LR = 1 << LGLR;
+  const int total = IL ? (LR << ltx) : (nlines << LGLR);
+  // physical leg strides (valid when the logical stride is a multiple of 16)
+  const int rd_stride = IL ? sbuf_phys(LR << ltx) : sbuf_phys(LR);
+  const int wr_stride = IL ? sbuf_phys(NS << ltx) : sbuf_phys(NS);
   C v[NB][R];
   int line_of[NB], out0[NB];
 #pragma unroll
@@ -323,31 +215,62 @@ __device__ __forceinline__ void stage_last_io(SBuf<C> buf, int lg, int ls, int l
     out0[b] = -1;
     line_of[b] = 0;
     if (g < total) {
-      const int line = IL ? (g & ((1 << ltx) - 1)) : (g >> lglr);
+      const int line = IL ? (g & ((1 << ltx) - 1)) : (g >> LGLR);
       const int j = IL ? (g >> ltx) : (g & (LR - 1));
-      const int k = j & (Ns - 1);
+      const int k = j & (NS - 1);
+      if constexpr (MODE == STAGE_FIRST) {
 #pragma unroll
-      for (int r = 0; r < R; ++r)
-        v[b][r] = IL ? buf[((j + r * LR) << ltx) + line] : buf[line * ls + j + r * LR];
-      if (k != 0) {
-        C w[R];
-        twiddles<R>(tw, k << (lgmax - __ffs(Ns * R) + 1), inv, w);
+        for (int r = 0; r < R; ++r) v[b][r] = load(line, j + r * LR);
+      } else {
+        const int l0 = IL ? ((j << ltx) + line) : (line * ls + j);
+        if ((IL ? ((LR << ltx) & 15) : (LR & 15)) == 0) {
+          const C* p0 = buf.p + sbuf_phys(l0);
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], w[r]);
+          for (int r = 0; r < R; ++r) v[b][r] = p0[r * rd_stride];
+        } else {
+#pragma unroll
+          for (int r = 0; r < R; ++r) v[b][r] = buf[l0 + (IL ? ((r * LR) << ltx) : r * LR)];
+        }
+        if (NS > 1 && k != 0) {
+          // twiddle w^(r k) = tw[r * k * Lmax / (NS R)]
+          C w[R];
+          twiddles<R>(tw, k << (lgmax - clog2(NS * R)), inv, w);
+#pragma unroll
+          for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], w[r]);
+        }
       }
       dftR<R>(v[b], inv);
       line_of[b] = line;
       out0[b] = (j - k) * R + k;
     }
   }
-  if (sync_mid) __syncthreads();
+  if (MODE == STAGE_MID || sync_io) __syncthreads();
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
     if (out0[b] >= 0) {
+      if constexpr (MODE == STAGE_LAST) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) epi(line_of[b], out0[b] + r * Ns, v[b][r]);
+        for (int r = 0; r < R; ++r) epi(line_of[b], out0[b] + r * NS, v[b][r]);
+      } else {
+        const int d0 = IL ? ((out0[b] << ltx) + line_of[b]) : (line_of[b] * ls + out0[b]);
+        // NS a multiple of 16: fixed physical stride; NS = 1: the R legs are
+        // R consecutive logical places inside one 16-element group (R | 16)
+        if (!IL && NS == 1) {
+          C* p0 = buf.p + sbuf_phys(d0);
+#pragma unroll
+          for (int r = 0; r < R; ++r) p0[r] = v[b][r];
+        } else if ((IL ? ((NS << ltx) & 15) : (NS & 15)) == 0) {
+          C* p0 = buf.p + sbuf_phys(d0);
+#pragma unroll
+          for (int r = 0; r < R; ++r) p0[r * wr_stride] = v[b][r];
+        } else {
+#pragma unroll
+          for (int r = 0; r < R; ++r) buf[d0 + (IL ? ((r * NS) << ltx) : r * NS)] = v[b][r];
+        }
+      }
     }
   }
+  if constexpr (MODE != STAGE_LAST) __syncthreads();
 }
 
 // Stage plan of a length-2^LG transform with VPT values per thread: radix 16
@@ -372,15 +295,9 @@ __device__ __forceinline__ void fft_io_stage(SBuf<C> buf, int ls, int ltx, int n
   typedef FftPlan<LG, VPT> P;
   constexpr int R = P::radix(ST);
   constexpr int Ns = P::ns(ST);
-  if constexpr (ST == 0) {
-    stage_first_io<R, VPT, IL>(buf, LG, ls, ltx, nlines, inv, load, sync_load);
-  } else if constexpr (ST == P::S - 1) {
-    stage_last_io<R, VPT, IL>(buf, LG, ls, ltx, nlines, Ns, tw, lgmax, inv, epi, sync_epi);
-  } else if constexpr (IL) {
-    stockham_stage_il<R, VPT>(buf, LG, ltx, Ns, tw, lgmax, inv);
-  } else {
-    stockham_stage<R, VPT>(buf, LG, ls, nlines, Ns, tw, lgmax, inv);
-  }
+  constexpr int MODE = ST == 0 ? STAGE_FIRST : (ST == P::S - 1 ? STAGE_LAST : STAGE_MID);
+  stage_ct<R, VPT, IL, LG, Ns, MODE>(buf, ls, ltx, nlines, tw, lgmax, inv, load, epi,
+                                     MODE == STAGE_FIRST ? sync_load : sync_epi);
   if constexpr (ST + 1 < P::S)
     fft_io_stage<LG, VPT, IL, ST + 1>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi);
 }
@@ -401,7 +318,8 @@ __device__ __forceinline__ void fft_io_ct(SBuf<C> buf, int ls, int ltx, int nlin
     // one stage: natural order in shared memory afterwards; each thread
     // hands on elements it reads (an epilogue writing the buffer rewrites
     // the element it was given)
-    stage_first_io<FftPlan<LG, VPT>::radix(0), VPT, IL>(buf, LG, ls, ltx, nlines, inv, load, sync_load);
+    stage_ct<FftPlan<LG, VPT>::radix(0), VPT, IL, LG, 1, STAGE_FIRST>(buf, ls, ltx, nlines, tw, lgmax, inv,
+                                                                      load, epi, sync_load);
     constexpr int L = 1 << LG;
     const int total = IL ? (L << ltx) : nlines * L;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
