@@ -249,15 +249,18 @@ __device__ __forceinline__ void body_rows_fwd(const RowsFwdArgs<T>& a, int bx, i
   const int npairs = (a.rows + 1) / 2;
   const int nl = min(NL, npairs - pair0);
   const T beta = (a.pre == PRE_PUPDATE) ? (T)a.st->beta : (T)0;
-  // loads first (U elements per thread in flight), then the stores
+  // loads first (U elements per thread in flight), then the stores.  Only
+  // the lower half of each line is written (n <= L/2); the transform's first
+  // stage reads the upper half as zeros.
   constexpr int U = 4;
-  const int tot = nl * L;
+  const int hL = L >> 1;
+  const int tot = nl * hL;
   for (int e0 = threadIdx.x; e0 < tot; e0 += THREADS * U) {
     T va[U], vb[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int e = e0 + u * THREADS;
-      const int q = e >> a.lg, j = e & (L - 1);
+      const int q = e >> (a.lg - 1), j = e & (hL - 1);
       const int ra = 2 * (pair0 + q), rb = ra + 1;
       va[u] = 0;
       vb[u] = 0;
@@ -281,7 +284,7 @@ __device__ __forceinline__ void body_rows_fwd(const RowsFwdArgs<T>& a, int bx, i
     for (int u = 0; u < U; ++u) {
       const int e = e0 + u * THREADS;
       if (e >= tot) continue;
-      const int q = e >> a.lg, j = e & (L - 1);
+      const int q = e >> (a.lg - 1), j = e & (hL - 1);
       const int ra = 2 * (pair0 + q), rb = ra + 1;
       T xa = va[u], xb = vb[u];
       if (j < a.n) {
@@ -303,7 +306,12 @@ __device__ __forceinline__ void body_rows_fwd(const RowsFwdArgs<T>& a, int bx, i
     }
   }
   __syncthreads();
-  fft_smem<VPT, false>(buf, a.lg, ls, 0, nl, a.tw, a.lgmax, false);
+  {
+    auto ld = [=](int q, int k) -> C { return k < hL ? buf[q * ls + k] : cmake<C>((T)0, (T)0); };
+    auto st = [=](int q, int k, C v) { buf[q * ls + k] = v; };
+    fft_io<VPT, false>(buf, a.lg, ls, 0, nl, a.tw, a.lgmax, false, ld, true, st, true);
+  }
+  __syncthreads();
   for (int q = 0; q < nl; ++q) {
     const int ra = 2 * (pair0 + q), rb = ra + 1;
     const bool hb = rb < a.rows;
@@ -365,7 +373,10 @@ __device__ __forceinline__ void body_cols(const ColsArgs<T>& a, int bx, int by) 
   const int o = by;
   const int ncol = min(TX, a.H - kx0);
   C* base = a.S + (size_t)o * a.ostride + kx0;
-  const int total = TX * L;
+  // the convolution's input has rows_in <= L/2 rows: only the lower half of
+  // the tile is written, the transform's first stage reads the rest as zeros
+  const int hL = L >> 1;
+  const int total = TX * (a.mode == COLS_CONV ? hL : L);
   for (int e0 = threadIdx.x; e0 < total; e0 += THREADS * U) {
     C v[U];
 #pragma unroll
@@ -387,7 +398,7 @@ __device__ __forceinline__ void body_cols(const ColsArgs<T>& a, int bx, int by) 
     const size_t soff = a.Lo ? (size_t)min(o, a.Lo - o) * a.sig_outer : 0;
     const T* __restrict__ sig = a.sig + soff + kx0;
     const long long sig_line = a.sig_line;
-    auto ld = [=](int c, int k) -> C { return buf[(k << ltx) + c]; };
+    auto ld = [=](int c, int k) -> C { return k < hL ? buf[(k << ltx) + c] : cmake<C>((T)0, (T)0); };
     auto epi = [=](int c, int k, C v) {
       if (c < ncol) v = cscale(v, sig[(size_t)min(k, L - k) * sig_line + c]);
       buf[(k << ltx) + c] = v;
@@ -576,32 +587,54 @@ __device__ __forceinline__ void body_dst_rows(const DstRowsArgs<T>& a, int bx, i
   const int NL = (VPT * THREADS) / L;
   const int row0 = bx * NL;
   const int nl = min(NL, a.rows - row0);
+  // Only the lower half of each line is written (n <= L/2); the transform's
+  // first stage reads the upper half as zeros.
   DotAcc<T> rr;
+  const int hL = L >> 1;
+  const int tot = nl * hL;
   if (a.pre == DPRE_UPDATE) {
     const T al = (T)a.st->alpha;
     T* __restrict__ xv = a.x;
     T* __restrict__ rv = a.r;
     const T* __restrict__ pv = a.p;
     const T* __restrict__ qv = a.q;
-#pragma unroll 4
-    for (int e = threadIdx.x; e < nl * L; e += THREADS) {
-      const int q = e >> a.lg, j = e & (L - 1);
-      C v = cmake<C>((T)0, (T)0);
-      if (j < a.n) {
-        const size_t idx = (size_t)(row0 + q) * a.n + j;
-        const T xn = xv[idx] + al * pv[idx];
-        const T rn = rv[idx] - al * qv[idx];
-        xv[idx] = xn;
-        rv[idx] = rn;
-        rr.add(rn * rn);
-        v = cscale(a.chirp[j], rn);
+    constexpr int U = 4;   // elements in flight per thread
+    for (int e0 = threadIdx.x; e0 < tot; e0 += THREADS * U) {
+      T xo[U], ro[U], po[U], qo[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * THREADS;
+        const int q = e >> (a.lg - 1), j = e & (hL - 1);
+        xo[u] = ro[u] = po[u] = qo[u] = (T)0;
+        if (e < tot && j < a.n) {
+          const size_t idx = (size_t)(row0 + q) * a.n + j;
+          xo[u] = xv[idx];
+          ro[u] = rv[idx];
+          po[u] = pv[idx];
+          qo[u] = qv[idx];
+        }
       }
-      buf[q * ls + j] = v;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * THREADS;
+        if (e >= tot) continue;
+        const int q = e >> (a.lg - 1), j = e & (hL - 1);
+        C v = cmake<C>((T)0, (T)0);
+        if (j < a.n) {
+          const size_t idx = (size_t)(row0 + q) * a.n + j;
+          const T rn = ro[u] - al * qo[u];
+          xv[idx] = xo[u] + al * po[u];
+          rv[idx] = rn;
+          rr.add(rn * rn);
+          v = cscale(a.chirp[j], rn);
+        }
+        buf[q * ls + j] = v;
+      }
     }
   } else {
 #pragma unroll 4
-    for (int e = threadIdx.x; e < nl * L; e += THREADS) {
-      const int q = e >> a.lg, j = e & (L - 1);
+    for (int e = threadIdx.x; e < tot; e += THREADS) {
+      const int q = e >> (a.lg - 1), j = e & (hL - 1);
       C v = cmake<C>((T)0, (T)0);
       if (j < a.n) v = cscale(a.chirp[j], a.in[(size_t)(row0 + q) * a.n + j]);
       buf[q * ls + j] = v;
@@ -611,7 +644,7 @@ __device__ __forceinline__ void body_dst_rows(const DstRowsArgs<T>& a, int bx, i
   {
     // forward FFT whose last stage multiplies by bhat on the way out
     const C* __restrict__ bhat = a.bhat;
-    auto ld = [=](int q, int k) -> C { return buf[q * ls + k]; };
+    auto ld = [=](int q, int k) -> C { return k < hL ? buf[q * ls + k] : cmake<C>((T)0, (T)0); };
     auto epi = [=](int q, int k, C v) { buf[q * ls + k] = cmul(v, bhat[k]); };
     fft_io<VPT, false>(buf, a.lg, ls, 0, nl, a.tw, a.lgmax, false, ld, true, epi, true);
   }
