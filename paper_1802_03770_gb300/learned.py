@@ -134,12 +134,25 @@ def main():
     ap.add_argument("--eval", type=int, default=32, help="held-out seeds to evaluate")
     ap.add_argument("--out", default=None)
     ap.add_argument("--report", default=None)
+    ap.add_argument("--load", default=None,
+                    help="evaluate these weights instead of training (e.g. weights/unet512.bin)")
+    ap.add_argument("--tensor-cores", action="store_true",
+                    help="run the network's 3x3 convolutions on the tcgen05 path")
     args = ap.parse_args()
-    net, hist = train(args.n, args.pairs, args.batch, args.lr, args.seed,
-                      max_seconds=args.max_seconds)
-    print(json.dumps({"history": hist}), flush=True)
-    if args.out:
-        net.save(args.out)
+    if args.load:
+        import torch
+        torch.cuda.init()
+        net = Net(args.n, args.n)
+        net.load(args.load)
+        hist = []
+    else:
+        net, hist = train(args.n, args.pairs, args.batch, args.lr, args.seed,
+                          max_seconds=args.max_seconds)
+        print(json.dumps({"history": hist}), flush=True)
+        if args.out:
+            net.save(args.out)
+    if args.tensor_cores:
+        net.tensor_cores(True)
     ev = evaluate(net, args.n, range(10000, 10000 + args.eval))
     summary = {
         "history": hist,
