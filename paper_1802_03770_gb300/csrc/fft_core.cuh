@@ -14,9 +14,10 @@
 // number of values a thread holds is VPT = lines * L / blockDim.x, a
 // compile-time bound chosen by the launcher.
 //
-// Twiddles come from a table tw[k] = exp(-2 pi i k / Lmax) computed on the
-// host in long double; a stage loads w, w^2, w^4 (and w^8) from it and forms
-// the other powers by complex products.
+// Twiddles: FP64 stages load w, w^2, w^4 (and w^8) from a table
+// tw[k] = exp(-2 pi i k / Lmax) computed on the host in long double; FP32
+// stages compute w with sincospif and the even powers by squaring; the
+// other powers are complex products (see twiddles()).
 //
 // Two storage layouts: lines of stride ls (element j of line q at
 // q * ls + j, ls a multiple of 16), and 2^ltx interleaved lines (element j
@@ -149,29 +150,41 @@ template <> struct LogR<4> { static constexpr int v = 2; };
 template <> struct LogR<8> { static constexpr int v = 3; };
 template <> struct LogR<16> { static constexpr int v = 4; };
 
-// w[r] = w1^r, r = 0..R-1, for w1 = tw[step] (conjugated for the inverse):
-// w1, w2, w4, w8 come from the table, the rest are products.
+// w[r] = w1^r, r = 0..R-1, for w1 = exp(-2 pi i step / Lmax) (conjugated
+// for the inverse).  FP64: w1, w2, w4, w8 come from the long-double table tw
+// and the rest are products.  FP32: w1 = sincospif(-2 step / Lmax) (the
+// argument is exact), w2, w4, w8 by squaring, the rest by products -- no
+// table load on the stage's critical path (measured 3 % faster solves on
+// the 1024^2 workload than the table, at unchanged iteration counts).
 template <int R, typename C>
-__device__ __forceinline__ void twiddles(const C* __restrict__ tw, int step, bool inv, C* w) {
+__device__ __forceinline__ void twiddles(const C* __restrict__ tw, int step, bool inv, C* w, int lgmax) {
   auto ld = [&](int i) {
-    C t = tw[i];
+    C t;
+    if constexpr (sizeof(t.x) == 4) {
+      float sn, cs;
+      sincospif(-(float)i * ldexpf(1.0f, 1 - lgmax), &sn, &cs);
+      t.x = cs;
+      t.y = sn;
+    } else {
+      t = tw[i];
+    }
     if (inv) t.y = -t.y;
     return t;
   };
   w[0] = cmake<C>(1, 0);
   if (R >= 2) w[1] = ld(step);
   if (R >= 4) {
-    w[2] = ld(2 * step);
+    w[2] = sizeof(w[0].x) == 4 ? cmul(w[1], w[1]) : ld(2 * step);
     w[3] = cmul(w[1], w[2]);
   }
   if (R >= 8) {
-    w[4] = ld(4 * step);
+    w[4] = sizeof(w[0].x) == 4 ? cmul(w[2], w[2]) : ld(4 * step);
     w[5] = cmul(w[4], w[1]);
     w[6] = cmul(w[4], w[2]);
     w[7] = cmul(w[4], w[3]);
   }
   if (R >= 16) {
-    w[8] = ld(8 * step);
+    w[8] = sizeof(w[0].x) == 4 ? cmul(w[4], w[4]) : ld(8 * step);
 #pragma unroll
     for (int r = 9; r < 16; ++r) w[r] = cmul(w[8], w[r - 8]);
   }
@@ -234,7 +247,7 @@ __device__ __forceinline__ void stage_ct(SBuf<C> buf, int ls, int ltx, int nline
         if (NS > 1 && k != 0) {
           // twiddle w^(r k) = tw[r * k * Lmax / (NS R)]
           C w[R];
-          twiddles<R>(tw, k << (lgmax - clog2(NS * R)), inv, w);
+          twiddles<R>(tw, k << (lgmax - clog2(NS * R)), inv, w, lgmax);
 #pragma unroll
           for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], w[r]);
         }
