@@ -14,7 +14,7 @@
 // number of values a thread holds is VPT = lines * L / blockDim.x, a
 // compile-time bound chosen by the launcher.
 //
-// Twiddles: FP64 stages load w, w^2, w^4 (and w^8) from a table
+// Twiddles: FP64 stages load every power w^r from a table
 // tw[k] = exp(-2 pi i k / Lmax) computed on the host in long double; FP32
 // stages compute w with sincospif and the even powers by squaring; the
 // other powers are complex products (see twiddles()).
@@ -151,8 +151,8 @@ template <> struct LogR<8> { static constexpr int v = 3; };
 template <> struct LogR<16> { static constexpr int v = 4; };
 
 // w[r] = w1^r, r = 0..R-1, for w1 = exp(-2 pi i step / Lmax) (conjugated
-// for the inverse).  FP64: w1, w2, w4, w8 come from the long-double table tw
-// and the rest are products.  FP32: w1 = sincospif(-2 step / Lmax) (the
+// for the inverse).  FP64: every power is loaded from the long-double table
+// tw (GB300's FP64 rate makes the loads cheaper than products).  FP32: w1 = sincospif(-2 step / Lmax) (the
 // argument is exact), w2, w4, w8 by squaring, the rest by products -- no
 // table load on the stage's critical path (measured 3 % faster solves on
 // the 1024^2 workload than the table, at unchanged iteration counts).
@@ -172,6 +172,13 @@ __device__ __forceinline__ void twiddles(const C* __restrict__ tw, int step, boo
     return t;
   };
   w[0] = cmake<C>(1, 0);
+  if constexpr (sizeof(w[0].x) == 8) {
+    // FP64: every power straight from the table (loads instead of FP64
+    // products; r * step < Lmax)
+#pragma unroll
+    for (int r = 1; r < R; ++r) w[r] = ld(r * step);
+    return;
+  }
   if (R >= 2) w[1] = ld(step);
   if (R >= 4) {
     w[2] = sizeof(w[0].x) == 4 ? cmul(w[1], w[1]) : ld(2 * step);
