@@ -423,6 +423,27 @@ fl_status true_residual(fl_plan* p, const double* u, double shift, double scale,
   return FL_OK;
 }
 
+// Target relative reduction of the next FP32 inner solve of the FP64
+// refinement.  need = tol / rel is the reduction still missing.  Within FP32
+// reach (need >= 1e-6) the step aims at half of it, so that it can be the
+// last one; otherwise at inner_tol.  floor is the true reduction the previous
+// step achieved when that fell short of its target by more than 3x: the
+// FP32 round-off of the operator limits what an inner solve can do to the
+// true residual, and asking for more than that only spends iterations.
+struct InnerTarget {
+  double floor = 0.0, eta = 0.0, rel = 0.0;
+  double next(double rel_now, double tol, double inner_tol) {
+    if (eta > 0.0 && rel > 0.0) {
+      const double ratio = rel_now / rel;
+      floor = ratio > 3.0 * eta ? ratio : 0.0;
+    }
+    const double need = rel_now > 0.0 ? tol / rel_now : 1.0;
+    eta = std::max(need >= 1e-6 ? 0.5 * need : inner_tol, floor);
+    rel = rel_now;
+    return eta;
+  }
+};
+
 // Solve (shift I + scale M) u = b, b already in v64.b; u in/out (device).
 bool trace_enabled();
 
@@ -539,6 +560,7 @@ fl_status solve_system(fl_plan* p, double* u, bool x0_nonzero, double shift, dou
     } else {
       int total = 0;
       result = FL_NOT_CONVERGED;
+      InnerTarget target;
       for (int outer = 0;; ++outer) {
         double rr = 0.0;
         if (outer == 0 && !x0_nonzero && !p->has_mask) {
@@ -560,11 +582,7 @@ fl_status solve_system(fl_plan* p, double* u, bool x0_nonzero, double shift, dou
         if (loc.rel_residual <= tol) { result = FL_OK; break; }
         if (!(rr == rr)) { result = fail(FL_BREAKDOWN, "NaN in the FP64 residual"); break; }
         if (outer >= p->max_outer) { result = fail(FL_NOT_CONVERGED, "refinement step cap reached"); break; }
-        // Inner target: reduce by inner_tol per step; when the remaining
-        // reduction tol / rel is within FP32 reach (>= 1e-6), aim at half of
-        // it so that this correction is the last one.
-        const double need = tol / loc.rel_residual;
-        const double eta = need >= 1e-6 ? std::min(p->inner_tol, 0.5 * need) : p->inner_tol;
+        const double eta = target.next(loc.rel_residual, tol, p->inner_tol);
         int its = 0;
         fl_status in;
         if (precision == FL_MODE_LEARNED) {
@@ -1191,6 +1209,7 @@ fl_status solve_batched_mixed(fl_plan* const* plans, int count, const double* co
   std::vector<PcgState> gh(count), sh(count);
   std::vector<double> rr(count), bb(count), tolh(count);
   std::vector<int> its(count, 0), outers(count, 0), conv(count, 0);
+  std::vector<InnerTarget> targets(count);
   memset(gh.data(), 0, count * sizeof(PcgState));
   FL_CUDA(cudaMemcpyAsync(gates, gh.data(), count * sizeof(PcgState), cudaMemcpyHostToDevice, bs));
   auto read_sums = [&](std::vector<double>& out) -> fl_status {
@@ -1225,8 +1244,7 @@ fl_status solve_batched_mixed(fl_plan* const* plans, int count, const double* co
       const double rel = bb[i] > 0 ? std::sqrt(rr[i] / bb[i]) : 0.0;
       conv[i] = rel <= tol;
       all = all && conv[i];
-      const double need = rel > 0 ? tol / rel : 1.0;
-      tolh[i] = need >= 1e-6 ? std::min(plans[i]->inner_tol, 0.5 * need) : plans[i]->inner_tol;
+      if (!conv[i]) tolh[i] = targets[i].next(rel, tol, plans[i]->inner_tol);
       gh[i].done = conv[i];
       if (!conv[i]) outers[i] = outer;
     }
