@@ -379,7 +379,12 @@ fl_status run_pcg(fl_plan* p, bool x0_nonzero, double shift, double scale, bool 
     gc.shift = shift;
     gc.scale = scale;
   }
+  // The next chunk covers the iterations the last chunk's convergence rate
+  // predicts are left (+1), in multiples of the graph's 4, between 4 and 32;
+  // iterations after convergence exit at entry but still cost a launch.
   int chunk = 4;
+  double rr_last = -1.0;
+  int it_last = 0;
   for (;;) {
     if (use_graph) {
       for (int c = 0; c < chunk / kGraphIters; ++c) {
@@ -392,7 +397,20 @@ fl_status run_pcg(fl_plan* p, bool x0_nonzero, double shift, double scale, bool 
     fl_status st = read_state(p);
     if (st != FL_OK) return st;
     if (p->st_host->done) break;
-    chunk = chunk < 32 ? chunk * 2 : 32;
+    const double rr = p->st_host->rr;
+    const int it = p->st_host->it;
+    int next = chunk < 32 ? chunk * 2 : 32;
+    if (rr_last > 0.0 && rr > 0.0 && rr < rr_last && it > it_last) {
+      const double per_it = std::log(rr / rr_last) / (it - it_last);
+      const double rem = std::log(p->st_host->tol2 / rr) / per_it;
+      if (rem >= 0.0 && rem < 1e6) {
+        const int want = (int)std::ceil(rem) + 1;
+        next = std::min(32, std::max(kGraphIters, (want + kGraphIters - 1) / kGraphIters * kGraphIters));
+      }
+    }
+    rr_last = rr;
+    it_last = it;
+    chunk = next;
   }
   *iters = p->st_host->it;
   switch (p->st_host->status) {
