@@ -108,12 +108,9 @@ cudaError_t launch_axpby(long long N, cudaStream_t s, double a, const T* x, doub
 template <typename T>
 cudaError_t launch_mask_copy_dot(long long N, cudaStream_t s, const T* src, const uint8_t* mask, T* dst,
                                  double* part, int* count);
-cudaError_t launch_accum_f32(long long N, cudaStream_t s, double* u, const float* x);
 cudaError_t launch_pcg_init(cudaStream_t s, PcgState* st, const double* bb_part, int bb_count,
                             const double* rr_part, int rr_count, const double* rz_part, int rz_count,
                             double tol, int maxit);
-cudaError_t launch_pcg_scalar(cudaStream_t s, PcgState* st, const double* rr_part, int rr_count,
-                              const double* rz_part, int rz_count);
 cudaError_t launch_sum(cudaStream_t s, const double* part, int count, double* out);
 cudaError_t build_symbol(const Geo& g, double c, double Z, double a, double expo, cudaStream_t s,
                          double* sig64, float* sig32, const double2* tw64);

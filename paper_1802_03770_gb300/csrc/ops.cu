@@ -77,12 +77,6 @@ __global__ void __launch_bounds__(kVecThreads) k_mask_copy_dot(const T* src, con
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
-__global__ void k_accum_f32(double* u, const float* x, long long N) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
-       i += (long long)gridDim.x * blockDim.x)
-    u[i] += (double)x[i];
-}
-
 // Scalar bookkeeping of CG (one CTA).
 __global__ void k_pcg_init(PcgState* st, const double* bb_part, int bb_count, const double* rr_part,
                            int rr_count, const double* rz_part, int rz_count, double tol, int maxit) {
@@ -105,15 +99,6 @@ __global__ void k_pcg_init(PcgState* st, const double* bb_part, int bb_count, co
     st->done = (bb == 0.0 || rr <= st->tol2) ? 1 : 0;
     if (!(rz > 0.0) && !st->done) { st->done = 1; st->status = 3; }
   }
-}
-
-__global__ void k_pcg_scalar(PcgState* st, const double* rr_part, int rr_count, const double* rz_part,
-                             int rz_count) {
-  __shared__ double red[32];
-  if (st->done) return;
-  const double rr = cta_sum_partials(rr_part, rr_count, red);
-  const double rz = cta_sum_partials(rz_part, rz_count, red);
-  if (threadIdx.x == 0) pcg_step(st, rr, rz);
 }
 
 __global__ void k_sum(const double* part, int count, double* out) {
@@ -474,24 +459,11 @@ cudaError_t launch_mask_copy_dot(long long N, cudaStream_t s, const T* src, cons
 template cudaError_t launch_mask_copy_dot<float>(long long, cudaStream_t, const float*, const uint8_t*, float*, double*, int*);
 template cudaError_t launch_mask_copy_dot<double>(long long, cudaStream_t, const double*, const uint8_t*, double*, double*, int*);
 
-cudaError_t launch_accum_f32(long long N, cudaStream_t s, double* u, const float* x) {
-  FL_KERNEL("accum_f32", s,
-            k_accum_f32<<<kVecBlocks, kVecThreads, 0, s>>>(u, x, N));
-  return cudaGetLastError();
-}
-
 cudaError_t launch_pcg_init(cudaStream_t s, PcgState* st, const double* bb_part, int bb_count,
                             const double* rr_part, int rr_count, const double* rz_part, int rz_count,
                             double tol, int maxit) {
   FL_KERNEL("pcg_init", s,
             k_pcg_init<<<1, 256, 0, s>>>(st, bb_part, bb_count, rr_part, rr_count, rz_part, rz_count, tol, maxit));
-  return cudaGetLastError();
-}
-
-cudaError_t launch_pcg_scalar(cudaStream_t s, PcgState* st, const double* rr_part, int rr_count,
-                              const double* rz_part, int rz_count) {
-  FL_KERNEL("pcg_scalar", s,
-            k_pcg_scalar<<<1, 256, 0, s>>>(st, rr_part, rr_count, rz_part, rz_count));
   return cudaGetLastError();
 }
 
