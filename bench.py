@@ -43,6 +43,28 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def rhs_seed(rank, step, j):
+    """Seed of the right-hand side of solve j of step `step` on `rank`:
+    every rank solves its own problems (replicas, weak scaling)."""
+    return 1000 * rank + 10 * step + j
+
+
+def max_over_ranks(values, world, device):
+    """Element-wise maximum over the ranks of per-rank times: the job takes
+    as long as its slowest rank.  One all-reduce, no data-path collective."""
+    if world == 1:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def job_rate(world, units_per_step, seconds_per_step):
+    """Whole-job throughput: the units all ranks processed per second."""
+    return world * units_per_step / seconds_per_step
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -207,7 +229,7 @@ def run_ours(args, rank, world, local):
     steps, warm = args.steps, args.warmup
     nsteps = steps + warm
     # inputs resident in HBM before timing: one RHS per (step, alpha)
-    rhs = [[torch.tensor(make_rhs(1000 * rank + 10 * s + j), dtype=torch.float64, device=dev)
+    rhs = [[torch.tensor(make_rhs(rhs_seed(rank, s, j)), dtype=torch.float64, device=dev)
             for j in range(len(ALPHAS))] for s in range(nsteps)]
     u = torch.zeros(N_SIDE * N_SIDE, dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -254,27 +276,28 @@ def run_ours(args, rank, world, local):
     for info in infos_f64:
         assert info["converged"] == 1, info
 
-    ms_t = torch.tensor([ms_mixed, ms_f64], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms_mixed, ms_f64 = float(ms_t[0]), float(ms_t[1])
+    ms_mixed, ms_f64 = max_over_ranks([ms_mixed, ms_f64], world, dev)
     solves_per_step = len(ALPHAS)
-    value = world * solves_per_step / (ms_mixed / 1e3)
-    value_f64 = world * solves_per_step / (ms_f64 / 1e3)
+    value = job_rate(world, solves_per_step, ms_mixed / 1e3)
+    value_f64 = job_rate(world, solves_per_step, ms_f64 / 1e3)
 
     # end to end: host arrays in, host arrays out, through the C ABI
-    f_host = [torch.from_numpy(make_rhs(5000 + j)).pin_memory() for j in range(len(ALPHAS))]
+    f_host = [torch.from_numpy(make_rhs(rhs_seed(rank, 50, j))).pin_memory()
+              for j in range(len(ALPHAS))]
     for j, p in enumerate(plans):
         p.solve_host(f_host[j].numpy(), tol=TOL, mode=mode_mixed)
     torch.cuda.synchronize()
     k_e2e = max(1, min(steps, 3))
+    dist_barrier()
     t0 = time.perf_counter()
     for _ in range(k_e2e):
         for j, p in enumerate(plans):
             _, info = p.solve_host(f_host[j].numpy(), tol=TOL, mode=mode_mixed)
             assert info["converged"] == 1
     e2e_s = (time.perf_counter() - t0) / k_e2e
-    e2e = {"value": world * solves_per_step / e2e_s, "unit": UNIT,
+    dist_barrier()
+    e2e_s = max_over_ranks([e2e_s], world, dev)[0]
+    e2e = {"value": job_rate(world, solves_per_step, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": solves_per_step * N_SIDE * N_SIDE * 8,
            "d2h_bytes_per_step": solves_per_step * N_SIDE * N_SIDE * 8}
 
