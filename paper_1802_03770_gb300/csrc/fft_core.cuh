@@ -104,7 +104,9 @@ template <typename C> __device__ __forceinline__ void dft8(C* v, bool inv) {
 
 // 16-point DFT as 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2,
 // X[k] = sum_n2 w16^(n2 k1) w4^(n2 k2) sum_n1 x[4 n1 + n2] w4^(n1 k1).
-template <typename C> __device__ __forceinline__ void dft16(C* v, bool inv) {
+// HALF: x[8..15] are zero (the zero-padded half of a line), so the inner
+// 4-point DFTs have two zero inputs.
+template <bool HALF = false, typename C> __device__ __forceinline__ void dft16(C* v, bool inv) {
   typedef decltype(C().x) T;
   const T c1 = (T)0.92387953251128675612818318939678828682;  // cos(pi/8)
   const T s1 = (T)0.38268343236508977172845998403039886676;  // sin(pi/8)
@@ -112,11 +114,20 @@ template <typename C> __device__ __forceinline__ void dft16(C* v, bool inv) {
   C a[4][4];
 #pragma unroll
   for (int n2 = 0; n2 < 4; ++n2) {
-    a[n2][0] = v[n2];
-    a[n2][1] = v[4 + n2];
-    a[n2][2] = v[8 + n2];
-    a[n2][3] = v[12 + n2];
-    dft4(a[n2], inv);
+    if (HALF) {
+      const C x0 = v[n2], x1 = v[4 + n2];
+      const C t = mul_mi(x1, inv);
+      a[n2][0] = cadd(x0, x1);
+      a[n2][1] = cadd(x0, t);
+      a[n2][2] = csub(x0, x1);
+      a[n2][3] = csub(x0, t);
+    } else {
+      a[n2][0] = v[n2];
+      a[n2][1] = v[4 + n2];
+      a[n2][2] = v[8 + n2];
+      a[n2][3] = v[12 + n2];
+      dft4(a[n2], inv);
+    }
   }
   // twiddles w16^(n2 k1): (1,1)=1, (1,2)=2, (1,3)=3, (2,1)=2, (2,2)=4, (2,3)=6, (3,1)=3, (3,2)=6, (3,3)=9
   a[1][1] = mul_rot(a[1][1], c1, s1, inv);
@@ -216,7 +227,8 @@ enum { STAGE_FIRST = 0, STAGE_MID = 1, STAGE_LAST = 2 };
 __device__ __forceinline__ int sbuf_phys(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int clog2(int x) { return x <= 1 ? 0 : 1 + clog2(x / 2); }
 
-template <int R, int VPT, bool IL, int LG, int NS, int MODE, typename C, typename Load, typename Epi>
+template <int R, int VPT, bool IL, int LG, int NS, int MODE, bool HALF, typename C, typename Load,
+          typename Epi>
 __device__ __forceinline__ void stage_ct(SBuf<C> buf, int ls, int ltx, int nlines,
                                          const C* __restrict__ tw, int lgmax, bool inv, Load& load,
                                          Epi& epi, bool sync_io) {
@@ -239,8 +251,10 @@ __device__ __forceinline__ void stage_ct(SBuf<C> buf, int ls, int ltx, int nline
       const int j = IL ? (g >> ltx) : (g & (LR - 1));
       const int k = j & (NS - 1);
       if constexpr (MODE == STAGE_FIRST) {
+        // HALF: legs R/2.. lie in the zero upper half of the line
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[b][r] = load(line, j + r * LR);
+        for (int r = 0; r < R; ++r)
+          v[b][r] = (HALF && 2 * r >= R) ? cmake<C>(0, 0) : load(line, j + r * LR);
       } else {
         const int l0 = IL ? ((j << ltx) + line) : (line * ls + j);
         if ((IL ? ((LR << ltx) & 15) : (LR & 15)) == 0) {
@@ -259,7 +273,8 @@ __device__ __forceinline__ void stage_ct(SBuf<C> buf, int ls, int ltx, int nline
           for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], w[r]);
         }
       }
-      dftR<R>(v[b], inv);
+      if constexpr (HALF && R == 16 && MODE == STAGE_FIRST) dft16<true>(v[b], inv);
+      else dftR<R>(v[b], inv);
       line_of[b] = line;
       out0[b] = (j - k) * R + k;
     }
@@ -308,7 +323,7 @@ struct FftPlan {
   __host__ __device__ static constexpr int ns(int s) { return s == 0 ? 1 : ns(s - 1) * radix(s - 1); }
 };
 
-template <int LG, int VPT, bool IL, int ST, typename C, typename Load, typename Epi>
+template <int LG, int VPT, bool IL, bool HALF, int ST, typename C, typename Load, typename Epi>
 __device__ __forceinline__ void fft_io_stage(SBuf<C> buf, int ls, int ltx, int nlines,
                                              const C* __restrict__ tw, int lgmax, bool inv, Load load,
                                              bool sync_load, Epi epi, bool sync_epi) {
@@ -316,10 +331,11 @@ __device__ __forceinline__ void fft_io_stage(SBuf<C> buf, int ls, int ltx, int n
   constexpr int R = P::radix(ST);
   constexpr int Ns = P::ns(ST);
   constexpr int MODE = ST == 0 ? STAGE_FIRST : (ST == P::S - 1 ? STAGE_LAST : STAGE_MID);
-  stage_ct<R, VPT, IL, LG, Ns, MODE>(buf, ls, ltx, nlines, tw, lgmax, inv, load, epi,
+  stage_ct<R, VPT, IL, LG, Ns, MODE, HALF>(buf, ls, ltx, nlines, tw, lgmax, inv, load, epi,
                                      MODE == STAGE_FIRST ? sync_load : sync_epi);
   if constexpr (ST + 1 < P::S)
-    fft_io_stage<LG, VPT, IL, ST + 1>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi);
+    fft_io_stage<LG, VPT, IL, HALF, ST + 1>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi,
+                                          sync_epi);
 }
 
 // A full transform of `nlines` lines (IL: 2^ltx interleaved lines) of length
@@ -328,18 +344,19 @@ __device__ __forceinline__ void fft_io_stage(SBuf<C> buf, int ls, int ltx, int n
 // shared buffer (a barrier separates its reads from the first stage's
 // writes); sync_epi: the epilogue writes the shared buffer.  The buffer is
 // free again after a barrier that follows the call.
-template <int LG, int VPT, bool IL, typename C, typename Load, typename Epi>
+template <int LG, int VPT, bool IL, bool HALF, typename C, typename Load, typename Epi>
 __device__ __forceinline__ void fft_io_ct(SBuf<C> buf, int ls, int ltx, int nlines,
                                           const C* __restrict__ tw, int lgmax, bool inv, Load load,
                                           bool sync_load, Epi epi, bool sync_epi) {
   if constexpr (FftPlan<LG, VPT>::S >= 2) {
-    fft_io_stage<LG, VPT, IL, 0>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi);
+    fft_io_stage<LG, VPT, IL, HALF, 0>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi,
+                                     sync_epi);
   } else {
     // one stage: natural order in shared memory afterwards; each thread
     // hands on elements it reads (an epilogue writing the buffer rewrites
     // the element it was given)
-    stage_ct<FftPlan<LG, VPT>::radix(0), VPT, IL, LG, 1, STAGE_FIRST>(buf, ls, ltx, nlines, tw, lgmax, inv,
-                                                                      load, epi, sync_load);
+    stage_ct<FftPlan<LG, VPT>::radix(0), VPT, IL, LG, 1, STAGE_FIRST, HALF>(buf, ls, ltx, nlines, tw,
+                                                                            lgmax, inv, load, epi, sync_load);
     constexpr int L = 1 << LG;
     const int total = IL ? (L << ltx) : nlines * L;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
@@ -350,20 +367,22 @@ __device__ __forceinline__ void fft_io_ct(SBuf<C> buf, int ls, int ltx, int nlin
   }
 }
 
-// Runtime length: dispatch to the compile-time plan (2^4 .. 2^11).
-template <int VPT, bool IL, typename C, typename Load, typename Epi>
+// Runtime length: dispatch to the compile-time plan (2^4 .. 2^11).  HALF:
+// the upper half of every input line is zero (a zero-padded line); the
+// loader is then not called for it.
+template <int VPT, bool IL, bool HALF = false, typename C, typename Load, typename Epi>
 __device__ __forceinline__ void fft_io(SBuf<C> buf, int lg, int ls, int ltx, int nlines,
                                        const C* __restrict__ tw, int lgmax, bool inv, Load load,
                                        bool sync_load, Epi epi, bool sync_epi) {
   switch (lg) {
-    case 11: fft_io_ct<11, VPT, IL>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
-    case 10: fft_io_ct<10, VPT, IL>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
-    case 9: fft_io_ct<9, VPT, IL>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
-    case 8: fft_io_ct<8, VPT, IL>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
-    case 7: fft_io_ct<7, VPT, IL>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
-    case 6: fft_io_ct<6, VPT, IL>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
-    case 5: fft_io_ct<5, VPT, IL>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
-    default: fft_io_ct<4, VPT, IL>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
+    case 11: fft_io_ct<11, VPT, IL, HALF>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
+    case 10: fft_io_ct<10, VPT, IL, HALF>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
+    case 9: fft_io_ct<9, VPT, IL, HALF>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
+    case 8: fft_io_ct<8, VPT, IL, HALF>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
+    case 7: fft_io_ct<7, VPT, IL, HALF>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
+    case 6: fft_io_ct<6, VPT, IL, HALF>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
+    case 5: fft_io_ct<5, VPT, IL, HALF>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
+    default: fft_io_ct<4, VPT, IL, HALF>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
   }
 }
 

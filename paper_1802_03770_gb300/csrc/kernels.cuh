@@ -309,7 +309,7 @@ __device__ __forceinline__ void body_rows_fwd(const RowsFwdArgs<T>& a, int bx, i
   {
     auto ld = [=](int q, int k) -> C { return k < hL ? buf[q * ls + k] : cmake<C>((T)0, (T)0); };
     auto st = [=](int q, int k, C v) { buf[q * ls + k] = v; };
-    fft_io<VPT, false>(buf, a.lg, ls, 0, nl, a.tw, a.lgmax, false, ld, true, st, true);
+    fft_io<VPT, false, true>(buf, a.lg, ls, 0, nl, a.tw, a.lgmax, false, ld, true, st, true);
   }
   __syncthreads();
   for (int q = 0; q < nl; ++q) {
@@ -403,7 +403,7 @@ __device__ __forceinline__ void body_cols(const ColsArgs<T>& a, int bx, int by) 
       if (c < ncol) v = cscale(v, sig[(size_t)min(k, L - k) * sig_line + c]);
       buf[(k << ltx) + c] = v;
     };
-    fft_io<VPT, true>(buf, a.lg, 0, ltx, TX, a.tw, a.lgmax, false, ld, true, epi, true);
+    fft_io<VPT, true, true>(buf, a.lg, 0, ltx, TX, a.tw, a.lgmax, false, ld, true, epi, true);
     __syncthreads();
     // inverse FFT whose last stage writes the kept rows to global
     const int rows_out = a.rows_out;
@@ -646,7 +646,7 @@ __device__ __forceinline__ void body_dst_rows(const DstRowsArgs<T>& a, int bx, i
     const C* __restrict__ bhat = a.bhat;
     auto ld = [=](int q, int k) -> C { return k < hL ? buf[q * ls + k] : cmake<C>((T)0, (T)0); };
     auto epi = [=](int q, int k, C v) { buf[q * ls + k] = cmul(v, bhat[k]); };
-    fft_io<VPT, false>(buf, a.lg, ls, 0, nl, a.tw, a.lgmax, false, ld, true, epi, true);
+    fft_io<VPT, false, true>(buf, a.lg, ls, 0, nl, a.tw, a.lgmax, false, ld, true, epi, true);
   }
   __syncthreads();
   DotAcc<T> dp;
