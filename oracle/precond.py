@@ -61,11 +61,28 @@ def eigenvalues(plan):
     return scale * lam
 
 
-def solve_box(plan, r, shift=0.0, scale=1.0):
-    """z = (shift I + scale C h^d L)^{-1} r on the full box by DST-I."""
-    if plan.mask is not None and not plan.mask.all():
-        raise ValueError("the DST preconditioner needs a full box")
+def _dst_solve(plan, r, shift, scale):
     r = np.asarray(r, dtype=np.float64).reshape(plan.n)
     rh = scipy.fft.dstn(r, type=1, norm="ortho")
     zh = rh / (shift + scale * eigenvalues(plan))
     return scipy.fft.idstn(zh, type=1, norm="ortho")
+
+
+def solve_box(plan, r, shift=0.0, scale=1.0):
+    """z = (shift I + scale C h^d L)^{-1} r on the full box by DST-I."""
+    if plan.mask is not None and not plan.mask.all():
+        raise ValueError("the DST preconditioner needs a full box")
+    return _dst_solve(plan, r, shift, scale)
+
+
+def solve_embedded(plan, r, shift=0.0, scale=1.0):
+    """Preconditioner of an occluded domain Omega inside the box (not the
+    paper's choice, which is a sparse Cholesky factorisation of L on Omega,
+    Sec. 4.3): z = R (shift I + scale C h^d L_box)^{-1} R^T r with R the
+    restriction to Omega, i.e. zero the residual outside Omega, solve on the
+    box by DST-I, zero the result outside Omega.  R B^{-1} R^T is symmetric
+    positive definite on the functions supported in Omega, so CG keeps its
+    guarantees.  Equal to solve_box on the full box."""
+    r = np.asarray(r, dtype=np.float64).reshape(plan.n)
+    m = np.ones(plan.n, bool) if plan.mask is None else plan.mask
+    return np.where(m, _dst_solve(plan, np.where(m, r, 0.0), shift, scale), 0.0)

@@ -30,6 +30,36 @@ def test_dst_solve_equals_sparse_solve():
     assert np.allclose(z, z2, rtol=0, atol=1e-12 * abs(z2).max())
 
 
+def test_embedded_preconditioner_is_restricted_box_inverse():
+    """Occluded domain: z = R B^{-1} R^T r with B the box FD operator, by an
+    independent sparse direct solve on the unmasked box; symmetric positive
+    definite on functions supported in Omega; equal to solve_box on the box."""
+    n = (11, 14)
+    ax0, ax1 = np.linspace(-1, 1, n[0]), np.linspace(-1, 1, n[1])
+    X, Y = np.meshgrid(ax0, ax1, indexing="ij")
+    mask = ~((X > 0) & (Y > 0))                       # an L-shape
+    rng = np.random.default_rng(7)
+    r = rng.standard_normal(n)
+    for shift, scale in [(0.0, 1.0), (1.0, 0.2)]:
+        pm = Plan(2, n, 0.05, 1.3, mask=mask)
+        box = Plan(2, n, 0.05, 1.3)
+        z = pc.solve_embedded(pm, r, shift, scale)
+        B = pc.fd_matrix(box) * scale + shift * np.eye(np.prod(n))
+        zd = np.linalg.solve(B, np.where(mask, r, 0.0).ravel()).reshape(n)
+        zd = np.where(mask, zd, 0.0)
+        assert np.allclose(z, zd, rtol=0, atol=1e-12 * abs(zd).max())
+        assert np.all(z[~mask] == 0.0)
+        # symmetric and positive on Omega
+        r2 = np.where(mask, rng.standard_normal(n), 0.0)
+        r1 = np.where(mask, r, 0.0)
+        a = np.vdot(pc.solve_embedded(pm, r1, shift, scale), r2)
+        b = np.vdot(r1, pc.solve_embedded(pm, r2, shift, scale))
+        assert abs(a - b) <= 1e-12 * abs(a)
+        assert np.vdot(pc.solve_embedded(pm, r1, shift, scale), r1) > 0
+        # no mask: the box solve
+        assert np.array_equal(pc.solve_embedded(box, r, shift, scale), pc.solve_box(box, r, shift, scale))
+
+
 def test_fd_part_is_the_stencil_of_M():
     """C h^d L carries exactly the (A2+A3) part of M: M - C h^d L has the
     pure kernel entries -C h^d |y_i - y_j|^{-(d+alpha)} off the diagonal."""
