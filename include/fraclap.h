@@ -122,8 +122,13 @@ fl_status fl_apply_f32(fl_plan* plan, const float* u_dev, float* y_dev);
 
 /* z = (shift I + scale C h^d L)^{-1} r on the full box (Sec. 3.1 with
  * shift = 0, scale = 1; Sec. 3.2 with shift = 1, scale = theta dt).
- * Requires a plan without mask, shift >= 0 and scale > 0 (FL_INVALID_ARG
- * otherwise).  r_dev, z_dev: N doubles, may not alias. */
+ * On a masked plan (occluded domain Omega) the box operator restricted to
+ * Omega: z = R (shift I + scale C h^d L_box)^{-1} R^T r, r read and z
+ * written only inside Omega (z = 0 outside).  This is not the paper's
+ * preconditioner for occluded domains (a sparse Cholesky factorisation of
+ * L on Omega, Sec. 4.3), but it is symmetric positive definite on Omega.
+ * Requires shift >= 0 and scale > 0 (FL_INVALID_ARG otherwise).
+ * r_dev, z_dev: N doubles, may not alias. */
 fl_status fl_precond(fl_plan* plan, double shift, double scale, const double* r_dev,
                      double* z_dev);
 fl_status fl_precond_f32(fl_plan* plan, double shift, double scale, const float* r_dev,
@@ -137,7 +142,8 @@ fl_status fl_precond_f32(fl_plan* plan, double shift, double scale, const float*
  *   maxit : cap on CG iterations (per inner solve in FL_MODE_MIXED)
  *   info  : nullable, filled on return
  * Returns FL_OK, FL_NOT_CONVERGED (u holds the last iterate), FL_BREAKDOWN,
- * FL_INVALID_ARG (a preconditioned solve on a masked plan). */
+ * FL_INVALID_ARG.  On a masked plan the FD preconditioner is the restricted
+ * box solve of fl_precond. */
 fl_status fl_solve_elliptic(fl_plan* plan, const double* f_dev, double* u_dev, int x0_nonzero,
                             double tol, int maxit, int mode, fl_solve_info* info);
 

@@ -81,6 +81,7 @@ struct PrecIO {
   const T* dotw = nullptr; double* dot_part = nullptr;
   PcgState* st = nullptr;
   int fin = 0;                // FIN_STEP: the last pass ends with the CG scalar step
+  const uint8_t* mask = nullptr;  // occluded domain: restrict input and output to Omega
 };
 
 // --- ops.cu: launchers (return the first CUDA error) --------------------------

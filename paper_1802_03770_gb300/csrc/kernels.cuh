@@ -573,6 +573,11 @@ struct DstRowsArgs {
   int fin;
   int nparts;
   const double* rr_in; int rr_count;
+  // nullable: Omega inside the box (occluded domain).  The first pass zeroes
+  // its DPRE_NONE input outside Omega (mask_in), the last pass its output
+  // (mask_out): the box solve restricted to Omega, R B^{-1} R^T.
+  const uint8_t* mask_in;
+  const uint8_t* mask_out;
 };
 
 template <typename T, int THREADS, int VPT>
@@ -636,7 +641,10 @@ __device__ __forceinline__ void body_dst_rows(const DstRowsArgs<T>& a, int bx, i
     for (int e = threadIdx.x; e < tot; e += THREADS) {
       const int q = e >> (a.lg - 1), j = e & (hL - 1);
       C v = cmake<C>((T)0, (T)0);
-      if (j < a.n) v = cscale(a.chirp[j], a.in[(size_t)(row0 + q) * a.n + j]);
+      if (j < a.n) {
+        const size_t idx = (size_t)(row0 + q) * a.n + j;
+        if (!a.mask_in || a.mask_in[idx]) v = cscale(a.chirp[j], a.in[idx]);
+      }
       buf[q * ls + j] = v;
     }
   }
@@ -656,12 +664,13 @@ __device__ __forceinline__ void body_dst_rows(const DstRowsArgs<T>& a, int bx, i
     const C* __restrict__ chirp = a.chirp;
     T* __restrict__ outp = a.out;
     const T* __restrict__ dw = a.dotw;
+    const uint8_t* __restrict__ mask = a.mask_out;
     const int n = a.n;
     auto ld = [=](int q, int k) -> C { return buf[q * ls + k]; };
     auto epi = [=, &dp](int q, int k, C v) {
       if (k < n) {
         const size_t idx = (size_t)(row0 + q) * n + k;
-        const T o = cmul(chirp[k], v).y * post;
+        const T o = (!mask || mask[idx]) ? cmul(chirp[k], v).y * post : (T)0;
         outp[idx] = o;
         if (dw) dp.add(o * dw[idx]);
       }

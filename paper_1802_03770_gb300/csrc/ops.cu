@@ -331,6 +331,7 @@ PrecChain<T> build_precond(const Geo& g, const Tables<T>& tb, const PrecIO<T>& i
     a.dotw = nullptr; a.dot_part = nullptr; a.post = 1.0;
     a.rows = (int)rows; a.n = nx; a.lg = g.lg[d - 1]; a.lgmax = g.lgmax; a.pre = io.pre;
     a.fin = FIN_NONE; a.nparts = ch.row_blocks; a.rr_in = nullptr; a.rr_count = 0;
+    a.mask_in = io.mask; a.mask_out = nullptr;
   }
   ch.ncols = 0;
   auto cols = [&](int axis, long long lstride, long long ostride, int nouter) {
@@ -375,6 +376,7 @@ PrecChain<T> build_precond(const Geo& g, const Tables<T>& tb, const PrecIO<T>& i
     const bool step = io.fin == FIN_STEP && io.dotw && io.dot_part && io.rr_part && io.st;
     a.fin = step ? FIN_STEP : FIN_NONE;
     a.nparts = ch.row_blocks; a.rr_in = io.rr_part; a.rr_count = ch.row_blocks;
+    a.mask_in = nullptr; a.mask_out = io.mask;
   }
   return ch;
 }

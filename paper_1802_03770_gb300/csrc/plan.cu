@@ -320,7 +320,7 @@ fl_status run_pcg(fl_plan* p, bool x0_nonzero, double shift, double scale, bool 
     FL_CUDA(prepare_precond<T>(g, tb, shift, scale, s));
     PrecIO<T> io;
     io.in = v.r; io.out = v.z; io.shift = shift; io.scale = scale;
-    io.dotw = v.r; io.dot_part = p->part[P_RZ];
+    io.dotw = v.r; io.dot_part = p->part[P_RZ]; io.mask = p->mask;
     FL_CUDA(launch_precond<T>(g, tb, s, io));
     rz_count = precond_partials<T>(g);
   } else {
@@ -352,6 +352,7 @@ fl_status run_pcg(fl_plan* p, bool x0_nonzero, double shift, double scale, bool 
       pi.pre = DPRE_UPDATE; pi.out = v.z; pi.shift = shift; pi.scale = scale;
       pi.x = v.x; pi.r = v.r; pi.p = v.p; pi.q = v.q; pi.rr_part = p->part[P_RR];
       pi.dotw = v.r; pi.dot_part = p->part[P_RZ]; pi.st = p->st; pi.fin = FIN_STEP;
+      pi.mask = p->mask;
       return launch_precond<T>(g, tb, qs, pi);
     }
     return launch_noprec_update<T>(g.N, qs, p->st, v.x, v.r, v.p, v.q, p->part[P_RR], 1, &cnt);
@@ -486,7 +487,7 @@ fl_status run_fpcg_learned(fl_plan* p, double shift, double scale, double tol, i
     if (fd) {
       PrecIO<float> io;
       io.in = v.r; io.out = p->z0; io.shift = shift; io.scale = scale;
-      io.st = const_cast<PcgState*>(st);
+      io.st = const_cast<PcgState*>(st); io.mask = p->mask;
       e = launch_precond<float>(g, p->t32, s, io);
     } else {
       e = launch_scale(v.r, p->z0, jac, g.N, st, s);
@@ -548,8 +549,6 @@ fl_status solve_system(fl_plan* p, double* u, bool x0_nonzero, double shift, dou
   bool use_prec = prec_mode == FL_PRECOND_FD || (prec_mode == FL_PRECOND_AUTO && p->alpha >= 1.0);
   if (prec_mode != FL_PRECOND_FD && prec_mode != FL_PRECOND_NONE && prec_mode != FL_PRECOND_AUTO)
     return fail(FL_INVALID_ARG, "unknown preconditioner mode");
-  if (use_prec && p->has_mask)
-    return fail(FL_INVALID_ARG, "the sine-transform preconditioner needs a plan without mask");
   if (!(tol > 0.0) || maxit < 1) return fail(FL_INVALID_ARG, "tol must be > 0 and maxit >= 1");
   if (precision == FL_MODE_LEARNED && (!p->net || p->has_mask))
     return fail(FL_INVALID_ARG, "FL_MODE_LEARNED needs a network attached to a plan without mask");
@@ -818,12 +817,11 @@ fl_status fl_precond(fl_plan* p, double shift, double scale, const double* r, do
   ProfScope prof_scope(p);
   if (!check_plan(p) || !r || !z) return fail(FL_INVALID_ARG, "NULL argument");
   if (r == z) return fail(FL_INVALID_ARG, "r and z may not alias");
-  if (p->has_mask) return fail(FL_INVALID_ARG, "the sine-transform preconditioner needs a plan without mask");
   if (!(scale > 0.0) || !(shift >= 0.0) || !std::isfinite(scale) || !std::isfinite(shift))
     return fail(FL_INVALID_ARG, "the preconditioner needs shift >= 0 and scale > 0");
   FL_CUDA(prepare_precond<double>(p->g, p->t64, shift, scale, p->stream));
   PrecIO<double> io;
-  io.in = r; io.out = z; io.shift = shift; io.scale = scale;
+  io.in = r; io.out = z; io.shift = shift; io.scale = scale; io.mask = p->mask;
   FL_CUDA(launch_precond<double>(p->g, p->t64, p->stream, io));
   return FL_OK;
 }
@@ -832,12 +830,11 @@ fl_status fl_precond_f32(fl_plan* p, double shift, double scale, const float* r,
   ProfScope prof_scope(p);
   if (!check_plan(p) || !r || !z) return fail(FL_INVALID_ARG, "NULL argument");
   if (r == z) return fail(FL_INVALID_ARG, "r and z may not alias");
-  if (p->has_mask) return fail(FL_INVALID_ARG, "the sine-transform preconditioner needs a plan without mask");
   if (!(scale > 0.0) || !(shift >= 0.0) || !std::isfinite(scale) || !std::isfinite(shift))
     return fail(FL_INVALID_ARG, "the preconditioner needs shift >= 0 and scale > 0");
   FL_CUDA(prepare_precond<float>(p->g, p->t32, shift, scale, p->stream));
   PrecIO<float> io;
-  io.in = r; io.out = z; io.shift = shift; io.scale = scale;
+  io.in = r; io.out = z; io.shift = shift; io.scale = scale; io.mask = p->mask;
   FL_CUDA(launch_precond<float>(p->g, p->t32, p->stream, io));
   return FL_OK;
 }
@@ -1135,8 +1132,6 @@ fl_status solve_batched_mixed(fl_plan* const* plans, int count, const double* co
     const Geo& g = p->g;
     const int vb = vec_blocks(g.N);
     prec[i] = prec_mode == FL_PRECOND_FD || (prec_mode == FL_PRECOND_AUTO && p->alpha >= 1.0);
-    if (prec[i] && p->has_mask)
-      return fail(FL_INVALID_ARG, "the sine-transform preconditioner needs plans without mask");
     PcgState* st = p->st;
     const PcgState* gate = gates + i;
     // FP64: right-hand side of the zero guess, then residuals with u += x32
@@ -1163,6 +1158,7 @@ fl_status solve_batched_mixed(fl_plan* const* plans, int count, const double* co
       FL_CUDA(prepare_precond<float>(g, p->t32, 0.0, 1.0, p->stream));
       PrecIO<float> pi;
       pi.in = p->v32.r; pi.out = p->v32.z; pi.dotw = p->v32.r; pi.dot_part = p->part[P_RZ];
+      pi.mask = p->mask;
       pi.st = const_cast<PcgState*>(gate);
       pinit.add(build_precond<float>(g, p->t32, pi));
     }
@@ -1180,7 +1176,7 @@ fl_status solve_batched_mixed(fl_plan* const* plans, int count, const double* co
       PrecIO<float> pu;
       pu.pre = DPRE_UPDATE; pu.out = p->v32.z; pu.x = p->v32.x; pu.r = p->v32.r; pu.p = p->v32.p;
       pu.q = p->v32.q; pu.rr_part = p->part[P_RR]; pu.dotw = p->v32.r; pu.dot_part = p->part[P_RZ];
-      pu.st = st; pu.fin = FIN_STEP;
+      pu.st = st; pu.fin = FIN_STEP; pu.mask = p->mask;
       pstep.add(build_precond<float>(g, p->t32, pu));
     } else {
       BVecArgs<float> nu = {};
