@@ -64,3 +64,10 @@ def test_single_process_needs_no_collective():
 def test_job_rate_counts_every_rank(world):
     # three solves per step in 30 ms on each of `world` ranks
     assert bench.job_rate(world, 3, 0.030) == pytest.approx(100.0 * world)
+
+
+def test_l_shape_sizes_match_the_paper():
+    """The L-shape workload uses the paper's domains: (n-1)^2 - (n/2)^2 points
+    (N = 12033 ... 784385 in the paper's L-shape table)."""
+    from paper_1802_03770_gb300.workloads import l_shape_mask
+    assert [int(l_shape_mask(n).sum()) for n in (128, 256, 512, 1024)] == [12033, 48641, 195585, 784385]
