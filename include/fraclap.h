@@ -126,7 +126,7 @@ fl_status fl_apply_f32(fl_plan* plan, const float* u_dev, float* y_dev);
  * Omega: z = R (shift I + scale C h^d L_box)^{-1} R^T r, r read and z
  * written only inside Omega (z = 0 outside).  This is not the paper's
  * preconditioner for occluded domains (a sparse Cholesky factorisation of
- * L on Omega, Sec. 4.3), but it is symmetric positive definite on Omega.
+ * L on Omega, Sec. 4.4), but it is symmetric positive definite on Omega.
  * Requires shift >= 0 and scale > 0 (FL_INVALID_ARG otherwise).
  * r_dev, z_dev: N doubles, may not alias. */
 fl_status fl_precond(fl_plan* plan, double shift, double scale, const double* r_dev,

@@ -78,7 +78,7 @@ def solve_box(plan, r, shift=0.0, scale=1.0):
 def solve_embedded(plan, r, shift=0.0, scale=1.0):
     """Preconditioner of an occluded domain Omega inside the box (not the
     paper's choice, which is a sparse Cholesky factorisation of L on Omega,
-    Sec. 4.3): z = R (shift I + scale C h^d L_box)^{-1} R^T r with R the
+    Sec. 4.4): z = R (shift I + scale C h^d L_box)^{-1} R^T r with R the
     restriction to Omega, i.e. zero the residual outside Omega, solve on the
     box by DST-I, zero the result outside Omega.  R B^{-1} R^T is symmetric
     positive definite on the functions supported in Omega, so CG keeps its

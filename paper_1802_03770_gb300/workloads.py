@@ -11,7 +11,7 @@ every step an FP32-CG + FP64-refinement solve of (I + dt M) u = u_prev to
 batched: 64 problems with sides uniform in {96, 128, ..., 768} and alpha ~
 U(0.3, 1.8), seeded Gaussian-mixture right-hand sides, to 1e-8, solved in
 lockstep (fl_solve_elliptic_batched) and, for comparison, one after another.
-lshape: the occluded-domain example (Sec. 4.3) at n = 128 .. 1024, alpha =
+lshape: the occluded-domain example (Sec. 4.4) at n = 128 .. 1024, alpha =
 1.75, FP64 CG with and without the FD preconditioner, to 1e-6 and 1e-9.
 Each prints one JSON line.
 """
@@ -76,7 +76,7 @@ def batched(count=64, seed=7):
 
 
 def l_shape_mask(n):
-    """The paper's L-shaped domain (Sec. 4.3): the (n-1)^2 interior points of
+    """The paper's L-shaped domain (Sec. 4.4): the (n-1)^2 interior points of
     the unit square (h = 1/n) without the (n/2)^2 points of one corner."""
     import numpy as np
     m = n - 1
