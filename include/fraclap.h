@@ -158,7 +158,13 @@ fl_status fl_solve_elliptic_host(fl_plan* plan, const double* f_host, double* u_
  *                             + dt (theta f_next + (1-theta) f_prev),
  * preconditioned with I + theta dt C h^d L (Sec. 3.2) and warm-started
  * from u_prev (Sec. 4.5).  f_prev_dev / f_next_dev are nullable (= 0).
- * u_next_dev may equal u_prev_dev. */
+ * u_next_dev may equal u_prev_dev.
+ * In FL_MODE_MIXED / FL_MODE_LEARNED the plan keeps M u_next from the
+ * step's last FP64 residual (N doubles, allocated at the first such step)
+ * with the array's address and a 64-bit hash of its contents; a following
+ * step whose u_prev is that array, unchanged, starts from it instead of
+ * applying M to u_prev again (one FP64 apply fewer per step, two for
+ * theta < 1).  Any other u_prev (or a changed one) is applied as usual. */
 fl_status fl_time_step(fl_plan* plan, double dt, double theta, const double* u_prev_dev,
                        const double* f_prev_dev, const double* f_next_dev, double* u_next_dev,
                        double tol, int maxit, int mode, fl_solve_info* info);

@@ -67,6 +67,7 @@ struct ApplyIO {
   double* partials = nullptr;
   int dot_self = 0;
   int fin = 0;                // FIN_PQ: the last CTA sets st->pq and st->alpha
+  T* outm = nullptr;          // nullable: M x (the apply itself) as well
 };
 
 // Inputs and outputs of one preconditioner solve.
@@ -113,6 +114,16 @@ cudaError_t launch_pcg_init(cudaStream_t s, PcgState* st, const double* bb_part,
                             const double* rr_part, int rr_count, const double* rz_part, int rz_count,
                             double tol, int maxit);
 cudaError_t launch_sum(cudaStream_t s, const double* part, int count, double* out);
+// r = b - shift u - scale mx (masked) from a known mx = M u: FP64 r is not
+// kept; r32 = (float) r and per-CTA partials of ||r||^2 are written.
+cudaError_t launch_residual_from(long long N, cudaStream_t s, const double* b, const double* u,
+                                 const double* mx, const uint8_t* mask, double shift, double scale,
+                                 float* r32, double* part, int* count);
+// y = u - c mx (b of a theta step from a known mx = M u)
+cudaError_t launch_axmy(long long N, cudaStream_t s, const double* u, double c, const double* mx,
+                        double* y);
+// order-independent 64-bit hash of the bits of N doubles, added into *h (zero it first)
+cudaError_t launch_hash(long long N, cudaStream_t s, const double* u, unsigned long long* h);
 cudaError_t build_symbol(const Geo& g, double c, double Z, double a, double expo, cudaStream_t s,
                          double* sig64, float* sig32, const double2* tw64);
 size_t partial_capacity(const Geo& g);

@@ -453,6 +453,7 @@ struct RowsInvArgs {
   int fin;                 // FIN_NONE or FIN_PQ (the last CTA sets fst->pq, fst->alpha)
   int nparts;              // CTAs of the pass (partials to sum)
   PcgState* fst;
+  T* outm;                 // nullable: M x itself (restricted to Omega)
 };
 
 template <typename T, int THREADS, int VPT>
@@ -505,7 +506,9 @@ __device__ __forceinline__ void body_rows_inv(const RowsInvArgs<T>& a, int bx, i
     for (int j = threadIdx.x; j < a.n; j += THREADS) {
       const size_t idx = base + j;
       const C z = lb[j];
-      T v = (half ? z.y : z.x) * cm;
+      const T mx = (a.mask && !a.mask[idx]) ? (T)0 : (half ? z.y : z.x);
+      if (a.outm) a.outm[idx] = mx;
+      T v = mx * cm;
       if (xin) v += cx * xin[idx];
       if (bin) v += cb * bin[idx];
       if (a.mask && !a.mask[idx]) v = (T)0;

@@ -101,6 +101,52 @@ __global__ void k_pcg_init(PcgState* st, const double* bb_part, int bb_count, co
   }
 }
 
+__global__ void __launch_bounds__(kVecThreads) k_residual_from(const double* b, const double* u,
+                                                                const double* mx, const uint8_t* mask,
+                                                                double shift, double scale, float* r32,
+                                                                double* part, long long N) {
+  __shared__ double red[32];
+  double v = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double r = (mask && !mask[i]) ? 0.0 : b[i] - shift * u[i] - scale * mx[i];
+    r32[i] = (float)r;
+    v += r * r;
+  }
+  const double s = cta_sum(v, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_axmy(const double* u, double c, const double* mx, double* y, long long N) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = u[i] - c * mx[i];
+}
+
+// The splitmix64 finaliser (Steele, Lea, Flood, "Fast splittable
+// pseudorandom number generators", OOPSLA 2014): a bijective 64-bit mixer.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
+  x ^= x >> 30;
+  x *= 0xbf58476d1ce4e5b9ull;
+  x ^= x >> 27;
+  x *= 0x94d049bb133111ebull;
+  x ^= x >> 31;
+  return x;
+}
+
+// Sum over i of mix64(bits(u_i) ^ mix64(i)) mod 2^64: independent of the
+// summation order; any change of the values changes their terms
+// pseudo-randomly (a uniform change, such as scaling the whole array by a
+// power of two, does not cancel out as it would with linear weights).
+__global__ void k_hash(const double* u, unsigned long long* h, long long N) {
+  unsigned long long acc = 0ull;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    acc += mix64((unsigned long long)__double_as_longlong(u[i]) ^ mix64((unsigned long long)i));
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(h, acc);
+}
+
 __global__ void k_sum(const double* part, int count, double* out) {
   __shared__ double red[32];
   const double s = cta_sum_partials(part, count, red);
@@ -291,6 +337,7 @@ ApplyChain<T> build_apply(const Geo& g, const Tables<T>& tb, const ApplyIO<T>& i
     a.rows_per_plane = rpp; a.plane_stride = pstride; a.dot_self = io.dot_self;
     a.fin = (io.partials && io.st) ? io.fin : FIN_NONE;
     a.nparts = ch.row_blocks; a.fst = io.st;
+    a.outm = io.outm;
   }
   return ch;
 }
@@ -466,6 +513,26 @@ cudaError_t launch_pcg_init(cudaStream_t s, PcgState* st, const double* bb_part,
                             double tol, int maxit) {
   FL_KERNEL("pcg_init", s,
             k_pcg_init<<<1, 256, 0, s>>>(st, bb_part, bb_count, rr_part, rr_count, rz_part, rz_count, tol, maxit));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_from(long long N, cudaStream_t s, const double* b, const double* u,
+                                 const double* mx, const uint8_t* mask, double shift, double scale,
+                                 float* r32, double* part, int* count) {
+  FL_KERNEL("residual_from", s,
+            k_residual_from<<<kVecBlocks, kVecThreads, 0, s>>>(b, u, mx, mask, shift, scale, r32, part, N));
+  *count = kVecBlocks;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axmy(long long N, cudaStream_t s, const double* u, double c, const double* mx,
+                        double* y) {
+  FL_KERNEL("axmy", s, k_axmy<<<kVecBlocks, kVecThreads, 0, s>>>(u, c, mx, y, N));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hash(long long N, cudaStream_t s, const double* u, unsigned long long* h) {
+  FL_KERNEL("hash", s, k_hash<<<kVecBlocks, kVecThreads, 0, s>>>(u, h, N));
   return cudaGetLastError();
 }
 

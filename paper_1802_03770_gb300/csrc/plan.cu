@@ -130,6 +130,15 @@ struct fl_plan {
   float* z0 = nullptr;     // base preconditioned residual
   float* feat = nullptr;   // network input, 3 x N
   double* lpart[3] = {nullptr, nullptr, nullptr};  // ||z0||^2, r.z, r.z_old partials
+  // M u of the last time step's result (fl_time_step): mu_cache holds
+  // M u_next of the previous step, valid for the array mu_of while its
+  // contents still hash to mu_hash
+  double* mu_cache = nullptr;
+  const double* mu_of = nullptr;
+  unsigned long long mu_hash = 0ull;
+  bool mu_valid = false;
+  unsigned long long* hash_dev = nullptr;
+  unsigned long long* hash_host = nullptr;  // pinned
 };
 
 namespace {
@@ -183,6 +192,7 @@ void free_plan(fl_plan* p) {
   for (void* v : p->allocs) cudaFree(v);
   if (p->st_host) cudaFreeHost(p->st_host);
   if (p->scalar_host) cudaFreeHost(p->scalar_host);
+  if (p->hash_host) cudaFreeHost(p->hash_host);
   delete p;
 }
 
@@ -540,8 +550,23 @@ fl_status run_fpcg_learned(fl_plan* p, double shift, double scale, double tol, i
   }
 }
 
+// Order-independent 64-bit hash of the N values of u (device), read back.
+fl_status hash_of(fl_plan* p, const double* u, unsigned long long* h) {
+  FL_CUDA(cudaMemsetAsync(p->hash_dev, 0, sizeof(unsigned long long), p->stream));
+  FL_CUDA(launch_hash(p->g.N, p->stream, u, p->hash_dev));
+  FL_CUDA(cudaMemcpyAsync(p->hash_host, p->hash_dev, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                          p->stream));
+  FL_CUDA(cudaStreamSynchronize(p->stream));
+  *h = *p->hash_host;
+  return FL_OK;
+}
+
+// mx0 (nullable, with x0_nonzero): M u of the initial u, so that the first
+// FP64 residual needs no apply; mx_out (nullable): every FP64 residual apply
+// of the refinement also stores M u there.
 fl_status solve_system(fl_plan* p, double* u, bool x0_nonzero, double shift, double scale,
-                       double tol, int maxit, int mode, fl_solve_info* info) {
+                       double tol, int maxit, int mode, fl_solve_info* info,
+                       const double* mx0 = nullptr, double* mx_out = nullptr) {
   const Geo& g = p->g;
   cudaStream_t s = p->stream;
   const int prec_mode = mode & 0xF0;
@@ -583,11 +608,17 @@ fl_status solve_system(fl_plan* p, double* u, bool x0_nonzero, double shift, dou
         if (outer == 0 && !x0_nonzero && !p->has_mask) {
           FL_CUDA(launch_copy_cast<float>(g.N, s, p->v64.b, p->v32.b));
           rr = bb;
+        } else if (outer == 0 && x0_nonzero && mx0) {
+          int cnt = 0;
+          FL_CUDA(launch_residual_from(g.N, s, p->v64.b, u, mx0, p->mask, shift, scale, p->v32.b,
+                                       p->part[P_RES], &cnt));
+          st = read_sum(p, p->part[P_RES], cnt, &rr);
+          if (st != FL_OK) return st;
         } else {
           ApplyIO<double> io;
           io.pre = outer > 0 ? PRE_ACCUM : PRE_NONE;
           io.u = u; io.acc = u; io.x32 = p->v32.x; io.mask = p->mask;
-          io.out32 = p->v32.b; io.x = u; io.b = p->v64.b;
+          io.out32 = p->v32.b; io.x = u; io.b = p->v64.b; io.outm = mx_out;
           io.cm = -scale; io.cx = -shift; io.cb = 1.0;
           io.partials = p->part[P_RES]; io.dot_self = 1;
           FL_CUDA(launch_apply<double>(g, p->t64, s, io));
@@ -871,12 +902,33 @@ fl_status fl_time_step(fl_plan* p, double dt, double theta, const double* u_prev
   const Geo& g = p->g;
   cudaStream_t s = p->stream;
   double* b = p->v64.b;
+  const int precision = mode & 0x0F;
+  const bool refine = precision == FL_MODE_MIXED || precision == FL_MODE_LEARNED;
+  // M u_prev from the previous step (its last FP64 residual apply) when
+  // u_prev is that step's result, unchanged since (same array, same hash)
+  bool cached = false;
+  if (refine) {
+    if (!p->mu_cache) FL_CUDA(dalloc(p, &p->mu_cache, g.N * sizeof(double)));
+    if (!p->hash_dev) FL_CUDA(dalloc(p, &p->hash_dev, sizeof(unsigned long long)));
+    if (!p->hash_host) FL_CUDA(cudaMallocHost((void**)&p->hash_host, sizeof(unsigned long long)));
+    if (p->mu_valid && p->mu_of == u_prev) {
+      unsigned long long h = 0ull;
+      fl_status st = hash_of(p, u_prev, &h);
+      if (st != FL_OK) return st;
+      cached = h == p->mu_hash;
+    }
+  }
+  p->mu_valid = false;
   // b = (I - (1-theta) dt M) u_prev + dt (theta f_next + (1-theta) f_prev)
   if (theta < 1.0) {
-    ApplyIO<double> io;
-    io.u = u_prev; io.mask = p->mask; io.out = b; io.x = u_prev;
-    io.cm = -(1.0 - theta) * dt; io.cx = 1.0;
-    FL_CUDA(launch_apply<double>(g, p->t64, s, io));
+    if (cached) {
+      FL_CUDA(launch_axmy(g.N, s, u_prev, (1.0 - theta) * dt, p->mu_cache, b));
+    } else {
+      ApplyIO<double> io;
+      io.u = u_prev; io.mask = p->mask; io.out = b; io.x = u_prev;
+      io.cm = -(1.0 - theta) * dt; io.cx = 1.0;
+      FL_CUDA(launch_apply<double>(g, p->t64, s, io));
+    }
   } else {
     FL_CUDA(cudaMemcpyAsync(b, u_prev, g.N * sizeof(double), cudaMemcpyDeviceToDevice, s));
   }
@@ -884,7 +936,18 @@ fl_status fl_time_step(fl_plan* p, double dt, double theta, const double* u_prev
   if (f_prev && theta < 1.0) FL_CUDA(launch_axpby<double>(g.N, s, (1.0 - theta) * dt, f_prev, 1.0, b));
   if (u_next != u_prev)
     FL_CUDA(cudaMemcpyAsync(u_next, u_prev, g.N * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  return solve_system(p, u_next, true, 1.0, theta * dt, tol, maxit, mode, info);
+  const fl_status res = solve_system(p, u_next, true, 1.0, theta * dt, tol, maxit, mode, info,
+                                     cached ? p->mu_cache : nullptr, refine ? p->mu_cache : nullptr);
+  if (refine && (res == FL_OK || res == FL_NOT_CONVERGED)) {
+    // the refinement's last FP64 residual apply stored M u_next
+    unsigned long long h = 0ull;
+    fl_status st = hash_of(p, u_next, &h);
+    if (st != FL_OK) return st;
+    p->mu_of = u_next;
+    p->mu_hash = h;
+    p->mu_valid = true;
+  }
+  return res;
 }
 
 long long fl_launch_count(void) { return g_launches.load(); }

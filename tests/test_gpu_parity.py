@@ -240,6 +240,35 @@ def test_solve_masked_preconditioned(mode):
 
 
 @pytest.mark.parametrize("theta", [1.0, 0.5])
+def test_consecutive_time_steps_reuse_m_u(theta):
+    """Three mixed steps u0 -> u1 -> u2 -> u3 (the second and third start from
+    the M u the previous step's last FP64 residual left), then a step from an
+    array changed in place (its hash differs: M u is recomputed) -- all
+    against the oracle's steps."""
+    n = (20, 18, 16)
+    h = 1.0 / 21
+    op = OPlan(3, n, h, 1.5)
+    u0 = inputs.gaussian_mixture(20, 3, 16, 4, 0.05, 0.15)[:, :18, :16].copy()
+    dt = 1e-3
+    p = Plan(3, n, h, 1.5)
+    a, b = gpu(u0), torch.empty(int(np.prod(n)), dtype=torch.float64, device="cuda")
+    ref = u0
+    for _ in range(3):
+        ref, _, ok, _ = osv.theta_step(op, ref, dt, theta, None, None, tol=1e-13)
+        assert ok
+        _, info = p.time_step(a, dt, theta, out=b, tol=1e-10, mode=_lib.FL_MODE_MIXED)
+        assert info["converged"] == 1
+        assert rel(host(b).reshape(n), ref) <= 1e-9
+        a, b = b, a
+    # change the current state in place: the cached M u must not be used
+    a.mul_(0.5)
+    ref, _, ok, _ = osv.theta_step(op, 0.5 * ref, dt, theta, None, None, tol=1e-13)
+    _, info = p.time_step(a, dt, theta, out=b, tol=1e-10, mode=_lib.FL_MODE_MIXED)
+    assert info["converged"] == 1
+    assert rel(host(b).reshape(n), ref) <= 1e-9
+
+
+@pytest.mark.parametrize("theta", [1.0, 0.5])
 @pytest.mark.parametrize("mode", [_lib.FL_MODE_F64, _lib.FL_MODE_MIXED])
 def test_time_step_3d(theta, mode):
     n = 24
