@@ -86,3 +86,78 @@ def solve_embedded(plan, r, shift=0.0, scale=1.0):
     r = np.asarray(r, dtype=np.float64).reshape(plan.n)
     m = np.ones(plan.n, bool) if plan.mask is None else plan.mask
     return np.where(m, _dst_solve(plan, np.where(m, r, 0.0), shift, scale), 0.0)
+
+
+# -- other members of the family (shift I + scale C h^d L) ---------------------
+#
+# Every preconditioner below is P = pshift I + pscale C h^d L on the box
+# (restricted to Omega as in solve_embedded), for the operator
+# sigma I + tau M (sigma = 0, tau = 1: the elliptic problem; sigma = 1,
+# tau = theta dt: a time step).  The paper's choice is pshift = sigma,
+# pscale = tau.
+
+
+def stencil_params(plan, sigma=0.0, tau=1.0):
+    """The alternative the paper mentions after its preconditioner (Sec. 3.1):
+    M~ = M with every entry outside the (2d+1)-point stencil set to zero.
+    By the entries of M,
+
+        M~ = C h^d [A1 I - h^-(d+alpha) S] + C h^d L,
+
+    S the nearest-neighbour sum.  With g = C h^d (A2+A3)/h^2 (< 0) and
+    C h^d L = g (S - 2d I) this is pshift I + pscale C h^d L with
+    pscale = 1 + C h^-alpha / |g| and pshift = C h^d (A1 - 2d h^-(d+alpha)).
+    Returns (pshift, pscale) of sigma I + tau M~."""
+    g = plan.C * plan.h ** plan.d * (plan.A2 + plan.A3) / plan.h ** 2
+    kappa = plan.C * plan.h ** (-plan.alpha)
+    ps = plan.C * plan.h ** plan.d * (plan.A1 - 2 * plan.d * plan.h ** (-(plan.d + plan.alpha)))
+    return sigma + tau * ps, tau * (1.0 + kappa / abs(g))
+
+
+def sine_mode(n, k):
+    """The separable DST-I eigenvector of L with wave numbers k (one per
+    axis): v_i = prod_a sin(pi k_a (i_a + 1) / (n_a + 1)), i_a = 0..n_a-1."""
+    v = np.ones(n)
+    for ax, (ni, ki) in enumerate(zip(n, k)):
+        s = np.sin(np.pi * ki * np.arange(1, ni + 1) / (ni + 1))
+        shape = [1] * len(n)
+        shape[ax] = ni
+        v = v * s.reshape(shape)
+    return v
+
+
+def extreme_quotients(plan, apply=None):
+    """Rayleigh quotients of the operator (default plan.apply) on the
+    lowest (k = 1 on every axis) and highest (k = n) sine modes, restricted
+    to Omega, and the eigenvalues of C h^d L on the box for those modes.
+    Returns (mu_lo, mu_hi, lam_lo, lam_hi)."""
+    apply = plan.apply if apply is None else apply
+    m = np.ones(plan.n, bool) if plan.mask is None else plan.mask
+    lam = eigenvalues(plan)
+    out = []
+    for k in ((1,) * plan.d, plan.n):
+        v = np.where(m, sine_mode(plan.n, k), 0.0)
+        out.append(float(np.sum(v * apply(v)) / np.sum(v * v)))
+    return out[0], out[1], float(lam.flat[0]), float(lam.flat[-1])
+
+
+def balanced_params(plan, sigma=0.0, tau=1.0, apply=None):
+    """FD preconditioner with a shift (not in the paper): P = x I + tau C h^d L
+    with x chosen so that the preconditioned operator's ratio
+    (sigma + tau mu) / (x + tau lam) is the same on the lowest and highest
+    sine modes:
+
+        x = tau (A lam_hi - B lam_lo) / (B - A),
+        A = sigma + tau mu_lo,  B = sigma + tau mu_hi,
+
+    kept >= 0 (P stays positive definite).  The symbol of M grows like
+    |xi|^alpha and that of L like |xi|^2; the shift flattens their ratio at
+    low frequencies, which the paper's choice (x = sigma) leaves growing like
+    |xi|^(alpha-2).  For a time step with a small tau the balance can lie
+    below sigma.
+    Returns (pshift, pscale) = (x, tau)."""
+    mu_lo, mu_hi, lam_lo, lam_hi = extreme_quotients(plan, apply)
+    a = sigma + tau * mu_lo
+    b = sigma + tau * mu_hi
+    x = tau * (a * lam_hi - b * lam_lo) / (b - a) if b > a else sigma
+    return max(0.0, x), tau
