@@ -57,9 +57,13 @@ enum {
                              preconditioner of the attached network        */
   FL_PRECOND_FD = 0x00,   /* FD-Laplacian preconditioner (Sec. 3.1, 3.2)   */
   FL_PRECOND_NONE = 0x10, /* plain CG                                      */
-  FL_PRECOND_AUTO = 0x20  /* FD preconditioner for alpha >= 1, none below
+  FL_PRECOND_AUTO = 0x20, /* FD preconditioner for alpha >= 1, none below
                              (Sec. 4.2: for alpha < 1 no preconditioning is
                              needed)                                       */
+  FL_PRECOND_SHIFTED = 0x30, /* FD preconditioner with the balanced shift of
+                                fl_precond_params (not in the paper)       */
+  FL_PRECOND_STENCIL = 0x40  /* the (2d+1)-point stencil part of M itself,
+                                the alternative remarked on in Sec. 3.1    */
 };
 
 typedef struct fl_plan fl_plan;
@@ -133,6 +137,31 @@ fl_status fl_precond(fl_plan* plan, double shift, double scale, const double* r_
                      double* z_dev);
 fl_status fl_precond_f32(fl_plan* plan, double shift, double scale, const float* r_dev,
                          float* z_dev);
+
+/* The preconditioner a solve uses in `mode` for the operator
+ * shift I + scale M (shift = 0, scale = 1: the elliptic problem; shift = 1,
+ * scale = theta dt: a time step) is z = (pshift I + pscale C h^d L)^{-1} r on
+ * the box (restricted to Omega on a masked plan), applied like fl_precond:
+ *   FL_PRECOND_FD (and AUTO with alpha >= 1): pshift = shift, pscale = scale
+ *     (Sec. 3.1; Sec. 3.2 for time steps).
+ *   FL_PRECOND_STENCIL: shift I + scale M~, M~ = M with the entries off the
+ *     (2d+1)-point stencil set to zero (Sec. 3.1 remarks on it): in terms
+ *     of c = C h^-alpha, the constant Z of M's diagonal and the stencil
+ *     weight a (< 0), pshift = shift + scale c (Z - 2d),
+ *     pscale = scale (1 - a) / (-a).
+ *   FL_PRECOND_SHIFTED: pscale = scale and pshift = x >= 0 balancing the
+ *     ratio (shift + scale mu) / (x + scale lam) between the lowest and the
+ *     highest sine modes v_k (k = 1 and k = n_i on every axis, restricted to
+ *     Omega), mu the Rayleigh quotient v^T M v / v^T v and lam the
+ *     eigenvalue of C h^d L: x = scale (A lam_hi - B lam_lo) / (B - A),
+ *     A = shift + scale mu_lo, B = shift + scale mu_hi.  The two quotients
+ *     are computed once per plan with FP64 applies (the first call waits
+ *     for the plan's stream) and cached.
+ *   FL_PRECOND_NONE (and AUTO with alpha < 1): none; *pshift = *pscale = 0.
+ * The precision bits of `mode` are ignored.  Requires shift >= 0 and
+ * scale > 0.  Returns FL_OK or FL_INVALID_ARG (unknown mode, NULL output). */
+fl_status fl_precond_params(fl_plan* plan, int mode, double shift, double scale, double* pshift,
+                            double* pscale);
 
 /* Solve M u = f (eq. matelliptic) to ||f - M u|| <= tol ||f||.
  *   f_dev : N doubles (device)

@@ -27,6 +27,8 @@ FL_MODE_LEARNED = 2
 FL_PRECOND_FD = 0x00
 FL_PRECOND_NONE = 0x10
 FL_PRECOND_AUTO = 0x20
+FL_PRECOND_SHIFTED = 0x30
+FL_PRECOND_STENCIL = 0x40
 
 
 class FlOpts(ctypes.Structure):
@@ -70,6 +72,7 @@ SIGNATURES = {
     "fl_apply_f32": (_I, [_P, _P, _P]),
     "fl_precond": (_I, [_P, _D, _D, _P, _P]),
     "fl_precond_f32": (_I, [_P, _D, _D, _P, _P]),
+    "fl_precond_params": (_I, [_P, _I, _D, _D, _P, _P]),
     "fl_solve_elliptic": (_I, [_P, _P, _P, _I, _D, _I, _I, ctypes.POINTER(FlSolveInfo)]),
     "fl_solve_elliptic_host": (_I, [_P, _P, _P, _D, _I, _I, ctypes.POINTER(FlSolveInfo)]),
     "fl_time_step": (_I, [_P, _D, _D, _P, _P, _P, _P, _D, _I, _I, ctypes.POINTER(FlSolveInfo)]),

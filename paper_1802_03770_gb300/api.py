@@ -203,6 +203,14 @@ class Plan:
         L.check(fn(self._h, float(shift), float(scale), _ptr(r), _ptr(z)), "fl_precond")
         return z
 
+    def precond_params(self, mode, shift=0.0, scale=1.0):
+        """(pshift, pscale) of the preconditioner (pshift I + pscale C h^d L)^-1
+        that a solve in `mode` uses for shift I + scale M; (0, 0) for none."""
+        ps, sc = ctypes.c_double(), ctypes.c_double()
+        L.check(self._lib.fl_precond_params(self._h, int(mode), float(shift), float(scale),
+                                            ctypes.byref(ps), ctypes.byref(sc)), "fl_precond_params")
+        return ps.value, sc.value
+
     # -- solves ----------------------------------------------------------------
     def solve(self, f, u=None, tol=1e-8, maxit=1000, mode=L.FL_MODE_MIXED, raise_on_fail=True):
         """Solve M u = f; returns (u, info dict)."""

@@ -114,6 +114,8 @@ cudaError_t launch_pcg_init(cudaStream_t s, PcgState* st, const double* bb_part,
                             const double* rr_part, int rr_count, const double* rz_part, int rz_count,
                             double tol, int maxit);
 cudaError_t launch_sum(cudaStream_t s, const double* part, int count, double* out);
+// v = the lowest (hi = 0) or highest (hi = 1) separable DST-I mode, 0 off the mask
+cudaError_t launch_sine_mode(const Geo& g, cudaStream_t s, double* v, const uint8_t* mask, int hi);
 // r = b - shift u - scale mx (masked) from a known mx = M u: FP64 r is not
 // kept; r32 = (float) r and per-CTA partials of ||r||^2 are written.
 cudaError_t launch_residual_from(long long N, cudaStream_t s, const double* b, const double* u,

@@ -147,6 +147,26 @@ __global__ void k_hash(const double* u, unsigned long long* h, long long N) {
   if ((threadIdx.x & 31) == 0) atomicAdd(h, acc);
 }
 
+// v_i = prod_a sin(pi k_a (i_a + 1) / (n_a + 1)) with k_a = 1 (lowest mode)
+// or k_a = n_a (highest), 0 off Omega: the separable DST-I eigenvectors of
+// the FD Laplacian with the smallest and the largest eigenvalue.
+__global__ void k_sine_mode(double* v, const uint8_t* mask, int d, int n0, int n1, int n2, int hi,
+                            long long N) {
+  const int ns[3] = {n0, n1, n2};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    long long rem = i;
+    double val = 1.0;
+    for (int ax = d - 1; ax >= 0; --ax) {
+      const long long j = rem % ns[ax];
+      rem /= ns[ax];
+      const long long k = hi ? ns[ax] : 1;
+      val *= sinpi((double)(k * (j + 1)) / (double)(ns[ax] + 1));
+    }
+    v[i] = (mask && !mask[i]) ? 0.0 : val;
+  }
+}
+
 __global__ void k_sum(const double* part, int count, double* out) {
   __shared__ double red[32];
   const double s = cta_sum_partials(part, count, red);
@@ -533,6 +553,12 @@ cudaError_t launch_axmy(long long N, cudaStream_t s, const double* u, double c, 
 
 cudaError_t launch_hash(long long N, cudaStream_t s, const double* u, unsigned long long* h) {
   FL_KERNEL("hash", s, k_hash<<<kVecBlocks, kVecThreads, 0, s>>>(u, h, N));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sine_mode(const Geo& g, cudaStream_t s, double* v, const uint8_t* mask, int hi) {
+  FL_KERNEL("sine_mode", s,
+            k_sine_mode<<<kVecBlocks, kVecThreads, 0, s>>>(v, mask, g.d, g.n[0], g.n[1], g.n[2], hi, g.N));
   return cudaGetLastError();
 }
 

@@ -92,7 +92,7 @@ struct GraphCache {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool use_prec = false;
-  double shift = 0.0, scale = 0.0;
+  double shift = 0.0, scale = 0.0, pshift = 0.0, pscale = 0.0;
   long long kernels = 0;
   void release() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -139,6 +139,10 @@ struct fl_plan {
   bool mu_valid = false;
   unsigned long long* hash_dev = nullptr;
   unsigned long long* hash_host = nullptr;  // pinned
+  // Rayleigh quotients of M on the lowest and highest sine modes
+  // (FL_PRECOND_SHIFTED), computed on first use
+  double mq_lo = 0.0, mq_hi = 0.0;
+  bool mq_valid = false;
 };
 
 namespace {
@@ -302,12 +306,98 @@ fl_status read_sum(fl_plan* p, const double* part, int count, double* out) {
   return FL_OK;
 }
 
+// The preconditioner of a solve: z = (shift I + scale C h^d L)^{-1} r on the
+// box (restricted to Omega), or none.
+struct PrecChoice {
+  bool use = false;
+  double shift = 0.0, scale = 0.0;
+};
+
+// Rayleigh quotients v^T M v / v^T v of the lowest and the highest sine
+// modes restricted to Omega, by FP64 applies (the CG direction buffers of
+// the FP64 workspace serve as scratch); once per plan.
+fl_status extreme_quotients(fl_plan* p) {
+  if (p->mq_valid) return FL_OK;
+  const Geo& g = p->g;
+  double* v = p->v64.p;
+  double q[2] = {0.0, 0.0};
+  for (int hi = 0; hi < 2; ++hi) {
+    FL_CUDA(launch_sine_mode(g, p->stream, v, p->mask, hi));
+    ApplyIO<double> io;
+    io.u = v; io.mask = p->mask; io.out = p->v64.q; io.x = v; io.cm = 1.0;
+    io.dotw = v; io.partials = p->part[P_AUX];
+    FL_CUDA(launch_apply<double>(g, p->t64, p->stream, io));
+    double vmv = 0.0, vv = 0.0;
+    fl_status st = read_sum(p, p->part[P_AUX], apply_partials<double>(g), &vmv);
+    if (st != FL_OK) return st;
+    int c = 0;
+    FL_CUDA(launch_dot<double>(g.N, p->stream, v, v, p->part[P_RES], &c));
+    st = read_sum(p, p->part[P_RES], c, &vv);
+    if (st != FL_OK) return st;
+    if (!(vv > 0.0)) return fail(FL_INVALID_ARG, "a sine mode vanishes on Omega");
+    q[hi] = vmv / vv;
+  }
+  p->mq_lo = q[0];
+  p->mq_hi = q[1];
+  p->mq_valid = true;
+  return FL_OK;
+}
+
+// Eigenvalue of C h^d L = cA (2d I - S) on the lowest (hi = 0) or highest
+// sine mode: cA sum_i 4 sin^2(pi k_i / (2 (n_i + 1))).
+double fd_mode_eigenvalue(const Geo& g, int hi) {
+  double lam = 0.0;
+  for (int i = 0; i < g.d; ++i) {
+    const double k = hi ? g.n[i] : 1.0;
+    const double sn = std::sin(3.14159265358979323846 * k / (2.0 * (g.n[i] + 1.0)));
+    lam += 4.0 * sn * sn;
+  }
+  return g.cA * lam;
+}
+
+// The preconditioner of `prec_mode` for the operator shift I + scale M.
+fl_status precond_params(fl_plan* p, int prec_mode, double shift, double scale, PrecChoice* pc) {
+  pc->use = true;
+  pc->shift = shift;
+  pc->scale = scale;
+  switch (prec_mode) {
+    case FL_PRECOND_FD:
+      return FL_OK;
+    case FL_PRECOND_AUTO:
+      if (p->alpha >= 1.0) return FL_OK;
+      *pc = PrecChoice();
+      return FL_OK;
+    case FL_PRECOND_NONE:
+      *pc = PrecChoice();
+      return FL_OK;
+    case FL_PRECOND_STENCIL:
+      // shift I + scale M~: M~ has c (Z - 2d a) on the diagonal and c (a - 1)
+      // on the stencil's neighbours, = c (Z - 2d) I + ((1 - a) / -a) cA (2d I - S)
+      pc->shift = shift + scale * p->c * (p->Z - 2.0 * p->g.d);
+      pc->scale = scale * (1.0 - p->a) / (-p->a);
+      return FL_OK;
+    case FL_PRECOND_SHIFTED: {
+      const fl_status st = extreme_quotients(p);
+      if (st != FL_OK) return st;
+      const double lam_lo = fd_mode_eigenvalue(p->g, 0), lam_hi = fd_mode_eigenvalue(p->g, 1);
+      const double A = shift + scale * p->mq_lo, B = shift + scale * p->mq_hi;
+      const double x = B > A ? scale * (A * lam_hi - B * lam_lo) / (B - A) : shift;
+      pc->shift = x > 0.0 ? x : 0.0;
+      return FL_OK;
+    }
+    default:
+      return fail(FL_INVALID_ARG, "unknown preconditioner mode");
+  }
+}
+
 // Preconditioned CG for (shift I + scale M) x = b in precision T, all
-// vectors in the plan's workspace of that precision (b = v.b, x = v.x).
+// vectors in the plan's workspace of that precision (b = v.b, x = v.x),
+// preconditioned by (pc.shift I + pc.scale C h^d L)^{-1} unless !pc.use.
 // Stops when ||r|| <= tol ||b||.  Returns the status of the solve.
 template <typename T>
-fl_status run_pcg(fl_plan* p, bool x0_nonzero, double shift, double scale, bool use_prec, double tol,
-                  int maxit, int* iters) {
+fl_status run_pcg(fl_plan* p, bool x0_nonzero, double shift, double scale, const PrecChoice& pc,
+                  double tol, int maxit, int* iters) {
+  const bool use_prec = pc.use;
   const Geo& g = p->g;
   Vecs<T>& v = vecs<T>(p);
   Tables<T>& tb = tables<T>(p);
@@ -327,9 +417,9 @@ fl_status run_pcg(fl_plan* p, bool x0_nonzero, double shift, double scale, bool 
   FL_CUDA(cudaMemsetAsync(v.p, 0, g.N * sizeof(T), s));
   T* z = use_prec ? v.z : v.r;
   if (use_prec) {
-    FL_CUDA(prepare_precond<T>(g, tb, shift, scale, s));
+    FL_CUDA(prepare_precond<T>(g, tb, pc.shift, pc.scale, s));
     PrecIO<T> io;
-    io.in = v.r; io.out = v.z; io.shift = shift; io.scale = scale;
+    io.in = v.r; io.out = v.z; io.shift = pc.shift; io.scale = pc.scale;
     io.dotw = v.r; io.dot_part = p->part[P_RZ]; io.mask = p->mask;
     FL_CUDA(launch_precond<T>(g, tb, s, io));
     rz_count = precond_partials<T>(g);
@@ -359,7 +449,7 @@ fl_status run_pcg(fl_plan* p, bool x0_nonzero, double shift, double scale, bool 
     int cnt = 0;
     if (use_prec) {
       PrecIO<T> pi;
-      pi.pre = DPRE_UPDATE; pi.out = v.z; pi.shift = shift; pi.scale = scale;
+      pi.pre = DPRE_UPDATE; pi.out = v.z; pi.shift = pc.shift; pi.scale = pc.scale;
       pi.x = v.x; pi.r = v.r; pi.p = v.p; pi.q = v.q; pi.rr_part = p->part[P_RR];
       pi.dotw = v.r; pi.dot_part = p->part[P_RZ]; pi.st = p->st; pi.fin = FIN_STEP;
       pi.mask = p->mask;
@@ -372,7 +462,8 @@ fl_status run_pcg(fl_plan* p, bool x0_nonzero, double shift, double scale, bool 
   // while the per-kernel profiler is on).
   GraphCache& gc = p->gcache[sizeof(T) == 4 ? 1 : 0];
   const bool use_graph = p->prof == nullptr && graphs_enabled();
-  if (use_graph && !(gc.exec && gc.use_prec == use_prec && gc.shift == shift && gc.scale == scale)) {
+  if (use_graph && !(gc.exec && gc.use_prec == use_prec && gc.shift == shift && gc.scale == scale &&
+                     gc.pshift == pc.shift && gc.pscale == pc.scale)) {
     gc.release();
     cudaStream_t cs = nullptr;
     FL_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -389,6 +480,8 @@ fl_status run_pcg(fl_plan* p, bool x0_nonzero, double shift, double scale, bool 
     gc.use_prec = use_prec;
     gc.shift = shift;
     gc.scale = scale;
+    gc.pshift = pc.shift;
+    gc.pscale = pc.scale;
   }
   // The next chunk covers the iterations the last chunk's convergence rate
   // predicts are left (+1), in multiples of the graph's 4, between 4 and 32;
@@ -571,19 +664,21 @@ fl_status solve_system(fl_plan* p, double* u, bool x0_nonzero, double shift, dou
   cudaStream_t s = p->stream;
   const int prec_mode = mode & 0xF0;
   const int precision = mode & 0x0F;
-  bool use_prec = prec_mode == FL_PRECOND_FD || (prec_mode == FL_PRECOND_AUTO && p->alpha >= 1.0);
-  if (prec_mode != FL_PRECOND_FD && prec_mode != FL_PRECOND_NONE && prec_mode != FL_PRECOND_AUTO)
-    return fail(FL_INVALID_ARG, "unknown preconditioner mode");
   if (!(tol > 0.0) || maxit < 1) return fail(FL_INVALID_ARG, "tol must be > 0 and maxit >= 1");
   if (precision == FL_MODE_LEARNED && (!p->net || p->has_mask))
     return fail(FL_INVALID_ARG, "FL_MODE_LEARNED needs a network attached to a plan without mask");
+  PrecChoice pc;
+  {
+    const fl_status ps = precond_params(p, prec_mode, shift, scale, &pc);
+    if (ps != FL_OK) return ps;
+  }
   fl_solve_info loc;
   memset(&loc, 0, sizeof(loc));
   fl_status result = FL_OK;
   if (precision == FL_MODE_F64) {
     if (x0_nonzero) FL_CUDA(cudaMemcpyAsync(p->v64.x, u, g.N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     int its = 0;
-    result = run_pcg<double>(p, x0_nonzero, shift, scale, use_prec, tol, maxit, &its);
+    result = run_pcg<double>(p, x0_nonzero, shift, scale, pc, tol, maxit, &its);
     if (result != FL_OK && result != FL_NOT_CONVERGED && result != FL_BREAKDOWN) return result;
     FL_CUDA(cudaMemcpyAsync(u, p->v64.x, g.N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     loc.iterations = its;
@@ -638,11 +733,11 @@ fl_status solve_system(fl_plan* p, double* u, bool x0_nonzero, double shift, dou
           in = run_fpcg_learned(p, shift, scale, eta, maxit, &its, &fallback);
           if (fallback) {   // plain preconditioned CG takes over this correction
             int its2 = 0;
-            in = run_pcg<float>(p, false, shift, scale, use_prec, eta, maxit, &its2);
+            in = run_pcg<float>(p, false, shift, scale, pc, eta, maxit, &its2);
             its += its2;
           }
         } else {
-          in = run_pcg<float>(p, false, shift, scale, use_prec, eta, maxit, &its);
+          in = run_pcg<float>(p, false, shift, scale, pc, eta, maxit, &its);
         }
         total += its;
         if (trace_enabled())
@@ -867,6 +962,20 @@ fl_status fl_precond_f32(fl_plan* p, double shift, double scale, const float* r,
   PrecIO<float> io;
   io.in = r; io.out = z; io.shift = shift; io.scale = scale; io.mask = p->mask;
   FL_CUDA(launch_precond<float>(p->g, p->t32, p->stream, io));
+  return FL_OK;
+}
+
+fl_status fl_precond_params(fl_plan* p, int mode, double shift, double scale, double* pshift,
+                            double* pscale) {
+  ProfScope prof_scope(p);
+  if (!check_plan(p) || !pshift || !pscale) return fail(FL_INVALID_ARG, "NULL argument");
+  if (!(scale > 0.0) || !(shift >= 0.0) || !std::isfinite(scale) || !std::isfinite(shift))
+    return fail(FL_INVALID_ARG, "the operator needs shift >= 0 and scale > 0");
+  PrecChoice pc;
+  const fl_status st = precond_params(p, mode & 0xF0, shift, scale, &pc);
+  if (st != FL_OK) return st;
+  *pshift = pc.use ? pc.shift : 0.0;
+  *pscale = pc.use ? pc.scale : 0.0;
   return FL_OK;
 }
 
@@ -1194,7 +1303,12 @@ fl_status solve_batched_mixed(fl_plan* const* plans, int count, const double* co
     fl_plan* p = plans[i];
     const Geo& g = p->g;
     const int vb = vec_blocks(g.N);
-    prec[i] = prec_mode == FL_PRECOND_FD || (prec_mode == FL_PRECOND_AUTO && p->alpha >= 1.0);
+    PrecChoice pc;
+    {
+      const fl_status ps = precond_params(p, prec_mode, 0.0, 1.0, &pc);
+      if (ps != FL_OK) return ps;
+    }
+    prec[i] = pc.use;
     PcgState* st = p->st;
     const PcgState* gate = gates + i;
     // FP64: right-hand side of the zero guess, then residuals with u += x32
@@ -1218,8 +1332,9 @@ fl_status solve_batched_mixed(fl_plan* const* plans, int count, const double* co
     const int pcount = precond_partials<float>(g);
     if (prec[i]) {
       // on the plan's stream, before the batched stream waits for it
-      FL_CUDA(prepare_precond<float>(g, p->t32, 0.0, 1.0, p->stream));
+      FL_CUDA(prepare_precond<float>(g, p->t32, pc.shift, pc.scale, p->stream));
       PrecIO<float> pi;
+      pi.shift = pc.shift; pi.scale = pc.scale;
       pi.in = p->v32.r; pi.out = p->v32.z; pi.dotw = p->v32.r; pi.dot_part = p->part[P_RZ];
       pi.mask = p->mask;
       pi.st = const_cast<PcgState*>(gate);
@@ -1237,6 +1352,7 @@ fl_status solve_batched_mixed(fl_plan* const* plans, int count, const double* co
     // the x/r update and the CG scalar step (in the last CTA of the last pass)
     if (prec[i]) {
       PrecIO<float> pu;
+      pu.shift = pc.shift; pu.scale = pc.scale;
       pu.pre = DPRE_UPDATE; pu.out = p->v32.z; pu.x = p->v32.x; pu.r = p->v32.r; pu.p = p->v32.p;
       pu.q = p->v32.q; pu.rr_part = p->part[P_RR]; pu.dotw = p->v32.r; pu.dot_part = p->part[P_RZ];
       pu.st = st; pu.fin = FIN_STEP; pu.mask = p->mask;
@@ -1408,7 +1524,8 @@ fl_status fl_solve_elliptic_batched(fl_plan* const* plans, int count, const doub
   }
   if (!(tol > 0.0) || maxit < 1) return fail(FL_INVALID_ARG, "tol must be > 0 and maxit >= 1");
   const int precision = mode & 0x0F, prec_mode = mode & 0xF0;
-  if (prec_mode != FL_PRECOND_FD && prec_mode != FL_PRECOND_NONE && prec_mode != FL_PRECOND_AUTO)
+  if (prec_mode != FL_PRECOND_FD && prec_mode != FL_PRECOND_NONE && prec_mode != FL_PRECOND_AUTO &&
+      prec_mode != FL_PRECOND_SHIFTED && prec_mode != FL_PRECOND_STENCIL)
     return fail(FL_INVALID_ARG, "unknown preconditioner mode");
   if (precision == FL_MODE_F64) {
     // plain FP64 CG: the problems one after another
