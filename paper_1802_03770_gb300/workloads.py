@@ -12,7 +12,11 @@ batched: 64 problems with sides uniform in {96, 128, ..., 768} and alpha ~
 U(0.3, 1.8), seeded Gaussian-mixture right-hand sides, to 1e-8, solved in
 lockstep (fl_solve_elliptic_batched) and, for comparison, one after another.
 lshape: the occluded-domain example (Sec. 4.4) at n = 128 .. 1024, alpha =
-1.75, FP64 CG with and without the FD preconditioner, to 1e-6 and 1e-9.
+1.75, FP64 CG with and without the FD preconditioner (and with its
+balanced shift), to 1e-6 and 1e-9.
+--precond picks the preconditioner of timestep and batched: fd (the
+paper's; batched default: auto, none for alpha < 1), shifted (FD with the
+balanced shift) or stencil (the stencil part of M).
 Each prints one JSON line.
 """
 
@@ -25,29 +29,35 @@ from . import inputs
 from .api import Plan, solve_batched
 
 
-def timestep(n=256, steps=100, alpha=1.5, dt=1e-3, seed=3):
+PRECONDS = {"fd": L.FL_PRECOND_FD, "auto": L.FL_PRECOND_AUTO, "shifted": L.FL_PRECOND_SHIFTED,
+            "stencil": L.FL_PRECOND_STENCIL}
+
+
+def timestep(n=256, steps=100, alpha=1.5, dt=1e-3, seed=3, precond="fd"):
     import torch
+    mode = L.FL_MODE_MIXED | PRECONDS[precond]
     p = Plan(3, (n, n, n), 1.0 / (n + 1), alpha)
     u = torch.tensor(inputs.gaussian_mixture(n, 3, 16, seed, 0.05, 0.15), dtype=torch.float64,
                      device="cuda").view(-1)
     nxt = torch.empty_like(u)
     its, ok = [], True
-    p.time_step(u, dt, 1.0, out=nxt, tol=1e-8)          # warm-up (not timed)
+    p.time_step(u, dt, 1.0, out=nxt, tol=1e-8, mode=mode)   # warm-up (not timed)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
-        _, info = p.time_step(u, dt, 1.0, out=nxt, tol=1e-8)
+        _, info = p.time_step(u, dt, 1.0, out=nxt, tol=1e-8, mode=mode)
         ok = ok and info["converged"] == 1
         its.append(info["iterations"])
         u, nxt = nxt, u
     torch.cuda.synchronize()
     t = time.perf_counter() - t0
-    return {"workload": f"backward Euler, 3D {n}^3, alpha {alpha}, dt {dt}", "steps": steps,
+    return {"workload": f"backward Euler, 3D {n}^3, alpha {alpha}, dt {dt}", "precond": precond,
+            "steps": steps,
             "seconds": t, "ms_per_step": 1e3 * t / steps, "mean_iterations": sum(its) / len(its),
             "all_converged": ok}
 
 
-def batched(count=64, seed=7):
+def batched(count=64, seed=7, precond="auto"):
     import torch
     sides = inputs.batch_sides(count, seed)
     alphas = inputs.alpha_draws(count, seed + 1)
@@ -56,19 +66,22 @@ def batched(count=64, seed=7):
         plans.append(Plan(2, (n, n), 1.0 / (n + 1), a))
         fs.append(torch.tensor(inputs.gaussian_mixture(n, 2, 16, 100 + i), dtype=torch.float64,
                                device="cuda").view(-1))
-    mode = L.FL_MODE_MIXED | L.FL_PRECOND_AUTO
+    mode = L.FL_MODE_MIXED | PRECONDS[precond]
     solve_batched(plans, fs, tol=1e-8, mode=mode)         # warm-up (graph capture)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     _, infos = solve_batched(plans, fs, tol=1e-8, mode=mode)
     torch.cuda.synchronize()
     tb = time.perf_counter() - t0
+    for p, f in zip(plans, fs):                          # warm-up (per-plan graph capture)
+        p.solve(f, tol=1e-8, mode=mode)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     for p, f in zip(plans, fs):
         p.solve(f, tol=1e-8, mode=mode)
     torch.cuda.synchronize()
     ts = time.perf_counter() - t0
-    return {"workload": f"{count} 2D problems, sides 96..768, alpha U(0.3,1.8)",
+    return {"workload": f"{count} 2D problems, sides 96..768, alpha U(0.3,1.8)", "precond": precond,
             "batched_seconds": tb, "batched_solves_per_s": count / tb,
             "sequential_seconds": ts, "sequential_solves_per_s": count / ts,
             "all_converged": all(i["converged"] == 1 for i in infos),
@@ -99,7 +112,8 @@ def lshape(sizes=(128, 256, 512, 1024), alpha=1.75):
         f = torch.tensor(np.where(mask, 1.0, 0.0), dtype=torch.float64, device="cuda").view(-1)
         row = {"n": n, "N": int(mask.sum())}
         for tol in (1e-6, 1e-9):
-            for name, pm in (("prec", L.FL_PRECOND_FD), ("plain", L.FL_PRECOND_NONE)):
+            for name, pm in (("prec", L.FL_PRECOND_FD), ("shifted", L.FL_PRECOND_SHIFTED),
+                             ("plain", L.FL_PRECOND_NONE)):
                 p.solve(f, tol=tol, mode=L.FL_MODE_F64 | pm, maxit=1000, raise_on_fail=False)
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
@@ -118,11 +132,12 @@ def main():
     ap.add_argument("which", choices=["timestep", "batched", "lshape"])
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--count", type=int, default=64)
+    ap.add_argument("--precond", choices=sorted(PRECONDS), default=None)
     args = ap.parse_args()
     if args.which == "timestep":
-        res = timestep(steps=args.steps)
+        res = timestep(steps=args.steps, precond=args.precond or "fd")
     elif args.which == "batched":
-        res = batched(args.count)
+        res = batched(args.count, precond=args.precond or "auto")
     else:
         res = lshape()
     print(json.dumps(res))
