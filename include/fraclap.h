@@ -117,6 +117,25 @@ fl_status fl_plan_destroy(fl_plan* plan);
 /* Constants and sizes of a plan (host struct filled). */
 fl_status fl_plan_describe(const fl_plan* plan, fl_plan_desc* desc);
 
+/* Column tiles of the strided FFT passes (no counterpart in the paper).
+ * A strided pass along axis i transforms tiles of tx consecutive lines in
+ * shared memory; tx is a power of two between 16 bytes of line element
+ * (2 FP32 / 1 FP64 complex values) and the widest tile a CTA holds
+ * (8192 FP32 / 4096 FP64 complex values over the padded length L_i, at most
+ * 64).  The tile width changes neither the arithmetic nor any result (each
+ * line is transformed the same way), only the launch shape.
+ *   tx[6]: FP32 axes 0..2, then FP64 axes 0..2; 0 = the widest tile.
+ * fl_plan_set_tiles sets them (FL_INVALID_ARG for a width out of range or
+ * not a power of two; entries of axes without a strided pass are ignored).
+ * fl_plan_autotune times, for each precision and each axis with a strided
+ * pass, every candidate width over a few operator applies and
+ * preconditioner solves on the plan's stream (axis by axis, the others
+ * kept), keeps the fastest, and writes the choice to tx_out (nullable).
+ * It uses the plan's workspaces, waits for the stream, and invalidates the
+ * plan's captured CG graphs; run it before solves, not during one. */
+fl_status fl_plan_set_tiles(fl_plan* plan, const int tx[6]);
+fl_status fl_plan_autotune(fl_plan* plan, int tx_out[6]);
+
 /* y = M u (Sec. 3.1, BTTB apply by FFT), FP64 throughout.  u_dev, y_dev:
  * device arrays of N doubles; they may not alias. */
 fl_status fl_apply(fl_plan* plan, const double* u_dev, double* y_dev);

@@ -73,6 +73,8 @@ SIGNATURES = {
     "fl_precond": (_I, [_P, _D, _D, _P, _P]),
     "fl_precond_f32": (_I, [_P, _D, _D, _P, _P]),
     "fl_precond_params": (_I, [_P, _I, _D, _D, _P, _P]),
+    "fl_plan_set_tiles": (_I, [_P, _P]),
+    "fl_plan_autotune": (_I, [_P, _P]),
     "fl_solve_elliptic": (_I, [_P, _P, _P, _I, _D, _I, _I, ctypes.POINTER(FlSolveInfo)]),
     "fl_solve_elliptic_host": (_I, [_P, _P, _P, _D, _I, _I, ctypes.POINTER(FlSolveInfo)]),
     "fl_time_step": (_I, [_P, _D, _D, _P, _P, _P, _P, _D, _I, _I, ctypes.POINTER(FlSolveInfo)]),

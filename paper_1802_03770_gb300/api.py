@@ -203,6 +203,19 @@ class Plan:
         L.check(fn(self._h, float(shift), float(scale), _ptr(r), _ptr(z)), "fl_precond")
         return z
 
+    def set_tiles(self, tx):
+        """Column-tile widths of the strided passes: six ints (FP32 axes 0..2,
+        FP64 axes 0..2; 0 = the widest tile)."""
+        arr = (ctypes.c_int * 6)(*[int(v) for v in tx])
+        L.check(self._lib.fl_plan_set_tiles(self._h, arr), "fl_plan_set_tiles")
+
+    def autotune(self):
+        """Time the candidate column tiles on the GPU and keep the fastest;
+        returns the six chosen widths (0 for axes without a strided pass)."""
+        arr = (ctypes.c_int * 6)()
+        L.check(self._lib.fl_plan_autotune(self._h, arr), "fl_plan_autotune")
+        return list(arr)
+
     def precond_params(self, mode, shift=0.0, scale=1.0):
         """(pshift, pscale) of the preconditioner (pshift I + pscale C h^d L)^-1
         that a solve in `mode` uses for shift I + scale M; (0, 0) for none."""

@@ -33,6 +33,15 @@ template <typename T> inline int row_lines(int L) { return (Cfg<T>::RT * Cfg<T>:
 template <typename T> inline int col_tx(int L) {
   return std::min(kMaxTx, (Cfg<T>::CT * Cfg<T>::CV) / L);
 }
+// the narrowest tile the tuner tries: 16 contiguous bytes per line element
+template <typename T> inline int min_tx() {
+  return std::max(1, 16 / (int)sizeof(typename Cplx<T>::type));
+}
+// column-tile width of a strided pass along `axis`: the plan's tuned width
+// if set, else the widest tile that fits the CTA
+template <typename T> inline int plan_tx(const Tables<T>& tb, int axis, int L) {
+  return tb.tx[axis] > 0 ? tb.tx[axis] : col_tx<T>(L);
+}
 // shared-memory bytes of `lines` lines of L complex values (padded, SBuf)
 template <typename T> inline size_t smem_bytes(int lines, int L) {
   return (size_t)sbuf_elems((long long)lines * L) * sizeof(typename Cplx<T>::type);

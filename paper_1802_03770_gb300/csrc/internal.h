@@ -45,6 +45,7 @@ struct Tables {
   T* mu[3] = {nullptr, nullptr, nullptr};  // eigenvalues of C h^d L per axis
   T* tri_tab = nullptr;       // per-column constants of the axis-0 tridiagonal solve
   double tri_shift = -1.0, tri_scale = -1.0;  // the shift and scale tri_tab holds
+  int tx[3] = {0, 0, 0};      // column-tile width of the strided passes per axis (0: default)
 };
 
 // Inputs and outputs of one operator apply.

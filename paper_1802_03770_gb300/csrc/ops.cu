@@ -332,7 +332,7 @@ ApplyChain<T> build_apply(const Geo& g, const Tables<T>& tb, const ApplyIO<T>& i
     a.rows_in = rows_in; a.rows_out = rows_out; a.lstride = lstride; a.ostride = ostride;
     a.nouter = nouter; a.mode = mode; a.sig_line = sig_line; a.sig_outer = sig_outer; a.Lo = Lo;
     const int L = g.L[axis];
-    const int tx = col_tx<T>(L);
+    const int tx = plan_tx<T>(tb, axis, L);
     a.ltx = ilog2i(tx);
     ch.cols_grid[ch.ncols] = dim3((g.H + tx - 1) / tx, nouter);
     ch.cols_smem[ch.ncols] = tile_bytes<T>(tx, L);
@@ -408,7 +408,7 @@ PrecChain<T> build_precond(const Geo& g, const Tables<T>& tb, const PrecIO<T>& i
     a.n = g.n[axis]; a.ncols = nx; a.lg = g.lg[axis]; a.lgmax = g.lgmax;
     a.ostride = ostride; a.lstride = lstride;
     const int L = g.L[axis];
-    const int tx = col_tx<T>(L);
+    const int tx = plan_tx<T>(tb, axis, L);
     a.ltx = ilog2i(tx);
     ch.cols_grid[ch.ncols] = dim3((nx + tx - 1) / tx, nouter);
     ch.cols_smem[ch.ncols] = tile_bytes<T>(tx, L);

@@ -771,6 +771,76 @@ fl_status solve_system(fl_plan* p, double* u, bool x0_nonzero, double shift, dou
 
 bool check_plan(const fl_plan* p) { return p != nullptr; }
 
+// Axes with a strided pass: 2D the convolution along axis 0; 3D also the
+// middle axis (forward/inverse FFT of the apply, DST of the preconditioner).
+int strided_axes(const Geo& g, int* axes) {
+  axes[0] = 0;
+  if (g.d == 3) {
+    axes[1] = 1;
+    return 2;
+  }
+  return 1;
+}
+
+// Column-tile widths of one precision by timing: per axis with a strided
+// pass (the others kept), every power of two from the widest tile down to
+// 16 bytes of line element; a trial is kReps FP32/FP64 applies each
+// followed by an FD preconditioner solve, on zero data, after one untimed
+// trial run.  Keeps the fastest width per axis.
+template <typename T>
+fl_status autotune_precision(fl_plan* p) {
+  constexpr int kReps = 5;
+  const Geo& g = p->g;
+  Tables<T>& tb = tables<T>(p);
+  Vecs<T>& v = vecs<T>(p);
+  cudaStream_t s = p->stream;
+  FL_CUDA(cudaMemsetAsync(v.p, 0, g.N * sizeof(T), s));
+  FL_CUDA(prepare_precond<T>(g, tb, 0.0, 1.0, s));
+  auto trial = [&]() -> cudaError_t {
+    ApplyIO<T> io;
+    io.u = v.p; io.mask = p->mask; io.out = v.q;
+    cudaError_t e = launch_apply<T>(g, tb, s, io);
+    if (e != cudaSuccess) return e;
+    PrecIO<T> pi;
+    pi.in = v.q; pi.out = v.z; pi.shift = 0.0; pi.scale = 1.0; pi.mask = p->mask;
+    return launch_precond<T>(g, tb, s, pi);
+  };
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  FL_CUDA(cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(ce, "cudaEventCreate");
+  }
+  int axes[2];
+  const int na = strided_axes(g, axes);
+  for (int ia = 0; ia < na && ce == cudaSuccess; ++ia) {
+    const int ax = axes[ia];
+    const int widest = col_tx<T>(g.L[ax]);
+    int best_tx = widest;
+    float best_ms = -1.0f;
+    for (int tx = widest; tx >= min_tx<T>() && ce == cudaSuccess; tx /= 2) {
+      tb.tx[ax] = tx;
+      ce = trial();
+      if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
+      for (int r = 0; r < kReps && ce == cudaSuccess; ++r) ce = trial();
+      if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+      if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+      if (ce == cudaSuccess && (best_ms < 0.0f || ms < best_ms)) {
+        best_ms = ms;
+        best_tx = tx;
+      }
+    }
+    tb.tx[ax] = best_tx;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (ce != cudaSuccess) return cuda_fail(ce, "tile autotuning");
+  return FL_OK;
+}
+
 // FRACLAP_TRACE=1 in the environment prints one line per refinement step.
 bool trace_enabled() {
   static const bool on = [] {
@@ -916,6 +986,53 @@ fl_status fl_plan_describe(const fl_plan* p, fl_plan_desc* desc) {
   desc->window_corr = p->a;
   desc->kernel0 = p->c * (p->Z - 2.0 * p->g.d * p->a);
   desc->workspace_bytes = p->bytes;
+  return FL_OK;
+}
+
+fl_status fl_plan_set_tiles(fl_plan* p, const int tx[6]) {
+  if (!check_plan(p) || !tx) return fail(FL_INVALID_ARG, "NULL argument");
+  int axes[2];
+  const int na = strided_axes(p->g, axes);
+  for (int prec = 0; prec < 2; ++prec) {
+    for (int ia = 0; ia < na; ++ia) {
+      const int ax = axes[ia];
+      const int v = tx[3 * prec + ax];
+      const int widest = prec == 0 ? col_tx<float>(p->g.L[ax]) : col_tx<double>(p->g.L[ax]);
+      const int narrowest = prec == 0 ? min_tx<float>() : min_tx<double>();
+      if (v != 0 && (v < narrowest || v > widest || (v & (v - 1)) != 0))
+        return fail(FL_INVALID_ARG, "tile width out of range or not a power of two");
+    }
+  }
+  for (int ia = 0; ia < na; ++ia) {
+    p->t32.tx[axes[ia]] = tx[axes[ia]];
+    p->t64.tx[axes[ia]] = tx[3 + axes[ia]];
+  }
+  p->gcache[0].release();
+  p->gcache[1].release();
+  return FL_OK;
+}
+
+fl_status fl_plan_autotune(fl_plan* p, int tx_out[6]) {
+  ProfScope prof_scope(nullptr);
+  if (!check_plan(p)) return fail(FL_INVALID_ARG, "NULL plan");
+  p->gcache[0].release();
+  p->gcache[1].release();
+  fl_status st = autotune_precision<float>(p);
+  if (st == FL_OK) st = autotune_precision<double>(p);
+  if (st != FL_OK) return st;
+  if (tx_out) {
+    for (int i = 0; i < 3; ++i) {
+      tx_out[i] = i < p->g.d ? plan_tx<float>(p->t32, i, p->g.L[i]) : 0;
+      tx_out[3 + i] = i < p->g.d ? plan_tx<double>(p->t64, i, p->g.L[i]) : 0;
+    }
+    int axes[2];
+    const int na = strided_axes(p->g, axes);
+    for (int i = 0; i < 3; ++i) {
+      bool strided = false;
+      for (int ia = 0; ia < na; ++ia) strided = strided || axes[ia] == i;
+      if (!strided) tx_out[i] = tx_out[3 + i] = 0;
+    }
+  }
   return FL_OK;
 }
 

@@ -16,7 +16,8 @@ lshape: the occluded-domain example (Sec. 4.4) at n = 128 .. 1024, alpha =
 balanced shift), to 1e-6 and 1e-9.
 --precond picks the preconditioner of timestep and batched: fd (the
 paper's; batched default: auto, none for alpha < 1), shifted (FD with the
-balanced shift) or stencil (the stencil part of M).
+balanced shift) or stencil (the stencil part of M).  --autotune tunes the
+column tiles of every batched plan (fl_plan_autotune) before timing.
 Each prints one JSON line.
 """
 
@@ -57,7 +58,7 @@ def timestep(n=256, steps=100, alpha=1.5, dt=1e-3, seed=3, precond="fd"):
             "all_converged": ok}
 
 
-def batched(count=64, seed=7, precond="auto"):
+def batched(count=64, seed=7, precond="auto", autotune=False):
     import torch
     sides = inputs.batch_sides(count, seed)
     alphas = inputs.alpha_draws(count, seed + 1)
@@ -66,6 +67,12 @@ def batched(count=64, seed=7, precond="auto"):
         plans.append(Plan(2, (n, n), 1.0 / (n + 1), a))
         fs.append(torch.tensor(inputs.gaussian_mixture(n, 2, 16, 100 + i), dtype=torch.float64,
                                device="cuda").view(-1))
+    t_tune = 0.0
+    if autotune:
+        t0 = time.perf_counter()
+        for p in plans:
+            p.autotune()
+        t_tune = time.perf_counter() - t0
     mode = L.FL_MODE_MIXED | PRECONDS[precond]
     solve_batched(plans, fs, tol=1e-8, mode=mode)         # warm-up (graph capture)
     torch.cuda.synchronize()
@@ -82,6 +89,7 @@ def batched(count=64, seed=7, precond="auto"):
     torch.cuda.synchronize()
     ts = time.perf_counter() - t0
     return {"workload": f"{count} 2D problems, sides 96..768, alpha U(0.3,1.8)", "precond": precond,
+            "autotuned_tiles": autotune, "autotune_seconds": t_tune,
             "batched_seconds": tb, "batched_solves_per_s": count / tb,
             "sequential_seconds": ts, "sequential_solves_per_s": count / ts,
             "all_converged": all(i["converged"] == 1 for i in infos),
@@ -133,11 +141,13 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--count", type=int, default=64)
     ap.add_argument("--precond", choices=sorted(PRECONDS), default=None)
+    ap.add_argument("--autotune", action="store_true",
+                    help="batched: tune every plan's column tiles before timing")
     args = ap.parse_args()
     if args.which == "timestep":
         res = timestep(steps=args.steps, precond=args.precond or "fd")
     elif args.which == "batched":
-        res = batched(args.count, precond=args.precond or "auto")
+        res = batched(args.count, precond=args.precond or "auto", autotune=args.autotune)
     else:
         res = lshape()
     print(json.dumps(res))
