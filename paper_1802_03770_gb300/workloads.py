@@ -3,6 +3,7 @@
     python -m paper_1802_03770_gb300.workloads timestep [--steps 100]
     python -m paper_1802_03770_gb300.workloads batched [--count 64]
     python -m paper_1802_03770_gb300.workloads lshape
+    python -m paper_1802_03770_gb300.workloads tiles
 
 timestep: 256^3 interior grid (512^3 padded FFT), alpha = 1.5, backward
 Euler dt = 1e-3, u0 = 16 seeded Gaussians (widths U(0.05, 0.15)), f = 0,
@@ -18,6 +19,9 @@ balanced shift), to 1e-6 and 1e-9.
 paper's; batched default: auto, none for alpha < 1), shifted (FD with the
 balanced shift) or stencil (the stencil part of M).  --autotune tunes the
 column tiles of every batched plan (fl_plan_autotune) before timing.
+tiles: one FP32 apply + FD preconditioner solve (the work of a CG
+iteration) on square 2D grids of side 96 .. 1024 and cubes of side 64 .. 256,
+alpha = 1, timed with the widest column tiles and after fl_plan_autotune.
 Each prints one JSON line.
 """
 
@@ -135,9 +139,41 @@ def lshape(sizes=(128, 256, 512, 1024), alpha=1.75):
     return {"workload": f"L-shaped domain, alpha {alpha}, FP64 CG, f = 1", "rows": rows}
 
 
+def tiles(shapes=((2, 96), (2, 128), (2, 192), (2, 256), (2, 384), (2, 512), (2, 768),
+                  (2, 1024), (3, 64), (3, 128), (3, 256)), reps=20):
+    import torch
+
+    def per_iteration_us(p, N):
+        u = torch.zeros(N, dtype=torch.float32, device="cuda")
+        for _ in range(2):
+            p.precond(p.apply(u))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            p.precond(p.apply(u))
+        e1.record()
+        torch.cuda.synchronize()
+        return 1e3 * e0.elapsed_time(e1) / reps
+
+    rows = []
+    for d, n in shapes:
+        p = Plan(d, (n,) * d, 1.0 / (n + 1), 1.0)
+        t_default = per_iteration_us(p, n ** d)
+        t0 = time.perf_counter()
+        tx = p.autotune()
+        t_tune = time.perf_counter() - t0
+        rows.append({"d": d, "n": n, "us_widest": round(t_default, 1),
+                     "us_tuned": round(per_iteration_us(p, n ** d), 1), "tiles": tx,
+                     "tune_seconds": round(t_tune, 3)})
+        p.close()
+    return {"workload": "FP32 apply + FD preconditioner solve, alpha 1", "rows": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("which", choices=["timestep", "batched", "lshape"])
+    ap.add_argument("which", choices=["timestep", "batched", "lshape", "tiles"])
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--count", type=int, default=64)
     ap.add_argument("--precond", choices=sorted(PRECONDS), default=None)
@@ -148,6 +184,8 @@ def main():
         res = timestep(steps=args.steps, precond=args.precond or "fd")
     elif args.which == "batched":
         res = batched(args.count, precond=args.precond or "auto", autotune=args.autotune)
+    elif args.which == "tiles":
+        res = tiles()
     else:
         res = lshape()
     print(json.dumps(res))
