@@ -4,6 +4,7 @@
     python -m paper_1802_03770_gb300.workloads batched [--count 64]
     python -m paper_1802_03770_gb300.workloads lshape
     python -m paper_1802_03770_gb300.workloads tiles
+    python -m paper_1802_03770_gb300.workloads richardson
 
 timestep: 256^3 interior grid (512^3 padded FFT), alpha = 1.5, backward
 Euler dt = 1e-3, u0 = 16 seeded Gaussians (widths U(0.05, 0.15)), f = 0,
@@ -22,6 +23,12 @@ column tiles of every batched plan (fl_plan_autotune) before timing.
 tiles: one FP32 apply + FD preconditioner solve (the work of a CG
 iteration) on square 2D grids of side 96 .. 1024 and cubes of side 64 .. 256,
 alpha = 1, timed with the widest column tiles and after fl_plan_autotune.
+richardson: the paper's grid error estimates (eq. rich) on the GPU:
+f = M g_1 and u = M^-1 1 on 255^2 / 511^2 / 1023^2 (Sec. 4.2) and
+63^3 / 127^3 / 255^3 (Sec. 4.3), and Crank-Nicolson to T = 0.25 with
+dt = 1/(n+1) from the cosine product (nu = 3, 11, 2) on 255^2 .. 1023^2 and
+31^3 .. 127^3 (Sec. 4.5); alpha = 1.25, 1.5, 1.75, FP64 applies, solves to
+1e-11 (mixed), time steps to 1e-11.
 Each prints one JSON line.
 """
 
@@ -171,9 +178,65 @@ def tiles(shapes=((2, 96), (2, 128), (2, 192), (2, 256), (2, 384), (2, 512), (2,
     return {"workload": "FP32 apply + FD preconditioner solve, alpha 1", "rows": rows}
 
 
+def _rates(c, m, f):
+    """R_p = (log ||f_f - f_m||_p - log ||f_m - f_c||_p) / log(1/2), p = 2, inf,
+    of three fields already restricted to the common coarse grid (eq. rich)."""
+    import numpy as np
+    out = {}
+    for p, name in ((2, "R2"), (np.inf, "Rinf")):
+        a = np.linalg.norm((f - m).ravel(), p)
+        b = np.linalg.norm((m - c).ravel(), p)
+        out[name] = float((np.log(a) - np.log(b)) / np.log(0.5))
+    return out
+
+
+def _on_coarse(v, n, k, d):
+    """Values of a grid of n = 2^k (n_c + 1) - 1 points per axis at the points
+    of the coarse grid (every 2^k-th point)."""
+    s = 2 ** k
+    return v.reshape((n,) * d)[(slice(s - 1, None, s),) * d]
+
+
+def richardson(alphas=(1.25, 1.5, 1.75), parts=("2d", "3d", "td2", "td3")):
+    import torch
+    grids = {"2d": (2, (255, 511, 1023)), "3d": (3, (63, 127, 255)),
+             "td2": (2, (255, 511, 1023)), "td3": (3, (31, 63, 127))}
+    rows = []
+    for part in parts:
+        d, ns = grids[part]
+        for alpha in alphas:
+            fs, us = [], []
+            for k, n in enumerate(ns):
+                p = Plan(d, (n,) * d, 1.0 / (n + 1), alpha)
+                if part in ("2d", "3d"):
+                    g1 = torch.tensor(inputs.cosine_product(n, d, (1, 1, 1)), dtype=torch.float64,
+                                      device="cuda").view(-1)
+                    fs.append(_on_coarse(p.apply(g1).cpu().numpy(), n, k, d))
+                    one = torch.ones(n ** d, dtype=torch.float64, device="cuda")
+                    u, info = p.solve(one, tol=1e-11, mode=L.FL_MODE_MIXED | L.FL_PRECOND_FD)
+                    assert info["converged"] == 1, info
+                else:
+                    dt = 1.0 / (n + 1)
+                    u = torch.tensor(inputs.cosine_product(n, d), dtype=torch.float64,
+                                     device="cuda").view(-1)
+                    nxt = torch.empty_like(u)
+                    for _ in range(round(0.25 / dt)):
+                        _, info = p.time_step(u, dt, 0.5, out=nxt, tol=1e-11,
+                                              mode=L.FL_MODE_MIXED | L.FL_PRECOND_FD)
+                        assert info["converged"] == 1, info
+                        u, nxt = nxt, u
+                us.append(_on_coarse(u.cpu().numpy(), n, k, d))
+                p.close()
+            row = {"part": part, "d": d, "grids": list(ns), "alpha": alpha, "u": _rates(*us)}
+            if fs:
+                row["f"] = _rates(*fs)
+            rows.append(row)
+    return {"workload": "grid error estimates (eq. rich)", "rows": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("which", choices=["timestep", "batched", "lshape", "tiles"])
+    ap.add_argument("which", choices=["timestep", "batched", "lshape", "tiles", "richardson"])
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--count", type=int, default=64)
     ap.add_argument("--precond", choices=sorted(PRECONDS), default=None)
@@ -186,6 +249,8 @@ def main():
         res = batched(args.count, precond=args.precond or "auto", autotune=args.autotune)
     elif args.which == "tiles":
         res = tiles()
+    elif args.which == "richardson":
+        res = richardson()
     else:
         res = lshape()
     print(json.dumps(res))
