@@ -3,6 +3,7 @@
     python -m paper_1802_03770_gb300.workloads timestep [--steps 100]
     python -m paper_1802_03770_gb300.workloads batched [--count 64]
     python -m paper_1802_03770_gb300.workloads lshape
+    python -m paper_1802_03770_gb300.workloads octagon
     python -m paper_1802_03770_gb300.workloads tiles
     python -m paper_1802_03770_gb300.workloads richardson
 
@@ -15,7 +16,8 @@ U(0.3, 1.8), seeded Gaussian-mixture right-hand sides, to 1e-8, solved in
 lockstep (fl_solve_elliptic_batched) and, for comparison, one after another.
 lshape: the occluded-domain example (Sec. 4.4) at n = 128 .. 1024, alpha =
 1.75, FP64 CG with and without the FD preconditioner (and with its
-balanced shift), to 1e-6 and 1e-9.
+balanced shift), to 1e-6 and 1e-9; octagon: the same on the paper's
+octagonal domain.
 --precond picks the preconditioner of timestep and batched: fd (the
 paper's; batched default: auto, none for alpha < 1), shifted (FD with the
 balanced shift) or stencil (the stencil part of M).  --autotune tunes the
@@ -117,7 +119,19 @@ def l_shape_mask(n):
     return mask
 
 
-def lshape(sizes=(128, 256, 512, 1024), alpha=1.75):
+def octagon_mask(n):
+    """The paper's octagonal domain (Sec. 4.4): the (n-1)^2 interior points
+    of the unit square (h = 1/n) without the four corner triangles
+    |x - c|_1 <= 1/4 (c a corner of the square).  The printed sizes
+    (Table tab:octagon2: N = 14145 ... 915969) fix the cut: symmetric legs of
+    1/4, the cut line excluded from Omega."""
+    import numpy as np
+    i = np.arange(1, n)
+    a = np.minimum(i, n - i)                # grid distance to the nearer edge
+    return (a[:, None] + a[None, :]) > n // 4
+
+
+def lshape(sizes=(128, 256, 512, 1024), alpha=1.75, shape="lshape"):
     """Plain FP64 CG with and without the FD preconditioner (restricted box
     solve) on the L-shaped domain, f = 1 on Omega, to 1e-6 and 1e-9 -- the
     shape of the paper's L-shape table (whose preconditioner is a sparse
@@ -126,7 +140,7 @@ def lshape(sizes=(128, 256, 512, 1024), alpha=1.75):
     import torch
     rows = []
     for n in sizes:
-        mask = l_shape_mask(n)
+        mask = l_shape_mask(n) if shape == "lshape" else octagon_mask(n)
         p = Plan(2, mask.shape, 1.0 / n, alpha, mask=mask)
         f = torch.tensor(np.where(mask, 1.0, 0.0), dtype=torch.float64, device="cuda").view(-1)
         row = {"n": n, "N": int(mask.sum())}
@@ -143,7 +157,8 @@ def lshape(sizes=(128, 256, 512, 1024), alpha=1.75):
                                           "seconds": time.perf_counter() - t0,
                                           "converged": info["converged"]}
         rows.append(row)
-    return {"workload": f"L-shaped domain, alpha {alpha}, FP64 CG, f = 1", "rows": rows}
+    name = "L-shaped" if shape == "lshape" else "octagonal"
+    return {"workload": f"{name} domain, alpha {alpha}, FP64 CG, f = 1", "rows": rows}
 
 
 def tiles(shapes=((2, 96), (2, 128), (2, 192), (2, 256), (2, 384), (2, 512), (2, 768),
@@ -236,7 +251,8 @@ def richardson(alphas=(1.25, 1.5, 1.75), parts=("2d", "3d", "td2", "td3")):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("which", choices=["timestep", "batched", "lshape", "tiles", "richardson"])
+    ap.add_argument("which", choices=["timestep", "batched", "lshape", "octagon", "tiles",
+                                      "richardson"])
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--count", type=int, default=64)
     ap.add_argument("--precond", choices=sorted(PRECONDS), default=None)
@@ -251,6 +267,8 @@ def main():
         res = tiles()
     elif args.which == "richardson":
         res = richardson()
+    elif args.which == "octagon":
+        res = lshape(shape="octagon")
     else:
         res = lshape()
     print(json.dumps(res))

@@ -71,3 +71,11 @@ def test_l_shape_sizes_match_the_paper():
     (N = 12033 ... 784385 in the paper's L-shape table)."""
     from paper_1802_03770_gb300.workloads import l_shape_mask
     assert [int(l_shape_mask(n).sum()) for n in (128, 256, 512, 1024)] == [12033, 48641, 195585, 784385]
+
+
+def test_octagon_sizes_match_the_paper():
+    """The octagonal domain's sizes printed in Table tab:octagon2."""
+    from paper_1802_03770_gb300.workloads import octagon_mask
+    assert [int(octagon_mask(n).sum()) for n in (128, 256, 512, 1024)] == [14145, 56961, 228609, 915969]
+    m = octagon_mask(128)
+    assert (m == m[::-1]).all() and (m == m[:, ::-1]).all() and (m == m.T).all()
