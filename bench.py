@@ -224,6 +224,7 @@ def run_ours(args, rank, world, local):
     plans = [Plan(2, (N_SIDE, N_SIDE), h, a) for a in ALPHAS]
     torch.cuda.synchronize()
     t_con = (time.perf_counter() - t0) / len(plans)
+    tiles = [p.autotune() for p in plans]     # column tiles (plan set-up, untimed)
     mode_mixed = _lib.FL_MODE_MIXED | _lib.FL_PRECOND_AUTO
     mode_f64 = _lib.FL_MODE_F64 | _lib.FL_PRECOND_AUTO
     steps, warm = args.steps, args.warmup
@@ -359,7 +360,7 @@ def run_ours(args, rank, world, local):
             "refinements": [i["outer_iterations"] for i in infos_shift[: len(ALPHAS)]]},
         "iterations_mixed": its_mixed,
         "refinements": [i["outer_iterations"] for i in infos_mixed[: len(ALPHAS)]],
-        "kernels": kernel_shares, "apply": apply,
+        "kernels": kernel_shares, "apply": apply, "tiles": tiles,
     }
 
 
@@ -479,7 +480,8 @@ def main():
                 "fp64_pcg": res["fp64_pcg"], "speedup_vs_fp64_pcg": res["speedup_vs_fp64_pcg"],
                 "balanced_shift": res["balanced_shift"],
                 "iterations_mixed": res["iterations_mixed"], "refinements": res["refinements"],
-                "t_con_s": res["t_con_s"], "apply": res["apply"], "kernels": res["kernels"]}
+                "t_con_s": res["t_con_s"], "apply": res["apply"], "kernels": res["kernels"],
+                "tiles": res["tiles"]}
         print(json.dumps(line))
     if world > 1:
         import torch
