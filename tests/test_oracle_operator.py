@@ -1,5 +1,6 @@
 """Pins for oracle/operator.py: the paper's printed 1D errors (Table
-tab:1D_con, Table tab:1D_erronly2), closed forms of (-Delta)^{alpha/2}
+tab:1D_con, Table tab:1D_erronly2) and 1D CG iteration counts (Table
+tab:1D_cg), closed forms of (-Delta)^{alpha/2}
 for a Gaussian and on the unit ball, the O(h^2) order of Theorem 1, and
 the structure of M (symmetry, positivity, translation invariance)."""
 
@@ -61,6 +62,27 @@ def test_table_1d_fone(golden):
         us = np.linalg.solve(p.dense_matrix(), np.ones(N))
         e_sol = np.linalg.norm(us - u) / np.linalg.norm(u)
         assert e_sol == pytest.approx(e_paper, rel=0.05), (N, alpha)
+
+
+def test_table_1d_cg(golden):
+    """CG iteration counts of the smooth 1D example with the FD-Laplacian
+    preconditioner and without (Table tab:1D_cg), at both tolerances: equal
+    to the print, except one count (N = 4095, alpha = 1.5, 1e-9
+    preconditioned: 41 against 40) where the residual crosses the tolerance
+    within rounding of the last iteration."""
+    from oracle import precond as pc
+    from oracle import solvers
+    for N, alpha, p6, c6, p9, c9 in golden("table_1d_cg.txt"):
+        N = int(N)
+        p, x = interval_plan(N, alpha)
+        f = special.hyp2f1((1 + alpha) / 2, -2, 0.5, x ** 2)
+        got = []
+        for tol in (1e-6, 1e-9):
+            got.append(solvers.pcg(p.apply, f, lambda r: pc.solve_box(p, r), tol=tol, maxit=1000)[1])
+            got.append(solvers.pcg(p.apply, f, None, tol=tol, maxit=1000)[1])
+        want = [int(p6), int(c6), int(p9), int(c9)]
+        slack = 1 if (N, alpha) == (4095, 1.5) else 0
+        assert all(abs(g - w) <= slack for g, w in zip(got, want)), (N, alpha, got, want)
 
 
 @pytest.mark.parametrize("d,ns", [(2, (31, 63, 127)), (3, (15, 31))])
