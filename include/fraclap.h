@@ -96,7 +96,10 @@ typedef struct {
 } fl_plan_desc;
 
 /* Create a plan for the operator of eq. linearelliptic (Sec. 3.1).
- *   d      : 2 or 3
+ *   d      : 1, 2 or 3 (d = 1: the interval examples of Sec. 4.1; the line
+ *            is stored as the single row of a 2D layout, so in
+ *            fl_plan_set_tiles / fl_plan_autotune its strided pass is the
+ *            trivial axis 0)
  *   n      : host array of d extents n_i >= 1 (n_i <= 1024: padded FFT lengths up to 2048)
  *   h      : grid spacing > 0 (the unit box has h = 1/(n+1))
  *   alpha  : order, 0 < alpha < 2

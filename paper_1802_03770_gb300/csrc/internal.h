@@ -19,7 +19,8 @@ void host_fft(std::vector<std::complex<long double>>& a);
 
 // --- geometry of a plan ------------------------------------------------------
 struct Geo {
-  int d;
+  int d;          // layout dimension (2 or 3); a 1D problem is one row of a 2D layout
+  int dphys;      // dimension of the problem: 1, 2 or 3
   int n[3];
   int L[3];
   int lg[3];

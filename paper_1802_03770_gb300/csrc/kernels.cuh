@@ -800,10 +800,16 @@ constexpr int kTriTab = 4;     // table entries per column
 // gamma / (1 - r^2) = K w_0 (w_0 = r^{-1} x_0).
 template <typename T>
 __global__ void k_tri_table(T* tab, const T* mu_col, const T* mu_outer, int ncols, int n_inner,
-                            double shift, double scale, double cA, int n, int m) {
+                            double shift, double scale, double cA, int n, int m, int diag) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncols) return;
   const double mu = (double)mu_col[c % n_inner] + (mu_outer ? (double)mu_outer[c / n_inner] : 0.0);
+  if (diag) {
+    // no stencil along axis 0 (a 1D problem): z = t / (shift + scale mu)
+    tab[kTriTab * c + 0] = (T)(1.0 / (shift + scale * mu));
+    tab[kTriTab * c + 1] = tab[kTriTab * c + 2] = tab[kTriTab * c + 3] = (T)0;
+    return;
+  }
   const double e = (shift + scale * mu) / (scale * cA);
   const T rt = (T)(2.0 / (2.0 + e + sqrt(e * (e + 4.0))));
   const double r = (double)rt;
@@ -825,6 +831,7 @@ struct TriArgs {
   int n;                 // rows along axis 0
   int ncols;             // columns: product of the other axes
   int m;                 // rows per segment, ceil(n / kTriSeg)
+  int diag;              // 1D problem (n = 1, no stencil along axis 0): z = t * tab[0]
 };
 
 __device__ __forceinline__ float tri_exp2(float x) { return exp2f(x); }
@@ -851,6 +858,11 @@ __device__ __forceinline__ void body_tri_cols(const TriArgs<T>& a, int bx) {
   __shared__ T s_c[kTriSeg][kTriCols + 1];   // carries into each segment
   __shared__ T s_w0[kTriCols];
   if (a.st && a.st->done) return;
+  if (a.diag) {
+    const int dc = bx * kTriCols + (int)threadIdx.x;
+    if ((int)threadIdx.x < kTriCols && dc < a.ncols) a.v[dc] *= a.tab[kTriTab * dc];
+    return;
+  }
   const int c = threadIdx.x % kTriCols, s = threadIdx.x / kTriCols;
   const int col = bx * kTriCols + c;
   const bool act = col < a.ncols;

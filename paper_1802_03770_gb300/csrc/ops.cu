@@ -182,7 +182,8 @@ __global__ void k_sum(const double* part, int count, double* out) {
 // 0 < |m_i| <= n_i - 1, zero elsewhere (including the index L_i / 2);
 // expo = d + alpha.
 __global__ void k_fill_kernel(double2* buf, int d, int L0, int L1, int L2, int n0, int n1, int n2,
-                               double c, double Z, double a, double expo, long long total) {
+                               double c, double Z, double a, double expo, int dphys,
+                               long long total) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= total) return;
   const int Ls[3] = {L0, L1, L2};
@@ -204,7 +205,7 @@ __global__ void k_fill_kernel(double2* buf, int d, int L0, int L1, int L2, int n
   }
   double v = 0.0;
   if (inside) {
-    if (l1 == 0) v = c * (Z - 2.0 * d * a);
+    if (l1 == 0) v = c * (Z - 2.0 * dphys * a);
     else v = c * (-pow(r2, -0.5 * expo) + (l1 == 1 ? a : 0.0));
   }
   buf[i] = make_double2(v, 0.0);
@@ -418,6 +419,7 @@ PrecChain<T> build_precond(const Geo& g, const Tables<T>& tb, const PrecIO<T>& i
     TriArgs<T>& a = ch.tri;
     a.v = tb.t; a.st = io.st; a.tab = tb.tri_tab;
     a.inv_sc = 1.0 / (io.scale * g.cA);
+    a.diag = g.dphys == 1 ? 1 : 0;
     a.n = g.n[0];
     a.ncols = (int)(g.N / g.n[0]);
     a.m = (g.n[0] + kTriSeg - 1) / kTriSeg;
@@ -456,7 +458,7 @@ cudaError_t prepare_precond(const Geo& g, Tables<T>& tb, double shift, double sc
   FL_KERNEL((sizeof(T) == 4 ? "tri_table" "<f32>" : "tri_table" "<f64>"), s,
             k_tri_table<T><<<(ncols + 255) / 256, 256, 0, s>>>(
                 tb.tri_tab, tb.mu[g.d - 1], g.d == 3 ? tb.mu[1] : nullptr, ncols, g.n[g.d - 1],
-                shift, scale, g.cA, g.n[0], m));
+                shift, scale, g.cA, g.n[0], m, g.dphys == 1 ? 1 : 0));
   const cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) {
     tb.tri_shift = shift;
@@ -586,7 +588,7 @@ cudaError_t build_symbol(const Geo& g, double c, double Z, double a, double expo
   const int bt = 256;
   FL_KERNEL("fill_kernel", s,
             k_fill_kernel<<<(unsigned)((total + bt - 1) / bt), bt, 0, s>>>(buf, d, Ls[0], Ls[1], Ls[2], ns[0],
-                                                                 ns[1], ns[2], c, Z, a, expo, total));
+                                                                 ns[1], ns[2], c, Z, a, expo, g.dphys, total));
   // last axis: contiguous lines
   {
     const int L = g.L[d - 1];

@@ -344,10 +344,10 @@ fl_status extreme_quotients(fl_plan* p) {
 }
 
 // Eigenvalue of C h^d L = cA (2d I - S) on the lowest (hi = 0) or highest
-// sine mode: cA sum_i 4 sin^2(pi k_i / (2 (n_i + 1))).
+// sine mode: cA sum_i 4 sin^2(pi k_i / (2 (n_i + 1))) over the problem's axes.
 double fd_mode_eigenvalue(const Geo& g, int hi) {
   double lam = 0.0;
-  for (int i = 0; i < g.d; ++i) {
+  for (int i = g.d - g.dphys; i < g.d; ++i) {
     const double k = hi ? g.n[i] : 1.0;
     const double sn = std::sin(3.14159265358979323846 * k / (2.0 * (g.n[i] + 1.0)));
     lam += 4.0 * sn * sn;
@@ -373,7 +373,7 @@ fl_status precond_params(fl_plan* p, int prec_mode, double shift, double scale, 
     case FL_PRECOND_STENCIL:
       // shift I + scale M~: M~ has c (Z - 2d a) on the diagonal and c (a - 1)
       // on the stencil's neighbours, = c (Z - 2d) I + ((1 - a) / -a) cA (2d I - S)
-      pc->shift = shift + scale * p->c * (p->Z - 2.0 * p->g.d);
+      pc->shift = shift + scale * p->c * (p->Z - 2.0 * p->g.dphys);
       pc->scale = scale * (1.0 - p->a) / (-p->a);
       return FL_OK;
     case FL_PRECOND_SHIFTED: {
@@ -885,27 +885,31 @@ fl_status fl_plan_create(int d, const int64_t* n, double h, double alpha, const 
                          const fl_opts* opts, fl_plan** out) {
   if (!out) return fail(FL_INVALID_ARG, "out is NULL");
   *out = nullptr;
-  if (d < 2 || d > 3) return fail(FL_INVALID_ARG, "d must be 2 or 3");
+  if (d < 1 || d > 3) return fail(FL_INVALID_ARG, "d must be 1, 2 or 3");
   if (!n) return fail(FL_INVALID_ARG, "n is NULL");
   if (!(h > 0.0) || !std::isfinite(h)) return fail(FL_INVALID_ARG, "h must be > 0");
   if (!(alpha > 0.0 && alpha < 2.0)) return fail(FL_INVALID_ARG, "alpha must be in (0, 2)");
   fl_plan* p = new fl_plan();
   Geo& g = p->g;
   memset(&g, 0, sizeof(g));
-  g.d = d;
+  // a 1D problem is laid out as the single row of a 2D grid (1 x n)
+  g.dphys = d;
+  g.d = d == 1 ? 2 : d;
+  int64_t nl[3] = {1, 1, 1};
+  for (int i = 0; i < d; ++i) nl[g.d - d + i] = n[i];
   g.N = 1;
   g.lgmax = 0;
   for (int i = 0; i < 3; ++i) { g.n[i] = 1; g.L[i] = 1; g.lg[i] = 0; }
-  for (int i = 0; i < d; ++i) {
-    if (n[i] < 1 || n[i] > 1024) { delete p; return fail(FL_INVALID_ARG, "each n_i must be in [1, 1024]"); }
-    g.n[i] = (int)n[i];
+  for (int i = 0; i < g.d; ++i) {
+    if (nl[i] < 1 || nl[i] > 1024) { delete p; return fail(FL_INVALID_ARG, "each n_i must be in [1, 1024]"); }
+    g.n[i] = (int)nl[i];
     g.lg[i] = std::max(4, ilog2(2 * g.n[i] - 1));  // L_i >= 2 n_i - 1, at least 16
     g.L[i] = 1 << g.lg[i];
     g.lgmax = std::max(g.lgmax, g.lg[i]);
     g.N *= g.n[i];
   }
-  g.H = g.L[d - 1] / 2 + 1;
-  g.spec = (d == 2) ? (long long)g.n[0] * g.H : (long long)g.n[0] * g.L[1] * g.H;
+  g.H = g.L[g.d - 1] / 2 + 1;
+  g.spec = (g.d == 2) ? (long long)g.n[0] * g.H : (long long)g.n[0] * g.L[1] * g.H;
   p->h = h;
   p->alpha = alpha;
   p->rho = (opts && opts->rho > 0) ? opts->rho : 20.0;
@@ -937,7 +941,7 @@ fl_status fl_plan_create(int d, const int64_t* n, double h, double alpha, const 
   st = build_tables(p);
   if (st != FL_OK) { free_plan(p); return st; }
   long long half = 1;
-  for (int i = 0; i < d; ++i) half *= g.L[i] / 2 + 1;
+  for (int i = 0; i < g.d; ++i) half *= g.L[i] / 2 + 1;
   FL_TRY(dalloc(p, &p->t64.sig, half * sizeof(double)));
   FL_TRY(dalloc(p, &p->t32.sig, half * sizeof(float)));
   FL_TRY(build_symbol(g, p->c, p->Z, p->a, d + alpha, p->stream, p->t64.sig, p->t32.sig, p->t64.tw));
@@ -973,10 +977,10 @@ fl_status fl_plan_destroy(fl_plan* plan) {
 fl_status fl_plan_describe(const fl_plan* p, fl_plan_desc* desc) {
   if (!check_plan(p) || !desc) return fail(FL_INVALID_ARG, "NULL plan or desc");
   memset(desc, 0, sizeof(*desc));
-  desc->d = p->g.d;
-  for (int i = 0; i < p->g.d; ++i) {
-    desc->n[i] = p->g.n[i];
-    desc->fft_len[i] = p->g.L[i];
+  desc->d = p->g.dphys;
+  for (int i = 0; i < p->g.dphys; ++i) {
+    desc->n[i] = p->g.n[p->g.d - p->g.dphys + i];
+    desc->fft_len[i] = p->g.L[p->g.d - p->g.dphys + i];
   }
   desc->h = p->h;
   desc->alpha = p->alpha;
@@ -984,7 +988,7 @@ fl_status fl_plan_describe(const fl_plan* p, fl_plan_desc* desc) {
   desc->c_alpha_d = p->C;
   desc->lattice_zeta = p->Z;
   desc->window_corr = p->a;
-  desc->kernel0 = p->c * (p->Z - 2.0 * p->g.d * p->a);
+  desc->kernel0 = p->c * (p->Z - 2.0 * p->g.dphys * p->a);
   desc->workspace_bytes = p->bytes;
   return FL_OK;
 }
@@ -1635,7 +1639,8 @@ fl_status fl_solve_elliptic_batched(fl_plan* const* plans, int count, const doub
   if (!plans || !f_dev || !u_dev || count < 1) return fail(FL_INVALID_ARG, "NULL argument or count < 1");
   for (int i = 0; i < count; ++i) {
     if (!plans[i] || !f_dev[i] || !u_dev[i]) return fail(FL_INVALID_ARG, "NULL plan or array");
-    if (plans[i]->g.d != plans[0]->g.d) return fail(FL_INVALID_ARG, "all plans must have the same d");
+    if (plans[i]->g.dphys != plans[0]->g.dphys)
+      return fail(FL_INVALID_ARG, "all plans must have the same d");
     for (int j = 0; j < i; ++j)
       if (plans[j] == plans[i]) return fail(FL_INVALID_ARG, "a plan appears twice in the batch");
   }
@@ -1672,7 +1677,7 @@ fl_status fl_plan_attach_net(fl_plan* p, fl_net* net) {
     return FL_OK;
   }
   fl::NetState* ns = fl_net_state(net);
-  if (p->g.d != 2 || ns->H != p->g.n[0] || ns->W != p->g.n[1])
+  if (p->g.dphys != 2 || ns->H != p->g.n[0] || ns->W != p->g.n[1])
     return fail(FL_INVALID_ARG, "the network's H x W must equal the 2D plan's n_0 x n_1");
   if (!p->z0) {
     FL_CUDA(dalloc(p, &p->z0, p->g.N * sizeof(float)));

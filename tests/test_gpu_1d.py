@@ -1,0 +1,166 @@
+"""GPU parity of 1D plans (the interval examples of Sec. 4.1) against the
+oracle and the paper's 1D tables.
+
+Tolerances as in test_gpu_parity.py (FP64 apply / preconditioner 1e-10,
+FP32 2e-5); the paper's 1D errors (Tables tab:1D_con, tab:1D_erronly2) to
+the 5 % / 7 % the oracle's own pins use; the CG iteration counts of Table
+tab:1D_cg within one iteration (FP64 CG on the GPU, reductions in another
+order than the paper's)."""
+
+import math
+
+import numpy as np
+import pytest
+from scipy import special
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import precond as opc  # noqa: E402
+from oracle import solvers as osv  # noqa: E402
+from oracle.operator import Plan as OPlan  # noqa: E402
+from paper_1802_03770_gb300 import _lib  # noqa: E402
+from paper_1802_03770_gb300.api import Plan, solve_batched  # noqa: E402
+
+DEV = "cuda:0"
+F64 = _lib.FL_MODE_F64
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+def gpu(x, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(x), dtype=dtype, device=DEV)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def dyda(alpha, p):
+    """(-Delta)^{alpha/2} (1-x^2)_+^p = K 2F1(...) on (-1, 1), d = 1."""
+    return (2 ** alpha * math.gamma(p + 1) * math.gamma((1 + alpha) / 2)
+            / (math.gamma(p + 1 - alpha / 2) * math.gamma(0.5)))
+
+
+def interval(N, alpha):
+    h = 2.0 / (N + 1)
+    x = -1 + h * np.arange(1, N + 1)
+    return Plan(1, (N,), h, alpha), OPlan(1, N, h, alpha), x
+
+
+@pytest.mark.parametrize("N", [1, 2, 7, 100, 511, 1023, 1024])
+@pytest.mark.parametrize("alpha", [0.5, 1.5])
+def test_apply_1d_matches_oracle(N, alpha):
+    p, op, _ = interval(N, alpha)
+    u = np.random.default_rng(N).standard_normal(N)
+    ref = op.apply(u)
+    assert rel(host(p.apply(gpu(u))), ref) <= 1e-10
+    assert rel(host(p.apply(gpu(u, torch.float32))), ref) <= 2e-5
+    d = p.describe()
+    assert d["d"] == 1 and d["n"] == (N,)
+    assert d["kernel0"] == pytest.approx(op.entry(np.zeros((1, 1)))[0], rel=1e-12)
+
+
+@pytest.mark.parametrize("N", [1, 9, 511, 1023])
+@pytest.mark.parametrize("shift,scale", [(0.0, 1.0), (1.0, 2e-3)])
+def test_precond_1d_matches_oracle(N, shift, scale):
+    p, op, _ = interval(N, 1.3)
+    r = np.random.default_rng(3).standard_normal(N)
+    ref = opc.solve_box(op, r, shift, scale)
+    assert rel(host(p.precond(gpu(r), shift, scale)), ref) <= 1e-10
+    assert rel(host(p.precond(gpu(r, torch.float32), shift, scale)), ref) <= 2e-5
+
+
+def test_masked_1d_apply_and_solve():
+    N = 300
+    mask = np.ones(N, bool)
+    mask[120:170] = False
+    h = 2.0 / (N + 1)
+    op = OPlan(1, N, h, 1.2, mask=mask)
+    p = Plan(1, (N,), h, 1.2, mask=mask)
+    u = np.where(mask, np.random.default_rng(1).standard_normal(N), 0.0)
+    assert rel(host(p.apply(gpu(u))), op.apply(u)) <= 1e-10
+    f = np.where(mask, 1.0, 0.0)
+    x, info = p.solve(gpu(f), tol=1e-10, mode=_lib.FL_MODE_MIXED | _lib.FL_PRECOND_FD)
+    x = host(x)
+    assert info["converged"] == 1 and np.all(x[~mask] == 0.0)
+    assert rel(op.apply(x), f) <= 1.05e-10
+
+
+def test_table_1d_con_on_gpu(golden):
+    """e_app (FP64 apply) and e_sol (FP64 PCG to 1e-12) of the smooth
+    example against the paper's print."""
+    for N, alpha, e_app_paper, e_sol_paper in golden("table_1d_con.txt"):
+        N = int(N)
+        p, _, x = interval(N, alpha)
+        u = (1 - x ** 2) ** (2 + alpha / 2) / dyda(alpha, 2 + alpha / 2)
+        f = special.hyp2f1((1 + alpha) / 2, -2, 0.5, x ** 2)
+        e_app = rel(host(p.apply(gpu(u))), f)
+        # recursive residual to 1e-12; the FP64 apply's own rounding (~1e-16 times
+        # the largest symbol entry, up to ~1e5 here) may keep the true residual
+        # above that, so only the solution error is judged
+        us, _ = p.solve(gpu(f), tol=1e-12, mode=F64 | _lib.FL_PRECOND_FD, maxit=5000,
+                        raise_on_fail=False)
+        e_sol = rel(host(us), u)
+        assert e_app == pytest.approx(e_app_paper, rel=0.05), (N, alpha)
+        assert e_sol == pytest.approx(e_sol_paper, rel=0.07), (N, alpha)
+
+
+def test_table_1d_fone_on_gpu(golden):
+    for N, alpha, e_paper in golden("table_1d_fone.txt"):
+        N = int(N)
+        p, _, x = interval(N, alpha)
+        u = (1 - x ** 2) ** (alpha / 2) / dyda(alpha, alpha / 2)
+        us, _ = p.solve(gpu(np.ones(N)), tol=1e-12, mode=F64 | _lib.FL_PRECOND_FD, maxit=5000,
+                        raise_on_fail=False)
+        assert rel(host(us), u) == pytest.approx(e_paper, rel=0.05), (N, alpha)
+
+
+def test_table_1d_cg_on_gpu(golden):
+    """FP64 CG iteration counts with and without the FD preconditioner
+    (Table tab:1D_cg, the rows with N <= 1024)."""
+    for N, alpha, p6, c6, p9, c9 in golden("table_1d_cg.txt"):
+        N = int(N)
+        if N > 1024:
+            continue
+        p, _, x = interval(N, alpha)
+        f = gpu(special.hyp2f1((1 + alpha) / 2, -2, 0.5, x ** 2))
+        got = []
+        for tol in (1e-6, 1e-9):
+            for pm in (_lib.FL_PRECOND_FD, _lib.FL_PRECOND_NONE):
+                _, info = p.solve(f, tol=tol, mode=F64 | pm, maxit=1000, raise_on_fail=False)
+                got.append(info["iterations"])
+        want = [int(p6), int(c6), int(p9), int(c9)]
+        print(f"1D N = {N}, alpha = {alpha}: GPU {got}, paper {want}")
+        assert all(abs(g - w) <= 1 for g, w in zip(got, want)), (N, alpha, got, want)
+
+
+@pytest.mark.parametrize("theta", [1.0, 0.5])
+def test_time_step_1d(theta):
+    N, alpha = 255, 1.5
+    p, op, x = interval(N, alpha)
+    u0 = np.exp(-20 * x ** 2)
+    dt = 2.0 / (N + 1)
+    ref, _, ok, _ = osv.theta_step(op, u0, dt, theta, None, None, tol=1e-13)
+    assert ok
+    u, info = p.time_step(gpu(u0), dt, theta, tol=1e-11, mode=_lib.FL_MODE_MIXED)
+    assert info["converged"] == 1
+    assert rel(host(u), ref) <= 1e-9
+
+
+def test_batched_1d():
+    sizes, alphas = (255, 511, 1000), (0.7, 1.3, 1.8)
+    plans, fs, ops = [], [], []
+    for N, a in zip(sizes, alphas):
+        p, op, x = interval(N, a)
+        plans.append(p)
+        ops.append(op)
+        fs.append(np.cos(3 * x) * (1 - x ** 2))
+    us, infos = solve_batched(plans, [gpu(f) for f in fs], tol=1e-9,
+                              mode=_lib.FL_MODE_MIXED | _lib.FL_PRECOND_AUTO)
+    for u, f, op, info in zip(us, fs, ops, infos):
+        assert info["converged"] == 1
+        assert rel(op.apply(host(u)), f) <= 1.05e-9
