@@ -1025,16 +1025,13 @@ fl_status fl_plan_autotune(fl_plan* p, int tx_out[6]) {
   if (st == FL_OK) st = autotune_precision<double>(p);
   if (st != FL_OK) return st;
   if (tx_out) {
-    for (int i = 0; i < 3; ++i) {
-      tx_out[i] = i < p->g.d ? plan_tx<float>(p->t32, i, p->g.L[i]) : 0;
-      tx_out[3 + i] = i < p->g.d ? plan_tx<double>(p->t64, i, p->g.L[i]) : 0;
-    }
+    for (int i = 0; i < 6; ++i) tx_out[i] = 0;
     int axes[2];
     const int na = strided_axes(p->g, axes);
-    for (int i = 0; i < 3; ++i) {
-      bool strided = false;
-      for (int ia = 0; ia < na; ++ia) strided = strided || axes[ia] == i;
-      if (!strided) tx_out[i] = tx_out[3 + i] = 0;
+    for (int ia = 0; ia < na; ++ia) {
+      const int ax = axes[ia];
+      tx_out[ax] = plan_tx<float>(p->t32, ax, p->g.L[ax]);
+      tx_out[3 + ax] = plan_tx<double>(p->t64, ax, p->g.L[ax]);
     }
   }
   return FL_OK;
