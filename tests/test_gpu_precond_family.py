@@ -164,3 +164,19 @@ def test_time_step_with_balanced_shift():
     u, info = p.time_step(gpu(u0), dt, 1.0, tol=1e-10, mode=_lib.FL_MODE_MIXED | SHIFTED)
     assert info["converged"] == 1
     assert rel(host(u).reshape(u0.shape), u_ref) <= 1e-9
+
+
+def test_modes_alternate_on_one_plan():
+    """The captured CG graphs are keyed by the preconditioner: alternating
+    FD, balanced shift, stencil and plain CG on one plan gives the iteration
+    counts of fresh plans."""
+    n = 200
+    h = 1.0 / (n + 1)
+    f = gpu(inputs.gaussian_mixture(n, 2, 16, 5))
+    modes = [_lib.FL_PRECOND_FD, SHIFTED, STENCIL, _lib.FL_PRECOND_NONE, _lib.FL_PRECOND_FD, SHIFTED]
+    shared = Plan(2, (n, n), h, 1.2)
+    for pm in modes:
+        _, a = shared.solve(f, tol=1e-9, mode=_lib.FL_MODE_MIXED | pm, maxit=3000)
+        _, b = Plan(2, (n, n), h, 1.2).solve(f, tol=1e-9, mode=_lib.FL_MODE_MIXED | pm, maxit=3000)
+        assert a["converged"] == 1 and b["converged"] == 1
+        assert a["iterations"] == b["iterations"], pm
