@@ -53,6 +53,19 @@ def test_invalid_arguments_fail_before_the_device(lib):
     assert lib.fl_plan_create(2, bad, 0.1, 1.0, None, None, ctypes.byref(h)) == _lib.FL_INVALID_ARG
     assert lib.fl_apply(None, None, None) == _lib.FL_INVALID_ARG
     assert lib.fl_plan_destroy(None) == _lib.FL_OK
+    # d = 0 and the bounds of a 1D plan
+    assert lib.fl_plan_create(0, n, 0.1, 1.0, None, None, ctypes.byref(h)) == _lib.FL_INVALID_ARG
+    for v in (0, 1025):
+        one = (ctypes.c_int64 * 1)(v)
+        assert lib.fl_plan_create(1, one, 0.1, 1.0, None, None, ctypes.byref(h)) == _lib.FL_INVALID_ARG
+        assert "n_i must be" in _lib.last_error()
+    # the calls added for preconditioner parameters and column tiles
+    out = ctypes.c_double()
+    assert lib.fl_precond_params(None, 0, 0.0, 1.0, ctypes.byref(out), ctypes.byref(out)) \
+        == _lib.FL_INVALID_ARG
+    tiles = (ctypes.c_int * 6)()
+    assert lib.fl_plan_set_tiles(None, tiles) == _lib.FL_INVALID_ARG
+    assert lib.fl_plan_autotune(None, tiles) == _lib.FL_INVALID_ARG
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
