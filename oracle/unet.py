@@ -17,6 +17,16 @@ pool = 2 x 2 average, up = 2 x 2 nearest, [a, b] = channel concatenation.
 Parameters are a dict name -> (W, bias); conv weights W[cout, cin, 3, 3].
 
 Loss: mean over the batch and the pixels of (y - t)^2.
+
+BF16-operand variant (bf16_operands=True): the network as its tensor-core
+convolutions define it.  Every 3 x 3 convolution multiplies the bfloat16
+rounding (8 significant bits, round to nearest, ties to even) of its input
+-- pooling, upsampling and concatenation applied first -- with the bfloat16
+weights, and in the backward pass the product that forms the input gradient
+takes the bfloat16 rounding of the upstream gradient.  Products are then
+summed exactly (FP64 here); the weight gradients use the unrounded layer
+input and upstream gradient.  The 1 x 1 head is not rounded.
+
 Test infrastructure only.
 """
 
@@ -42,6 +52,15 @@ def init_params(seed, cin=3, c=(16, 32, 64), dtype=np.float64):
         params[name] = (rng.standard_normal((co, ci, k, k)).astype(dtype) * dtype(std),
                         np.zeros(co, dtype))
     return params
+
+
+def bf16_round(a):
+    """Round to the nearest value with an 8-bit significand (bfloat16),
+    ties to even; zeros stay zero.  a = m 2^e with 1/2 <= |m| < 1, so the
+    rounded value is rint(m 2^8) 2^(e-8)."""
+    a = np.asarray(a, dtype=np.float64)
+    m, e = np.frexp(a)
+    return np.ldexp(np.rint(np.ldexp(m, 8)), e - 8)
 
 
 def conv(x, w, b):
@@ -92,13 +111,16 @@ def up_backward(g):
     return g.reshape(C, H // 2, 2, W // 2, 2).sum(axis=(2, 4))
 
 
-def forward(params, x, keep=False):
+def forward(params, x, keep=False, bf16_operands=False):
     """y = N(x) for one sample x[cin, H, W]; with keep=True also the
-    activations needed by backward."""
+    activations needed by backward.  bf16_operands: the 3 x 3 convolutions
+    take the bfloat16 rounding of their input (see the module docstring)."""
     acts = {}
 
     def cr(name, inp):
-        z = conv(inp, *params[name])
+        w, b = params[name]
+        q = bf16_round(inp) if bf16_operands and w.shape[-1] == 3 else inp
+        z = conv(q, w, b)
         a = np.maximum(z, 0)
         acts[name] = (inp, z)
         return a
@@ -115,14 +137,19 @@ def forward(params, x, keep=False):
     return (y, acts) if keep else y
 
 
-def backward(params, acts, gy):
-    """Parameter gradients for upstream gradient gy[1, H, W]."""
+def backward(params, acts, gy, bf16_operands=False):
+    """Parameter gradients for upstream gradient gy[1, H, W].
+    bf16_operands: the input gradient of each 3 x 3 convolution is formed
+    from the bfloat16 rounding of its upstream gradient."""
     grads = {}
 
     def bk(name, g_out):
         inp, z = acts[name]
+        w = params[name][0]
         gz = g_out * (z > 0) if name != "head" else g_out
-        dx, dw, db = conv_backward(inp, params[name][0], gz)
+        dx, dw, db = conv_backward(inp, w, gz)
+        if bf16_operands and w.shape[-1] == 3:
+            dx, _, _ = conv_backward(inp, w, bf16_round(gz))
         grads[name] = (dw, db)
         return dx
 
@@ -140,17 +167,17 @@ def backward(params, acts, gy):
     return grads
 
 
-def loss_and_grads(params, xs, ts):
+def loss_and_grads(params, xs, ts, bf16_operands=False):
     """Mean squared error over a batch (xs[B, cin, H, W], ts[B, 1, H, W])
-    and its parameter gradients."""
+    and its parameter gradients (of the BF16-operand variant if asked)."""
     total = 0.0
     grads = None
     npix = ts[0].size
     for x, t in zip(xs, ts):
-        y, acts = forward(params, x, keep=True)
+        y, acts = forward(params, x, keep=True, bf16_operands=bf16_operands)
         r = y - t
         total += float(np.sum(r * r)) / npix
-        g = backward(params, acts, 2.0 * r / npix / len(xs))
+        g = backward(params, acts, 2.0 * r / npix / len(xs), bf16_operands=bf16_operands)
         if grads is None:
             grads = g
         else:
