@@ -252,14 +252,19 @@ int fl_profile_read(fl_plan* plan, fl_kernel_stat* stats, int max_stats);
  *     (16 MiB): n_0 * (L_1/2 + 1) <= 2^21 in 2D (1024 x 1024 fits),
  *     n_0 * L_1 * (L_2/2 + 1) <= 2^21 in 3D (64^3 fits).  Larger plans get
  *     FL_INVALID_ARG and nothing runs.
- *   - Every GPU that loads the library holds the 16 MiB array until the
- *     process exits.
- *   - The first call on a device looks the array's device address up (with
- *     that device current); make that first call before any stream capture.
+ *   - Set-up: fl_plan_create, with the plan's device current, loads the
+ *     library's code module on that device (where it was not loaded yet),
+ *     which places the 16 MiB array there, and looks up the array's device
+ *     address.  The array then stays on that device until the process
+ *     exits.  Create the plan before any stream capture.
+ *   - The plan's device must be current when this is called
+ *     (FL_INVALID_ARG otherwise).
  *   - All calls, on every plan and stream of a device, share the one array
  *     and it keeps the last call's contents: calls that overlap on the GPU
  *     race and give wrong results.  Nothing in it needs to start at zero.
- *   - Arguments, layout and errors are those of fl_apply_f32. */
+ *   - Arguments, layout and errors are otherwise those of fl_apply_f32; the
+ *     result equals fl_apply_f32's bit for bit (same kernels, same launch
+ *     shapes). */
 fl_status fl_apply_f32_static(fl_plan* plan, const float* u_dev, float* y_dev);
 
 /* Solve count independent problems M_i u_i = f_i (each eq. matelliptic with

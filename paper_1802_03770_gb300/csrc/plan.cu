@@ -104,6 +104,7 @@ struct GraphCache {
 
 struct fl_plan {
   Geo g;
+  int device = 0;          // CUDA device current at fl_plan_create
   double h, alpha, rho;
   double C, Z, a, c;
   double inner_tol;
@@ -879,6 +880,10 @@ const char* fl_last_error_string(void) { return g_err.c_str(); }
 
 void fl_set_error_string(const char* msg) { g_err = msg ? msg : ""; }
 
+namespace {
+fl_status static_spec_lookup(int dev);
+}  // namespace
+
 extern "C" {
 
 fl_status fl_plan_create(int d, const int64_t* n, double h, double alpha, const uint8_t* mask,
@@ -924,6 +929,13 @@ fl_status fl_plan_create(int d, const int64_t* n, double h, double alpha, const 
   fl_status st = FL_OK;
   cudaError_t e = configure_kernels();
   if (e != cudaSuccess) { free_plan(p); return cuda_fail(e, "configure_kernels"); }
+  e = cudaGetDevice(&p->device);
+  if (e != cudaSuccess) { free_plan(p); return cuda_fail(e, "cudaGetDevice"); }
+  // set-up of fl_apply_f32_static on this device: the module holding its
+  // scratch array is loaded and the array's address looked up now, not at
+  // the first call
+  st = static_spec_lookup(p->device);
+  if (st != FL_OK) { free_plan(p); return st; }
 #define FL_TRY(x)                                   \
   do {                                              \
     cudaError_t e__ = (x);                          \
@@ -1210,26 +1222,25 @@ int fl_profile_read(fl_plan* p, fl_kernel_stat* stats, int max_stats) {
 // --- allocation-free FP32 apply ----------------------------------------------
 // The half-spectrum workspace of fl_apply_f32_static.  In host code the name
 // g_static_spec is only a stand-in: the kernels get the device address that
-// cudaGetSymbolAddress returns for the current device.
+// cudaGetSymbolAddress returns with the plan's device current, looked up by
+// fl_plan_create (set-up time) and kept per device.
 namespace {
 constexpr long long kStaticSpecElems = 1LL << 21;  // complex floats, 16 MiB
+constexpr int kMaxDevices = 256;
 __device__ __align__(256) float2 g_static_spec[kStaticSpecElems];
 std::mutex g_static_mu;
-float2* g_static_addr[256] = {nullptr};
+float2* g_static_addr[kMaxDevices] = {nullptr};
 
-// Device address of g_static_spec on the current device, looked up once per
-// device.
-fl_status static_spec_address(float2** out) {
-  int dev = 0;
-  FL_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 256) return fail(FL_INVALID_ARG, "device ordinal out of range");
+// Looks up (once) the device address of g_static_spec on device `dev`,
+// which must be the current device.
+fl_status static_spec_lookup(int dev) {
+  if (dev < 0 || dev >= kMaxDevices) return fail(FL_INVALID_ARG, "device ordinal out of range");
   std::lock_guard<std::mutex> lock(g_static_mu);
   if (!g_static_addr[dev]) {
     void* ptr = nullptr;
     FL_CUDA(cudaGetSymbolAddress(&ptr, g_static_spec));
     g_static_addr[dev] = reinterpret_cast<float2*>(ptr);
   }
-  *out = g_static_addr[dev];
   return FL_OK;
 }
 }  // namespace
@@ -1242,9 +1253,16 @@ fl_status fl_apply_f32_static(fl_plan* p, const float* u, float* y) {
   if (u == y) return fail(FL_INVALID_ARG, "u and y may not alias");
   if (p->g.spec > kStaticSpecElems)
     return fail(FL_INVALID_ARG, "plan too large for the static scratch (2^21 complex floats)");
+  int dev = -1;
+  FL_CUDA(cudaGetDevice(&dev));
+  if (dev != p->device)
+    return fail(FL_INVALID_ARG, "fl_apply_f32_static: the plan's device must be current");
   float2* scratch = nullptr;
-  fl_status st = static_spec_address(&scratch);
-  if (st != FL_OK) return st;
+  {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    scratch = g_static_addr[p->device];
+  }
+  if (!scratch) return fail(FL_INVALID_ARG, "static scratch not set up for the plan's device");
   Tables<float> tb = p->t32;
   tb.S = scratch;
   ApplyIO<float> io;

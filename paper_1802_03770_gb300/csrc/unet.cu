@@ -299,6 +299,7 @@ __global__ void __launch_bounds__(TC_M) k_conv_tc(ConvArgs a, int tmem_cols) {
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
                          ((uint32_t)(TC_M >> 4) << 24);
   bool ok = true;
+  uint32_t fail_phase = 0;
   for (int ch = 0; ch < nchunks; ++ch) {
     const int k0 = ch * TC_KC;
     // A: im2col of the 8 x 16 pixel tile
@@ -341,16 +342,33 @@ __global__ void __launch_bounds__(TC_M) k_conv_tc(ConvArgs a, int tmem_cols) {
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                    :: "r"(mb) : "memory");
     }
-    // the MMAs read sa / sb: wait before the next chunk overwrites them
-    ok = mbar_wait(mb, (uint32_t)(ch & 1)) && ok;
+    // the MMAs read sa / sb: wait before the next chunk overwrites them.
+    // A wait that gives up (in any thread) ends the loop for the whole CTA:
+    // no more refills of sa / sb, no more MMAs.
+    const bool got = mbar_wait(mb, (uint32_t)(ch & 1));
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (__syncthreads_or(!got)) {
+      ok = false;
+      fail_phase = (uint32_t)(ch & 1);
+      break;
+    }
+  }
+  if (!ok) {
+    // one more bounded wait for the MMAs in flight before TMEM is released
+    if (tid == 0) {
+      mbar_wait(mb, fail_phase);
+      if (a.err) atomicExch(a.err, 1);
+    }
     __syncthreads();
   }
-  if (!ok && a.err) atomicExch(a.err, 1);
   // epilogue: lane p of TMEM holds pixel p
   const int p = warp * 32 + (tid & 31);
   const int y = y0 + (p >> 4), x = x0 + (p & 15);
   for (int c0 = 0; c0 < N; c0 += 16) {
+    if (!ok) {   // outputs of a tile whose MMAs did not complete are zeroed
+      for (int j = 0; j < 16; ++j) a.out[((size_t)(c0 + j) * a.H + y) * a.W + x] = 0.f;
+      continue;
+    }
     uint32_t v[16];
     const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
     asm volatile(
@@ -364,7 +382,7 @@ __global__ void __launch_bounds__(TC_M) k_conv_tc(ConvArgs a, int tmem_cols) {
       const int co = c0 + j;
       float z = __uint_as_float(v[j]) + (a.bias ? a.bias[co] : 0.f);
       if (a.relu) z = fmaxf(z, 0.f);
-      a.out[((size_t)co * a.H + y) * a.W + x] = ok ? z : 0.f;
+      a.out[((size_t)co * a.H + y) * a.W + x] = z;
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

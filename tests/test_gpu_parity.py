@@ -73,8 +73,12 @@ def test_apply_direct_sum_small(d, n):
     assert rel(y, op.apply_direct(u)) <= 1e-10
 
 
-@pytest.mark.parametrize("d,n", [(2, (64, 64)), (2, (37, 53)), (3, (33, 20, 31))])
+@pytest.mark.parametrize("d,n", [(2, (64, 64)), (2, (37, 53)), (3, (33, 20, 31)),
+                                 (2, (1024, 1024)), (2, (1000, 333)), (3, (128, 128, 128))])
 def test_apply_f32(d, n):
+    """FP32 apply against the oracle, including the launch shapes of the
+    full-size workloads (L = 2048: 128 x 16 row passes, 512 x 16 column
+    passes, radix-16 stage plans, zero-half first stages; 3D L = 256)."""
     h = 1.0 / (max(n) + 1)
     op = OPlan(d, n, h, 1.3)
     rng = np.random.default_rng(12)
@@ -316,6 +320,32 @@ def test_full_size_2d_1024_apply_and_mixed_solve():
     assert rel(op.apply(host(u)), f) <= 1.05e-8
 
 
+@pytest.mark.parametrize("alpha", [0.5, 1.0, 1.5])
+def test_full_size_2d_1024_mixed_solution_error(alpha):
+    """The 1024 x 1024 workload's mixed solves (FP32 inner CG + FP64
+    refinement to 1e-8, the bench's preconditioner choice) against a tight
+    FP64 oracle solve (1e-12): the FP64 residual recomputed by the oracle
+    and the solution's relative error, printed.  The error is bounded by
+    cond(M) times the residual; cond(M) ~ (n+1)^alpha here, at most ~3e4."""
+    n = 1024
+    h = 1.0 / (n + 1)
+    f = inputs.gaussian_mixture(n, 2, 32, 0)
+    op = OPlan(2, n, h, alpha)
+    p = Plan(2, (n, n), h, alpha)
+    u, info = p.solve(gpu(f), tol=1e-8, mode=_lib.FL_MODE_MIXED | _lib.FL_PRECOND_AUTO, maxit=2000)
+    u = host(u)
+    assert info["converged"] == 1
+    res = rel(op.apply(u), f)
+    u_ref, its, ok, _ = osv.solve_elliptic(op, f, 1e-12, 4000, alpha >= 1.0)
+    assert ok
+    err = rel(u, u_ref)
+    print(f"1024^2 alpha={alpha}: mixed {info['iterations']} inner its, {info['outer_iterations']} "
+          f"refinements, oracle residual {res:.3e}, error vs FP64 oracle {err:.3e} "
+          f"(oracle {its} its to 1e-12)")
+    assert res <= 1.05e-8
+    assert err <= 3e4 * 1.05e-8
+
+
 def _direct_samples(op, u, idx):
     """(M u)_i at sample points i by the plain definition (O(N) each)."""
     pts = op.points()
@@ -341,6 +371,12 @@ def test_full_size_3d_256_apply_samples():
     got = np.array([y[i] for i in idx])
     scale = np.abs(y).max()
     assert np.max(np.abs(got - ref)) <= 1e-10 * scale
+    # the FP32 apply at the same points, against the definition applied to
+    # the FP32-rounded input
+    y32 = host(p.apply(gpu(u, torch.float32))).astype(np.float64)
+    ref32 = _direct_samples(op, u.astype(np.float32).astype(np.float64), idx)
+    got32 = np.array([y32[i] for i in idx])
+    assert np.max(np.abs(got32 - ref32)) <= 2e-5 * scale
 
 
 def test_table_td_its_on_gpu(golden):

@@ -132,3 +132,81 @@ def test_tensor_core_forward_matches_cuda_core_forward():
         l1 = net.train_step(xs, ts, lr=1e-3)
     net.check()
     assert l1 < l0
+
+
+def test_gpu_adam_matches_oracle_adam_step():
+    """Two Adam steps of the GPU kernel against oracle.unet.adam_step, given
+    the same parameters and the gradients the GPU formed.  The GPU works in
+    FP32: per entry the bound is 1e-5 of the step plus two FP32 units of the
+    parameter (the rounding of w - lr u)."""
+    net, _ = setup_net(seed=14)
+    rng = np.random.default_rng(15)
+    state = {}
+    lr = 1e-3
+    for step in range(2):
+        xs = torch.tensor(rng.standard_normal((2, 3, 64, 64)), dtype=torch.float32, device="cuda:0")
+        ts = torch.tensor(rng.standard_normal((2, 1, 64, 64)), dtype=torch.float32, device="cuda:0")
+        p0 = net.get_params().astype(np.float64)
+        net.train_step(xs, ts, lr=lr)
+        p1, g = net.get_params(grads=True)
+        ref = flatten64(unet.adam_step(unflatten(p0), unflatten(g), state, lr=lr))
+        d_ref = p0 - ref
+        assert np.count_nonzero(d_ref) > 0.9 * d_ref.size
+        err = np.abs(p1.astype(np.float64) - ref)
+        bound = 1e-5 * np.abs(d_ref) + 2.0 ** -22 * np.abs(ref) + 1e-12
+        assert np.all(err <= bound), (step, float(np.max(err / bound)))
+
+
+def flatten64(params):
+    return np.concatenate([np.ravel(a) for name in unet.LAYERS for a in params[name]])
+
+
+@pytest.mark.parametrize("H", [64, 128])
+def test_tensor_core_forward_matches_bf16_oracle(H):
+    """tcgen05 forward (BF16 operands, FP32 accumulation in TMEM) against the
+    oracle's BF16-operand network summed in FP64.  Bound 2e-4 (relative
+    2-norm): FP32 accumulation error (~1e-6) plus the rare operand whose
+    FP32 and FP64 values round to different BF16 neighbours (each such
+    flip perturbs one operand by 2^-8 of its value; a few tens occur per
+    forward); a wrong tap, channel or tile costs O(1)."""
+    net, params = setup_net(H=H, seed=16, tensor_cores=True)
+    x = np.random.default_rng(17).standard_normal((3, H, H)).astype(np.float32)
+    y = net.forward(torch.tensor(x, device="cuda:0").view(-1)).cpu().numpy()
+    net.check()
+    ref = unet.forward(params, x.astype(np.float64), bf16_operands=True)[0].ravel()
+    exact = unet.forward(params, x.astype(np.float64))[0].ravel()
+    err = np.linalg.norm(y - ref) / np.linalg.norm(ref)
+    print(f"H={H}: tcgen05 vs BF16 oracle {err:.2e}, BF16 oracle vs exact network "
+          f"{np.linalg.norm(ref - exact) / np.linalg.norm(exact):.2e}")
+    assert err <= 2e-4
+
+
+def test_tensor_core_gradients_match_bf16_oracle():
+    """A training step's loss and per-layer gradients on the tcgen05 path
+    against the oracle's BF16-operand network (its input-gradient products
+    take the BF16 upstream gradient; the weight gradients use the FP32
+    values): loss to 1e-4, every layer's gradient to 1e-3 (relative
+    2-norm, the forward bound grown by the backward pass)."""
+    net, params = setup_net(seed=18, tensor_cores=True)
+    rng = np.random.default_rng(19)
+    xs = rng.standard_normal((2, 3, 64, 64)).astype(np.float32)
+    ts = rng.standard_normal((2, 1, 64, 64)).astype(np.float32)
+    loss = net.loss_grad(torch.tensor(xs, device="cuda:0"), torch.tensor(ts, device="cuda:0"))
+    net.check()
+    ref_loss, ref_grads = unet.loss_and_grads(params, xs.astype(np.float64), ts.astype(np.float64),
+                                              bf16_operands=True)
+    assert loss == pytest.approx(ref_loss, rel=1e-4)
+    _, g = net.get_params(grads=True)
+    gref = flatten(ref_grads)
+    shapes = unet.layer_shapes()
+    i = 0
+    worst = 0.0
+    for name in unet.LAYERS:
+        co, ci, k = shapes[name]
+        n = co * ci * k * k + co
+        a, b = g[i:i + n].astype(np.float64), gref[i:i + n].astype(np.float64)
+        e = np.linalg.norm(a - b) / (np.linalg.norm(b) + 1e-30)
+        worst = max(worst, e)
+        assert e <= 1e-3, (name, e)
+        i += n
+    print(f"tcgen05 gradients vs BF16 oracle: worst layer {worst:.2e}")

@@ -17,6 +17,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+from oracle.operator import Plan as OPlan  # noqa: E402
 from paper_1802_03770_gb300 import _lib  # noqa: E402
 from paper_1802_03770_gb300.api import Plan  # noqa: E402
 
@@ -32,15 +33,22 @@ def _apply(fn, plan, u):
 
 
 @pytest.mark.parametrize("d,n", [(2, (1024, 1024)), (2, (37, 53)), (3, (40, 50, 60))])
-def test_static_apply_matches_plan_apply_twice(d, n):
+def test_static_apply_matches_oracle_and_plan_apply_twice(d, n):
+    """Two calls in a row on the shared scratch: each within the FP32 apply
+    tolerance of the FP64 oracle (applied to the FP32-rounded input) and
+    bit for bit equal to fl_apply_f32 (the same kernels and launch shapes)."""
     lib = _lib.load()
-    plan = Plan(d, n, 1.0 / (max(n) + 1), 1.3)
+    h = 1.0 / (max(n) + 1)
+    plan = Plan(d, n, h, 1.3)
     rng = np.random.default_rng(20)
-    u = torch.tensor(rng.standard_normal(n), dtype=torch.float32, device="cuda:0")
-    ref = _apply(lib.fl_apply_f32, plan, u)
-    for _ in range(2):   # two calls in a row on the shared scratch
+    u64 = rng.standard_normal(n).astype(np.float32).astype(np.float64)
+    ref = OPlan(d, n, h, 1.3).apply(u64).ravel()
+    u = torch.tensor(u64.ravel(), dtype=torch.float32, device="cuda:0")
+    y_plan = _apply(lib.fl_apply_f32, plan, u)
+    for _ in range(2):
         y = _apply(lib.fl_apply_f32_static, plan, u)
         assert np.linalg.norm(y - ref) <= TOL * np.linalg.norm(ref)
+        assert np.array_equal(y, y_plan)
 
 
 def test_static_apply_rejects_plans_beyond_the_scratch():
