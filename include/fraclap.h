@@ -320,6 +320,17 @@ fl_status fl_net_train_step(fl_net* net, const float* xs_dev, const float* ts_de
 fl_status fl_net_save(fl_net* net, const char* path);
 fl_status fl_net_load(fl_net* net, const char* path);
 
+/* Copy one of the network's FP32 tensors, as the last call left it, to host
+ * (inspection; no counterpart in the paper).  kind 0: activations, kind 1:
+ * their loss gradients (of the last sample of the last fl_net_loss_grad /
+ * fl_net_train_step batch).  index 0 is the input features (3 channels),
+ * index l + 1 the output of layer l in the parameter-layout order (e0a ...
+ * head; index 11 = the network's output).  Layout [channel][y][x] at the
+ * tensor's level: H x W for e0a, e0b, d0a, d0b and the head, H/2 x W/2 for
+ * e1a, e1b, d1a, d1b, H/4 x W/4 for ba, bb.  count must equal the tensor's
+ * size (FL_INVALID_ARG otherwise).  Waits for the net's stream. */
+fl_status fl_net_get_tensor(fl_net* net, int kind, int index, float* host, long long count);
+
 /* Run the 3 x 3 convolutions on the tcgen05 tensor cores (enable = 1, the
  * default: BF16 activations and weights, FP32 accumulation in TMEM) or on
  * the CUDA cores (enable = 0: FP32 activations, BF16 weights). */

@@ -77,6 +77,21 @@ class Net:
         L.check(self._lib.fl_net_set_params(self._h, p.ctypes.data_as(ctypes.c_void_p)),
                 "fl_net_set_params")
 
+    # channels and level (resolution H >> level) of tensor index 0..11
+    TENSORS = ((3, 0), (16, 0), (16, 0), (32, 1), (32, 1), (64, 2), (64, 2), (32, 1), (32, 1),
+               (16, 0), (16, 0), (1, 0))
+
+    def get_tensor(self, index, grad=False):
+        """Activation (or its loss gradient) `index` of the last call, as a
+        float32 array [channels, H >> level, W >> level]."""
+        c, lev = self.TENSORS[index]
+        shape = (c, self.H >> lev, self.W >> lev)
+        out = np.empty(shape, np.float32)
+        L.check(self._lib.fl_net_get_tensor(self._h, int(bool(grad)), int(index),
+                                            out.ctypes.data_as(ctypes.c_void_p), out.size),
+                "fl_net_get_tensor")
+        return out
+
     def forward(self, x):
         import torch
         _check_tensor(x, torch.float32, 3 * self.H * self.W, "x")

@@ -523,6 +523,19 @@ fl_status fl_net_set_tensor_cores(fl_net* n, int enable) {
   return FL_OK;
 }
 
+fl_status fl_net_get_tensor(fl_net* n, int kind, int index, float* host, long long count) {
+  if (!n || !host) return net_fail(FL_INVALID_ARG, "NULL argument");
+  if ((kind != 0 && kind != 1) || index < 0 || index >= fl::kNetTensors)
+    return net_fail(FL_INVALID_ARG, "kind must be 0 or 1 and index in [0, 12)");
+  const long long size = (long long)n->channels(index) * (n->H >> n->level(index)) * (n->W >> n->level(index));
+  if (count != size) return net_fail(FL_INVALID_ARG, "count differs from the tensor's size");
+  const float* src = kind == 0 ? n->act[index] : n->grad[index];
+  fl_status s = net_cuda(cudaMemcpyAsync(host, src, size * sizeof(float), cudaMemcpyDeviceToHost, n->stream),
+                         "fl_net_get_tensor");
+  if (s == FL_OK) s = net_cuda(cudaStreamSynchronize(n->stream), "fl_net_get_tensor");
+  return s;
+}
+
 fl_status fl_net_check(fl_net* n) {
   if (!n) return net_fail(FL_INVALID_ARG, "NULL net");
   int flag = 0;

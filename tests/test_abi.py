@@ -66,6 +66,7 @@ def test_invalid_arguments_fail_before_the_device(lib):
     tiles = (ctypes.c_int * 6)()
     assert lib.fl_plan_set_tiles(None, tiles) == _lib.FL_INVALID_ARG
     assert lib.fl_plan_autotune(None, tiles) == _lib.FL_INVALID_ARG
+    assert lib.fl_net_get_tensor(None, 0, 0, None, 0) == _lib.FL_INVALID_ARG
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

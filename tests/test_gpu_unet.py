@@ -151,7 +151,7 @@ def test_gpu_adam_matches_oracle_adam_step():
         p1, g = net.get_params(grads=True)
         ref = flatten64(unet.adam_step(unflatten(p0), unflatten(g), state, lr=lr))
         d_ref = p0 - ref
-        assert np.count_nonzero(d_ref) > 0.9 * d_ref.size
+        assert np.count_nonzero(d_ref) > 0.5 * d_ref.size   # not vacuous (dead ReLUs have g = 0)
         err = np.abs(p1.astype(np.float64) - ref)
         bound = 1e-5 * np.abs(d_ref) + 2.0 ** -22 * np.abs(ref) + 1e-12
         assert np.all(err <= bound), (step, float(np.max(err / bound)))
@@ -161,32 +161,113 @@ def flatten64(params):
     return np.concatenate([np.ravel(a) for name in unet.LAYERS for a in params[name]])
 
 
+# Sources of each layer's input, as oracle.unet.forward assembles it:
+# (tensor index, routing); tensor index 0 = the input features, l + 1 = the
+# output of layer l (the numbering of Net.get_tensor).
+SOURCES = {"e0a": [(0, "direct")], "e0b": [(1, "direct")], "e1a": [(2, "pool")],
+           "e1b": [(3, "direct")], "ba": [(4, "pool")], "bb": [(5, "direct")],
+           "d1a": [(6, "up"), (4, "direct")], "d1b": [(7, "direct")],
+           "d0a": [(8, "up"), (2, "direct")], "d0b": [(9, "direct")], "head": [(10, "direct")]}
+ROUTE = {"direct": lambda x: x, "pool": unet.pool, "up": unet.up}
+ROUTE_BACK = {"direct": lambda g: g, "pool": unet.pool_backward, "up": unet.up_backward}
+
+
+def _layer_input(acts, name):
+    return np.concatenate([ROUTE[mode](acts[i]) for i, mode in SOURCES[name]])
+
+
 @pytest.mark.parametrize("H", [64, 128])
-def test_tensor_core_forward_matches_bf16_oracle(H):
-    """tcgen05 forward (BF16 operands, FP32 accumulation in TMEM) against the
-    oracle's BF16-operand network summed in FP64.  Bound 2e-4 (relative
-    2-norm): FP32 accumulation error (~1e-6) plus the rare operand whose
-    FP32 and FP64 values round to different BF16 neighbours (each such
-    flip perturbs one operand by 2^-8 of its value; a few tens occur per
-    forward); a wrong tap, channel or tile costs O(1)."""
+def test_tensor_core_forward_layers_match_bf16_oracle(H):
+    """Every layer of the tcgen05 forward against the oracle's BF16-operand
+    convolution of the GPU's own input activations (pooling, upsampling and
+    concatenation as the oracle assembles them, then BF16 rounding), summed
+    in FP64: relative 2-norm <= 1e-5 per layer (FP32 accumulation of at most
+    9 x 96 products, bias and ReLU; a wrong tap, channel, tile or rounding
+    costs >= 1e-3).  End to end the two differ more (rounding boundaries
+    crossed differently cascade through ten layers): bounded by 3e-3,
+    against ~8e-3 between the BF16-operand and the exact network."""
     net, params = setup_net(H=H, seed=16, tensor_cores=True)
     x = np.random.default_rng(17).standard_normal((3, H, H)).astype(np.float32)
     y = net.forward(torch.tensor(x, device="cuda:0").view(-1)).cpu().numpy()
     net.check()
-    ref = unet.forward(params, x.astype(np.float64), bf16_operands=True)[0].ravel()
+    acts = [net.get_tensor(i).astype(np.float64) for i in range(12)]
+    assert np.array_equal(acts[0], x)
+    worst = 0.0
+    for li, name in enumerate(unet.LAYERS):
+        w, b = params[name]
+        inp = _layer_input(acts, name)
+        q = unet.bf16_round(inp) if w.shape[-1] == 3 else inp
+        z = unet.conv(q, w, b)
+        ref = np.maximum(z, 0) if name != "head" else z
+        e = np.linalg.norm(acts[li + 1] - ref) / np.linalg.norm(ref)
+        worst = max(worst, e)
+        assert e <= 1e-5, (name, e)
+    ref_end = unet.forward(params, x.astype(np.float64), bf16_operands=True)[0].ravel()
     exact = unet.forward(params, x.astype(np.float64))[0].ravel()
-    err = np.linalg.norm(y - ref) / np.linalg.norm(ref)
-    print(f"H={H}: tcgen05 vs BF16 oracle {err:.2e}, BF16 oracle vs exact network "
-          f"{np.linalg.norm(ref - exact) / np.linalg.norm(exact):.2e}")
-    assert err <= 2e-4
+    err = np.linalg.norm(y - ref_end) / np.linalg.norm(ref_end)
+    print(f"H={H}: worst layer {worst:.2e}; end to end tcgen05 vs BF16 oracle {err:.2e}, BF16 "
+          f"oracle vs exact network {np.linalg.norm(ref_end - exact) / np.linalg.norm(exact):.2e}")
+    assert err <= 3e-3
 
 
-def test_tensor_core_gradients_match_bf16_oracle():
-    """A training step's loss and per-layer gradients on the tcgen05 path
-    against the oracle's BF16-operand network (its input-gradient products
-    take the BF16 upstream gradient; the weight gradients use the FP32
-    values): loss to 1e-4, every layer's gradient to 1e-3 (relative
-    2-norm, the forward bound grown by the backward pass)."""
+def test_tensor_core_backward_layers_match_bf16_oracle():
+    """One sample's backward pass on the tcgen05 path, layer by layer, from
+    the GPU's own activations and upstream gradients: the loss gradient of
+    the output, each layer's weight and bias gradients (FP32 on the CUDA
+    cores: relative 2-norm <= 1e-4) and the gradient each tensor receives
+    from its consumers (input-gradient products of BF16 upstream gradients
+    on the tensor cores, routed back through pooling, upsampling and
+    concatenation: <= 1e-5)."""
+    H = 64
+    net, params = setup_net(H=H, seed=18, tensor_cores=True)
+    rng = np.random.default_rng(19)
+    xs = rng.standard_normal((1, 3, H, H)).astype(np.float32)
+    ts = rng.standard_normal((1, 1, H, H)).astype(np.float32)
+    loss = net.loss_grad(torch.tensor(xs, device="cuda:0"), torch.tensor(ts, device="cuda:0"))
+    net.check()
+    acts = [net.get_tensor(i).astype(np.float64) for i in range(12)]
+    grads = [net.get_tensor(i, grad=True).astype(np.float64) for i in range(12)]
+    r = acts[11] - ts[0]
+    assert loss == pytest.approx(float(np.mean(r * r)), rel=1e-6)
+    assert np.linalg.norm(grads[11] - 2 * r / r.size) <= 1e-6 * np.linalg.norm(2 * r / r.size)
+    _, g = net.get_params(grads=True)
+    shapes = unet.layer_shapes()
+    expect = [np.zeros_like(a) for a in acts]
+    i = 0
+    worst_w, worst_x = 0.0, 0.0
+    for li, name in enumerate(unet.LAYERS):
+        w, _ = params[name]
+        co, ci, k = shapes[name]
+        nw = co * ci * k * k
+        o = li + 1
+        gz = grads[o] * (acts[o] > 0) if name != "head" else grads[o]
+        inp = _layer_input(acts, name)
+        dx, dw, db = unet.conv_backward(inp, w, gz)
+        ew = np.linalg.norm(g[i:i + nw] - dw.ravel()) / np.linalg.norm(dw)
+        eb = np.linalg.norm(g[i + nw:i + nw + co] - db) / np.linalg.norm(db)
+        worst_w = max(worst_w, ew, eb)
+        assert ew <= 1e-4 and eb <= 1e-4, (name, ew, eb)
+        i += nw + co
+        if k == 3:
+            dx, _, _ = unet.conv_backward(inp, w, unet.bf16_round(gz))
+        c0 = 0
+        for src, mode in SOURCES[name]:
+            nc = acts[src].shape[0]
+            expect[src] += ROUTE_BACK[mode](dx[c0:c0 + nc])
+            c0 += nc
+    for t in range(1, 11):
+        e = np.linalg.norm(grads[t] - expect[t]) / np.linalg.norm(expect[t])
+        worst_x = max(worst_x, e)
+        assert e <= 1e-5, (t, e)
+    print(f"tcgen05 backward vs BF16 oracle: weight gradients {worst_w:.2e}, "
+          f"activation gradients {worst_x:.2e}")
+
+
+def test_tensor_core_training_gradients_stay_near_the_bf16_oracle():
+    """End to end over a batch of two, the tcgen05 training gradients and
+    loss stay near the oracle's BF16-operand network (rounding boundaries
+    crossed differently cascade, as in the forward): loss to 1e-3, every
+    layer's gradient to 2e-2."""
     net, params = setup_net(seed=18, tensor_cores=True)
     rng = np.random.default_rng(19)
     xs = rng.standard_normal((2, 3, 64, 64)).astype(np.float32)
@@ -195,18 +276,14 @@ def test_tensor_core_gradients_match_bf16_oracle():
     net.check()
     ref_loss, ref_grads = unet.loss_and_grads(params, xs.astype(np.float64), ts.astype(np.float64),
                                               bf16_operands=True)
-    assert loss == pytest.approx(ref_loss, rel=1e-4)
+    assert loss == pytest.approx(ref_loss, rel=1e-3)
     _, g = net.get_params(grads=True)
     gref = flatten(ref_grads)
     shapes = unet.layer_shapes()
     i = 0
-    worst = 0.0
     for name in unet.LAYERS:
         co, ci, k = shapes[name]
         n = co * ci * k * k + co
         a, b = g[i:i + n].astype(np.float64), gref[i:i + n].astype(np.float64)
-        e = np.linalg.norm(a - b) / (np.linalg.norm(b) + 1e-30)
-        worst = max(worst, e)
-        assert e <= 1e-3, (name, e)
+        assert np.linalg.norm(a - b) <= 2e-2 * np.linalg.norm(b), name
         i += n
-    print(f"tcgen05 gradients vs BF16 oracle: worst layer {worst:.2e}")
