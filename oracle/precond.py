@@ -76,9 +76,8 @@ def solve_box(plan, r, shift=0.0, scale=1.0):
 
 
 def solve_embedded(plan, r, shift=0.0, scale=1.0):
-    """Preconditioner of an occluded domain Omega inside the box (not the
-    paper's choice, which is a sparse Cholesky factorisation of L on Omega,
-    Sec. 4.4): z = R (shift I + scale C h^d L_box)^{-1} R^T r with R the
+    """A cheaper preconditioner of an occluded domain Omega inside the box
+    (not the paper's choice, which is L on Omega itself, solve_domain): z = R (shift I + scale C h^d L_box)^{-1} R^T r with R the
     restriction to Omega, i.e. zero the residual outside Omega, solve on the
     box by DST-I, zero the result outside Omega.  R B^{-1} R^T is symmetric
     positive definite on the functions supported in Omega, so CG keeps its
@@ -86,6 +85,23 @@ def solve_embedded(plan, r, shift=0.0, scale=1.0):
     r = np.asarray(r, dtype=np.float64).reshape(plan.n)
     m = np.ones(plan.n, bool) if plan.mask is None else plan.mask
     return np.where(m, _dst_solve(plan, np.where(m, r, 0.0), shift, scale), 0.0)
+
+
+def solve_domain(plan, r, shift=0.0, scale=1.0):
+    """The paper's preconditioner on an occluded domain Omega (Sec. 4.4):
+    z = (shift I + scale C h^d L_Omega)^{-1} r with L_Omega the
+    finite-difference Laplacian on the points of Omega and Dirichlet
+    conditions on every point outside it (fd_matrix keeps only neighbours in
+    Omega).  The paper factorises it by sparse Cholesky; here a sparse direct
+    solve (scipy's SuperLU) is the library step.  z = 0 outside Omega; equal
+    to solve_box on the full box."""
+    import scipy.sparse.linalg as spla
+    r = np.asarray(r, dtype=np.float64).reshape(plan.n)
+    m = np.ones(plan.n, bool) if plan.mask is None else plan.mask
+    A = (scale * fd_matrix(plan) + shift * sps.identity(int(m.sum()))).tocsc()
+    z = np.zeros(plan.n)
+    z[m] = spla.spsolve(A, r[m])
+    return z
 
 
 # -- other members of the family (shift I + scale C h^d L) ---------------------

@@ -119,3 +119,58 @@ def test_shifted_preconditioners_against_the_paper_choice():
             assert its["balanced"] < 0.6 * its["L"] and its["balanced"] < 0.6 * its["plain"]
         else:
             assert its["stencil"] > its["L"] and its["balanced"] <= its["L"]
+
+
+# -- the paper's preconditioner on occluded domains (Sec. 4.4) -----------------
+
+def _l_shape(n):
+    m = n - 1
+    mask = np.ones((m, m), dtype=bool)
+    mask[m - n // 2:, m - n // 2:] = False
+    return mask
+
+
+def _octagon(n):
+    i = np.arange(1, n)
+    a = np.minimum(i, n - i)
+    return (a[:, None] + a[None, :]) > n // 4
+
+
+def test_solve_domain_is_the_box_solve_on_the_full_box():
+    p = Plan(2, (9, 12), 0.05, 1.3)
+    r = np.random.default_rng(40).standard_normal((9, 12))
+    for shift, scale in ((0.0, 1.0), (1.0, 0.3)):
+        assert np.allclose(pc.solve_domain(p, r, shift, scale), pc.solve_box(p, r, shift, scale),
+                           rtol=0, atol=1e-12 * np.abs(pc.solve_box(p, r, shift, scale)).max())
+
+
+def test_solve_domain_has_dirichlet_conditions_on_the_hole():
+    """z solves the shifted FD equation at every point of Omega with z = 0
+    at the hole's points (the 5-point stencil written out here)."""
+    n = 16
+    mask = _l_shape(n)
+    p = Plan(2, mask.shape, 1.0 / n, 1.6, mask=mask)
+    r = np.where(mask, np.random.default_rng(41).standard_normal(mask.shape), 0.0)
+    shift, scale = 0.7, 1.3
+    z = pc.solve_domain(p, r, shift, scale)
+    assert np.all(z[~mask] == 0.0)
+    g = p.C * p.h ** 2 * (p.A2 + p.A3) / p.h ** 2       # C h^d L = g (S - 4 I), g < 0
+    zp = np.pad(z, 1)
+    s = zp[:-2, 1:-1] + zp[2:, 1:-1] + zp[1:-1, :-2] + zp[1:-1, 2:]
+    lhs = shift * z + scale * g * (s - 4 * z)
+    assert np.allclose(lhs[mask], r[mask], rtol=0, atol=1e-10 * np.abs(r).max())
+
+
+@pytest.mark.parametrize("shape,paper", [("lshape", (10, 14)), ("octagon", (10, 14))])
+def test_occluded_iteration_counts_of_the_paper(shape, paper):
+    """Tables tab:L2 and tab:octagon2, first row (n = 128: N = 12033 and
+    14145), alpha = 1.75, f = 1 on Omega, CG with L_Omega: the printed
+    preconditioned counts at 1e-6 and 1e-9."""
+    n = 128
+    mask = _l_shape(n) if shape == "lshape" else _octagon(n)
+    assert int(mask.sum()) == (12033 if shape == "lshape" else 14145)
+    p = Plan(2, mask.shape, 1.0 / n, 1.75, mask=mask)
+    f = np.where(mask, 1.0, 0.0)
+    its = tuple(solvers.pcg(p.apply, f, lambda r: pc.solve_domain(p, r), None, tol, 1000)[1]
+                for tol in (1e-6, 1e-9))
+    assert its == paper
