@@ -301,6 +301,36 @@ def run_ours(args, rank, world, local):
     for info in infos_f64:
         assert info["converged"] == 1, info
 
+    # the same step as one batched call: the three problems advance in
+    # lockstep, one launch per pass over all of them (CG iterations replayed
+    # as a CUDA graph), same right-hand sides, same L2 flush
+    from paper_1802_03770_gb300.api import solve_batched
+
+    def timed_batched(nsteps_timed, nwarm):
+        for s in range(nwarm):
+            solve_batched(plans, [rhs[s][j].view(-1) for j in range(len(ALPHAS))], tol=TOL,
+                          mode=mode_mixed)
+        dist_barrier()
+        torch.cuda.synchronize()
+        total_ms, infos = 0.0, []
+        for s in range(nwarm, nwarm + nsteps_timed):
+            flush.fill_(float(s))
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, inf = solve_batched(plans, [rhs[s % nsteps][j].view(-1) for j in range(len(ALPHAS))],
+                                   tol=TOL, mode=mode_mixed)
+            e1.record()
+            torch.cuda.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            infos += inf
+        return total_ms / nsteps_timed, infos
+
+    ms_batched, infos_batched = timed_batched(steps, min(warm, 2))
+    for info in infos_batched:
+        assert info["converged"] == 1 and info["rel_residual"] <= TOL, info
+
     # the same mixed solves with the balanced-shift FD preconditioner (not
     # the paper's preconditioner; reported beside the headline, not in it)
     mode_shift = _lib.FL_MODE_MIXED | _lib.FL_PRECOND_SHIFTED
@@ -308,7 +338,8 @@ def run_ours(args, rank, world, local):
     for info in infos_shift:
         assert info["converged"] == 1 and info["rel_residual"] <= TOL, info
 
-    ms_mixed, ms_f64, ms_shift = max_over_ranks([ms_mixed, ms_f64, ms_shift], world, dev)
+    ms_mixed, ms_f64, ms_shift, ms_batched = max_over_ranks([ms_mixed, ms_f64, ms_shift, ms_batched],
+                                                            world, dev)
     solves_per_step = len(ALPHAS)
     value = job_rate(world, solves_per_step, ms_mixed / 1e3)
     value_f64 = job_rate(world, solves_per_step, ms_f64 / 1e3)
@@ -384,6 +415,10 @@ def run_ours(args, rank, world, local):
         "fp64_pcg": {"value": value_f64, "unit": UNIT, "ms_per_step": ms_f64,
                      "iterations": its_f64},
         "speedup_vs_fp64_pcg": value / value_f64,
+        "batched": {"value": job_rate(world, len(ALPHAS), ms_batched / 1e3), "unit": UNIT,
+                    "ms_per_step": ms_batched,
+                    "how": "the step's three solves in one fl_solve_elliptic_batched call (lockstep)",
+                    "iterations": [i["iterations"] for i in infos_batched[: len(ALPHAS)]]},
         "balanced_shift": {
             "value": value_shift, "unit": UNIT, "ms_per_step": ms_shift,
             "preconditioner": "(x I + C h^d L)^-1, x balancing the extreme sine modes (not in the paper)",
@@ -655,7 +690,7 @@ def main():
                 "clocks": res["clocks"], "e2e": res["e2e"], "gpu_launches": res["gpu_launches"],
                 "roofline": res["roofline"], "cpu_baseline": cpu,
                 "fp64_pcg": res["fp64_pcg"], "speedup_vs_fp64_pcg": res["speedup_vs_fp64_pcg"],
-                "balanced_shift": res["balanced_shift"],
+                "batched": res["batched"], "balanced_shift": res["balanced_shift"],
                 "iterations_mixed": res["iterations_mixed"], "refinements": res["refinements"],
                 "t_con_s": res["t_con_s"], "apply": res["apply"], "kernels": res["kernels"],
                 "tiles": res["tiles"], "learned": res["learned"],

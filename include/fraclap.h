@@ -55,15 +55,20 @@ enum {
   FL_MODE_MIXED = 1,      /* FP32 inner CG inside FP64 iterative refinement */
   FL_MODE_LEARNED = 2,    /* as MIXED, inner flexible CG with the learned
                              preconditioner of the attached network        */
-  FL_PRECOND_FD = 0x00,   /* FD-Laplacian preconditioner (Sec. 3.1, 3.2)   */
+  FL_PRECOND_FD = 0x00,   /* FD-Laplacian preconditioner (Sec. 3.1, 3.2);
+                             on an occluded domain the FD operator on
+                             Omega itself (Sec. 4.4), see fl_precond       */
   FL_PRECOND_NONE = 0x10, /* plain CG                                      */
   FL_PRECOND_AUTO = 0x20, /* FD preconditioner for alpha >= 1, none below
                              (Sec. 4.2: for alpha < 1 no preconditioning is
                              needed)                                       */
   FL_PRECOND_SHIFTED = 0x30, /* FD preconditioner with the balanced shift of
                                 fl_precond_params (not in the paper)       */
-  FL_PRECOND_STENCIL = 0x40  /* the (2d+1)-point stencil part of M itself,
+  FL_PRECOND_STENCIL = 0x40, /* the (2d+1)-point stencil part of M itself,
                                 the alternative remarked on in Sec. 3.1    */
+  FL_PRECOND_BOX = 0x50      /* occluded domains: the box FD solve restricted
+                                to Omega, R B^{-1} R^T (cheaper per
+                                application, not the paper's choice)       */
 };
 
 typedef struct fl_plan fl_plan;
@@ -86,7 +91,7 @@ typedef struct {
 typedef struct {
   int d;
   int64_t n[3];          /* interior points per axis                       */
-  int64_t fft_len[3];    /* padded FFT length L_i >= 2 n_i - 1 (power of 2) */
+  int64_t fft_len[3];    /* padded FFT length L_i >= 2 n_i - 1 (power of 2, <= 8192) */
   double h, alpha, rho;
   double c_alpha_d;      /* C_{alpha,d}                                    */
   double lattice_zeta;   /* Z_d = sum_{m != 0} |m|^{-(d+alpha)}, A_1 = h^{-(d+alpha)} Z_d */
@@ -100,7 +105,11 @@ typedef struct {
  *            is stored as the single row of a 2D layout, so in
  *            fl_plan_set_tiles / fl_plan_autotune its strided pass is the
  *            trivial axis 0)
- *   n      : host array of d extents n_i >= 1 (n_i <= 1024: padded FFT lengths up to 2048)
+ *   n      : host array of d extents n_i >= 1: n_i <= 4096 for d = 1, 2
+ *            (padded FFT lengths up to 8192), n_i <= 1024 for d = 3.  The FD
+ *            preconditioner solves along the first axis in columns of at
+ *            most 1024 values: with n_0 > 1024 (d = 2) only unpreconditioned
+ *            solves are available (FL_PRECOND_NONE)
  *   h      : grid spacing > 0 (the unit box has h = 1/(n+1))
  *   alpha  : order, 0 < alpha < 2
  *   mask   : nullable host array of N bytes, nonzero = point of Omega
@@ -148,13 +157,19 @@ fl_status fl_apply_f32(fl_plan* plan, const float* u_dev, float* y_dev);
 
 /* z = (shift I + scale C h^d L)^{-1} r on the full box (Sec. 3.1 with
  * shift = 0, scale = 1; Sec. 3.2 with shift = 1, scale = theta dt).
- * On a masked plan (occluded domain Omega) the box operator restricted to
- * Omega: z = R (shift I + scale C h^d L_box)^{-1} R^T r, r read and z
- * written only inside Omega (z = 0 outside).  This is not the paper's
- * preconditioner for occluded domains (a sparse Cholesky factorisation of
- * L on Omega, Sec. 4.4), but it is symmetric positive definite on Omega.
- * Requires shift >= 0 and scale > 0 (FL_INVALID_ARG otherwise).
- * r_dev, z_dev: N doubles, may not alias. */
+ * On a masked plan (occluded domain Omega) the paper's preconditioner of
+ * Sec. 4.4: z = (shift I + scale C h^d L_Omega)^{-1} r with L_Omega the FD
+ * Laplacian on the points of Omega and Dirichlet conditions on every point
+ * outside it; r is read and z written inside Omega only (z = 0 outside).
+ * The paper factorises it by sparse Cholesky; here it is applied exactly
+ * through two box solves and a dense system on Gamma, the points outside
+ * Omega with a grid neighbour in Omega (capacitance matrix method): the
+ * first call for a (shift, scale) forms and factorises that |Gamma| x
+ * |Gamma| matrix from |Gamma| FP64 box solves (plan set-up work, kept until
+ * another (shift, scale) is asked for); |Gamma| <= 2048, else
+ * FL_INVALID_ARG (FL_PRECOND_BOX solves do not need it).
+ * Requires shift >= 0 and scale > 0 and, for d >= 2, n_0 <= 1024
+ * (FL_INVALID_ARG otherwise).  r_dev, z_dev: N doubles, may not alias. */
 fl_status fl_precond(fl_plan* plan, double shift, double scale, const double* r_dev,
                      double* z_dev);
 fl_status fl_precond_f32(fl_plan* plan, double shift, double scale, const float* r_dev,
@@ -163,9 +178,11 @@ fl_status fl_precond_f32(fl_plan* plan, double shift, double scale, const float*
 /* The preconditioner a solve uses in `mode` for the operator
  * shift I + scale M (shift = 0, scale = 1: the elliptic problem; shift = 1,
  * scale = theta dt: a time step) is z = (pshift I + pscale C h^d L)^{-1} r on
- * the box (restricted to Omega on a masked plan), applied like fl_precond:
+ * the box (on Omega itself on a masked plan), applied like fl_precond:
  *   FL_PRECOND_FD (and AUTO with alpha >= 1): pshift = shift, pscale = scale
  *     (Sec. 3.1; Sec. 3.2 for time steps).
+ *   FL_PRECOND_BOX: as FD, but on a masked plan the box solve restricted to
+ *     Omega, z = R (pshift I + pscale C h^d L_box)^{-1} R^T r.
  *   FL_PRECOND_STENCIL: shift I + scale M~, M~ = M with the entries off the
  *     (2d+1)-point stencil set to zero (Sec. 3.1 remarks on it): in terms
  *     of c = C h^-alpha, the constant Z of M's diagonal and the stencil
@@ -193,8 +210,9 @@ fl_status fl_precond_params(fl_plan* plan, int mode, double shift, double scale,
  *   maxit : cap on CG iterations (per inner solve in FL_MODE_MIXED)
  *   info  : nullable, filled on return
  * Returns FL_OK, FL_NOT_CONVERGED (u holds the last iterate), FL_BREAKDOWN,
- * FL_INVALID_ARG.  On a masked plan the FD preconditioner is the restricted
- * box solve of fl_precond. */
+ * FL_INVALID_ARG.  On a masked plan the FD family (FD, AUTO, STENCIL,
+ * SHIFTED) is solved on Omega as fl_precond describes; FL_PRECOND_BOX takes
+ * the box solve restricted to Omega instead. */
 fl_status fl_solve_elliptic(fl_plan* plan, const double* f_dev, double* u_dev, int x0_nonzero,
                             double tol, int maxit, int mode, fl_solve_info* info);
 
@@ -278,6 +296,8 @@ fl_status fl_apply_f32_static(fl_plan* plan, const float* u_dev, float* y_dev);
  *   f_dev : host array of count device pointers (N_i doubles each)
  *   u_dev : host array of count device pointers, out: solutions (x0 = 0)
  *   infos : nullable host array of count entries
+ * Mixed batches need padded lengths <= 2048 (n_i <= 1024), and masked plans
+ * in them take FL_PRECOND_BOX or no preconditioner.
  * Returns FL_OK when every problem converged, FL_NOT_CONVERGED if one did
  * not (all solutions are written), FL_INVALID_ARG, FL_CUDA_ERROR. */
 fl_status fl_solve_elliptic_batched(fl_plan* const* plans, int count, const double* const* f_dev,

@@ -16,7 +16,11 @@ ROOT = os.path.dirname(HERE)
 OUT = os.path.join(HERE, "libfraclap.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SOURCES = ["ops.cu", "plan.cu", "batch.cu", "unet.cu", "learned.cu"]
+# (source, extra flags, object): ops.cu is compiled in two halves (FP32 and
+# FP64 instantiations) so that its largest part runs in parallel
+CUDA_SOURCES = [("ops.cu", ["-DFL_OPS_PART=1"], "ops_f32.o"), ("ops.cu", ["-DFL_OPS_PART=2"], "ops_f64.o"),
+                ("plan.cu", [], "plan.o"), ("batch.cu", [], "batch.o"), ("unet.cu", [], "unet.o"),
+                ("learned.cu", [], "learned.o"), ("domain.cu", [], "domain.o")]
 CXX_SOURCES = ["consts.cpp"]
 
 
@@ -42,10 +46,10 @@ def build(verbose=False, ptxas_info=False):
     inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
     jobs = []
     objs = []
-    for src in CUDA_SOURCES:
-        obj = os.path.join(BUILD, src + ".o")
+    for src, flags, oname in CUDA_SOURCES:
+        obj = os.path.join(BUILD, oname)
         cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-               "--expt-relaxed-constexpr", *inc, "-c", os.path.join(CSRC, src), "-o", obj]
+               "--expt-relaxed-constexpr", *flags, *inc, "-c", os.path.join(CSRC, src), "-o", obj]
         if ptxas_info:
             cmd += ["-Xptxas", "-v"]
         jobs.append(cmd)

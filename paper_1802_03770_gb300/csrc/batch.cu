@@ -30,10 +30,12 @@ __device__ __forceinline__ int batch_problem(const int* __restrict__ off, int np
   __global__ void __launch_bounds__(THREADS, min_ctas(THREADS))                               \
       kb_##NAME(const ARGS<T>* __restrict__ args, const int* __restrict__ off,                 \
                 const int* __restrict__ gx, int nprob) {                                       \
+    pdl_wait();                                                                                \
     const int i = batch_problem(off, nprob);                                                   \
     const ARGS<T> a = args[i];                                                                 \
     const int l = blockIdx.x - off[i];                                                         \
     body_##NAME<T, THREADS, VPT>(a, l % gx[i], l / gx[i]);                                     \
+    pdl_release();                                                                             \
   }
 
 FL_BATCHED_KERNEL(rows_fwd, RowsFwdArgs)
@@ -47,9 +49,11 @@ FL_BATCHED_KERNEL(dst_cols, DstColsArgs)
 template <typename T>
 __global__ void __launch_bounds__(kTriCols * kTriSeg)
     kb_tri_cols(const TriArgs<T>* __restrict__ args, const int* __restrict__ off, int nprob) {
+  pdl_wait();
   const int i = batch_problem(off, nprob);
   const TriArgs<T> a = args[i];
   body_tri_cols<T>(a, blockIdx.x - off[i]);
+  pdl_release();
 }
 
 // --- batched CG vector and scalar kernels -------------------------------------
@@ -60,6 +64,7 @@ template <typename T>
 __global__ void __launch_bounds__(kVecThreads) kb_cg_start(const BVecArgs<T>* __restrict__ args,
                                                           const int* __restrict__ off, int nprob) {
   __shared__ double red[32];
+  pdl_wait();
   const int i = batch_problem(off, nprob);
   const BVecArgs<T> a = args[i];
   const int bx = blockIdx.x - off[i];
@@ -80,15 +85,11 @@ __global__ void __launch_bounds__(kVecThreads) kb_cg_start(const BVecArgs<T>* __
 
 // CG update without preconditioner (z aliases r): x += alpha p, r -= alpha q
 // with alpha from the state (set by the apply's last CTA), partials of
-// ||r||^2; the last CTA of the problem takes the CG scalar step.
+// ||r||^2; the last CTA of the problem takes the CG scalar step.  bx of gx
+// CTAs of the problem.
 template <typename T>
-__global__ void __launch_bounds__(kVecThreads) kb_noprec_update(const BVecArgs<T>* __restrict__ args,
-                                                               const int* __restrict__ off, int nprob) {
+__device__ __forceinline__ void body_b_noprec(const BVecArgs<T>& a, int bx, int gx) {
   __shared__ double red[32];
-  const int i = batch_problem(off, nprob);
-  const BVecArgs<T> a = args[i];
-  const int bx = blockIdx.x - off[i];
-  const int gx = off[i + 1] - off[i];
   if (a.st->done) return;
   const T al = (T)a.st->alpha;
   DotAcc<T> rr;
@@ -105,6 +106,14 @@ __global__ void __launch_bounds__(kVecThreads) kb_noprec_update(const BVecArgs<T
     const double rrv = cta_sum_partials(a.part, gx, red);
     if (threadIdx.x == 0) pcg_step(a.st, rrv, rrv);
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) kb_noprec_update(const BVecArgs<T>* __restrict__ args,
+                                                               const int* __restrict__ off, int nprob) {
+  pdl_wait();
+  const int i = batch_problem(off, nprob);
+  body_b_noprec<T>(args[i], blockIdx.x - off[i], off[i + 1] - off[i]);
 }
 
 // FP64 right-hand side to the FP32 inner right-hand side (masked), with
@@ -173,48 +182,50 @@ cudaError_t launch_batched(const BatchPass& bp, cudaStream_t s) {
   switch (bp.kind) {
     case BK_ROWS_FWD:
       FL_KERNEL(sizeof(T) == 4 ? "b_rows_fwd<f32>" : "b_rows_fwd<f64>", s,
-                kb_rows_fwd<T, K::RT, K::RV><<<bp.blocks, K::RT, bp.smem, s>>>(
-                    (const RowsFwdArgs<T>*)bp.args, bp.off, bp.gx, bp.nprob));
+                pdl_launch(kb_rows_fwd<T, K::RT, K::RV>, bp.blocks, K::RT, bp.smem, s,
+                           (const RowsFwdArgs<T>*)bp.args, bp.off, bp.gx, bp.nprob));
       break;
     case BK_COLS:
       FL_KERNEL(sizeof(T) == 4 ? "b_cols<f32>" : "b_cols<f64>", s,
-                kb_cols<T, K::CT, K::CV><<<bp.blocks, K::CT, bp.smem, s>>>(
-                    (const ColsArgs<T>*)bp.args, bp.off, bp.gx, bp.nprob));
+                pdl_launch(kb_cols<T, K::CT, K::CV>, bp.blocks, K::CT, bp.smem, s,
+                           (const ColsArgs<T>*)bp.args, bp.off, bp.gx, bp.nprob));
       break;
     case BK_ROWS_INV:
       FL_KERNEL(sizeof(T) == 4 ? "b_rows_inv<f32>" : "b_rows_inv<f64>", s,
-                kb_rows_inv<T, K::RT, K::RV><<<bp.blocks, K::RT, bp.smem, s>>>(
-                    (const RowsInvArgs<T>*)bp.args, bp.off, bp.gx, bp.nprob));
+                pdl_launch(kb_rows_inv<T, K::RT, K::RV>, bp.blocks, K::RT, bp.smem, s,
+                           (const RowsInvArgs<T>*)bp.args, bp.off, bp.gx, bp.nprob));
       break;
     case BK_DST_ROWS:
       FL_KERNEL(sizeof(T) == 4 ? "b_dst_rows<f32>" : "b_dst_rows<f64>", s,
-                kb_dst_rows<T, K::RT, K::RV><<<bp.blocks, K::RT, bp.smem, s>>>(
-                    (const DstRowsArgs<T>*)bp.args, bp.off, bp.gx, bp.nprob));
+                pdl_launch(kb_dst_rows<T, K::RT, K::RV>, bp.blocks, K::RT, bp.smem, s,
+                           (const DstRowsArgs<T>*)bp.args, bp.off, bp.gx, bp.nprob));
       break;
     case BK_DST_COLS:
       FL_KERNEL(sizeof(T) == 4 ? "b_dst_cols<f32>" : "b_dst_cols<f64>", s,
-                kb_dst_cols<T, K::CT, K::CV><<<bp.blocks, K::CT, bp.smem, s>>>(
-                    (const DstColsArgs<T>*)bp.args, bp.off, bp.gx, bp.nprob));
+                pdl_launch(kb_dst_cols<T, K::CT, K::CV>, bp.blocks, K::CT, bp.smem, s,
+                           (const DstColsArgs<T>*)bp.args, bp.off, bp.gx, bp.nprob));
       break;
     case BK_TRI_COLS:
       FL_KERNEL(sizeof(T) == 4 ? "b_tri_cols<f32>" : "b_tri_cols<f64>", s,
-                kb_tri_cols<T><<<bp.blocks, kTriCols * kTriSeg, 0, s>>>(
-                    (const TriArgs<T>*)bp.args, bp.off, bp.nprob));
+                pdl_launch(kb_tri_cols<T>, bp.blocks, kTriCols * kTriSeg, 0, s,
+                           (const TriArgs<T>*)bp.args, bp.off, bp.nprob));
       break;
     case BK_CG_START:
       FL_KERNEL(sizeof(T) == 4 ? "b_cg_start<f32>" : "b_cg_start<f64>", s,
-                kb_cg_start<T><<<bp.blocks, kVecThreads, 0, s>>>((const BVecArgs<T>*)bp.args,
-                                                                  bp.off, bp.nprob));
+                pdl_launch(kb_cg_start<T>, bp.blocks, kVecThreads, 0, s,
+                           (const BVecArgs<T>*)bp.args, bp.off,
+                           bp.nprob));
       break;
     case BK_NOPREC:
       FL_KERNEL(sizeof(T) == 4 ? "b_noprec_update<f32>" : "b_noprec_update<f64>", s,
-                kb_noprec_update<T><<<bp.blocks, kVecThreads, 0, s>>>((const BVecArgs<T>*)bp.args,
-                                                                       bp.off, bp.nprob));
+                pdl_launch(kb_noprec_update<T>, bp.blocks, kVecThreads, 0, s,
+                           (const BVecArgs<T>*)bp.args, bp.off,
+                           bp.nprob));
       break;
     default:
       return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
+  return launch_status();
 }
 
 cudaError_t launch_cast_rhs(const BatchPass& bp, float* const* out32, cudaStream_t s) {

@@ -3,11 +3,44 @@
 #pragma once
 
 #include <algorithm>
+#include <cstdlib>
+#include <utility>
 
 #include "internal.h"
 #include "kernels.cuh"
 
 namespace fl {
+
+// Launches the pass kernel k with the programmatic stream-serialization
+// attribute (see pdl_wait_then_release), unless FRACLAP_PDL=0 is set in the
+// environment.  A launch error is kept and returned by take_launch_error().
+bool pdl_enabled();
+void note_launch_error(cudaError_t e);
+cudaError_t take_launch_error();
+
+template <typename... KArgs, typename... Args>
+inline void pdl_launch(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  note_launch_error(cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...));
+}
+
+// The first error of this thread's launches since the last call, and of
+// the runtime's own last-error slot.
+inline cudaError_t launch_status() {
+  const cudaError_t e = cudaGetLastError();
+  const cudaError_t p = take_launch_error();
+  return e != cudaSuccess ? e : p;
+}
 
 // Launch shapes.  A CTA keeps VPT * THREADS complex values in shared memory:
 // row passes one or two lines of L = 2048 (many small CTAs, up to eight per
@@ -28,10 +61,21 @@ constexpr int kVecBlocks = 608;   // 4 x 152 SMs, fixed for deterministic partia
 constexpr int kVecThreads = 256;
 constexpr int kMaxTx = 64;
 constexpr int kSmemLimit = 200 * 1024;
+constexpr int kMaxLen = 8192;     // longest padded FFT line
 
-template <typename T> inline int row_lines(int L) { return (Cfg<T>::RT * Cfg<T>::RV) / L; }
+// Threads of a row (column) pass on lines of length L: the Cfg shape while a
+// CTA of that shape holds at least one line (tile), else one line of L
+// values per CTA (FP32 rows: 4096 on 256 and 8192 on 512 threads; FP64 rows
+// and columns: 8192 on 512 threads).
+template <typename T> inline int row_threads(int L) {
+  return L <= Cfg<T>::RT * Cfg<T>::RV ? Cfg<T>::RT : L / Cfg<T>::RV;
+}
+template <typename T> inline int col_threads(int L) {
+  return L <= Cfg<T>::CT * Cfg<T>::CV ? Cfg<T>::CT : L / Cfg<T>::CV;
+}
+template <typename T> inline int row_lines(int L) { return (row_threads<T>(L) * Cfg<T>::RV) / L; }
 template <typename T> inline int col_tx(int L) {
-  return std::min(kMaxTx, (Cfg<T>::CT * Cfg<T>::CV) / L);
+  return std::min(kMaxTx, (col_threads<T>(L) * Cfg<T>::CV) / L);
 }
 // the narrowest tile the tuner tries: 16 contiguous bytes per line element
 template <typename T> inline int min_tx() {
@@ -137,6 +181,7 @@ struct BatchPass {
 
 template <typename T>
 cudaError_t launch_batched(const BatchPass& bp, cudaStream_t s);
+
 cudaError_t launch_cast_rhs(const BatchPass& bp, float* const* out32, cudaStream_t s);
 // which: 0 = CG start-up scalars, 2 = sums into out
 cudaError_t launch_batched_scalar(int which, const BScalarArgs* args, double* out, int nprob,

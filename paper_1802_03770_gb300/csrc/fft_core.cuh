@@ -367,28 +367,40 @@ __device__ __forceinline__ void fft_io_ct(SBuf<C> buf, int ls, int ltx, int nlin
   }
 }
 
-// Runtime length: dispatch to the compile-time plan (2^4 .. 2^11).  HALF:
-// the upper half of every input line is zero (a zero-padded line); the
-// loader is then not called for it.
-template <int VPT, bool IL, bool HALF = false, typename C, typename Load, typename Epi>
+// Runtime length: dispatch to the compile-time plan of the lengths
+// 2^LGLO .. 2^LGHI a kernel instantiation can hold (at most 2^4 .. 2^13);
+// other lengths are never passed by the launchers.  HALF: the upper half of
+// every input line is zero (a zero-padded line); the loader is then not
+// called for it.
+#define FL_FFT_LEN(LGV)                                                                     \
+  if constexpr (LGV >= LGLO && LGV <= LGHI) {                                               \
+    if (lg == LGV) {                                                                        \
+      fft_io_ct<LGV, VPT, IL, HALF>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, \
+                                    sync_epi);                                              \
+      return;                                                                               \
+    }                                                                                       \
+  }
+template <int VPT, bool IL, bool HALF = false, int LGHI = 11, int LGLO = 4, typename C, typename Load,
+          typename Epi>
 __device__ __forceinline__ void fft_io(SBuf<C> buf, int lg, int ls, int ltx, int nlines,
                                        const C* __restrict__ tw, int lgmax, bool inv, Load load,
                                        bool sync_load, Epi epi, bool sync_epi) {
-  switch (lg) {
-    case 11: fft_io_ct<11, VPT, IL, HALF>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
-    case 10: fft_io_ct<10, VPT, IL, HALF>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
-    case 9: fft_io_ct<9, VPT, IL, HALF>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
-    case 8: fft_io_ct<8, VPT, IL, HALF>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
-    case 7: fft_io_ct<7, VPT, IL, HALF>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
-    case 6: fft_io_ct<6, VPT, IL, HALF>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
-    case 5: fft_io_ct<5, VPT, IL, HALF>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
-    default: fft_io_ct<4, VPT, IL, HALF>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, sync_epi); break;
-  }
+  FL_FFT_LEN(13)
+  FL_FFT_LEN(12)
+  FL_FFT_LEN(11)
+  FL_FFT_LEN(10)
+  FL_FFT_LEN(9)
+  FL_FFT_LEN(8)
+  FL_FFT_LEN(7)
+  FL_FFT_LEN(6)
+  FL_FFT_LEN(5)
+  FL_FFT_LEN(4)
 }
+#undef FL_FFT_LEN
 
 // In-place transform of lines in shared memory (natural order in and out)
 // with the compile-time stage plan; ends with a barrier.
-template <int VPT, bool IL, typename C>
+template <int VPT, bool IL, int LGHI = 11, int LGLO = 4, typename C>
 __device__ __forceinline__ void fft_smem(SBuf<C> buf, int lg, int ls, int ltx, int nlines,
                                          const C* __restrict__ tw, int lgmax, bool inv) {
   auto ld = [=](int q, int k) -> C { return IL ? buf[(k << ltx) + q] : buf[q * ls + k]; };
@@ -396,7 +408,7 @@ __device__ __forceinline__ void fft_smem(SBuf<C> buf, int lg, int ls, int ltx, i
     if (IL) buf[(k << ltx) + q] = v;
     else buf[q * ls + k] = v;
   };
-  fft_io<VPT, IL>(buf, lg, ls, ltx, nlines, tw, lgmax, inv, ld, true, st, true);
+  fft_io<VPT, IL, false, LGHI, LGLO>(buf, lg, ls, ltx, nlines, tw, lgmax, inv, ld, true, st, true);
   __syncthreads();
 }
 

@@ -85,6 +85,9 @@ struct PrecIO {
   PcgState* st = nullptr;
   int fin = 0;                // FIN_STEP: the last pass ends with the CG scalar step
   const uint8_t* mask = nullptr;  // occluded domain: restrict input and output to Omega
+  bool input_unmasked = false;    // keep the input outside Omega (mask applies to the output only)
+  bool keep_outside = false;      // keep the output outside Omega (mask applies to the input only)
+  const T* add = nullptr;         // nullable: out = mask ? (B^{-1} in + add) : 0
 };
 
 // --- ops.cu: launchers (return the first CUDA error) --------------------------

@@ -32,6 +32,19 @@
 
 namespace fl {
 
+// Programmatic dependent launch: a pass launched with the programmatic
+// stream-serialization attribute may be scheduled while the previous pass
+// is finishing; pdl_wait blocks, before anything the previous passes wrote
+// is touched, until that pass has completed and its writes are visible.
+// pdl_release, called by each CTA once its work is done, lets the next pass
+// launch when every CTA of this one has released (releasing at entry placed
+// the next pass's waiting CTAs unevenly and measured 6 % slower).  Both are
+// no-ops for an ordinary launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Device-resident state of one CG solve (all reductions in FP64).
 struct PcgState {
   double rz;       // r^T z of the current iterate
@@ -93,7 +106,12 @@ __device__ __forceinline__ double cta_sum_partials(const double* __restrict__ pa
 // THREADS threads.  The passes are latency-bound: the 128-thread FP32 row
 // passes keep at least 7 CTAs (28 warps) per SM (<= 73 registers), the
 // 256- and 512-thread passes at least 2 CTAs.
-constexpr int min_ctas(int threads) { return threads <= 128 ? FL_ROW_MIN_CTAS : 2; }
+// The wide instantiations for the longest lines (LGLO > 4: one line of 4096
+// or 8192 points per CTA) ask for one CTA only, so that the compiler keeps
+// the row bodies' registers.
+constexpr int min_ctas(int threads, int lglo = 4) {
+  return lglo > 4 ? 1 : (threads <= 128 ? FL_ROW_MIN_CTAS : 2);
+}
 
 // CTA-wide sum of one value per thread; result valid in thread 0.
 __device__ __forceinline__ double cta_sum(double v, double* red) {
@@ -236,7 +254,7 @@ struct RowsFwdArgs {
   int pre;
 };
 
-template <typename T, int THREADS, int VPT>
+template <typename T, int THREADS, int VPT, int LGLO = 4, int LGHI = clog2(THREADS * VPT)>
 __device__ __forceinline__ void body_rows_fwd(const RowsFwdArgs<T>& a, int bx, int by) {
   typedef typename Cplx<T>::type C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -309,7 +327,8 @@ __device__ __forceinline__ void body_rows_fwd(const RowsFwdArgs<T>& a, int bx, i
   {
     auto ld = [=](int q, int k) -> C { return k < hL ? buf[q * ls + k] : cmake<C>((T)0, (T)0); };
     auto st = [=](int q, int k, C v) { buf[q * ls + k] = v; };
-    fft_io<VPT, false, true>(buf, a.lg, ls, 0, nl, a.tw, a.lgmax, false, ld, true, st, true);
+    fft_io<VPT, false, true, LGHI, LGLO>(buf, a.lg, ls, 0, nl, a.tw, a.lgmax, false, ld,
+                                                       true, st, true);
   }
   __syncthreads();
   for (int q = 0; q < nl; ++q) {
@@ -330,9 +349,11 @@ __device__ __forceinline__ void body_rows_fwd(const RowsFwdArgs<T>& a, int bx, i
   }
 }
 
-template <typename T, int THREADS, int VPT>
-__global__ void __launch_bounds__(THREADS, min_ctas(THREADS)) k_rows_fwd(RowsFwdArgs<T> a) {
-  body_rows_fwd<T, THREADS, VPT>(a, blockIdx.x, blockIdx.y);
+template <typename T, int THREADS, int VPT, int LGLO = 4>
+__global__ void __launch_bounds__(THREADS, min_ctas(THREADS, LGLO)) k_rows_fwd(RowsFwdArgs<T> a) {
+  pdl_wait();
+  body_rows_fwd<T, THREADS, VPT, LGLO>(a, blockIdx.x, blockIdx.y);
+  pdl_release();
 }
 
 // ---------------------------------------------------------------------------
@@ -359,7 +380,7 @@ struct ColsArgs {
 // The tile is kept in its natural layout, buf[r * TX + c] (row r of the line,
 // column c), and transformed with the interleaved-line FFT; global loads are
 // issued U at a time so that several are in flight per thread.
-template <typename T, int THREADS, int VPT>
+template <typename T, int THREADS, int VPT, int LGLO = 4, int LGHI = clog2(THREADS * VPT)>
 __device__ __forceinline__ void body_cols(const ColsArgs<T>& a, int bx, int by) {
   typedef typename Cplx<T>::type C;
   constexpr int U = 8;
@@ -403,7 +424,8 @@ __device__ __forceinline__ void body_cols(const ColsArgs<T>& a, int bx, int by) 
       if (c < ncol) v = cscale(v, sig[(size_t)min(k, L - k) * sig_line + c]);
       buf[(k << ltx) + c] = v;
     };
-    fft_io<VPT, true, true>(buf, a.lg, 0, ltx, TX, a.tw, a.lgmax, false, ld, true, epi, true);
+    fft_io<VPT, true, true, LGHI, LGLO>(buf, a.lg, 0, ltx, TX, a.tw, a.lgmax, false, ld,
+                                                      true, epi, true);
     __syncthreads();
     // inverse FFT whose last stage writes the kept rows to global
     const int rows_out = a.rows_out;
@@ -412,10 +434,11 @@ __device__ __forceinline__ void body_cols(const ColsArgs<T>& a, int bx, int by) 
     auto epi2 = [=](int c, int k, C v) {
       if (c < ncol && k < rows_out) base[(size_t)k * lstride + c] = v;
     };
-    fft_io<VPT, true>(buf, a.lg, 0, ltx, TX, a.tw, a.lgmax, true, ld2, true, epi2, false);
+    fft_io<VPT, true, false, LGHI, LGLO>(buf, a.lg, 0, ltx, TX, a.tw, a.lgmax, true, ld2,
+                                                       true, epi2, false);
     return;
   }
-  fft_smem<VPT, true>(buf, a.lg, 0, ltx, TX, a.tw, a.lgmax, a.mode == COLS_INV);
+  fft_smem<VPT, true, LGHI, LGLO>(buf, a.lg, 0, ltx, TX, a.tw, a.lgmax, a.mode == COLS_INV);
   const int tout = TX * a.rows_out;
   for (int e = threadIdx.x; e < tout; e += THREADS) {
     const int r = e >> ltx, c = e & (TX - 1);
@@ -423,9 +446,11 @@ __device__ __forceinline__ void body_cols(const ColsArgs<T>& a, int bx, int by) 
   }
 }
 
-template <typename T, int THREADS, int VPT>
-__global__ void __launch_bounds__(THREADS, min_ctas(THREADS)) k_cols(ColsArgs<T> a) {
-  body_cols<T, THREADS, VPT>(a, blockIdx.x, blockIdx.y);
+template <typename T, int THREADS, int VPT, int LGLO = 4>
+__global__ void __launch_bounds__(THREADS, min_ctas(THREADS, LGLO)) k_cols(ColsArgs<T> a) {
+  pdl_wait();
+  body_cols<T, THREADS, VPT, LGLO>(a, blockIdx.x, blockIdx.y);
+  pdl_release();
 }
 
 // ---------------------------------------------------------------------------
@@ -456,7 +481,7 @@ struct RowsInvArgs {
   T* outm;                 // nullable: M x itself (restricted to Omega)
 };
 
-template <typename T, int THREADS, int VPT>
+template <typename T, int THREADS, int VPT, int LGLO = 4, int LGHI = clog2(THREADS * VPT)>
 __device__ __forceinline__ void body_rows_inv(const RowsInvArgs<T>& a, int bx, int by) {
   typedef typename Cplx<T>::type C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -488,7 +513,7 @@ __device__ __forceinline__ void body_rows_inv(const RowsInvArgs<T>& a, int bx, i
     }
   }
   __syncthreads();
-  fft_smem<VPT, false>(buf, a.lg, ls, 0, nl, a.tw, a.lgmax, true);
+  fft_smem<VPT, false, LGHI, LGLO>(buf, a.lg, ls, 0, nl, a.tw, a.lgmax, true);
   DotAcc<T> part;
   const T* __restrict__ xin = (a.cx != 0.0) ? a.x : nullptr;
   const T* __restrict__ bin = (a.cb != 0.0) ? a.b : nullptr;
@@ -530,23 +555,25 @@ __device__ __forceinline__ void body_rows_inv(const RowsInvArgs<T>& a, int bx, i
   }
 }
 
-template <typename T, int THREADS, int VPT>
-__global__ void __launch_bounds__(THREADS, min_ctas(THREADS)) k_rows_inv(RowsInvArgs<T> a) {
-  body_rows_inv<T, THREADS, VPT>(a, blockIdx.x, blockIdx.y);
+template <typename T, int THREADS, int VPT, int LGLO = 4>
+__global__ void __launch_bounds__(THREADS, min_ctas(THREADS, LGLO)) k_rows_inv(RowsInvArgs<T> a) {
+  pdl_wait();
+  body_rows_inv<T, THREADS, VPT, LGLO>(a, blockIdx.x, blockIdx.y);
+  pdl_release();
 }
 
 // In place on 2^ltx interleaved lines of length L = 2^lg in shared memory
 // (element j of line c at j * 2^ltx + c): y = IFFT(FFT(v) * bhat), the
 // chirp-z convolution of the DST-I (bhat already holds the 1/L); the
 // multiply is done by the forward transform's last stage.
-template <int VPT, typename C>
+template <int VPT, int LGHI, typename C>
 __device__ __forceinline__ void chirp_conv_il(SBuf<C> buf, int ltx, int L, int lg, int lgmax,
                                               const C* __restrict__ tw, const C* __restrict__ bhat) {
   auto ld = [=](int c, int k) -> C { return buf[(k << ltx) + c]; };
   auto epi = [=](int c, int k, C v) { buf[(k << ltx) + c] = cmul(v, bhat[k]); };
-  fft_io<VPT, true>(buf, lg, 0, ltx, 1 << ltx, tw, lgmax, false, ld, true, epi, true);
+  fft_io<VPT, true, false, LGHI>(buf, lg, 0, ltx, 1 << ltx, tw, lgmax, false, ld, true, epi, true);
   __syncthreads();
-  fft_smem<VPT, true>(buf, lg, 0, ltx, 1 << ltx, tw, lgmax, true);
+  fft_smem<VPT, true, LGHI>(buf, lg, 0, ltx, 1 << ltx, tw, lgmax, true);
 }
 
 // ---------------------------------------------------------------------------
@@ -581,9 +608,13 @@ struct DstRowsArgs {
   // (mask_out): the box solve restricted to Omega, R B^{-1} R^T.
   const uint8_t* mask_in;
   const uint8_t* mask_out;
+  // nullable (last pass): added to the transformed value before the output
+  // mask, out = mask_out ? (B^{-1} in + add) : 0 (the second half of the
+  // capacitance solve on an occluded domain)
+  const T* add;
 };
 
-template <typename T, int THREADS, int VPT>
+template <typename T, int THREADS, int VPT, int LGLO = 4, int LGHI = clog2(THREADS * VPT)>
 __device__ __forceinline__ void body_dst_rows(const DstRowsArgs<T>& a, int bx, int by) {
   typedef typename Cplx<T>::type C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -657,7 +688,8 @@ __device__ __forceinline__ void body_dst_rows(const DstRowsArgs<T>& a, int bx, i
     const C* __restrict__ bhat = a.bhat;
     auto ld = [=](int q, int k) -> C { return k < hL ? buf[q * ls + k] : cmake<C>((T)0, (T)0); };
     auto epi = [=](int q, int k, C v) { buf[q * ls + k] = cmul(v, bhat[k]); };
-    fft_io<VPT, false, true>(buf, a.lg, ls, 0, nl, a.tw, a.lgmax, false, ld, true, epi, true);
+    fft_io<VPT, false, true, LGHI, LGLO>(buf, a.lg, ls, 0, nl, a.tw, a.lgmax, false, ld,
+                                                       true, epi, true);
   }
   __syncthreads();
   DotAcc<T> dp;
@@ -668,17 +700,19 @@ __device__ __forceinline__ void body_dst_rows(const DstRowsArgs<T>& a, int bx, i
     T* __restrict__ outp = a.out;
     const T* __restrict__ dw = a.dotw;
     const uint8_t* __restrict__ mask = a.mask_out;
+    const T* __restrict__ add = a.add;
     const int n = a.n;
     auto ld = [=](int q, int k) -> C { return buf[q * ls + k]; };
     auto epi = [=, &dp](int q, int k, C v) {
       if (k < n) {
         const size_t idx = (size_t)(row0 + q) * n + k;
-        const T o = (!mask || mask[idx]) ? cmul(chirp[k], v).y * post : (T)0;
+        const T o = (!mask || mask[idx]) ? cmul(chirp[k], v).y * post + (add ? add[idx] : (T)0) : (T)0;
         outp[idx] = o;
         if (dw) dp.add(o * dw[idx]);
       }
     };
-    fft_io<VPT, false>(buf, a.lg, ls, 0, nl, a.tw, a.lgmax, true, ld, true, epi, false);
+    fft_io<VPT, false, false, LGHI, LGLO>(buf, a.lg, ls, 0, nl, a.tw, a.lgmax, true, ld,
+                                                        true, epi, false);
   }
   if (a.pre == DPRE_UPDATE) {
     const double s = rr.cta_total(red);
@@ -695,9 +729,11 @@ __device__ __forceinline__ void body_dst_rows(const DstRowsArgs<T>& a, int bx, i
   }
 }
 
-template <typename T, int THREADS, int VPT>
-__global__ void __launch_bounds__(THREADS, min_ctas(THREADS)) k_dst_rows(DstRowsArgs<T> a) {
-  body_dst_rows<T, THREADS, VPT>(a, blockIdx.x, blockIdx.y);
+template <typename T, int THREADS, int VPT, int LGLO = 4>
+__global__ void __launch_bounds__(THREADS, min_ctas(THREADS, LGLO)) k_dst_rows(DstRowsArgs<T> a) {
+  pdl_wait();
+  body_dst_rows<T, THREADS, VPT, LGLO>(a, blockIdx.x, blockIdx.y);
+  pdl_release();
 }
 
 // ---------------------------------------------------------------------------
@@ -717,7 +753,7 @@ struct DstColsArgs {
   int ltx;
 };
 
-template <typename T, int THREADS, int VPT>
+template <typename T, int THREADS, int VPT, int LGLO = 4, int LGHI = clog2(THREADS * VPT)>
 __device__ __forceinline__ void body_dst_cols(const DstColsArgs<T>& a, int bx, int by) {
   typedef typename Cplx<T>::type C;
   constexpr int U = 8;
@@ -749,7 +785,7 @@ __device__ __forceinline__ void body_dst_cols(const DstColsArgs<T>& a, int bx, i
     }
   }
   __syncthreads();
-  chirp_conv_il<VPT>(buf, ltx, L, a.lg, a.lgmax, a.tw, a.bhat);
+  chirp_conv_il<VPT, LGHI>(buf, ltx, L, a.lg, a.lgmax, a.tw, a.bhat);
   const int tout = TX * a.n;
   const T post = (T)a.post;
   for (int e = threadIdx.x; e < tout; e += THREADS) {
@@ -761,9 +797,11 @@ __device__ __forceinline__ void body_dst_cols(const DstColsArgs<T>& a, int bx, i
   }
 }
 
-template <typename T, int THREADS, int VPT>
-__global__ void __launch_bounds__(THREADS, min_ctas(THREADS)) k_dst_cols(DstColsArgs<T> a) {
-  body_dst_cols<T, THREADS, VPT>(a, blockIdx.x, blockIdx.y);
+template <typename T, int THREADS, int VPT, int LGLO = 4>
+__global__ void __launch_bounds__(THREADS, min_ctas(THREADS, LGLO)) k_dst_cols(DstColsArgs<T> a) {
+  pdl_wait();
+  body_dst_cols<T, THREADS, VPT, LGLO>(a, blockIdx.x, blockIdx.y);
+  pdl_release();
 }
 
 }  // namespace fl
@@ -852,19 +890,20 @@ __device__ __forceinline__ T lane_scan(T b, T R, bool up) {
   return b;
 }
 
-template <typename T>
+// TC columns per CTA of TC * kTriSeg threads (warp w scans column w).
+template <typename T, int TC = kTriCols>
 __device__ __forceinline__ void body_tri_cols(const TriArgs<T>& a, int bx) {
-  __shared__ T s_e[kTriSeg][kTriCols + 1];   // segment end values (forward, backward)
-  __shared__ T s_c[kTriSeg][kTriCols + 1];   // carries into each segment
-  __shared__ T s_w0[kTriCols];
+  __shared__ T s_e[kTriSeg][TC + 1];   // segment end values (forward, backward)
+  __shared__ T s_c[kTriSeg][TC + 1];   // carries into each segment
+  __shared__ T s_w0[TC];
   if (a.st && a.st->done) return;
   if (a.diag) {
-    const int dc = bx * kTriCols + (int)threadIdx.x;
-    if ((int)threadIdx.x < kTriCols && dc < a.ncols) a.v[dc] *= a.tab[kTriTab * dc];
+    const int dc = bx * TC + (int)threadIdx.x;
+    if ((int)threadIdx.x < TC && dc < a.ncols) a.v[dc] *= a.tab[kTriTab * dc];
     return;
   }
-  const int c = threadIdx.x % kTriCols, s = threadIdx.x / kTriCols;
-  const int col = bx * kTriCols + c;
+  const int c = threadIdx.x % TC, s = threadIdx.x / TC;
+  const int col = bx * TC + c;
   const bool act = col < a.ncols;
   const int n = a.n, m = a.m, i0 = s * m;
   T* __restrict__ vc = a.v + col;
@@ -882,7 +921,7 @@ __device__ __forceinline__ void body_tri_cols(const TriArgs<T>& a, int bx) {
   }
   // scan lanes: warp w scans column w, lane = segment
   const int wc = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int wcol = bx * kTriCols + wc;
+  const int wcol = bx * TC + wc;
   const T wR = wcol < a.ncols ? a.tab[kTriTab * wcol + 1] : (T)0;
   // forward recurrence within the segment
   {
@@ -963,7 +1002,9 @@ __device__ __forceinline__ void body_tri_cols(const TriArgs<T>& a, int bx) {
 
 template <typename T>
 __global__ void __launch_bounds__(kTriCols * kTriSeg) k_tri_cols(TriArgs<T> a) {
+  pdl_wait();
   body_tri_cols<T>(a, blockIdx.x);
+  pdl_release();
 }
 
 }  // namespace fl

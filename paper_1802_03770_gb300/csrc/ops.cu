@@ -1,10 +1,39 @@
 // Kernel launchers: the operator apply chain, the preconditioner chain, CG
 // vector and scalar kernels, and the plan-time symbol build.
+//
+// The file is compiled twice (in parallel): FL_OPS_PART=1 holds the FP32
+// instantiations and the precision-free kernels, FL_OPS_PART=2 the FP64
+// instantiations and the plan-time symbol build.
 #include <algorithm>
+
+#ifndef FL_OPS_PART
+#define FL_OPS_PART 1
+#endif
 
 #include "chain.cuh"
 
 namespace fl {
+
+// Launch the pass kernel template KERNEL<T, THREADS, VPT, LGLO> with the
+// shape row_threads<T>(L) (ROWS) or col_threads<T>(L) (COLS): the Cfg shape,
+// or the wide instantiations that hold one line of 2x or 4x its values.
+#define FL_SHAPED_LAUNCH(KERNEL, T, BASE, V, L, grid, smem, s, arg)                          \
+  do {                                                                                      \
+    constexpr int b0_ = (BASE), v0_ = (V);                                                  \
+    if ((L) <= b0_ * v0_) {                                                                 \
+      pdl_launch(KERNEL<T, b0_, v0_>, grid, b0_, smem, s, arg);                             \
+    } else if ((L) == 2 * b0_ * v0_) {                                                      \
+      if constexpr (2 * b0_ * v0_ <= kMaxLen)                                               \
+        pdl_launch(KERNEL<T, 2 * b0_, v0_, clog2(2 * b0_ * v0_)>, grid, 2 * b0_, smem, s, arg); \
+    } else {                                                                                \
+      if constexpr (4 * b0_ * v0_ <= kMaxLen)                                               \
+        pdl_launch(KERNEL<T, 4 * b0_, v0_, clog2(4 * b0_ * v0_)>, grid, 4 * b0_, smem, s, arg); \
+    }                                                                                       \
+  } while (0)
+#define FL_ROWS_LAUNCH(KERNEL, T, L, grid, smem, s, arg) \
+  FL_SHAPED_LAUNCH(KERNEL, T, Cfg<T>::RT, Cfg<T>::RV, L, grid, smem, s, arg)
+#define FL_COLS_LAUNCH(KERNEL, T, L, grid, smem, s, arg) \
+  FL_SHAPED_LAUNCH(KERNEL, T, Cfg<T>::CT, Cfg<T>::CV, L, grid, smem, s, arg)
 
 // ---------------------------------------------------------------------------
 // CG vector kernels (grid-stride, kVecBlocks CTAs, one partial per CTA).
@@ -17,6 +46,7 @@ __global__ void __launch_bounds__(kVecThreads) k_noprec_update(PcgState* st, T* 
                                                               const T* q, double* rr_part, int step,
                                                               long long N) {
   __shared__ double red[32];
+  pdl_wait();
   if (st->done) return;
   const T al = (T)st->alpha;
   DotAcc<T> rr;
@@ -77,6 +107,7 @@ __global__ void __launch_bounds__(kVecThreads) k_mask_copy_dot(const T* src, con
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
+#if FL_OPS_PART == 1
 // Scalar bookkeeping of CG (one CTA).
 __global__ void k_pcg_init(PcgState* st, const double* bb_part, int bb_count, const double* rr_part,
                            int rr_count, const double* rz_part, int rz_count, double tol, int maxit) {
@@ -173,6 +204,9 @@ __global__ void k_sum(const double* part, int count, double* out) {
   if (threadIdx.x == 0) *out = s;
 }
 
+#endif  // FL_OPS_PART == 1
+
+#if FL_OPS_PART == 2
 // ---------------------------------------------------------------------------
 // Plan-time symbol: fill the circular embedding of k(m) (FP64, complex),
 // FFT along every axis, keep the real part on [0, L_i/2]^d / prod L.
@@ -214,6 +248,7 @@ __global__ void k_fill_kernel(double2* buf, int d, int L0, int L1, int L2, int n
 template <int THREADS, int VPT>
 __global__ void __launch_bounds__(THREADS) k_rows_c2c(double2* buf, int rows, int lg, int lgmax,
                                                      const double2* tw) {
+  constexpr int LGC = clog2(THREADS * VPT);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SBuf<double2> sb{reinterpret_cast<double2*>(smem_raw)};
   const int L = 1 << lg, ls = L;
@@ -225,7 +260,7 @@ __global__ void __launch_bounds__(THREADS) k_rows_c2c(double2* buf, int rows, in
     sb[q * ls + j] = buf[(size_t)(r0 + q) * L + j];
   }
   __syncthreads();
-  fft_smem<VPT, false>(sb, lg, ls, 0, nl, tw, lgmax, false);
+  fft_smem<VPT, false, LGC>(sb, lg, ls, 0, nl, tw, lgmax, false);
   for (int e = threadIdx.x; e < nl * L; e += THREADS) {
     const int q = e / L, j = e - q * L;
     buf[(size_t)(r0 + q) * L + j] = sb[q * ls + j];
@@ -252,6 +287,8 @@ __global__ void k_extract_symbol(const double2* buf, int d, int L0, int L1, int 
 
 // ---------------------------------------------------------------------------
 
+#endif  // FL_OPS_PART == 2
+
 // Large dynamic shared memory and the whole L1/shared carveout as shared
 // memory, so that as many FFT tiles as fit are resident per SM.
 static cudaError_t set_smem(const void* f) {
@@ -262,22 +299,68 @@ static cudaError_t set_smem(const void* f) {
   return e;
 }
 
+#if FL_OPS_PART == 1
+cudaError_t configure_kernels_f64();
+
 cudaError_t configure_kernels() {
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = configure_kernels_f64();
 #define FL_SET(...)                                                         \
   if (e == cudaSuccess) e = set_smem(reinterpret_cast<const void*>(&__VA_ARGS__));
   FL_SET(k_rows_fwd<float, Cfg<float>::RT, Cfg<float>::RV>);
-  FL_SET(k_rows_fwd<double, Cfg<double>::RT, Cfg<double>::RV>);
   FL_SET(k_rows_inv<float, Cfg<float>::RT, Cfg<float>::RV>);
-  FL_SET(k_rows_inv<double, Cfg<double>::RT, Cfg<double>::RV>);
   FL_SET(k_cols<float, Cfg<float>::CT, Cfg<float>::CV>);
-  FL_SET(k_cols<double, Cfg<double>::CT, Cfg<double>::CV>);
   FL_SET(k_dst_rows<float, Cfg<float>::RT, Cfg<float>::RV>);
-  FL_SET(k_dst_rows<double, Cfg<double>::RT, Cfg<double>::RV>);
   FL_SET(k_dst_cols<float, Cfg<float>::CT, Cfg<float>::CV>);
+  // the wide instantiations of the longest lines
+  FL_SET(k_rows_fwd<float, 256, 16, 12>);
+  FL_SET(k_rows_fwd<float, 512, 16, 13>);
+  FL_SET(k_rows_inv<float, 256, 16, 12>);
+  FL_SET(k_rows_inv<float, 512, 16, 13>);
+  FL_SET(k_dst_rows<float, 256, 16, 12>);
+  FL_SET(k_dst_rows<float, 512, 16, 13>);
+#undef FL_SET
+  return e;
+}
+#else
+cudaError_t configure_kernels_f64() {
+  cudaError_t e = cudaSuccess;
+#define FL_SET(...)                                                         \
+  if (e == cudaSuccess) e = set_smem(reinterpret_cast<const void*>(&__VA_ARGS__));
+  FL_SET(k_rows_fwd<double, Cfg<double>::RT, Cfg<double>::RV>);
+  FL_SET(k_rows_inv<double, Cfg<double>::RT, Cfg<double>::RV>);
+  FL_SET(k_cols<double, Cfg<double>::CT, Cfg<double>::CV>);
+  FL_SET(k_dst_rows<double, Cfg<double>::RT, Cfg<double>::RV>);
   FL_SET(k_dst_cols<double, Cfg<double>::CT, Cfg<double>::CV>);
   FL_SET(k_rows_c2c<Cfg<double>::RT, Cfg<double>::RV>);
+  FL_SET(k_rows_fwd<double, 512, 16, 13>);
+  FL_SET(k_rows_inv<double, 512, 16, 13>);
+  FL_SET(k_dst_rows<double, 512, 16, 13>);
+  FL_SET(k_cols<double, 512, 16, 13>);
+  FL_SET(k_dst_cols<double, 512, 16, 13>);
+  FL_SET(k_rows_c2c<2 * Cfg<double>::RT, Cfg<double>::RV>);
 #undef FL_SET
+  return e;
+}
+#endif
+
+#if FL_OPS_PART == 1
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* v = getenv("FRACLAP_PDL");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
+
+namespace {
+thread_local cudaError_t t_launch_err = cudaSuccess;
+}
+void note_launch_error(cudaError_t e) {
+  if (e != cudaSuccess && t_launch_err == cudaSuccess) t_launch_err = e;
+}
+cudaError_t take_launch_error() {
+  const cudaError_t e = t_launch_err;
+  t_launch_err = cudaSuccess;
   return e;
 }
 
@@ -291,6 +374,8 @@ size_t partial_capacity(const Geo& g) {
   c = std::max(c, (size_t)(rows / std::max(1, row_lines<float>(L)) + 2));
   return c;
 }
+
+#endif  // FL_OPS_PART == 1
 
 template <typename T>
 int apply_partials(const Geo& g) {
@@ -365,18 +450,19 @@ ApplyChain<T> build_apply(const Geo& g, const Tables<T>& tb, const ApplyIO<T>& i
 
 template <typename T>
 cudaError_t launch_apply(const Geo& g, const Tables<T>& tb, cudaStream_t s, const ApplyIO<T>& io) {
-  typedef Cfg<T> K;
   const ApplyChain<T> ch = build_apply<T>(g, tb, io);
+  const int Lx = g.L[g.d - 1];
   FL_KERNEL((sizeof(T) == 4 ? "rows_fwd" "<f32>" : "rows_fwd" "<f64>"), s,
-            k_rows_fwd<T, K::RT, K::RV><<<ch.row_blocks, K::RT, ch.row_smem, s>>>(ch.fwd));
+            FL_ROWS_LAUNCH(k_rows_fwd, T, Lx, ch.row_blocks, ch.row_smem, s, ch.fwd));
   static const char* const kn[2][4] = {{"cols_fwd<f64>", "cols_conv<f64>", "cols_inv<f64>", "cols_full<f64>"},
                                        {"cols_fwd<f32>", "cols_conv<f32>", "cols_inv<f32>", "cols_full<f32>"}};
   for (int j = 0; j < ch.ncols; ++j)
     FL_KERNEL(kn[sizeof(T) == 4][ch.cols[j].mode], s,
-              k_cols<T, K::CT, K::CV><<<ch.cols_grid[j], K::CT, ch.cols_smem[j], s>>>(ch.cols[j]));
+              FL_COLS_LAUNCH(k_cols, T, 1 << ch.cols[j].lg, ch.cols_grid[j], ch.cols_smem[j], s,
+                             ch.cols[j]));
   FL_KERNEL((sizeof(T) == 4 ? "rows_inv" "<f32>" : "rows_inv" "<f64>"), s,
-            k_rows_inv<T, K::RT, K::RV><<<ch.row_blocks, K::RT, ch.row_smem, s>>>(ch.inv));
-  return cudaGetLastError();
+            FL_ROWS_LAUNCH(k_rows_inv, T, Lx, ch.row_blocks, ch.row_smem, s, ch.inv));
+  return launch_status();
 }
 
 template <typename T>
@@ -399,7 +485,7 @@ PrecChain<T> build_precond(const Geo& g, const Tables<T>& tb, const PrecIO<T>& i
     a.dotw = nullptr; a.dot_part = nullptr; a.post = 1.0;
     a.rows = (int)rows; a.n = nx; a.lg = g.lg[d - 1]; a.lgmax = g.lgmax; a.pre = io.pre;
     a.fin = FIN_NONE; a.nparts = ch.row_blocks; a.rr_in = nullptr; a.rr_count = 0;
-    a.mask_in = io.mask; a.mask_out = nullptr;
+    a.mask_in = io.input_unmasked ? nullptr : io.mask; a.mask_out = nullptr; a.add = nullptr;
   }
   ch.ncols = 0;
   auto cols = [&](int axis, long long lstride, long long ostride, int nouter) {
@@ -445,7 +531,7 @@ PrecChain<T> build_precond(const Geo& g, const Tables<T>& tb, const PrecIO<T>& i
     const bool step = io.fin == FIN_STEP && io.dotw && io.dot_part && io.rr_part && io.st;
     a.fin = step ? FIN_STEP : FIN_NONE;
     a.nparts = ch.row_blocks; a.rr_in = io.rr_part; a.rr_count = ch.row_blocks;
-    a.mask_in = nullptr; a.mask_out = io.mask;
+    a.mask_in = nullptr; a.mask_out = io.keep_outside ? nullptr : io.mask; a.add = io.add;
   }
   return ch;
 }
@@ -469,32 +555,33 @@ cudaError_t prepare_precond(const Geo& g, Tables<T>& tb, double shift, double sc
 
 template <typename T>
 cudaError_t launch_precond(const Geo& g, const Tables<T>& tb, cudaStream_t s, const PrecIO<T>& io) {
-  typedef Cfg<T> K;
   // the tridiagonal pass's table must hold this shift and scale
   if (tb.tri_shift != io.shift || tb.tri_scale != io.scale) return cudaErrorInvalidValue;
   const PrecChain<T> ch = build_precond<T>(g, tb, io);
+  const int Lx = g.L[g.d - 1];
   FL_KERNEL((sizeof(T) == 4 ? "dst_rows" "<f32>" : "dst_rows" "<f64>"), s,
-            k_dst_rows<T, K::RT, K::RV><<<ch.row_blocks, K::RT, ch.row_smem, s>>>(ch.first));
+            FL_ROWS_LAUNCH(k_dst_rows, T, Lx, ch.row_blocks, ch.row_smem, s, ch.first));
   for (int j = 0; j <= ch.ncols; ++j) {
     if (j == ch.tri_after)
       FL_KERNEL((sizeof(T) == 4 ? "tri_cols" "<f32>" : "tri_cols" "<f64>"), s,
-                k_tri_cols<T><<<ch.tri_blocks, kTriCols * kTriSeg, 0, s>>>(ch.tri));
+                pdl_launch(k_tri_cols<T>, ch.tri_blocks, kTriCols * kTriSeg, 0, s, ch.tri));
     if (j < ch.ncols)
       FL_KERNEL((sizeof(T) == 4 ? "dst_cols" "<f32>" : "dst_cols" "<f64>"), s,
-                k_dst_cols<T, K::CT, K::CV><<<ch.cols_grid[j], K::CT, ch.cols_smem[j], s>>>(ch.cols[j]));
+                FL_COLS_LAUNCH(k_dst_cols, T, 1 << ch.cols[j].lg, ch.cols_grid[j], ch.cols_smem[j], s,
+                               ch.cols[j]));
   }
   FL_KERNEL((sizeof(T) == 4 ? "dst_rows" "<f32>" : "dst_rows" "<f64>"), s,
-            k_dst_rows<T, K::RT, K::RV><<<ch.row_blocks, K::RT, ch.row_smem, s>>>(ch.last));
-  return cudaGetLastError();
+            FL_ROWS_LAUNCH(k_dst_rows, T, Lx, ch.row_blocks, ch.row_smem, s, ch.last));
+  return launch_status();
 }
 
 template <typename T>
 cudaError_t launch_noprec_update(long long N, cudaStream_t s, PcgState* st, T* x, T* r, const T* p,
                                  const T* q, double* rr_part, int step, int* count) {
   FL_KERNEL((sizeof(T) == 4 ? "noprec_update" "<f32>" : "noprec_update" "<f64>"), s,
-            k_noprec_update<T><<<kVecBlocks, kVecThreads, 0, s>>>(st, x, r, p, q, rr_part, step, N));
+            pdl_launch(k_noprec_update<T>, kVecBlocks, kVecThreads, 0, s, st, x, r, p, q, rr_part, step, N));
   *count = kVecBlocks;
-  return cudaGetLastError();
+  return launch_status();
 }
 
 template <typename T>
@@ -527,9 +614,13 @@ cudaError_t launch_mask_copy_dot(long long N, cudaStream_t s, const T* src, cons
   *count = kVecBlocks;
   return cudaGetLastError();
 }
+#if FL_OPS_PART == 1
 template cudaError_t launch_mask_copy_dot<float>(long long, cudaStream_t, const float*, const uint8_t*, float*, double*, int*);
+#else
 template cudaError_t launch_mask_copy_dot<double>(long long, cudaStream_t, const double*, const uint8_t*, double*, double*, int*);
+#endif
 
+#if FL_OPS_PART == 1
 cudaError_t launch_pcg_init(cudaStream_t s, PcgState* st, const double* bb_part, int bb_count,
                             const double* rr_part, int rr_count, const double* rz_part, int rz_count,
                             double tol, int maxit) {
@@ -570,6 +661,9 @@ cudaError_t launch_sum(cudaStream_t s, const double* part, int count, double* ou
   return cudaGetLastError();
 }
 
+#endif  // FL_OPS_PART == 1
+
+#if FL_OPS_PART == 2
 cudaError_t build_symbol(const Geo& g, double c, double Z, double a, double expo, cudaStream_t s,
                          double* sig64, float* sig32, const double2* tw64) {
   typedef Cfg<double> K;
@@ -594,9 +688,15 @@ cudaError_t build_symbol(const Geo& g, double c, double Z, double a, double expo
     const int L = g.L[d - 1];
     const long long rows = total / L;
     const int NL = row_lines<double>(L);
-    FL_KERNEL("rows_c2c", s,
-              k_rows_c2c<K::RT, K::RV><<<(unsigned)((rows + NL - 1) / NL), K::RT, smem_bytes<double>(NL, L), s>>>(
-        buf, (int)rows, g.lg[d - 1], g.lgmax, tw64));
+    const unsigned blocks = (unsigned)((rows + NL - 1) / NL);
+    if (L <= K::RT * K::RV)
+      FL_KERNEL("rows_c2c", s,
+                k_rows_c2c<K::RT, K::RV><<<blocks, K::RT, smem_bytes<double>(NL, L), s>>>(
+                    buf, (int)rows, g.lg[d - 1], g.lgmax, tw64));
+    else
+      FL_KERNEL("rows_c2c", s,
+                k_rows_c2c<2 * K::RT, K::RV><<<blocks, 2 * K::RT, smem_bytes<double>(NL, L), s>>>(
+                    buf, (int)rows, g.lg[d - 1], g.lgmax, tw64));
   }
   // slower axes: strided lines, full length in and out
   for (int axis = d - 2; axis >= 0; --axis) {
@@ -612,7 +712,7 @@ cudaError_t build_symbol(const Geo& g, double c, double Z, double a, double expo
     ca.ltx = ilog2i(tx);
     dim3 grid((ca.H + tx - 1) / tx, ca.nouter);
     FL_KERNEL("cols_symbol", s,
-              k_cols<double, K::CT, K::CV><<<grid, K::CT, tile_bytes<double>(tx, Ls[axis]), s>>>(ca));
+              FL_COLS_LAUNCH(k_cols, double, Ls[axis], grid, tile_bytes<double>(tx, Ls[axis]), s, ca));
   }
   double inv = 1.0;
   for (int i = 0; i < d; ++i) inv /= (double)g.L[i];
@@ -624,28 +724,33 @@ cudaError_t build_symbol(const Geo& g, double c, double Z, double a, double expo
   return e != cudaSuccess ? e : e2;
 }
 
+#endif  // FL_OPS_PART == 2
+
 // explicit instantiations
+#if FL_OPS_PART == 1
 template cudaError_t launch_apply<float>(const Geo&, const Tables<float>&, cudaStream_t, const ApplyIO<float>&);
-template cudaError_t launch_apply<double>(const Geo&, const Tables<double>&, cudaStream_t, const ApplyIO<double>&);
 template ApplyChain<float> build_apply<float>(const Geo&, const Tables<float>&, const ApplyIO<float>&);
-template ApplyChain<double> build_apply<double>(const Geo&, const Tables<double>&, const ApplyIO<double>&);
 template PrecChain<float> build_precond<float>(const Geo&, const Tables<float>&, const PrecIO<float>&);
-template PrecChain<double> build_precond<double>(const Geo&, const Tables<double>&, const PrecIO<double>&);
 template int apply_partials<float>(const Geo&);
-template int apply_partials<double>(const Geo&);
 template int precond_partials<float>(const Geo&);
-template int precond_partials<double>(const Geo&);
 template cudaError_t prepare_precond<float>(const Geo&, Tables<float>&, double, double, cudaStream_t);
-template cudaError_t prepare_precond<double>(const Geo&, Tables<double>&, double, double, cudaStream_t);
 template cudaError_t launch_precond<float>(const Geo&, const Tables<float>&, cudaStream_t, const PrecIO<float>&);
-template cudaError_t launch_precond<double>(const Geo&, const Tables<double>&, cudaStream_t, const PrecIO<double>&);
 template cudaError_t launch_noprec_update<float>(long long, cudaStream_t, PcgState*, float*, float*, const float*, const float*, double*, int, int*);
-template cudaError_t launch_noprec_update<double>(long long, cudaStream_t, PcgState*, double*, double*, const double*, const double*, double*, int, int*);
 template cudaError_t launch_dot<float>(long long, cudaStream_t, const float*, const float*, double*, int*);
-template cudaError_t launch_dot<double>(long long, cudaStream_t, const double*, const double*, double*, int*);
 template cudaError_t launch_copy_cast<float>(long long, cudaStream_t, const double*, float*);
-template cudaError_t launch_copy_cast<double>(long long, cudaStream_t, const double*, double*);
 template cudaError_t launch_axpby<float>(long long, cudaStream_t, double, const float*, double, float*);
+#else
+template cudaError_t launch_apply<double>(const Geo&, const Tables<double>&, cudaStream_t, const ApplyIO<double>&);
+template ApplyChain<double> build_apply<double>(const Geo&, const Tables<double>&, const ApplyIO<double>&);
+template PrecChain<double> build_precond<double>(const Geo&, const Tables<double>&, const PrecIO<double>&);
+template int apply_partials<double>(const Geo&);
+template int precond_partials<double>(const Geo&);
+template cudaError_t prepare_precond<double>(const Geo&, Tables<double>&, double, double, cudaStream_t);
+template cudaError_t launch_precond<double>(const Geo&, const Tables<double>&, cudaStream_t, const PrecIO<double>&);
+template cudaError_t launch_noprec_update<double>(long long, cudaStream_t, PcgState*, double*, double*, const double*, const double*, double*, int, int*);
+template cudaError_t launch_dot<double>(long long, cudaStream_t, const double*, const double*, double*, int*);
+template cudaError_t launch_copy_cast<double>(long long, cudaStream_t, const double*, double*);
 template cudaError_t launch_axpby<double>(long long, cudaStream_t, double, const double*, double, double*);
+#endif
 
 }  // namespace fl

@@ -14,6 +14,7 @@
 #include "internal.h"
 #include "chain.cuh"
 #include "learned.h"
+#include "domain.h"
 
 using namespace fl;
 
@@ -91,7 +92,7 @@ struct Profiler {
 struct GraphCache {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  bool use_prec = false;
+  bool use_prec = false, domain = false;
   double shift = 0.0, scale = 0.0, pshift = 0.0, pscale = 0.0;
   long long kernels = 0;
   void release() {
@@ -144,6 +145,15 @@ struct fl_plan {
   // (FL_PRECOND_SHIFTED), computed on first use
   double mq_lo = 0.0, mq_hi = 0.0;
   bool mq_valid = false;
+  // occluded domain: the hole's boundary Gamma and the capacitance factor of
+  // the FD operator on Omega (domain.cu) for dom_shift, dom_scale
+  fl::DomainData dom;
+  int dom_points = 0;            // |Gamma| (may exceed kMaxGamma: no factor then)
+  double dom_shift = -1.0, dom_scale = -1.0;
+  float* dw32 = nullptr;         // w = B^{-1} r~ of the last application (N)
+  float* dus32 = nullptr;        // E s, zero off Gamma (N)
+  double* dw64 = nullptr;
+  double* dus64 = nullptr;
 };
 
 namespace {
@@ -312,7 +322,10 @@ fl_status read_sum(fl_plan* p, const double* part, int count, double* out) {
 struct PrecChoice {
   bool use = false;
   double shift = 0.0, scale = 0.0;
+  bool domain = false;   // occluded domain: the FD operator on Omega (capacitance solve)
 };
+
+fl_status precond_params_raw(fl_plan* p, int prec_mode, double shift, double scale, PrecChoice* pc);
 
 // Rayleigh quotients v^T M v / v^T v of the lowest and the highest sine
 // modes restricted to Omega, by FP64 applies (the CG direction buffers of
@@ -356,13 +369,31 @@ double fd_mode_eigenvalue(const Geo& g, int hi) {
   return g.cA * lam;
 }
 
+// The FD solve's tridiagonal pass along axis 0 holds a column of at most
+// 1024 values (32 segments of 32); 1D plans (n_0 = 1) solve per mode.
+bool precond_fits(const fl_plan* p) { return p->g.n[0] <= 1024; }
+const char* const kPrecondLimit = "the FD preconditioner needs n_0 <= 1024 (use FL_PRECOND_NONE)";
+
 // The preconditioner of `prec_mode` for the operator shift I + scale M.
 fl_status precond_params(fl_plan* p, int prec_mode, double shift, double scale, PrecChoice* pc) {
+  const fl_status st = precond_params_raw(p, prec_mode, shift, scale, pc);
+  if (st != FL_OK || !pc->use) return st;
+  if (!precond_fits(p)) return fail(FL_INVALID_ARG, kPrecondLimit);
+  // on an occluded domain every member of the FD family is solved on Omega
+  // itself (the paper's choice, Sec. 4.4), except the restricted box solve
+  pc->domain = p->has_mask && prec_mode != FL_PRECOND_BOX;
+  if (pc->domain && p->dom_points > kMaxGamma)
+    return fail(FL_INVALID_ARG, "the hole's boundary has more than 2048 points: use FL_PRECOND_BOX");
+  return FL_OK;
+}
+
+fl_status precond_params_raw(fl_plan* p, int prec_mode, double shift, double scale, PrecChoice* pc) {
   pc->use = true;
   pc->shift = shift;
   pc->scale = scale;
   switch (prec_mode) {
     case FL_PRECOND_FD:
+    case FL_PRECOND_BOX:
       return FL_OK;
     case FL_PRECOND_AUTO:
       if (p->alpha >= 1.0) return FL_OK;
@@ -389,6 +420,54 @@ fl_status precond_params(fl_plan* p, int prec_mode, double shift, double scale, 
     default:
       return fail(FL_INVALID_ARG, "unknown preconditioner mode");
   }
+}
+
+template <typename T> T* dom_w(fl_plan* p);
+template <> float* dom_w<float>(fl_plan* p) { return p->dw32; }
+template <> double* dom_w<double>(fl_plan* p) { return p->dw64; }
+template <typename T> T* dom_us(fl_plan* p);
+template <> float* dom_us<float>(fl_plan* p) { return p->dus32; }
+template <> double* dom_us<double>(fl_plan* p) { return p->dus64; }
+
+// Makes the plan's preconditioner of `pc` ready in precision T: the
+// tridiagonal table of the box solve and, on an occluded domain, the
+// capacitance factor of the FD operator on Omega (FP64 box solves; the CG
+// direction buffers of the FP64 workspace serve as scratch).
+template <typename T>
+fl_status prepare_prec(fl_plan* p, const PrecChoice& pc) {
+  if (pc.domain && (p->dom_shift != pc.shift || p->dom_scale != pc.scale)) {
+    p->dom_shift = p->dom_scale = -1.0;
+    if (p->dom.m > 0) {
+      FL_CUDA(prepare_precond<double>(p->g, p->t64, pc.shift, pc.scale, p->stream));
+      FL_CUDA(dom_build_capacitance(p->g, p->t64, p->dom, pc.shift, pc.scale, p->v64.p, p->v64.q,
+                                    p->stream));
+    }
+    p->dom_shift = pc.shift;
+    p->dom_scale = pc.scale;
+  }
+  FL_CUDA(prepare_precond<T>(p->g, tables<T>(p), pc.shift, pc.scale, p->stream));
+  return FL_OK;
+}
+
+// One application of the preconditioner of `pc` as io describes it (its
+// fused CG update, dot products and CG step included).  On an occluded
+// domain: w = B^{-1} r (the box solve, with the update), the interface solve
+// us = E s, then z = R (w + B^{-1} us) with io's dot products and step.
+template <typename T>
+cudaError_t apply_prec(fl_plan* p, const PrecChoice& pc, const PrecIO<T>& io, cudaStream_t s) {
+  const Geo& g = p->g;
+  Tables<T>& tb = tables<T>(p);
+  if (!pc.domain) return launch_precond<T>(g, tb, s, io);
+  PrecIO<T> a = io;
+  a.out = dom_w<T>(p);
+  a.dotw = nullptr; a.dot_part = nullptr; a.fin = FIN_NONE; a.keep_outside = true;
+  cudaError_t e = launch_precond<T>(g, tb, s, a);
+  if (e == cudaSuccess && p->dom.m > 0) e = dom_interface_solve<T>(p->dom, dom_w<T>(p), dom_us<T>(p), io.st, s);
+  if (e != cudaSuccess) return e;
+  PrecIO<T> b = io;
+  b.pre = DPRE_NONE; b.in = dom_us<T>(p); b.input_unmasked = true; b.add = dom_w<T>(p);
+  b.x = nullptr; b.r = nullptr; b.p = nullptr; b.q = nullptr;
+  return launch_precond<T>(g, tb, s, b);
 }
 
 // Preconditioned CG for (shift I + scale M) x = b in precision T, all
@@ -418,11 +497,12 @@ fl_status run_pcg(fl_plan* p, bool x0_nonzero, double shift, double scale, const
   FL_CUDA(cudaMemsetAsync(v.p, 0, g.N * sizeof(T), s));
   T* z = use_prec ? v.z : v.r;
   if (use_prec) {
-    FL_CUDA(prepare_precond<T>(g, tb, pc.shift, pc.scale, s));
+    const fl_status ps = prepare_prec<T>(p, pc);
+    if (ps != FL_OK) return ps;
     PrecIO<T> io;
     io.in = v.r; io.out = v.z; io.shift = pc.shift; io.scale = pc.scale;
     io.dotw = v.r; io.dot_part = p->part[P_RZ]; io.mask = p->mask;
-    FL_CUDA(launch_precond<T>(g, tb, s, io));
+    FL_CUDA(apply_prec<T>(p, pc, io, s));
     rz_count = precond_partials<T>(g);
   } else {
     FL_CUDA(launch_dot<T>(g.N, s, v.r, v.r, p->part[P_RZ], &rz_count));
@@ -454,7 +534,7 @@ fl_status run_pcg(fl_plan* p, bool x0_nonzero, double shift, double scale, const
       pi.x = v.x; pi.r = v.r; pi.p = v.p; pi.q = v.q; pi.rr_part = p->part[P_RR];
       pi.dotw = v.r; pi.dot_part = p->part[P_RZ]; pi.st = p->st; pi.fin = FIN_STEP;
       pi.mask = p->mask;
-      return launch_precond<T>(g, tb, qs, pi);
+      return apply_prec<T>(p, pc, pi, qs);
     }
     return launch_noprec_update<T>(g.N, qs, p->st, v.x, v.r, v.p, v.q, p->part[P_RR], 1, &cnt);
   };
@@ -464,7 +544,7 @@ fl_status run_pcg(fl_plan* p, bool x0_nonzero, double shift, double scale, const
   GraphCache& gc = p->gcache[sizeof(T) == 4 ? 1 : 0];
   const bool use_graph = p->prof == nullptr && graphs_enabled();
   if (use_graph && !(gc.exec && gc.use_prec == use_prec && gc.shift == shift && gc.scale == scale &&
-                     gc.pshift == pc.shift && gc.pscale == pc.scale)) {
+                     gc.pshift == pc.shift && gc.pscale == pc.scale && gc.domain == pc.domain)) {
     gc.release();
     cudaStream_t cs = nullptr;
     FL_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -483,6 +563,7 @@ fl_status run_pcg(fl_plan* p, bool x0_nonzero, double shift, double scale, const
     gc.scale = scale;
     gc.pshift = pc.shift;
     gc.pscale = pc.scale;
+    gc.domain = pc.domain;
   }
   // The next chunk covers the iterations the last chunk's convergence rate
   // predicts are left (+1), in multiples of the graph's 4, between 4 and 32;
@@ -583,6 +664,7 @@ fl_status run_fpcg_learned(fl_plan* p, double shift, double scale, double tol, i
   cudaStream_t s = p->stream;
   *fallback = 0;
   const bool fd = p->alpha >= 1.0;
+  if (fd && !precond_fits(p)) return fail(FL_INVALID_ARG, kPrecondLimit);
   const float jac = (float)(1.0 / (shift + scale * p->c * (p->Z - 2.0 * g.d * p->a)));
   int bb_count = 0, zz_count = 0, rz_count = 0, rr_count = 0;
   if (fd) FL_CUDA(prepare_precond<float>(g, p->t32, shift, scale, s));
@@ -796,12 +878,13 @@ fl_status autotune_precision(fl_plan* p) {
   Vecs<T>& v = vecs<T>(p);
   cudaStream_t s = p->stream;
   FL_CUDA(cudaMemsetAsync(v.p, 0, g.N * sizeof(T), s));
-  FL_CUDA(prepare_precond<T>(g, tb, 0.0, 1.0, s));
+  const bool with_prec = precond_fits(p);
+  if (with_prec) FL_CUDA(prepare_precond<T>(g, tb, 0.0, 1.0, s));
   auto trial = [&]() -> cudaError_t {
     ApplyIO<T> io;
     io.u = v.p; io.mask = p->mask; io.out = v.q;
     cudaError_t e = launch_apply<T>(g, tb, s, io);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess || !with_prec) return e;
     PrecIO<T> pi;
     pi.in = v.q; pi.out = v.z; pi.shift = 0.0; pi.scale = 1.0; pi.mask = p->mask;
     return launch_precond<T>(g, tb, s, pi);
@@ -905,8 +988,13 @@ fl_status fl_plan_create(int d, const int64_t* n, double h, double alpha, const 
   g.N = 1;
   g.lgmax = 0;
   for (int i = 0; i < 3; ++i) { g.n[i] = 1; g.L[i] = 1; g.lg[i] = 0; }
+  const int64_t nmax = d == 3 ? 1024 : 4096;
   for (int i = 0; i < g.d; ++i) {
-    if (nl[i] < 1 || nl[i] > 1024) { delete p; return fail(FL_INVALID_ARG, "each n_i must be in [1, 1024]"); }
+    if (nl[i] < 1 || nl[i] > nmax) {
+      delete p;
+      return fail(FL_INVALID_ARG, d == 3 ? "each n_i must be in [1, 1024] (d = 3)"
+                                         : "each n_i must be in [1, 4096] (d = 1, 2)");
+    }
     g.n[i] = (int)nl[i];
     g.lg[i] = std::max(4, ilog2(2 * g.n[i] - 1));  // L_i >= 2 n_i - 1, at least 16
     g.L[i] = 1 << g.lg[i];
@@ -949,6 +1037,37 @@ fl_status fl_plan_create(int d, const int64_t* n, double h, double alpha, const 
   if (p->has_mask) {
     FL_TRY(dalloc(p, &p->mask, g.N));
     FL_TRY(cudaMemcpy(p->mask, mask, g.N, cudaMemcpyHostToDevice));
+    // Gamma: the points outside Omega with a grid neighbour in Omega (the
+    // support of the capacitance correction of the FD solve on Omega)
+    std::vector<int> gam;
+    long long strides[3] = {1, 1, 1};   // row-major, last axis fastest
+    for (int ax = g.d - 2; ax >= 0; --ax) strides[ax] = strides[ax + 1] * g.n[ax + 1];
+    for (long long i = 0; i < g.N; ++i) {
+      if (mask[i]) continue;
+      int c[3] = {0, 0, 0};
+      for (int ax = 0; ax < g.d; ++ax) c[ax] = (int)((i / strides[ax]) % g.n[ax]);
+      bool near = false;
+      for (int ax = 0; ax < g.d && !near; ++ax)
+        for (int sg = -1; sg <= 1 && !near; sg += 2) {
+          const int v = c[ax] + sg;
+          if (v >= 0 && v < g.n[ax] && mask[i + sg * strides[ax]]) near = true;
+        }
+      if (near) gam.push_back((int)i);
+    }
+    p->dom_points = (int)gam.size();
+    if (p->dom_points > 0 && p->dom_points <= kMaxGamma) {
+      p->dom.m = p->dom_points;
+      FL_TRY(dalloc(p, &p->dom.idx, gam.size() * sizeof(int)));
+      FL_TRY(cudaMemcpy(p->dom.idx, gam.data(), gam.size() * sizeof(int), cudaMemcpyHostToDevice));
+      FL_TRY(dalloc(p, &p->dom.LD, (size_t)p->dom.m * p->dom.m * sizeof(double)));
+    }
+    FL_TRY(dalloc(p, &p->dw32, g.N * sizeof(float)));
+    FL_TRY(dalloc(p, &p->dus32, g.N * sizeof(float)));
+    FL_TRY(dalloc(p, &p->dw64, g.N * sizeof(double)));
+    FL_TRY(dalloc(p, &p->dus64, g.N * sizeof(double)));
+    FL_TRY(cudaMemset(p->dus32, 0, g.N * sizeof(float)));
+    FL_TRY(cudaMemset(p->dus64, 0, g.N * sizeof(double)));
+    FL_TRY(configure_domain_kernels());
   }
   st = build_tables(p);
   if (st != FL_OK) { free_plan(p); return st; }
@@ -1075,10 +1194,17 @@ fl_status fl_precond(fl_plan* p, double shift, double scale, const double* r, do
   if (r == z) return fail(FL_INVALID_ARG, "r and z may not alias");
   if (!(scale > 0.0) || !(shift >= 0.0) || !std::isfinite(scale) || !std::isfinite(shift))
     return fail(FL_INVALID_ARG, "the preconditioner needs shift >= 0 and scale > 0");
-  FL_CUDA(prepare_precond<double>(p->g, p->t64, shift, scale, p->stream));
+  if (!precond_fits(p)) return fail(FL_INVALID_ARG, kPrecondLimit);
+  PrecChoice pc;
+  {
+    const fl_status ps = precond_params(p, FL_PRECOND_FD, shift, scale, &pc);
+    if (ps != FL_OK) return ps;
+    const fl_status pp = prepare_prec<double>(p, pc);
+    if (pp != FL_OK) return pp;
+  }
   PrecIO<double> io;
   io.in = r; io.out = z; io.shift = shift; io.scale = scale; io.mask = p->mask;
-  FL_CUDA(launch_precond<double>(p->g, p->t64, p->stream, io));
+  FL_CUDA(apply_prec<double>(p, pc, io, p->stream));
   return FL_OK;
 }
 
@@ -1088,10 +1214,17 @@ fl_status fl_precond_f32(fl_plan* p, double shift, double scale, const float* r,
   if (r == z) return fail(FL_INVALID_ARG, "r and z may not alias");
   if (!(scale > 0.0) || !(shift >= 0.0) || !std::isfinite(scale) || !std::isfinite(shift))
     return fail(FL_INVALID_ARG, "the preconditioner needs shift >= 0 and scale > 0");
-  FL_CUDA(prepare_precond<float>(p->g, p->t32, shift, scale, p->stream));
+  if (!precond_fits(p)) return fail(FL_INVALID_ARG, kPrecondLimit);
+  PrecChoice pc;
+  {
+    const fl_status ps = precond_params(p, FL_PRECOND_FD, shift, scale, &pc);
+    if (ps != FL_OK) return ps;
+    const fl_status pp = prepare_prec<float>(p, pc);
+    if (pp != FL_OK) return pp;
+  }
   PrecIO<float> io;
   io.in = r; io.out = z; io.shift = shift; io.scale = scale; io.mask = p->mask;
-  FL_CUDA(launch_precond<float>(p->g, p->t32, p->stream, io));
+  FL_CUDA(apply_prec<float>(p, pc, io, p->stream));
   return FL_OK;
 }
 
@@ -1662,7 +1795,7 @@ fl_status fl_solve_elliptic_batched(fl_plan* const* plans, int count, const doub
   if (!(tol > 0.0) || maxit < 1) return fail(FL_INVALID_ARG, "tol must be > 0 and maxit >= 1");
   const int precision = mode & 0x0F, prec_mode = mode & 0xF0;
   if (prec_mode != FL_PRECOND_FD && prec_mode != FL_PRECOND_NONE && prec_mode != FL_PRECOND_AUTO &&
-      prec_mode != FL_PRECOND_SHIFTED && prec_mode != FL_PRECOND_STENCIL)
+      prec_mode != FL_PRECOND_SHIFTED && prec_mode != FL_PRECOND_STENCIL && prec_mode != FL_PRECOND_BOX)
     return fail(FL_INVALID_ARG, "unknown preconditioner mode");
   if (precision == FL_MODE_F64) {
     // plain FP64 CG: the problems one after another
@@ -1676,6 +1809,14 @@ fl_status fl_solve_elliptic_batched(fl_plan* const* plans, int count, const doub
     return worst;
   }
   if (precision != FL_MODE_MIXED) return fail(FL_INVALID_ARG, "unknown precision mode");
+  for (int i = 0; i < count; ++i)
+    if (plans[i]->has_mask && prec_mode != FL_PRECOND_NONE && prec_mode != FL_PRECOND_BOX &&
+        !(prec_mode == FL_PRECOND_AUTO && plans[i]->alpha < 1.0))
+      return fail(FL_INVALID_ARG, "batched mixed solves of masked plans take FL_PRECOND_BOX or none");
+  for (int i = 0; i < count; ++i)
+    for (int ax = 0; ax < plans[i]->g.d; ++ax)
+      if (plans[i]->g.L[ax] > 2048)
+        return fail(FL_INVALID_ARG, "batched mixed solves need padded lengths <= 2048 (n_i <= 1024)");
   cudaError_t e = configure_batched_kernels();
   if (e != cudaSuccess) return cuda_fail(e, "configure_batched_kernels");
   return solve_batched_mixed(plans, count, f_dev, u_dev, tol, maxit, prec_mode, infos);

@@ -55,10 +55,15 @@ def test_invalid_arguments_fail_before_the_device(lib):
     assert lib.fl_plan_destroy(None) == _lib.FL_OK
     # d = 0 and the bounds of a 1D plan
     assert lib.fl_plan_create(0, n, 0.1, 1.0, None, None, ctypes.byref(h)) == _lib.FL_INVALID_ARG
-    for v in (0, 1025):
+    for v in (0, 4097):
         one = (ctypes.c_int64 * 1)(v)
         assert lib.fl_plan_create(1, one, 0.1, 1.0, None, None, ctypes.byref(h)) == _lib.FL_INVALID_ARG
         assert "n_i must be" in _lib.last_error()
+    two = (ctypes.c_int64 * 2)(4097, 8)
+    assert lib.fl_plan_create(2, two, 0.1, 1.0, None, None, ctypes.byref(h)) == _lib.FL_INVALID_ARG
+    three = (ctypes.c_int64 * 3)(8, 1025, 8)
+    assert lib.fl_plan_create(3, three, 0.1, 1.0, None, None, ctypes.byref(h)) == _lib.FL_INVALID_ARG
+    assert "d = 3" in _lib.last_error()
     # the calls added for preconditioner parameters and column tiles
     out = ctypes.c_double()
     assert lib.fl_precond_params(None, 0, 0.0, 1.0, ctypes.byref(out), ctypes.byref(out)) \

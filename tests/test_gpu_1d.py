@@ -51,7 +51,7 @@ def interval(N, alpha):
     return Plan(1, (N,), h, alpha), OPlan(1, N, h, alpha), x
 
 
-@pytest.mark.parametrize("N", [1, 2, 7, 100, 511, 1023, 1024])
+@pytest.mark.parametrize("N", [1, 2, 7, 100, 511, 1023, 1024, 2047, 3000, 4095, 4096])
 @pytest.mark.parametrize("alpha", [0.5, 1.5])
 def test_apply_1d_matches_oracle(N, alpha):
     p, op, _ = interval(N, alpha)
@@ -64,7 +64,7 @@ def test_apply_1d_matches_oracle(N, alpha):
     assert d["kernel0"] == pytest.approx(op.entry(np.zeros((1, 1)))[0], rel=1e-12)
 
 
-@pytest.mark.parametrize("N", [1, 9, 511, 1023])
+@pytest.mark.parametrize("N", [1, 9, 511, 1023, 2047, 4095])
 @pytest.mark.parametrize("shift,scale", [(0.0, 1.0), (1.0, 2e-3)])
 def test_precond_1d_matches_oracle(N, shift, scale):
     p, op, _ = interval(N, 1.3)
@@ -121,11 +121,11 @@ def test_table_1d_fone_on_gpu(golden):
 
 def test_table_1d_cg_on_gpu(golden):
     """FP64 CG iteration counts with and without the FD preconditioner
-    (Table tab:1D_cg, the rows with N <= 1024)."""
+    (Table tab:1D_cg, every row: N = 511 ... 4095, padded lengths up to
+    8192), every row reported first."""
+    rows = []
     for N, alpha, p6, c6, p9, c9 in golden("table_1d_cg.txt"):
         N = int(N)
-        if N > 1024:
-            continue
         p, _, x = interval(N, alpha)
         f = gpu(special.hyp2f1((1 + alpha) / 2, -2, 0.5, x ** 2))
         got = []
@@ -135,7 +135,35 @@ def test_table_1d_cg_on_gpu(golden):
                 got.append(info["iterations"])
         want = [int(p6), int(c6), int(p9), int(c9)]
         print(f"1D N = {N}, alpha = {alpha}: GPU {got}, paper {want}")
-        assert all(abs(g - w) <= 1 for g, w in zip(got, want)), (N, alpha, got, want)
+        rows.append((N, alpha, got, want))
+    for N, alpha, got, want in rows:
+        # the unpreconditioned counts to one iteration everywhere; the
+        # preconditioned ones at N >= 2047 to three (the GPU's FP64 CG
+        # reaches 1e-9 up to three iterations before the print there, e.g.
+        # 54 against 57 at N = 2047, alpha = 1.25; the oracle's CG matches
+        # the print)
+        slack = [3 if N >= 2047 else 1, 1, 3 if N >= 2047 else 1, 1]
+        assert all(abs(g - w) <= sl for g, w, sl in zip(got, want, slack)), (N, alpha, got, want)
+
+
+def test_table_1d_long_rows_on_gpu(golden):
+    """The N = 2047 and 4095 rows (padded lengths 4096 and 8192): e_app of
+    Table tab:1D_con (FP64 apply) and e_sol of Table tab:1D_erronly2 (f = 1,
+    FP64 PCG to 1e-12) to the printed two digits (5 %, as the oracle's pins
+    of the same rows)."""
+    for N, alpha, e_app_paper, _ in golden("table_1d_con_long.txt"):
+        N = int(N)
+        p, _, x = interval(N, alpha)
+        u = (1 - x ** 2) ** (2 + alpha / 2) / dyda(alpha, 2 + alpha / 2)
+        f = special.hyp2f1((1 + alpha) / 2, -2, 0.5, x ** 2)
+        assert rel(host(p.apply(gpu(u))), f) == pytest.approx(e_app_paper, rel=0.05), (N, alpha)
+    for N, alpha, e_paper in golden("table_1d_fone_long.txt"):
+        N = int(N)
+        p, _, x = interval(N, alpha)
+        u = (1 - x ** 2) ** (alpha / 2) / dyda(alpha, alpha / 2)
+        us, _ = p.solve(gpu(np.ones(N)), tol=1e-12, mode=F64 | _lib.FL_PRECOND_FD, maxit=5000,
+                        raise_on_fail=False)
+        assert rel(host(us), u) == pytest.approx(e_paper, rel=0.05), (N, alpha)
 
 
 @pytest.mark.parametrize("theta", [1.0, 0.5])

@@ -87,6 +87,40 @@ def test_apply_f32(d, n):
     assert rel(y, op.apply(u.astype(np.float32).astype(np.float64))) <= 2e-5
 
 
+@pytest.mark.parametrize("d,n", [(2, (1, 4095)), (2, (3, 2500)), (2, (2100, 7)), (2, (1500, 40)),
+                                 (2, (40, 1500))])
+def test_apply_long_lines(d, n):
+    """Padded lengths 4096 and 8192 (n_i up to 4095) along the row axis (the
+    wide row-pass instantiations: one line per CTA of 256 or 512 threads)
+    and along the strided axis (FP32 tiles of two or one column; the FP64
+    column pass on 512 threads): FP64 to 1e-10, FP32 to 2e-5."""
+    h = 1.0 / (max(n) + 1)
+    op = OPlan(d, n, h, 1.3)
+    u = np.random.default_rng(22).standard_normal(n)
+    p = Plan(d, n, h, 1.3)
+    assert rel(host(p.apply(gpu(u))), op.apply(u)) <= 1e-10
+    u32 = u.astype(np.float32).astype(np.float64)
+    assert rel(host(p.apply(gpu(u, torch.float32))), op.apply(u32)) <= 2e-5
+
+
+def test_long_first_axis_rejects_the_fd_preconditioner():
+    """The FD solve's tridiagonal pass holds columns of at most 1024 values:
+    a plan with n_0 > 1024 solves with plain CG and refuses the FD
+    preconditioner with FL_INVALID_ARG."""
+    n = (1100, 8)
+    h = 1.0 / 1101
+    op = OPlan(2, n, h, 0.8)
+    p = Plan(2, n, h, 0.8)
+    f = np.random.default_rng(23).standard_normal(n)
+    with pytest.raises(_lib.FracLapError, match="INVALID_ARG"):
+        p.precond(gpu(f))
+    with pytest.raises(_lib.FracLapError, match="INVALID_ARG"):
+        p.solve(gpu(f), mode=_lib.FL_MODE_F64 | _lib.FL_PRECOND_FD)
+    u, info = p.solve(gpu(f), tol=1e-9, mode=_lib.FL_MODE_MIXED | _lib.FL_PRECOND_NONE, maxit=3000)
+    assert info["converged"] == 1
+    assert rel(op.apply(host(u)), f) <= 1.05e-9
+
+
 def test_apply_masked():
     n = (41, 30)
     rng = np.random.default_rng(13)
@@ -204,43 +238,84 @@ def _l_shape(n):
     return ~np.logical_and.reduce([g > 0 for g in G])
 
 
-@pytest.mark.parametrize("d,n", [(2, (48, 40)), (3, (12, 10, 14))])
+@pytest.mark.parametrize("d,n", [(2, (48, 40)), (3, (12, 10, 14)), (2, (127, 127))])
 @pytest.mark.parametrize("shift,scale", [(0.0, 1.0), (1.0, 2e-3)])
 def test_precond_masked_matches_oracle(d, n, shift, scale):
-    """Occluded domain: the box FD solve restricted to Omega."""
+    """Occluded domain: the FD operator on Omega with Dirichlet conditions
+    on the hole (the paper's preconditioner, Sec. 4.4), applied by the box
+    solve and the hole boundary's capacitance matrix, against the oracle's
+    sparse direct solve: FP64 to 1e-10; FP32 box solves (the interface
+    system in FP64) to 1e-4 -- the capacitance solve amplifies the FP32
+    box solves' rounding by the conditioning of the interface system."""
     mask = _l_shape(n)
     h = 1.0 / (max(n) + 1)
     op = OPlan(d, n, h, 1.4, mask=mask)
     r = np.random.default_rng(21).standard_normal(n)
-    z_ref = opc.solve_embedded(op, r, shift, scale)
+    z_ref = opc.solve_domain(op, r, shift, scale)
     p = Plan(d, n, h, 1.4, mask=mask)
     z = host(p.precond(gpu(r), shift, scale))
     assert np.all(z[~mask] == 0.0)
-    assert rel(z, z_ref) <= 1e-10
+    e64 = rel(z, z_ref)
     z32 = host(p.precond(gpu(r, torch.float32), shift, scale))
-    assert rel(z32, z_ref) <= 2e-5
+    e32 = rel(z32, z_ref)
+    print(f"masked precond {n}: FP64 {e64:.1e}, FP32 {e32:.1e}")
+    assert e64 <= 1e-10
+    assert e32 <= 1e-4
 
 
 @pytest.mark.parametrize("mode", [_lib.FL_MODE_F64, _lib.FL_MODE_MIXED])
 def test_solve_masked_preconditioned(mode):
-    """L-shaped domain, alpha = 1.5: the restricted box preconditioner
-    converges to the same solution as plain CG, in fewer iterations."""
+    """L-shaped domain, alpha = 1.5: the FD operator on Omega, the restricted
+    box solve and plain CG converge to the same solution; the paper's
+    preconditioner takes the fewest iterations."""
     n = (64, 64)
     mask = _l_shape(n)
     h = 1.0 / 65
     op = OPlan(2, n, h, 1.5, mask=mask)
     f = np.where(mask, inputs.gaussian_mixture(64, 2, 8, 3), 0.0)
     p = Plan(2, n, h, 1.5, mask=mask)
-    u, info = p.solve(gpu(f), tol=1e-9, mode=mode | _lib.FL_PRECOND_FD)
-    u = host(u)
-    assert info["converged"] == 1
-    assert np.all(u[~mask] == 0.0)
-    assert rel(op.apply(u), f) <= 1.05e-9
-    u0, info0 = p.solve(gpu(f), tol=1e-9, mode=mode | _lib.FL_PRECOND_NONE)
-    assert rel(u, host(u0)) <= 1e-6
-    print(f"L-shape 64^2, alpha 1.5: {info['iterations']} preconditioned vs "
-          f"{info0['iterations']} plain CG iterations")
-    assert info["iterations"] < info0["iterations"]
+    its = {}
+    sols = {}
+    for name, pm in (("domain", _lib.FL_PRECOND_FD), ("box", _lib.FL_PRECOND_BOX),
+                     ("plain", _lib.FL_PRECOND_NONE)):
+        u, info = p.solve(gpu(f), tol=1e-9, mode=mode | pm)
+        u = host(u)
+        assert info["converged"] == 1 and np.all(u[~mask] == 0.0)
+        assert rel(op.apply(u), f) <= 1.05e-9
+        its[name] = info["iterations"]
+        sols[name] = u
+    assert rel(sols["domain"], sols["plain"]) <= 1e-6 and rel(sols["box"], sols["plain"]) <= 1e-6
+    print(f"L-shape 64^2, alpha 1.5: iterations {its}")
+    assert its["domain"] < its["box"] < its["plain"]
+
+
+def _octagon(n):
+    i = np.arange(1, n)
+    a = np.minimum(i, n - i)
+    return (a[:, None] + a[None, :]) > n // 4
+
+
+def _l_shape_paper(n):
+    m = n - 1
+    mask = np.ones((m, m), dtype=bool)
+    mask[m - n // 2:, m - n // 2:] = False
+    return mask
+
+
+@pytest.mark.parametrize("shape", ["lshape", "octagon"])
+def test_occluded_tables_first_rows_on_gpu(shape):
+    """Tables tab:L2 and tab:octagon2, n = 128 and 256 (N = 12033 / 48641 and
+    14145 / 56961), alpha = 1.75, f = 1 on Omega, FP64 CG with the FD
+    operator on Omega: the oracle's counts (10 / 14 and 12 / 16, which are
+    the print's for n = 128 and within one of it for n = 256)."""
+    for n, want in ((128, (10, 14)), (256, (12, 16))):
+        mask = _l_shape_paper(n) if shape == "lshape" else _octagon(n)
+        p = Plan(2, mask.shape, 1.0 / n, 1.75, mask=mask)
+        f = gpu(np.where(mask, 1.0, 0.0))
+        got = tuple(p.solve(f, tol=tol, mode=_lib.FL_MODE_F64 | _lib.FL_PRECOND_FD,
+                            maxit=1000)[1]["iterations"] for tol in (1e-6, 1e-9))
+        print(f"{shape} n = {n} (N = {int(mask.sum())}): {got}")
+        assert got == want, (shape, n, got)
 
 
 @pytest.mark.parametrize("theta", [1.0, 0.5])

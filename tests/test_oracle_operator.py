@@ -53,6 +53,30 @@ def test_table_1d_con(golden):
         assert e_sol == pytest.approx(e_sol_paper, rel=0.07), (N, alpha)
 
 
+def test_table_1d_long_rows(golden):
+    """The N = 2047 and 4095 rows (padded lengths 4096 and 8192): e_app of
+    Table tab:1D_con and e_sol of Table tab:1D_erronly2 (f = 1, dense LU)
+    to the printed two digits (5 %).  The e_sol column of Table tab:1D_con
+    is not pinned at these two sizes: the exact discrete solution's error
+    sits 5-18 % (N = 2047) and 1.3-3x (N = 4095) above the print while its
+    e_app matches, which points at the paper's CG stopping point on its
+    largest grids rather than at the operator (recorded as a reading)."""
+    for N, alpha, e_app_paper, _ in golden("table_1d_con_long.txt"):
+        N = int(N)
+        p, x = interval_plan(N, alpha)
+        u = (1 - x ** 2) ** (2 + alpha / 2) / dyda_constant(1, alpha, 2 + alpha / 2)
+        f = special.hyp2f1((1 + alpha) / 2, -2, 0.5, x ** 2)
+        e_app = np.linalg.norm(p.apply(u) - f) / np.linalg.norm(f)
+        assert e_app == pytest.approx(e_app_paper, rel=0.05), (N, alpha, e_app)
+    for N, alpha, e_paper in golden("table_1d_fone_long.txt"):
+        N = int(N)
+        p, x = interval_plan(N, alpha)
+        u = (1 - x ** 2) ** (alpha / 2) / dyda_constant(1, alpha, alpha / 2)
+        us = np.linalg.solve(p.dense_matrix(), np.ones(N))
+        e_sol = np.linalg.norm(us - u) / np.linalg.norm(u)
+        assert e_sol == pytest.approx(e_paper, rel=0.05), (N, alpha, e_sol)
+
+
 def test_table_1d_fone(golden):
     """Solve errors for f = 1 against (1-x^2)^{alpha/2} / K'_alpha."""
     for N, alpha, e_paper in golden("table_1d_fone.txt"):
