@@ -54,6 +54,14 @@ template <typename C> __device__ __forceinline__ C cmake(decltype(C().x) a, decl
 }
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return cmake<C>(a.x + b.x, a.y + b.y); }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { return cmake<C>(a.x - b.x, a.y - b.y); }
+#if defined(__CUDA_ARCH__) && !defined(FL_SCALAR_CADD)
+// FP32: both halves in one paired add (sm_100 family), same rounding as two
+// scalar adds.
+template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) { return __fadd2_rn(a, b); }
+template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
+  return __fadd2_rn(a, make_float2(-b.x, -b.y));
+}
+#endif
 template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
   return cmake<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
