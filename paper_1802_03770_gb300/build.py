@@ -16,10 +16,12 @@ ROOT = os.path.dirname(HERE)
 OUT = os.path.join(HERE, "libfraclap.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-# (source, extra flags, object): ops.cu is compiled in two halves (FP32 and
-# FP64 instantiations) so that its largest part runs in parallel
+# (source, extra flags, object): ops.cu and batch.cu are compiled in two
+# halves each (FP32 and FP64 instantiations) so that their largest parts run
+# in parallel
 CUDA_SOURCES = [("ops.cu", ["-DFL_OPS_PART=1"], "ops_f32.o"), ("ops.cu", ["-DFL_OPS_PART=2"], "ops_f64.o"),
-                ("plan.cu", [], "plan.o"), ("batch.cu", [], "batch.o"), ("unet.cu", [], "unet.o"),
+                ("plan.cu", [], "plan.o"), ("batch.cu", ["-DFL_BATCH_PART=1"], "batch_f32.o"),
+                ("batch.cu", ["-DFL_BATCH_PART=2"], "batch_f64.o"), ("unet.cu", [], "unet.o"),
                 ("learned.cu", [], "learned.o"), ("domain.cu", [], "domain.o")]
 CXX_SOURCES = ["consts.cpp"]
 

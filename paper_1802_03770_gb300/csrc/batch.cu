@@ -116,6 +116,10 @@ __global__ void __launch_bounds__(kVecThreads) kb_noprec_update(const BVecArgs<T
   body_b_noprec<T>(args[i], blockIdx.x - off[i], off[i + 1] - off[i]);
 }
 
+// This file is compiled in two halves (FL_BATCH_PART 1: the FP32 passes and
+// the precision-free kernels, 2: the FP64 passes) so that its template
+// instantiations compile in parallel; without FL_BATCH_PART it holds both.
+#if !defined(FL_BATCH_PART) || FL_BATCH_PART == 1
 // FP64 right-hand side to the FP32 inner right-hand side (masked), with
 // partials of ||b||^2 -- the residual of the zero initial guess.
 __global__ void __launch_bounds__(kVecThreads) kb_cast_rhs(const BVecArgs<double>* __restrict__ args,
@@ -173,6 +177,8 @@ __global__ void kb_sum(const BScalarArgs* __restrict__ args, double* out, int np
   if (threadIdx.x == 0) out[blockIdx.x] = s;
 }
 
+#endif
+
 // --- launchers --------------------------------------------------------------
 
 template <typename T>
@@ -228,6 +234,7 @@ cudaError_t launch_batched(const BatchPass& bp, cudaStream_t s) {
   return launch_status();
 }
 
+#if !defined(FL_BATCH_PART) || FL_BATCH_PART == 1
 cudaError_t launch_cast_rhs(const BatchPass& bp, float* const* out32, cudaStream_t s) {
   if (bp.nprob == 0) return cudaSuccess;
   FL_KERNEL("b_cast_rhs", s,
@@ -246,27 +253,44 @@ cudaError_t launch_batched_scalar(int which, const BScalarArgs* args, double* ou
   return cudaGetLastError();
 }
 
+#endif
+
+static cudaError_t set_batched_smem(const void* f) {
+  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+  return e;
+}
+
+cudaError_t configure_batched_kernels_f64();
+
+#if !defined(FL_BATCH_PART) || FL_BATCH_PART == 1
 cudaError_t configure_batched_kernels() {
-  cudaError_t e = cudaSuccess;
-  auto set = [&](const void* f) {
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
-                               cudaSharedmemCarveoutMaxShared);
-  };
-  set(reinterpret_cast<const void*>(&kb_rows_fwd<float, Cfg<float>::RT, Cfg<float>::RV>));
-  set(reinterpret_cast<const void*>(&kb_rows_fwd<double, Cfg<double>::RT, Cfg<double>::RV>));
-  set(reinterpret_cast<const void*>(&kb_rows_inv<float, Cfg<float>::RT, Cfg<float>::RV>));
-  set(reinterpret_cast<const void*>(&kb_rows_inv<double, Cfg<double>::RT, Cfg<double>::RV>));
-  set(reinterpret_cast<const void*>(&kb_cols<float, Cfg<float>::CT, Cfg<float>::CV>));
-  set(reinterpret_cast<const void*>(&kb_cols<double, Cfg<double>::CT, Cfg<double>::CV>));
-  set(reinterpret_cast<const void*>(&kb_dst_rows<float, Cfg<float>::RT, Cfg<float>::RV>));
-  set(reinterpret_cast<const void*>(&kb_dst_cols<float, Cfg<float>::CT, Cfg<float>::CV>));
+  cudaError_t e = configure_batched_kernels_f64();
+  for (const void* f : {reinterpret_cast<const void*>(&kb_rows_fwd<float, Cfg<float>::RT, Cfg<float>::RV>),
+                        reinterpret_cast<const void*>(&kb_rows_inv<float, Cfg<float>::RT, Cfg<float>::RV>),
+                        reinterpret_cast<const void*>(&kb_cols<float, Cfg<float>::CT, Cfg<float>::CV>),
+                        reinterpret_cast<const void*>(&kb_dst_rows<float, Cfg<float>::RT, Cfg<float>::RV>),
+                        reinterpret_cast<const void*>(&kb_dst_cols<float, Cfg<float>::CT, Cfg<float>::CV>)})
+    if (e == cudaSuccess) e = set_batched_smem(f);
   return e;
 }
 
 template cudaError_t launch_batched<float>(const BatchPass&, cudaStream_t);
+#endif
+
+#if !defined(FL_BATCH_PART) || FL_BATCH_PART == 2
+cudaError_t configure_batched_kernels_f64() {
+  cudaError_t e = cudaSuccess;
+  for (const void* f : {reinterpret_cast<const void*>(&kb_rows_fwd<double, Cfg<double>::RT, Cfg<double>::RV>),
+                        reinterpret_cast<const void*>(&kb_rows_inv<double, Cfg<double>::RT, Cfg<double>::RV>),
+                        reinterpret_cast<const void*>(&kb_cols<double, Cfg<double>::CT, Cfg<double>::CV>)})
+    if (e == cudaSuccess) e = set_batched_smem(f);
+  return e;
+}
+
 template cudaError_t launch_batched<double>(const BatchPass&, cudaStream_t);
+#endif
 
 }  // namespace fl

@@ -59,7 +59,7 @@ template <> struct Cfg<double> {
 
 constexpr int kVecBlocks = 608;   // 4 x 152 SMs, fixed for deterministic partials
 constexpr int kVecThreads = 256;
-constexpr int kMaxTx = 64;
+constexpr int kMaxTx = 1 << kMaxLtx;
 constexpr int kSmemLimit = 200 * 1024;
 constexpr int kMaxLen = 8192;     // longest padded FFT line
 
@@ -93,6 +93,11 @@ template <typename T> inline size_t smem_bytes(int lines, int L) {
 // interleaved tile of tx columns of length L (padded, SBuf)
 template <typename T> inline size_t tile_bytes(int tx, int L) {
   return (size_t)sbuf_elems((long long)tx * L) * sizeof(typename Cplx<T>::type);
+}
+// shared-memory bytes of a convolution pass: the FFT tile and, beside it,
+// the symbol's rows 0..L/2 for the tile's columns
+template <typename T> inline size_t conv_tile_bytes(int tx, int L) {
+  return tile_bytes<T>(tx, L) + (size_t)(L / 2 + 1) * tx * sizeof(T);
 }
 inline int ilog2i(int v) {
   int l = 0;

@@ -7,7 +7,8 @@
 // radix-R DFT in registers and writes leg r to (j / Ns) Ns R + k + r Ns
 // (Govindaraju et al., SC'08).  After the last stage the line is in natural
 // order.  Stages are radix 16 (when a thread may hold 16 values), then radix
-// 8, with one radix-4 or radix-2 stage for the remainder of log2 L.
+// 8, with one radix-4 or radix-2 stage for the remainder of log2 L (see
+// FftPlan).
 //
 // Every stage is in place: each thread loads all legs of the butterflies it
 // owns into registers, the CTA synchronises, then every thread writes.  The
@@ -318,10 +319,12 @@ __device__ __forceinline__ void stage_ct(SBuf<C> buf, int ls, int ltx, int nline
 
 // Stage plan of a length-2^LG transform with VPT values per thread: radix 16
 // while at least four factors of two remain (if VPT allows), then radix 8,
-// then one radix-4 or radix-2 stage (n16, n8, tail).
+// then one radix-4 or radix-2 stage (n16, n8, tail).  A radix-2 remainder
+// (LG = 1 mod 4) is avoided by taking 8 x 4 for the last 16 x 2: a radix-2
+// stage gives every thread VPT/2 butterflies, each with its own twiddle.
 template <int LG, int VPT>
 struct FftPlan {
-  static constexpr int n16 = VPT >= 16 ? LG / 4 : 0;
+  static constexpr int n16 = VPT >= 16 ? (LG % 4 == 1 && LG >= 5 ? LG / 4 - 1 : LG / 4) : 0;
   static constexpr int n8 = (LG - 4 * n16) / 3;
   static constexpr int tail = LG - 4 * n16 - 3 * n8;
   static constexpr int S = n16 + n8 + (tail > 0 ? 1 : 0);

@@ -113,6 +113,19 @@ constexpr int min_ctas(int threads, int lglo = 4) {
   return lglo > 4 ? 1 : (threads <= 128 ? FL_ROW_MIN_CTAS : 2);
 }
 
+// Column tiles: at most 2^kMaxLtx columns; a CTA of THREADS x VPT values
+// holds 2^widest_ltx columns of lines of 2^lg.  The strided passes run the
+// widest tile of every length from 2^kFixedLgMin up with the length and the
+// width as compile-time constants (their bodies are inlined with constant
+// arguments, so the index arithmetic of the loads, the stages and the
+// epilogues folds); other shapes (tuned narrower tiles, short lines) take
+// the same body with runtime values.
+constexpr int kMaxLtx = 6;
+constexpr int kFixedLgMin = 8;
+__host__ __device__ constexpr int widest_ltx(int threads, int vpt, int lg) {
+  return clog2(threads * vpt) - lg < kMaxLtx ? clog2(threads * vpt) - lg : kMaxLtx;
+}
+
 // CTA-wide sum of one value per thread; result valid in thread 0.
 __device__ __forceinline__ double cta_sum(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -254,13 +267,13 @@ struct RowsFwdArgs {
   int pre;
 };
 
-template <typename T, int THREADS, int VPT, int LGLO = 4, int LGHI = clog2(THREADS * VPT)>
-__device__ __forceinline__ void body_rows_fwd(const RowsFwdArgs<T>& a, int bx, int by) {
+template <typename T, int THREADS, int VPT, int LGLO, int LGHI>
+__device__ __forceinline__ void body_rows_fwd_at(const RowsFwdArgs<T>& a, int bx, int by, const int lg) {
   typedef typename Cplx<T>::type C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SBuf<C> buf{reinterpret_cast<C*>(smem_raw)};
   if (a.st && a.st->done) return;
-  const int L = 1 << a.lg;
+  const int L = 1 << lg;
   const int ls = L;
   const int NL = (VPT * THREADS) / L;       // complex lines (row pairs) per CTA
   const int pair0 = bx * NL;
@@ -278,7 +291,7 @@ __device__ __forceinline__ void body_rows_fwd(const RowsFwdArgs<T>& a, int bx, i
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int e = e0 + u * THREADS;
-      const int q = e >> (a.lg - 1), j = e & (hL - 1);
+      const int q = e >> (lg - 1), j = e & (hL - 1);
       const int ra = 2 * (pair0 + q), rb = ra + 1;
       va[u] = 0;
       vb[u] = 0;
@@ -302,7 +315,7 @@ __device__ __forceinline__ void body_rows_fwd(const RowsFwdArgs<T>& a, int bx, i
     for (int u = 0; u < U; ++u) {
       const int e = e0 + u * THREADS;
       if (e >= tot) continue;
-      const int q = e >> (a.lg - 1), j = e & (hL - 1);
+      const int q = e >> (lg - 1), j = e & (hL - 1);
       const int ra = 2 * (pair0 + q), rb = ra + 1;
       T xa = va[u], xb = vb[u];
       if (j < a.n) {
@@ -327,7 +340,7 @@ __device__ __forceinline__ void body_rows_fwd(const RowsFwdArgs<T>& a, int bx, i
   {
     auto ld = [=](int q, int k) -> C { return k < hL ? buf[q * ls + k] : cmake<C>((T)0, (T)0); };
     auto st = [=](int q, int k, C v) { buf[q * ls + k] = v; };
-    fft_io<VPT, false, true, LGHI, LGLO>(buf, a.lg, ls, 0, nl, a.tw, a.lgmax, false, ld,
+    fft_io<VPT, false, true, LGHI, LGLO>(buf, lg, ls, 0, nl, a.tw, a.lgmax, false, ld,
                                                        true, st, true);
   }
   __syncthreads();
@@ -347,6 +360,26 @@ __device__ __forceinline__ void body_rows_fwd(const RowsFwdArgs<T>& a, int bx, i
       if (hb) Sb[k] = cmake<C>((z.y - w.y) * (T)0.5, (w.x - z.x) * (T)0.5);
     }
   }
+}
+
+// body_rows_fwd with the line length 2^LG .. 2^LGHI as a compile-time
+// constant (the lengths below 2^kFixedLgMin at run time)
+template <typename T, int THREADS, int VPT, int LGLO, int LGHI, int LG>
+__device__ __forceinline__ void body_rows_fwd_fixed(const RowsFwdArgs<T>& a, int bx, int by) {
+  if constexpr (LG <= LGHI) {
+    if (a.lg == LG) {
+      body_rows_fwd_at<T, THREADS, VPT, LGLO, LGHI>(a, bx, by, LG);
+      return;
+    }
+    body_rows_fwd_fixed<T, THREADS, VPT, LGLO, LGHI, LG + 1>(a, bx, by);
+  } else if constexpr (LGLO < kFixedLgMin) {
+    body_rows_fwd_at<T, THREADS, VPT, LGLO, LGHI>(a, bx, by, a.lg);
+  }
+}
+
+template <typename T, int THREADS, int VPT, int LGLO = 4, int LGHI = clog2(THREADS * VPT)>
+__device__ __forceinline__ void body_rows_fwd(const RowsFwdArgs<T>& a, int bx, int by) {
+  body_rows_fwd_fixed<T, THREADS, VPT, LGLO, LGHI, (LGLO > kFixedLgMin ? LGLO : kFixedLgMin)>(a, bx, by);
 }
 
 template <typename T, int THREADS, int VPT, int LGLO = 4>
@@ -380,15 +413,15 @@ struct ColsArgs {
 // The tile is kept in its natural layout, buf[r * TX + c] (row r of the line,
 // column c), and transformed with the interleaved-line FFT; global loads are
 // issued U at a time so that several are in flight per thread.
-template <typename T, int THREADS, int VPT, int LGLO = 4, int LGHI = clog2(THREADS * VPT)>
-__device__ __forceinline__ void body_cols(const ColsArgs<T>& a, int bx, int by) {
+template <typename T, int THREADS, int VPT, int LGLO, int LGHI>
+__device__ __forceinline__ void body_cols_at(const ColsArgs<T>& a, int bx, int by, const int lg,
+                                             const int ltx) {
   typedef typename Cplx<T>::type C;
   constexpr int U = 8;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SBuf<C> buf{reinterpret_cast<C*>(smem_raw)};
   if (a.st && a.st->done) return;
-  const int L = 1 << a.lg;
-  const int ltx = a.ltx;
+  const int L = 1 << lg;
   const int TX = 1 << ltx;
   const int kx0 = bx * TX;
   const int o = by;
@@ -398,6 +431,22 @@ __device__ __forceinline__ void body_cols(const ColsArgs<T>& a, int bx, int by) 
   // the tile is written, the transform's first stage reads the rest as zeros
   const int hL = L >> 1;
   const int total = TX * (a.mode == COLS_CONV ? hL : L);
+  // convolution: the symbol's rows kk = 0..L/2 for the tile's columns are
+  // staged in shared memory beside the FFT tile (ssig[kk * TX + c]); their
+  // loads are issued together with the tile's, so that the forward
+  // transform's last stage multiplies without a global load in flight
+  T* ssig = reinterpret_cast<T*>(smem_raw + sbuf_elems((long long)TX * L) * sizeof(C));
+  const T* __restrict__ sig = a.sig + kx0;
+  if (a.mode == COLS_CONV && a.Lo) sig += (size_t)min(o, a.Lo - o) * a.sig_outer;
+  const int nsym = a.mode == COLS_CONV ? ((hL + 1) << ltx) : 0;
+  constexpr int SU = VPT / 2 + 1;   // (L/2 + 1) TX <= SU THREADS when TX <= THREADS
+  T sv[SU];
+#pragma unroll
+  for (int u = 0; u < SU; ++u) {
+    const int e = threadIdx.x + u * THREADS;
+    const int kk = e >> ltx, c = e & (TX - 1);
+    sv[u] = (e < nsym && c < ncol) ? sig[(size_t)kk * a.sig_line + c] : (T)0;
+  }
   for (int e0 = threadIdx.x; e0 < total; e0 += THREADS * U) {
     C v[U];
 #pragma unroll
@@ -413,18 +462,22 @@ __device__ __forceinline__ void body_cols(const ColsArgs<T>& a, int bx, int by) 
       if (e < total) buf[e] = v[u];
     }
   }
+#pragma unroll
+  for (int u = 0; u < SU; ++u) {
+    const int e = threadIdx.x + u * THREADS;
+    if (e < nsym) ssig[e] = sv[u];
+  }
+  for (int e = threadIdx.x + SU * THREADS; e < nsym; e += THREADS) {
+    const int kk = e >> ltx, c = e & (TX - 1);
+    ssig[e] = c < ncol ? sig[(size_t)kk * a.sig_line + c] : (T)0;
+  }
   __syncthreads();
   if (a.mode == COLS_CONV) {
-    // forward FFT whose last stage multiplies by the symbol on the way out
-    const size_t soff = a.Lo ? (size_t)min(o, a.Lo - o) * a.sig_outer : 0;
-    const T* __restrict__ sig = a.sig + soff + kx0;
-    const long long sig_line = a.sig_line;
+    // forward FFT whose last stage multiplies by the staged symbol on the
+    // way out (columns beyond ncol are scaled by 0 and never stored)
     auto ld = [=](int c, int k) -> C { return k < hL ? buf[(k << ltx) + c] : cmake<C>((T)0, (T)0); };
-    auto epi = [=](int c, int k, C v) {
-      if (c < ncol) v = cscale(v, sig[(size_t)min(k, L - k) * sig_line + c]);
-      buf[(k << ltx) + c] = v;
-    };
-    fft_io<VPT, true, true, LGHI, LGLO>(buf, a.lg, 0, ltx, TX, a.tw, a.lgmax, false, ld,
+    auto epi = [=](int c, int k, C v) { buf[(k << ltx) + c] = cscale(v, ssig[(min(k, L - k) << ltx) + c]); };
+    fft_io<VPT, true, true, LGHI, LGLO>(buf, lg, 0, ltx, TX, a.tw, a.lgmax, false, ld,
                                                       true, epi, true);
     __syncthreads();
     // inverse FFT whose last stage writes the kept rows to global
@@ -434,16 +487,37 @@ __device__ __forceinline__ void body_cols(const ColsArgs<T>& a, int bx, int by) 
     auto epi2 = [=](int c, int k, C v) {
       if (c < ncol && k < rows_out) base[(size_t)k * lstride + c] = v;
     };
-    fft_io<VPT, true, false, LGHI, LGLO>(buf, a.lg, 0, ltx, TX, a.tw, a.lgmax, true, ld2,
+    fft_io<VPT, true, false, LGHI, LGLO>(buf, lg, 0, ltx, TX, a.tw, a.lgmax, true, ld2,
                                                        true, epi2, false);
     return;
   }
-  fft_smem<VPT, true, LGHI, LGLO>(buf, a.lg, 0, ltx, TX, a.tw, a.lgmax, a.mode == COLS_INV);
+  fft_smem<VPT, true, LGHI, LGLO>(buf, lg, 0, ltx, TX, a.tw, a.lgmax, a.mode == COLS_INV);
   const int tout = TX * a.rows_out;
   for (int e = threadIdx.x; e < tout; e += THREADS) {
     const int r = e >> ltx, c = e & (TX - 1);
     if (c < ncol) base[(size_t)r * a.lstride + c] = buf[e];
   }
+}
+
+// body_cols for the widest tile of lengths 2^LG .. 2^LGHI as compile-time
+// shapes, else with the plan's runtime shape
+template <typename T, int THREADS, int VPT, int LGLO, int LGHI, int LG>
+__device__ __forceinline__ void body_cols_fixed(const ColsArgs<T>& a, int bx, int by) {
+  if constexpr (LG <= LGHI) {
+    constexpr int W = widest_ltx(THREADS, VPT, LG);
+    if (a.lg == LG && a.ltx == W) {
+      body_cols_at<T, THREADS, VPT, LGLO, LGHI>(a, bx, by, LG, W);
+      return;
+    }
+    body_cols_fixed<T, THREADS, VPT, LGLO, LGHI, LG + 1>(a, bx, by);
+  } else {
+    body_cols_at<T, THREADS, VPT, LGLO, LGHI>(a, bx, by, a.lg, a.ltx);
+  }
+}
+
+template <typename T, int THREADS, int VPT, int LGLO = 4, int LGHI = clog2(THREADS * VPT)>
+__device__ __forceinline__ void body_cols(const ColsArgs<T>& a, int bx, int by) {
+  body_cols_fixed<T, THREADS, VPT, LGLO, LGHI, (LGLO > kFixedLgMin ? LGLO : kFixedLgMin)>(a, bx, by);
 }
 
 template <typename T, int THREADS, int VPT, int LGLO = 4>
@@ -481,14 +555,14 @@ struct RowsInvArgs {
   T* outm;                 // nullable: M x itself (restricted to Omega)
 };
 
-template <typename T, int THREADS, int VPT, int LGLO = 4, int LGHI = clog2(THREADS * VPT)>
-__device__ __forceinline__ void body_rows_inv(const RowsInvArgs<T>& a, int bx, int by) {
+template <typename T, int THREADS, int VPT, int LGLO, int LGHI>
+__device__ __forceinline__ void body_rows_inv_at(const RowsInvArgs<T>& a, int bx, int by, const int lg) {
   typedef typename Cplx<T>::type C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SBuf<C> buf{reinterpret_cast<C*>(smem_raw)};
   __shared__ double red[32];
   if (a.st && a.st->done) return;
-  const int L = 1 << a.lg;
+  const int L = 1 << lg;
   const int ls = L;
   const int NL = (VPT * THREADS) / L;
   const int pair0 = bx * NL;
@@ -513,7 +587,7 @@ __device__ __forceinline__ void body_rows_inv(const RowsInvArgs<T>& a, int bx, i
     }
   }
   __syncthreads();
-  fft_smem<VPT, false, LGHI, LGLO>(buf, a.lg, ls, 0, nl, a.tw, a.lgmax, true);
+  fft_smem<VPT, false, LGHI, LGLO>(buf, lg, ls, 0, nl, a.tw, a.lgmax, true);
   DotAcc<T> part;
   const T* __restrict__ xin = (a.cx != 0.0) ? a.x : nullptr;
   const T* __restrict__ bin = (a.cb != 0.0) ? a.b : nullptr;
@@ -553,6 +627,26 @@ __device__ __forceinline__ void body_rows_inv(const RowsInvArgs<T>& a, int bx, i
       }
     }
   }
+}
+
+// body_rows_inv with the line length 2^LG .. 2^LGHI as a compile-time
+// constant (the lengths below 2^kFixedLgMin at run time)
+template <typename T, int THREADS, int VPT, int LGLO, int LGHI, int LG>
+__device__ __forceinline__ void body_rows_inv_fixed(const RowsInvArgs<T>& a, int bx, int by) {
+  if constexpr (LG <= LGHI) {
+    if (a.lg == LG) {
+      body_rows_inv_at<T, THREADS, VPT, LGLO, LGHI>(a, bx, by, LG);
+      return;
+    }
+    body_rows_inv_fixed<T, THREADS, VPT, LGLO, LGHI, LG + 1>(a, bx, by);
+  } else if constexpr (LGLO < kFixedLgMin) {
+    body_rows_inv_at<T, THREADS, VPT, LGLO, LGHI>(a, bx, by, a.lg);
+  }
+}
+
+template <typename T, int THREADS, int VPT, int LGLO = 4, int LGHI = clog2(THREADS * VPT)>
+__device__ __forceinline__ void body_rows_inv(const RowsInvArgs<T>& a, int bx, int by) {
+  body_rows_inv_fixed<T, THREADS, VPT, LGLO, LGHI, (LGLO > kFixedLgMin ? LGLO : kFixedLgMin)>(a, bx, by);
 }
 
 template <typename T, int THREADS, int VPT, int LGLO = 4>
@@ -614,14 +708,14 @@ struct DstRowsArgs {
   const T* add;
 };
 
-template <typename T, int THREADS, int VPT, int LGLO = 4, int LGHI = clog2(THREADS * VPT)>
-__device__ __forceinline__ void body_dst_rows(const DstRowsArgs<T>& a, int bx, int by) {
+template <typename T, int THREADS, int VPT, int LGLO, int LGHI>
+__device__ __forceinline__ void body_dst_rows_at(const DstRowsArgs<T>& a, int bx, int by, const int lg) {
   typedef typename Cplx<T>::type C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SBuf<C> buf{reinterpret_cast<C*>(smem_raw)};
   __shared__ double red[32];
   if (a.st && a.st->done) return;
-  const int L = 1 << a.lg;
+  const int L = 1 << lg;
   const int ls = L;
   const int NL = (VPT * THREADS) / L;
   const int row0 = bx * NL;
@@ -643,7 +737,7 @@ __device__ __forceinline__ void body_dst_rows(const DstRowsArgs<T>& a, int bx, i
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int e = e0 + u * THREADS;
-        const int q = e >> (a.lg - 1), j = e & (hL - 1);
+        const int q = e >> (lg - 1), j = e & (hL - 1);
         xo[u] = ro[u] = po[u] = qo[u] = (T)0;
         if (e < tot && j < a.n) {
           const size_t idx = (size_t)(row0 + q) * a.n + j;
@@ -657,7 +751,7 @@ __device__ __forceinline__ void body_dst_rows(const DstRowsArgs<T>& a, int bx, i
       for (int u = 0; u < U; ++u) {
         const int e = e0 + u * THREADS;
         if (e >= tot) continue;
-        const int q = e >> (a.lg - 1), j = e & (hL - 1);
+        const int q = e >> (lg - 1), j = e & (hL - 1);
         C v = cmake<C>((T)0, (T)0);
         if (j < a.n) {
           const size_t idx = (size_t)(row0 + q) * a.n + j;
@@ -673,7 +767,7 @@ __device__ __forceinline__ void body_dst_rows(const DstRowsArgs<T>& a, int bx, i
   } else {
 #pragma unroll 4
     for (int e = threadIdx.x; e < tot; e += THREADS) {
-      const int q = e >> (a.lg - 1), j = e & (hL - 1);
+      const int q = e >> (lg - 1), j = e & (hL - 1);
       C v = cmake<C>((T)0, (T)0);
       if (j < a.n) {
         const size_t idx = (size_t)(row0 + q) * a.n + j;
@@ -688,7 +782,7 @@ __device__ __forceinline__ void body_dst_rows(const DstRowsArgs<T>& a, int bx, i
     const C* __restrict__ bhat = a.bhat;
     auto ld = [=](int q, int k) -> C { return k < hL ? buf[q * ls + k] : cmake<C>((T)0, (T)0); };
     auto epi = [=](int q, int k, C v) { buf[q * ls + k] = cmul(v, bhat[k]); };
-    fft_io<VPT, false, true, LGHI, LGLO>(buf, a.lg, ls, 0, nl, a.tw, a.lgmax, false, ld,
+    fft_io<VPT, false, true, LGHI, LGLO>(buf, lg, ls, 0, nl, a.tw, a.lgmax, false, ld,
                                                        true, epi, true);
   }
   __syncthreads();
@@ -711,7 +805,7 @@ __device__ __forceinline__ void body_dst_rows(const DstRowsArgs<T>& a, int bx, i
         if (dw) dp.add(o * dw[idx]);
       }
     };
-    fft_io<VPT, false, false, LGHI, LGLO>(buf, a.lg, ls, 0, nl, a.tw, a.lgmax, true, ld,
+    fft_io<VPT, false, false, LGHI, LGLO>(buf, lg, ls, 0, nl, a.tw, a.lgmax, true, ld,
                                                         true, epi, false);
   }
   if (a.pre == DPRE_UPDATE) {
@@ -727,6 +821,26 @@ __device__ __forceinline__ void body_dst_rows(const DstRowsArgs<T>& a, int bx, i
       if (threadIdx.x == 0) pcg_step(a.st, rrv, rz);
     }
   }
+}
+
+// body_dst_rows with the line length 2^LG .. 2^LGHI as a compile-time
+// constant (the lengths below 2^kFixedLgMin at run time)
+template <typename T, int THREADS, int VPT, int LGLO, int LGHI, int LG>
+__device__ __forceinline__ void body_dst_rows_fixed(const DstRowsArgs<T>& a, int bx, int by) {
+  if constexpr (LG <= LGHI) {
+    if (a.lg == LG) {
+      body_dst_rows_at<T, THREADS, VPT, LGLO, LGHI>(a, bx, by, LG);
+      return;
+    }
+    body_dst_rows_fixed<T, THREADS, VPT, LGLO, LGHI, LG + 1>(a, bx, by);
+  } else if constexpr (LGLO < kFixedLgMin) {
+    body_dst_rows_at<T, THREADS, VPT, LGLO, LGHI>(a, bx, by, a.lg);
+  }
+}
+
+template <typename T, int THREADS, int VPT, int LGLO = 4, int LGHI = clog2(THREADS * VPT)>
+__device__ __forceinline__ void body_dst_rows(const DstRowsArgs<T>& a, int bx, int by) {
+  body_dst_rows_fixed<T, THREADS, VPT, LGLO, LGHI, (LGLO > kFixedLgMin ? LGLO : kFixedLgMin)>(a, bx, by);
 }
 
 template <typename T, int THREADS, int VPT, int LGLO = 4>
@@ -753,15 +867,15 @@ struct DstColsArgs {
   int ltx;
 };
 
-template <typename T, int THREADS, int VPT, int LGLO = 4, int LGHI = clog2(THREADS * VPT)>
-__device__ __forceinline__ void body_dst_cols(const DstColsArgs<T>& a, int bx, int by) {
+template <typename T, int THREADS, int VPT, int LGLO, int LGHI>
+__device__ __forceinline__ void body_dst_cols_at(const DstColsArgs<T>& a, int bx, int by, const int lg,
+                                                 const int ltx) {
   typedef typename Cplx<T>::type C;
   constexpr int U = 8;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SBuf<C> buf{reinterpret_cast<C*>(smem_raw)};
   if (a.st && a.st->done) return;
-  const int L = 1 << a.lg;
-  const int ltx = a.ltx;
+  const int L = 1 << lg;
   const int TX = 1 << ltx;
   const int c0 = bx * TX;
   const int o = by;
@@ -785,7 +899,7 @@ __device__ __forceinline__ void body_dst_cols(const DstColsArgs<T>& a, int bx, i
     }
   }
   __syncthreads();
-  chirp_conv_il<VPT, LGHI>(buf, ltx, L, a.lg, a.lgmax, a.tw, a.bhat);
+  chirp_conv_il<VPT, LGHI>(buf, ltx, L, lg, a.lgmax, a.tw, a.bhat);
   const int tout = TX * a.n;
   const T post = (T)a.post;
   for (int e = threadIdx.x; e < tout; e += THREADS) {
@@ -795,6 +909,25 @@ __device__ __forceinline__ void body_dst_cols(const DstColsArgs<T>& a, int bx, i
       base[(size_t)r * a.lstride + c] = y.y * post;
     }
   }
+}
+
+template <typename T, int THREADS, int VPT, int LGLO, int LGHI, int LG>
+__device__ __forceinline__ void body_dst_cols_fixed(const DstColsArgs<T>& a, int bx, int by) {
+  if constexpr (LG <= LGHI) {
+    constexpr int W = widest_ltx(THREADS, VPT, LG);
+    if (a.lg == LG && a.ltx == W) {
+      body_dst_cols_at<T, THREADS, VPT, LGLO, LGHI>(a, bx, by, LG, W);
+      return;
+    }
+    body_dst_cols_fixed<T, THREADS, VPT, LGLO, LGHI, LG + 1>(a, bx, by);
+  } else {
+    body_dst_cols_at<T, THREADS, VPT, LGLO, LGHI>(a, bx, by, a.lg, a.ltx);
+  }
+}
+
+template <typename T, int THREADS, int VPT, int LGLO = 4, int LGHI = clog2(THREADS * VPT)>
+__device__ __forceinline__ void body_dst_cols(const DstColsArgs<T>& a, int bx, int by) {
+  body_dst_cols_fixed<T, THREADS, VPT, LGLO, LGHI, (LGLO > kFixedLgMin ? LGLO : kFixedLgMin)>(a, bx, by);
 }
 
 template <typename T, int THREADS, int VPT, int LGLO = 4>
