@@ -136,7 +136,11 @@ def make_rhs(seed):
 # arrays stay in L2.  An entry holds only for the kernel source it was taken
 # from: it is keyed by the SHA-256 of the CUDA sources (kernel_source_sha)
 # and reported as null for any other source.
-NCU_DRAM_BYTES = {}
+NCU_DRAM_BYTES = {
+    # k_dst_rows<float, 128, 16>, 1024^2: 16920832 (first pass) and 8570112
+    # (last pass) bytes read, 0 written (profiles/dst_rows_f32_2d1024.md)
+    "dst_rows<f32>": ("e2451693f203ddda", 12745472),
+}
 
 
 def kernel_source_sha():
@@ -600,6 +604,23 @@ def profile_case():
     print(json.dumps(info))
 
 
+def profile_case_3d(n=256):
+    """Five FP32 applies on the 3D time-step grid (n^3 interior, (2n)^3 padded
+    FFT), from a seeded field; the passes of the first are the captured ones."""
+    import torch
+    from paper_1802_03770_gb300 import inputs
+    from paper_1802_03770_gb300.api import Plan
+    p = Plan(3, (n, n, n), 1.0 / (n + 1), 1.5)
+    x = torch.tensor(inputs.gaussian_mixture(n, 3, 16, 3, 0.05, 0.15), dtype=torch.float32,
+                     device="cuda:0").view(-1)
+    y = torch.empty_like(x)
+    for _ in range(5):
+        p.apply(x, y)
+    torch.cuda.synchronize()
+    print(json.dumps({"n": n, "y_norm": float(y.norm())}))
+    p.close()
+
+
 def cores_used():
     try:
         return len(os.sched_getaffinity(0))
@@ -618,9 +639,14 @@ def main():
     ap.add_argument("--no-3d", action="store_true", help="skip the 3D 256^3 time-step entry")
     ap.add_argument("--profile-case", action="store_true",
                     help="run two mixed solves at alpha = 1.5 and exit (for ncu captures)")
+    ap.add_argument("--profile-case-3d", action="store_true",
+                    help="run five FP32 applies on the 256^3 grid and exit (for ncu captures)")
     args = ap.parse_args()
     if args.profile_case:
         profile_case()
+        return
+    if args.profile_case_3d:
+        profile_case_3d()
         return
     rank, world, local = dist_env()
     config = {"workload": WORKLOAD, "n": N_SIDE, "fft_len": 2 * N_SIDE, "alphas": list(ALPHAS),

@@ -94,10 +94,15 @@ template <typename T> inline size_t smem_bytes(int lines, int L) {
 template <typename T> inline size_t tile_bytes(int tx, int L) {
   return (size_t)sbuf_elems((long long)tx * L) * sizeof(typename Cplx<T>::type);
 }
-// shared-memory bytes of a convolution pass: the FFT tile and, beside it,
-// the symbol's rows 0..L/2 for the tile's columns
+// shared-memory bytes of a strided pass: the FFT tile, then (FP32) the
+// line length's twiddle table
+template <typename T> inline size_t cols_bytes(int tx, int L) {
+  return tile_bytes<T>(tx, L) + (sizeof(T) == 4 ? (size_t)L * sizeof(typename Cplx<T>::type) : 0);
+}
+// ... and for a convolution pass, then the symbol's rows 0..L/2 for the
+// tile's columns
 template <typename T> inline size_t conv_tile_bytes(int tx, int L) {
-  return tile_bytes<T>(tx, L) + (size_t)(L / 2 + 1) * tx * sizeof(T);
+  return cols_bytes<T>(tx, L) + (size_t)(L / 2 + 1) * tx * sizeof(T);
 }
 inline int ilog2i(int v) {
   int l = 0;

@@ -171,16 +171,17 @@ template <> struct LogR<8> { static constexpr int v = 3; };
 template <> struct LogR<16> { static constexpr int v = 4; };
 
 // w[r] = w1^r, r = 0..R-1, for w1 = exp(-2 pi i step / Lmax) (conjugated
-// for the inverse).  FP64: every power is loaded from the long-double table
-// tw (GB300's FP64 rate makes the loads cheaper than products).  FP32: w1 = sincospif(-2 step / Lmax) (the
+// for the inverse).  FP64, and FP32 with TWT (tw then points to a copy of
+// the table in shared memory): every power is loaded from the long-double
+// table tw (GB300's FP64 rate makes the loads cheaper than products).  FP32: w1 = sincospif(-2 step / Lmax) (the
 // argument is exact), w2, w4, w8 by squaring, the rest by products -- no
 // table load on the stage's critical path (measured 3 % faster solves on
 // the 1024^2 workload than the table, at unchanged iteration counts).
-template <int R, typename C>
+template <int R, bool TWT = false, typename C>
 __device__ __forceinline__ void twiddles(const C* __restrict__ tw, int step, bool inv, C* w, int lgmax) {
   auto ld = [&](int i) {
     C t;
-    if constexpr (sizeof(t.x) == 4) {
+    if constexpr (sizeof(t.x) == 4 && !TWT) {
       float sn, cs;
       sincospif(-(float)i * ldexpf(1.0f, 1 - lgmax), &sn, &cs);
       t.x = cs;
@@ -192,9 +193,9 @@ __device__ __forceinline__ void twiddles(const C* __restrict__ tw, int step, boo
     return t;
   };
   w[0] = cmake<C>(1, 0);
-  if constexpr (sizeof(w[0].x) == 8) {
-    // FP64: every power straight from the table (loads instead of FP64
-    // products; r * step < Lmax)
+  if constexpr (sizeof(w[0].x) == 8 || TWT) {
+    // FP64, and FP32 with a table (TWT): every power straight from the table
+    // (loads instead of products; r * step < Lmax)
 #pragma unroll
     for (int r = 1; r < R; ++r) w[r] = ld(r * step);
     return;
@@ -236,8 +237,8 @@ enum { STAGE_FIRST = 0, STAGE_MID = 1, STAGE_LAST = 2 };
 __device__ __forceinline__ int sbuf_phys(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int clog2(int x) { return x <= 1 ? 0 : 1 + clog2(x / 2); }
 
-template <int R, int VPT, bool IL, int LG, int NS, int MODE, bool HALF, typename C, typename Load,
-          typename Epi>
+template <int R, int VPT, bool IL, int LG, int NS, int MODE, bool HALF, bool TWT, typename C,
+          typename Load, typename Epi>
 __device__ __forceinline__ void stage_ct(SBuf<C> buf, int ls, int ltx, int nlines,
                                          const C* __restrict__ tw, int lgmax, bool inv, Load& load,
                                          Epi& epi, bool sync_io) {
@@ -277,7 +278,7 @@ __device__ __forceinline__ void stage_ct(SBuf<C> buf, int ls, int ltx, int nline
         if (NS > 1 && k != 0) {
           // twiddle w^(r k) = tw[r * k * Lmax / (NS R)]
           C w[R];
-          twiddles<R>(tw, k << (lgmax - clog2(NS * R)), inv, w, lgmax);
+          twiddles<R, TWT>(tw, k << (lgmax - clog2(NS * R)), inv, w, lgmax);
 #pragma unroll
           for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], w[r]);
         }
@@ -334,7 +335,7 @@ struct FftPlan {
   __host__ __device__ static constexpr int ns(int s) { return s == 0 ? 1 : ns(s - 1) * radix(s - 1); }
 };
 
-template <int LG, int VPT, bool IL, bool HALF, int ST, typename C, typename Load, typename Epi>
+template <int LG, int VPT, bool IL, bool HALF, bool TWT, int ST, typename C, typename Load, typename Epi>
 __device__ __forceinline__ void fft_io_stage(SBuf<C> buf, int ls, int ltx, int nlines,
                                              const C* __restrict__ tw, int lgmax, bool inv, Load load,
                                              bool sync_load, Epi epi, bool sync_epi) {
@@ -342,11 +343,11 @@ __device__ __forceinline__ void fft_io_stage(SBuf<C> buf, int ls, int ltx, int n
   constexpr int R = P::radix(ST);
   constexpr int Ns = P::ns(ST);
   constexpr int MODE = ST == 0 ? STAGE_FIRST : (ST == P::S - 1 ? STAGE_LAST : STAGE_MID);
-  stage_ct<R, VPT, IL, LG, Ns, MODE, HALF>(buf, ls, ltx, nlines, tw, lgmax, inv, load, epi,
-                                     MODE == STAGE_FIRST ? sync_load : sync_epi);
+  stage_ct<R, VPT, IL, LG, Ns, MODE, HALF, TWT>(buf, ls, ltx, nlines, tw, lgmax, inv, load, epi,
+                                          MODE == STAGE_FIRST ? sync_load : sync_epi);
   if constexpr (ST + 1 < P::S)
-    fft_io_stage<LG, VPT, IL, HALF, ST + 1>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi,
-                                          sync_epi);
+    fft_io_stage<LG, VPT, IL, HALF, TWT, ST + 1>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load,
+                                               epi, sync_epi);
 }
 
 // A full transform of `nlines` lines (IL: 2^ltx interleaved lines) of length
@@ -355,19 +356,19 @@ __device__ __forceinline__ void fft_io_stage(SBuf<C> buf, int ls, int ltx, int n
 // shared buffer (a barrier separates its reads from the first stage's
 // writes); sync_epi: the epilogue writes the shared buffer.  The buffer is
 // free again after a barrier that follows the call.
-template <int LG, int VPT, bool IL, bool HALF, typename C, typename Load, typename Epi>
+template <int LG, int VPT, bool IL, bool HALF, bool TWT, typename C, typename Load, typename Epi>
 __device__ __forceinline__ void fft_io_ct(SBuf<C> buf, int ls, int ltx, int nlines,
                                           const C* __restrict__ tw, int lgmax, bool inv, Load load,
                                           bool sync_load, Epi epi, bool sync_epi) {
   if constexpr (FftPlan<LG, VPT>::S >= 2) {
-    fft_io_stage<LG, VPT, IL, HALF, 0>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi,
-                                     sync_epi);
+    fft_io_stage<LG, VPT, IL, HALF, TWT, 0>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi,
+                                          sync_epi);
   } else {
     // one stage: natural order in shared memory afterwards; each thread
     // hands on elements it reads (an epilogue writing the buffer rewrites
     // the element it was given)
-    stage_ct<FftPlan<LG, VPT>::radix(0), VPT, IL, LG, 1, STAGE_FIRST, HALF>(buf, ls, ltx, nlines, tw,
-                                                                            lgmax, inv, load, epi, sync_load);
+    stage_ct<FftPlan<LG, VPT>::radix(0), VPT, IL, LG, 1, STAGE_FIRST, HALF, TWT>(
+        buf, ls, ltx, nlines, tw, lgmax, inv, load, epi, sync_load);
     constexpr int L = 1 << LG;
     const int total = IL ? (L << ltx) : nlines * L;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
@@ -386,13 +387,13 @@ __device__ __forceinline__ void fft_io_ct(SBuf<C> buf, int ls, int ltx, int nlin
 #define FL_FFT_LEN(LGV)                                                                     \
   if constexpr (LGV >= LGLO && LGV <= LGHI) {                                               \
     if (lg == LGV) {                                                                        \
-      fft_io_ct<LGV, VPT, IL, HALF>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi, \
-                                    sync_epi);                                              \
+      fft_io_ct<LGV, VPT, IL, HALF, TWT>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, \
+                                         epi, sync_epi);                                    \
       return;                                                                               \
     }                                                                                       \
   }
-template <int VPT, bool IL, bool HALF = false, int LGHI = 11, int LGLO = 4, typename C, typename Load,
-          typename Epi>
+template <int VPT, bool IL, bool HALF = false, int LGHI = 11, int LGLO = 4, bool TWT = false, typename C,
+          typename Load, typename Epi>
 __device__ __forceinline__ void fft_io(SBuf<C> buf, int lg, int ls, int ltx, int nlines,
                                        const C* __restrict__ tw, int lgmax, bool inv, Load load,
                                        bool sync_load, Epi epi, bool sync_epi) {
@@ -411,7 +412,7 @@ __device__ __forceinline__ void fft_io(SBuf<C> buf, int lg, int ls, int ltx, int
 
 // In-place transform of lines in shared memory (natural order in and out)
 // with the compile-time stage plan; ends with a barrier.
-template <int VPT, bool IL, int LGHI = 11, int LGLO = 4, typename C>
+template <int VPT, bool IL, int LGHI = 11, int LGLO = 4, bool TWT = false, typename C>
 __device__ __forceinline__ void fft_smem(SBuf<C> buf, int lg, int ls, int ltx, int nlines,
                                          const C* __restrict__ tw, int lgmax, bool inv) {
   auto ld = [=](int q, int k) -> C { return IL ? buf[(k << ltx) + q] : buf[q * ls + k]; };
@@ -419,7 +420,7 @@ __device__ __forceinline__ void fft_smem(SBuf<C> buf, int lg, int ls, int ltx, i
     if (IL) buf[(k << ltx) + q] = v;
     else buf[q * ls + k] = v;
   };
-  fft_io<VPT, IL, false, LGHI, LGLO>(buf, lg, ls, ltx, nlines, tw, lgmax, inv, ld, true, st, true);
+  fft_io<VPT, IL, false, LGHI, LGLO, TWT>(buf, lg, ls, ltx, nlines, tw, lgmax, inv, ld, true, st, true);
   __syncthreads();
 }
 

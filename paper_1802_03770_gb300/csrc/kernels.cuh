@@ -45,6 +45,16 @@ __device__ __forceinline__ void pdl_release() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Asynchronous global -> shared copies of 4, 8 or 16 bytes (no registers
+// held while in flight); cp_async_wait_all() waits for the calling thread's
+// own copies, a barrier then makes them visible to the CTA.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(sa), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Device-resident state of one CG solve (all reductions in FP64).
 struct PcgState {
   double rz;       // r^T z of the current iterate
@@ -122,6 +132,7 @@ constexpr int min_ctas(int threads, int lglo = 4) {
 // the same body with runtime values.
 constexpr int kMaxLtx = 6;
 constexpr int kFixedLgMin = 8;
+
 __host__ __device__ constexpr int widest_ltx(int threads, int vpt, int lg) {
   return clog2(threads * vpt) - lg < kMaxLtx ? clog2(threads * vpt) - lg : kMaxLtx;
 }
@@ -414,7 +425,7 @@ struct ColsArgs {
 // column c), and transformed with the interleaved-line FFT; global loads are
 // issued U at a time so that several are in flight per thread.
 template <typename T, int THREADS, int VPT, int LGLO, int LGHI>
-__device__ __forceinline__ void body_cols_at(const ColsArgs<T>& a, int bx, int by, const int lg,
+__device__ __forceinline__ void body_cols_at(const ColsArgs<T>& a, int kx0, int by, const int lg,
                                              const int ltx) {
   typedef typename Cplx<T>::type C;
   constexpr int U = 8;
@@ -423,7 +434,6 @@ __device__ __forceinline__ void body_cols_at(const ColsArgs<T>& a, int bx, int b
   if (a.st && a.st->done) return;
   const int L = 1 << lg;
   const int TX = 1 << ltx;
-  const int kx0 = bx * TX;
   const int o = by;
   const int ncol = min(TX, a.H - kx0);
   C* base = a.S + (size_t)o * a.ostride + kx0;
@@ -432,20 +442,27 @@ __device__ __forceinline__ void body_cols_at(const ColsArgs<T>& a, int bx, int b
   const int hL = L >> 1;
   const int total = TX * (a.mode == COLS_CONV ? hL : L);
   // convolution: the symbol's rows kk = 0..L/2 for the tile's columns are
-  // staged in shared memory beside the FFT tile (ssig[kk * TX + c]); their
-  // loads are issued together with the tile's, so that the forward
+  // staged in shared memory beside the FFT tile (ssig[kk * TX + c]) by
+  // asynchronous copies issued before the tile's loads, so that the forward
   // transform's last stage multiplies without a global load in flight
-  T* ssig = reinterpret_cast<T*>(smem_raw + sbuf_elems((long long)TX * L) * sizeof(C));
+  // FP32: the twiddles of this line length, exp(-2 pi i m / L) for m < L
+  // (every 2^(lgmax - lg)-th entry of the plan's table), are copied to
+  // shared memory beside the tile (stw): the stages then load every power
+  // of a butterfly's twiddle instead of computing it
+  constexpr bool TWT = sizeof(T) == 4;
+  C* stw = reinterpret_cast<C*>(smem_raw + sbuf_elems((long long)TX * L) * sizeof(C));
+  T* ssig = reinterpret_cast<T*>(smem_raw + (sbuf_elems((long long)TX * L) + (TWT ? L : 0)) * sizeof(C));
+  const C* twp = TWT ? stw : a.tw;
+  const int twlg = TWT ? lg : a.lgmax;
+  if constexpr (TWT)
+    for (int m = threadIdx.x; m < L; m += THREADS) cp_async<sizeof(C)>(&stw[m], &a.tw[m << (a.lgmax - lg)]);
   const T* __restrict__ sig = a.sig + kx0;
   if (a.mode == COLS_CONV && a.Lo) sig += (size_t)min(o, a.Lo - o) * a.sig_outer;
   const int nsym = a.mode == COLS_CONV ? ((hL + 1) << ltx) : 0;
-  constexpr int SU = VPT / 2 + 1;   // (L/2 + 1) TX <= SU THREADS when TX <= THREADS
-  T sv[SU];
-#pragma unroll
-  for (int u = 0; u < SU; ++u) {
-    const int e = threadIdx.x + u * THREADS;
+  for (int e = threadIdx.x; e < nsym; e += THREADS) {
     const int kk = e >> ltx, c = e & (TX - 1);
-    sv[u] = (e < nsym && c < ncol) ? sig[(size_t)kk * a.sig_line + c] : (T)0;
+    if (c < ncol) cp_async<sizeof(T)>(&ssig[e], &sig[(size_t)kk * a.sig_line + c]);
+    else ssig[e] = (T)0;
   }
   for (int e0 = threadIdx.x; e0 < total; e0 += THREADS * U) {
     C v[U];
@@ -462,23 +479,15 @@ __device__ __forceinline__ void body_cols_at(const ColsArgs<T>& a, int bx, int b
       if (e < total) buf[e] = v[u];
     }
   }
-#pragma unroll
-  for (int u = 0; u < SU; ++u) {
-    const int e = threadIdx.x + u * THREADS;
-    if (e < nsym) ssig[e] = sv[u];
-  }
-  for (int e = threadIdx.x + SU * THREADS; e < nsym; e += THREADS) {
-    const int kk = e >> ltx, c = e & (TX - 1);
-    ssig[e] = c < ncol ? sig[(size_t)kk * a.sig_line + c] : (T)0;
-  }
+  cp_async_wait_all();
   __syncthreads();
   if (a.mode == COLS_CONV) {
     // forward FFT whose last stage multiplies by the staged symbol on the
     // way out (columns beyond ncol are scaled by 0 and never stored)
     auto ld = [=](int c, int k) -> C { return k < hL ? buf[(k << ltx) + c] : cmake<C>((T)0, (T)0); };
     auto epi = [=](int c, int k, C v) { buf[(k << ltx) + c] = cscale(v, ssig[(min(k, L - k) << ltx) + c]); };
-    fft_io<VPT, true, true, LGHI, LGLO>(buf, lg, 0, ltx, TX, a.tw, a.lgmax, false, ld,
-                                                      true, epi, true);
+    fft_io<VPT, true, true, LGHI, LGLO, TWT>(buf, lg, 0, ltx, TX, twp, twlg, false, ld, true, epi,
+                                            true);
     __syncthreads();
     // inverse FFT whose last stage writes the kept rows to global
     const int rows_out = a.rows_out;
@@ -487,11 +496,11 @@ __device__ __forceinline__ void body_cols_at(const ColsArgs<T>& a, int bx, int b
     auto epi2 = [=](int c, int k, C v) {
       if (c < ncol && k < rows_out) base[(size_t)k * lstride + c] = v;
     };
-    fft_io<VPT, true, false, LGHI, LGLO>(buf, lg, 0, ltx, TX, a.tw, a.lgmax, true, ld2,
-                                                       true, epi2, false);
+    fft_io<VPT, true, false, LGHI, LGLO, TWT>(buf, lg, 0, ltx, TX, twp, twlg, true, ld2, true, epi2,
+                                             false);
     return;
   }
-  fft_smem<VPT, true, LGHI, LGLO>(buf, lg, 0, ltx, TX, a.tw, a.lgmax, a.mode == COLS_INV);
+  fft_smem<VPT, true, LGHI, LGLO, TWT>(buf, lg, 0, ltx, TX, twp, twlg, a.mode == COLS_INV);
   const int tout = TX * a.rows_out;
   for (int e = threadIdx.x; e < tout; e += THREADS) {
     const int r = e >> ltx, c = e & (TX - 1);
@@ -499,19 +508,28 @@ __device__ __forceinline__ void body_cols_at(const ColsArgs<T>& a, int bx, int b
   }
 }
 
-// body_cols for the widest tile of lengths 2^LG .. 2^LGHI as compile-time
-// shapes, else with the plan's runtime shape
+// the tile width of column block bx: the plan's, narrowed for a partial
+// last tile to the smallest power of two that holds its columns (each
+// column's transform is the same at any width)
+__device__ __forceinline__ int block_ltx(int ltx, int bx, int ncols) {
+  const int left = ncols - (bx << ltx);
+  while (ltx > 0 && (1 << (ltx - 1)) >= left) --ltx;
+  return ltx;
+}
+
+// body_cols for the full tiles of the widest width of lengths 2^LG ..
+// 2^LGHI as compile-time shapes, else with runtime shapes
 template <typename T, int THREADS, int VPT, int LGLO, int LGHI, int LG>
 __device__ __forceinline__ void body_cols_fixed(const ColsArgs<T>& a, int bx, int by) {
   if constexpr (LG <= LGHI) {
     constexpr int W = widest_ltx(THREADS, VPT, LG);
-    if (a.lg == LG && a.ltx == W) {
-      body_cols_at<T, THREADS, VPT, LGLO, LGHI>(a, bx, by, LG, W);
+    if (a.lg == LG && a.ltx == W && ((bx + 1) << W) <= a.H) {
+      body_cols_at<T, THREADS, VPT, LGLO, LGHI>(a, bx << W, by, LG, W);
       return;
     }
     body_cols_fixed<T, THREADS, VPT, LGLO, LGHI, LG + 1>(a, bx, by);
   } else {
-    body_cols_at<T, THREADS, VPT, LGLO, LGHI>(a, bx, by, a.lg, a.ltx);
+    body_cols_at<T, THREADS, VPT, LGLO, LGHI>(a, bx << a.ltx, by, a.lg, block_ltx(a.ltx, bx, a.H));
   }
 }
 
@@ -568,22 +586,50 @@ __device__ __forceinline__ void body_rows_inv_at(const RowsInvArgs<T>& a, int bx
   const int pair0 = bx * NL;
   const int npairs = (a.rows + 1) / 2;
   const int nl = min(NL, npairs - pair0);
-  for (int q = 0; q < nl; ++q) {
-    const int ra = 2 * (pair0 + q), rb = ra + 1;
-    const bool hb = rb < a.rows;
-    const typename Cplx<T>::type* __restrict__ Sa =
-        a.S + ((size_t)(ra / a.rows_per_plane) * a.plane_stride + ra % a.rows_per_plane) * a.H;
-    const typename Cplx<T>::type* __restrict__ Sb =
-        hb ? a.S + ((size_t)(rb / a.rows_per_plane) * a.plane_stride + rb % a.rows_per_plane) * a.H
-           : nullptr;
+  // Z[k] = Xa[k] + i Xb[k];  Z[L-k] = conj(Xa[k]) + i conj(Xb[k]) for the
+  // row pair (ra, rb) = (2p, 2p + 1) of line q
+  auto spec_row = [&](int row) -> const C* {
+    return a.S + ((size_t)(row / a.rows_per_plane) * a.plane_stride + row % a.rows_per_plane) * a.H;
+  };
+  auto put = [&](int q, int k, C xa, C xb) {
     const SBuf<C> lb = buf.at(q * ls);
+    lb[k] = cmake<C>(xa.x - xb.y, xa.y + xb.x);
+    if (k > 0 && k < a.H - 1) lb[L - k] = cmake<C>(xa.x + xb.y, xb.x - xa.y);
+  };
+  constexpr int QB = 4;
+  if (NL >= QB) {
+    // several row pairs per CTA (short lines): the pairs' loads of one
+    // column range are issued together, one round trip per THREADS
+    // columns instead of one per pair
+    for (int q0 = 0; q0 < nl; q0 += QB) {
+      const C* Sa[QB];
+      const C* Sb[QB];
+#pragma unroll
+      for (int qq = 0; qq < QB; ++qq) {
+        const int ra = 2 * (pair0 + q0 + qq);
+        Sa[qq] = spec_row(ra);
+        Sb[qq] = (q0 + qq < nl && ra + 1 < a.rows) ? spec_row(ra + 1) : nullptr;
+      }
+      for (int k = threadIdx.x; k < a.H; k += THREADS) {
+        C xa[QB], xb[QB];
+#pragma unroll
+        for (int qq = 0; qq < QB; ++qq) {
+          xa[qq] = q0 + qq < nl ? Sa[qq][k] : cmake<C>((T)0, (T)0);
+          xb[qq] = Sb[qq] ? Sb[qq][k] : cmake<C>((T)0, (T)0);
+        }
+#pragma unroll
+        for (int qq = 0; qq < QB; ++qq)
+          if (q0 + qq < nl) put(q0 + qq, k, xa[qq], xb[qq]);
+      }
+    }
+  } else {
+    for (int q = 0; q < nl; ++q) {
+      const int ra = 2 * (pair0 + q);
+      const C* __restrict__ Sa = spec_row(ra);
+      const C* __restrict__ Sb = ra + 1 < a.rows ? spec_row(ra + 1) : nullptr;
 #pragma unroll 4
-    for (int k = threadIdx.x; k < a.H; k += THREADS) {
-      const C xa = Sa[k];
-      const C xb = hb ? Sb[k] : cmake<C>((T)0, (T)0);
-      // Z[k] = Xa[k] + i Xb[k];  Z[L-k] = conj(Xa[k]) + i conj(Xb[k])
-      lb[k] = cmake<C>(xa.x - xb.y, xa.y + xb.x);
-      if (k > 0 && k < a.H - 1) lb[L - k] = cmake<C>(xa.x + xb.y, xb.x - xa.y);
+      for (int k = threadIdx.x; k < a.H; k += THREADS)
+        put(q, k, Sa[k], Sb ? Sb[k] : cmake<C>((T)0, (T)0));
     }
   }
   __syncthreads();
@@ -660,14 +706,14 @@ __global__ void __launch_bounds__(THREADS, min_ctas(THREADS, LGLO)) k_rows_inv(R
 // (element j of line c at j * 2^ltx + c): y = IFFT(FFT(v) * bhat), the
 // chirp-z convolution of the DST-I (bhat already holds the 1/L); the
 // multiply is done by the forward transform's last stage.
-template <int VPT, int LGHI, typename C>
+template <int VPT, int LGHI, bool TWT = false, typename C>
 __device__ __forceinline__ void chirp_conv_il(SBuf<C> buf, int ltx, int L, int lg, int lgmax,
                                               const C* __restrict__ tw, const C* __restrict__ bhat) {
   auto ld = [=](int c, int k) -> C { return buf[(k << ltx) + c]; };
   auto epi = [=](int c, int k, C v) { buf[(k << ltx) + c] = cmul(v, bhat[k]); };
-  fft_io<VPT, true, false, LGHI>(buf, lg, 0, ltx, 1 << ltx, tw, lgmax, false, ld, true, epi, true);
+  fft_io<VPT, true, false, LGHI, 4, TWT>(buf, lg, 0, ltx, 1 << ltx, tw, lgmax, false, ld, true, epi, true);
   __syncthreads();
-  fft_smem<VPT, true, LGHI>(buf, lg, 0, ltx, 1 << ltx, tw, lgmax, true);
+  fft_smem<VPT, true, LGHI, 4, TWT>(buf, lg, 0, ltx, 1 << ltx, tw, lgmax, true);
 }
 
 // ---------------------------------------------------------------------------
@@ -868,7 +914,7 @@ struct DstColsArgs {
 };
 
 template <typename T, int THREADS, int VPT, int LGLO, int LGHI>
-__device__ __forceinline__ void body_dst_cols_at(const DstColsArgs<T>& a, int bx, int by, const int lg,
+__device__ __forceinline__ void body_dst_cols_at(const DstColsArgs<T>& a, int c0, int by, const int lg,
                                                  const int ltx) {
   typedef typename Cplx<T>::type C;
   constexpr int U = 8;
@@ -877,11 +923,15 @@ __device__ __forceinline__ void body_dst_cols_at(const DstColsArgs<T>& a, int bx
   if (a.st && a.st->done) return;
   const int L = 1 << lg;
   const int TX = 1 << ltx;
-  const int c0 = bx * TX;
   const int o = by;
   const int ncol = min(TX, a.ncols - c0);
   T* base = a.v + (size_t)o * a.ostride + c0;
   const int total = TX * L;
+  // FP32: the line length's twiddles in shared memory (as in body_cols_at)
+  constexpr bool TWT = sizeof(T) == 4;
+  C* stw = reinterpret_cast<C*>(smem_raw + sbuf_elems((long long)TX * L) * sizeof(C));
+  if constexpr (TWT)
+    for (int m = threadIdx.x; m < L; m += THREADS) cp_async<sizeof(C)>(&stw[m], &a.tw[m << (a.lgmax - lg)]);
   for (int e0 = threadIdx.x; e0 < total; e0 += THREADS * U) {
     T v[U];
 #pragma unroll
@@ -898,8 +948,9 @@ __device__ __forceinline__ void body_dst_cols_at(const DstColsArgs<T>& a, int bx
       if (e < total) buf[e] = r < a.n ? cscale(a.chirp[r], v[u]) : cmake<C>((T)0, (T)0);
     }
   }
+  cp_async_wait_all();
   __syncthreads();
-  chirp_conv_il<VPT, LGHI>(buf, ltx, L, lg, a.lgmax, a.tw, a.bhat);
+  chirp_conv_il<VPT, LGHI, TWT>(buf, ltx, L, lg, TWT ? lg : a.lgmax, TWT ? stw : a.tw, a.bhat);
   const int tout = TX * a.n;
   const T post = (T)a.post;
   for (int e = threadIdx.x; e < tout; e += THREADS) {
@@ -915,13 +966,13 @@ template <typename T, int THREADS, int VPT, int LGLO, int LGHI, int LG>
 __device__ __forceinline__ void body_dst_cols_fixed(const DstColsArgs<T>& a, int bx, int by) {
   if constexpr (LG <= LGHI) {
     constexpr int W = widest_ltx(THREADS, VPT, LG);
-    if (a.lg == LG && a.ltx == W) {
-      body_dst_cols_at<T, THREADS, VPT, LGLO, LGHI>(a, bx, by, LG, W);
+    if (a.lg == LG && a.ltx == W && ((bx + 1) << W) <= a.ncols) {
+      body_dst_cols_at<T, THREADS, VPT, LGLO, LGHI>(a, bx << W, by, LG, W);
       return;
     }
     body_dst_cols_fixed<T, THREADS, VPT, LGLO, LGHI, LG + 1>(a, bx, by);
   } else {
-    body_dst_cols_at<T, THREADS, VPT, LGLO, LGHI>(a, bx, by, a.lg, a.ltx);
+    body_dst_cols_at<T, THREADS, VPT, LGLO, LGHI>(a, bx << a.ltx, by, a.lg, block_ltx(a.ltx, bx, a.ncols));
   }
 }
 

@@ -421,7 +421,7 @@ ApplyChain<T> build_apply(const Geo& g, const Tables<T>& tb, const ApplyIO<T>& i
     const int tx = plan_tx<T>(tb, axis, L);
     a.ltx = ilog2i(tx);
     ch.cols_grid[ch.ncols] = dim3((g.H + tx - 1) / tx, nouter);
-    ch.cols_smem[ch.ncols] = mode == COLS_CONV ? conv_tile_bytes<T>(tx, L) : tile_bytes<T>(tx, L);
+    ch.cols_smem[ch.ncols] = mode == COLS_CONV ? conv_tile_bytes<T>(tx, L) : cols_bytes<T>(tx, L);
     ch.ncols++;
   };
   if (d == 2) {
@@ -498,7 +498,7 @@ PrecChain<T> build_precond(const Geo& g, const Tables<T>& tb, const PrecIO<T>& i
     const int tx = plan_tx<T>(tb, axis, L);
     a.ltx = ilog2i(tx);
     ch.cols_grid[ch.ncols] = dim3((nx + tx - 1) / tx, nouter);
-    ch.cols_smem[ch.ncols] = tile_bytes<T>(tx, L);
+    ch.cols_smem[ch.ncols] = cols_bytes<T>(tx, L);
     ch.ncols++;
   };
   {

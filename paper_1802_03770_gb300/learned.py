@@ -131,6 +131,8 @@ def main():
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--max-seconds", type=float, default=None)
+    ap.add_argument("--pool", type=int, default=16,
+                    help="training plans: seeded orders alpha ~ U(0.3, 1.8), cycled over the steps")
     ap.add_argument("--eval", type=int, default=32, help="held-out seeds to evaluate")
     ap.add_argument("--out", default=None)
     ap.add_argument("--report", default=None)
@@ -146,7 +148,7 @@ def main():
         net.load(args.load)
         hist = []
     else:
-        net, hist = train(args.n, args.pairs, args.batch, args.lr, args.seed,
+        net, hist = train(args.n, args.pairs, args.batch, args.lr, args.seed, pool=args.pool,
                           max_seconds=args.max_seconds)
         print(json.dumps({"history": hist}), flush=True)
         if args.out:
