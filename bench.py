@@ -439,6 +439,9 @@ def run_ours(args, rank, world, local):
 LEARNED_N = 512
 LEARNED_SEEDS = 32
 WEIGHTS = os.path.join(ROOT, "paper_1802_03770_gb300", "weights", "unet512.bin")
+# the weights' alpha gate (learned.py --gate-out, chosen on validation seeds
+# 20000.. with their own alpha draws, disjoint from the held-out seeds here)
+WEIGHTS_GATE = os.path.join(ROOT, "paper_1802_03770_gb300", "weights", "unet512_gate.txt")
 
 
 def learned_arm(dev, seeds=LEARNED_SEEDS):
@@ -447,7 +450,10 @@ def learned_arm(dev, seeds=LEARNED_SEEDS):
     sides of 16 seeded Gaussians, to 1e-8: plain FP64 CG, the mixed path and
     the mixed path with the trained network, each (plan, mode) warmed up on
     another right-hand side first.  Solves/s over the timed solves and mean
-    iterations per mode."""
+    iterations per mode.  `learned` runs FL_MODE_LEARNED with the weights'
+    alpha gate (the network only in the alpha bands where it lowered the
+    validation iteration count, plain preconditioned CG elsewhere);
+    `learned_network_always` runs it without the gate."""
     import torch
     from paper_1802_03770_gb300 import _lib, inputs
     from paper_1802_03770_gb300.api import Net, Plan
@@ -457,10 +463,13 @@ def learned_arm(dev, seeds=LEARNED_SEEDS):
     net = Net(n, n)
     net.load(WEIGHTS)
     net.tensor_cores(True)
+    gated = os.path.exists(WEIGHTS_GATE)
     alphas = inputs.alpha_draws(seeds, 777)
     modes = {"fp64": _lib.FL_MODE_F64 | _lib.FL_PRECOND_AUTO,
              "mixed": _lib.FL_MODE_MIXED | _lib.FL_PRECOND_AUTO,
              "learned": _lib.FL_MODE_LEARNED | _lib.FL_PRECOND_AUTO}
+    if gated:
+        modes["learned_network_always"] = _lib.FL_MODE_LEARNED | _lib.FL_PRECOND_AUTO
     ms = {k: 0.0 for k in modes}
     its = {k: [] for k in modes}
     ok = True
@@ -473,6 +482,10 @@ def learned_arm(dev, seeds=LEARNED_SEEDS):
         fw = torch.tensor(inputs.gaussian_mixture(n, 2, 16, 30000 + k), dtype=torch.float64,
                           device=dev).view(-1)
         for name, mode in modes.items():
+            if name == "learned" and gated:
+                net.load_gate(WEIGHTS_GATE)
+            elif name == "learned_network_always":
+                net.set_alpha_gate()
             p.solve(fw, tol=TOL, mode=mode, maxit=4000)          # warm-up (untimed)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -489,6 +502,8 @@ def learned_arm(dev, seeds=LEARNED_SEEDS):
     out = {"workload": f"elliptic solve 2D {n}x{n}, alpha ~ U(0.3,1.8), RHS 16 seeded Gaussians, "
                        f"{seeds} held-out seeds 10000..{10000 + seeds - 1}, to 1e-8",
            "network": "3-level U-Net 16/32/64, BF16 weights, tcgen05 3x3 convolutions",
+           "gate": ("alpha bands where the network lowered the validation iteration count "
+                    "(weights/unet512_gate.txt); plain preconditioned CG elsewhere") if gated else None,
            "all_converged": ok}
     for name in modes:
         out[name] = {"value": seeds / (ms[name] / 1e3), "unit": UNIT,

@@ -355,6 +355,17 @@ fl_status fl_net_get_tensor(fl_net* net, int kind, int index, float* host, long 
  * default: BF16 activations and weights, FP32 accumulation in TMEM) or on
  * the CUDA cores (enable = 0: FP32 activations, BF16 weights). */
 fl_status fl_net_set_tensor_cores(fl_net* net, int enable);
+/* Alpha gate: with bands > 0, FL_MODE_LEARNED solves of a plan of order
+ * alpha use the network only when alpha lies in [lo, hi) and in an enabled
+ * band (the interval split into `bands` equal bands, enabled[b] != 0; host
+ * array, copied); otherwise they run the plain FP32 preconditioned CG of
+ * FL_MODE_MIXED.  bands = 0 removes the gate (the network serves every
+ * alpha, the default).  The gate is chosen from held-out solves where the
+ * network lowers the iteration count (learned.py).  FL_INVALID_ARG for a
+ * NULL net, lo >= hi, non-finite bounds, bands < 0 or > 4096, or a NULL
+ * array with bands > 0. */
+fl_status fl_net_set_alpha_gate(fl_net* net, double lo, double hi, int bands, const uint8_t* enabled);
+
 /* FL_DEVICE_TIMEOUT if a bounded tensor-core wait of an earlier call gave up
  * (its outputs were zeroed), else FL_OK; waits for the net's stream. */
 fl_status fl_net_check(fl_net* net);

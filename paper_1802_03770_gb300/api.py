@@ -31,6 +31,17 @@ def launch_count():
     return int(L.load().fl_launch_count())
 
 
+def read_gate(path):
+    """(lo, hi, enabled flags) of a gate file: comment lines start with '#',
+    then a line "lo hi bands" and a line of `bands` 0/1 flags."""
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.lstrip().startswith("#")]
+    lo, hi, bands = float(rows[0][0]), float(rows[0][1]), int(rows[0][2])
+    flags = [int(v) for v in rows[1]]
+    if len(flags) != bands:
+        raise ValueError(f"{path}: {len(flags)} flags for {bands} bands")
+    return lo, hi, flags
+
+
 class Net:
     """The U-Net of the learned preconditioner (fl_net_*); H, W multiples of 64."""
 
@@ -61,6 +72,19 @@ class Net:
 
     def check(self):
         L.check(self._lib.fl_net_check(self._h), "fl_net_check")
+
+    def set_alpha_gate(self, lo=0.0, hi=0.0, enabled=()):
+        """FL_MODE_LEARNED uses the network only for alpha in [lo, hi) in an
+        enabled band (len(enabled) equal bands); no bands = no gate."""
+        flags = np.ascontiguousarray([1 if e else 0 for e in enabled], dtype=np.uint8)
+        L.check(self._lib.fl_net_set_alpha_gate(self._h, float(lo), float(hi), int(flags.size),
+                                                flags.ctypes.data_as(ctypes.c_void_p) if flags.size else None),
+                "fl_net_set_alpha_gate")
+
+    def load_gate(self, path):
+        """Set the alpha gate from a gate file written by learned.write_gate."""
+        lo, hi, flags = read_gate(path)
+        self.set_alpha_gate(lo, hi, flags)
 
     def get_params(self, grads=False):
         p = np.empty(self.nparams, np.float32)

@@ -2,6 +2,7 @@
 // master, BF16 copy, Adam moments), activations and gradients, forward,
 // backward, training step, checkpoint files.  The architecture is described
 // in unet.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -516,6 +517,28 @@ cudaError_t launch_fpcg_scalar(PcgState* st, const double* rr_part, int rr_count
 fl::NetState* fl_net_state(fl_net* n) { return n; }
 
 extern "C" {
+
+bool fl::NetState::alpha_enabled(double alpha) const {
+  if (gate.empty()) return true;
+  if (!(alpha >= gate_lo && alpha < gate_hi)) return false;
+  const int b = std::min((int)gate.size() - 1,
+                         (int)((alpha - gate_lo) / (gate_hi - gate_lo) * (double)gate.size()));
+  return gate[b] != 0;
+}
+
+fl_status fl_net_set_alpha_gate(fl_net* n, double lo, double hi, int bands, const uint8_t* enabled) {
+  if (!n) return net_fail(FL_INVALID_ARG, "NULL net");
+  if (bands == 0) {
+    n->gate.clear();
+    return FL_OK;
+  }
+  if (bands < 0 || bands > 4096 || !enabled || !std::isfinite(lo) || !std::isfinite(hi) || !(lo < hi))
+    return net_fail(FL_INVALID_ARG, "alpha gate: need lo < hi (finite), 0 < bands <= 4096, enabled != NULL");
+  n->gate_lo = lo;
+  n->gate_hi = hi;
+  n->gate.assign(enabled, enabled + bands);
+  return FL_OK;
+}
 
 fl_status fl_net_set_tensor_cores(fl_net* n, int enable) {
   if (!n) return net_fail(FL_INVALID_ARG, "NULL net");

@@ -40,6 +40,12 @@ struct NetState {
   double* lpart = nullptr;
   int step = 0;
   int use_tc = 1;              // 3 x 3 convolutions on tcgen05 (BF16 operands)
+  // alpha gate (fl_net_set_alpha_gate): empty = the network serves every
+  // alpha; else alpha in [gate_lo, gate_hi) split into gate.size() equal
+  // bands, the network serving the enabled ones only
+  double gate_lo = 0.0, gate_hi = 0.0;
+  std::vector<uint8_t> gate;
+  bool alpha_enabled(double alpha) const;
   int* err = nullptr;          // device flag of the bounded tensor-core waits
   std::vector<void*> allocs;
 

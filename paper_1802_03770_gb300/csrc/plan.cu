@@ -811,7 +811,7 @@ fl_status solve_system(fl_plan* p, double* u, bool x0_nonzero, double shift, dou
         const double eta = target.next(loc.rel_residual, tol, p->inner_tol);
         int its = 0;
         fl_status in;
-        if (precision == FL_MODE_LEARNED) {
+        if (precision == FL_MODE_LEARNED && p->net->alpha_enabled(p->alpha)) {
           int fallback = 0;
           in = run_fpcg_learned(p, shift, scale, eta, maxit, &its, &fallback);
           if (fallback) {   // plain preconditioned CG takes over this correction

@@ -92,11 +92,11 @@ def train(n=512, pairs=20000, batch=4, lr=1e-3, seed=0, pool=16, log_every=50, n
     return net, hist
 
 
-def evaluate(net, n=512, seeds=range(10000, 10256), tol=1e-8, pool=16):
+def evaluate(net, n=512, seeds=range(10000, 10256), tol=1e-8, pool=16, alpha_seed=777):
     """Held-out comparison: iterations and wall time of FL_MODE_MIXED (plain
     FD-preconditioned CG inside refinement) vs FL_MODE_LEARNED."""
     import torch
-    alphas = inputs.alpha_draws(len(seeds), 777)
+    alphas = inputs.alpha_draws(len(seeds), alpha_seed)
     res = []
     cache = {}
     for k, sd in enumerate(seeds):
@@ -123,6 +123,35 @@ def evaluate(net, n=512, seeds=range(10000, 10256), tol=1e-8, pool=16):
     return res
 
 
+GATE_LO, GATE_HI, GATE_BANDS = 0.3, 1.8, 15
+
+
+def choose_gate(rows, lo=GATE_LO, hi=GATE_HI, bands=GATE_BANDS):
+    """Alpha gate from validation solves (`rows` of evaluate, network always
+    on): a band is enabled when the mean learned iteration count of its
+    solves is below the mean plain count.  Returns (flags, per-band stats)."""
+    stats = []
+    for b in range(bands):
+        a0 = lo + (hi - lo) * b / bands
+        a1 = lo + (hi - lo) * (b + 1) / bands
+        sel = [r for r in rows if a0 <= r["alpha"] < a1]
+        pl = float(np.mean([r["plain"]["iterations"] for r in sel])) if sel else float("nan")
+        le = float(np.mean([r["learned"]["iterations"] for r in sel])) if sel else float("nan")
+        stats.append((a0, a1, len(sel), pl, le))
+    flags = [1 if (s[2] > 0 and s[4] < s[3]) else 0 for s in stats]
+    return flags, stats
+
+
+def write_gate(path, flags, stats, note, lo=GATE_LO, hi=GATE_HI):
+    with open(path, "w") as fh:
+        fh.write(f"# alpha gate: {note}\n")
+        fh.write("# band: alpha range, validation solves, mean plain / learned iterations\n")
+        for (a0, a1, cnt, pl, le), f in zip(stats, flags):
+            fh.write(f"# [{a0:.2f}, {a1:.2f}): {cnt} solves, {pl:.1f} / {le:.1f} -> {'on' if f else 'off'}\n")
+        fh.write(f"{lo} {hi} {len(flags)}\n")
+        fh.write(" ".join(str(f) for f in flags) + "\n")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=512)
@@ -140,6 +169,10 @@ def main():
                     help="evaluate these weights instead of training (e.g. weights/unet512.bin)")
     ap.add_argument("--tensor-cores", action="store_true",
                     help="run the network's 3x3 convolutions on the tcgen05 path")
+    ap.add_argument("--gate-out", default=None,
+                    help="choose the alpha gate on validation seeds 20000... (own alpha draws) "
+                         "and write it here; the held-out evaluation then runs gated")
+    ap.add_argument("--gate-seeds", type=int, default=256)
     args = ap.parse_args()
     if args.load:
         import torch
@@ -155,6 +188,15 @@ def main():
             net.save(args.out)
     if args.tensor_cores:
         net.tensor_cores(True)
+    gate = None
+    if args.gate_out:
+        val = evaluate(net, args.n, range(20000, 20000 + args.gate_seeds), alpha_seed=555)
+        flags, stats = choose_gate(val)
+        write_gate(args.gate_out, flags, stats,
+                   f"{args.gate_seeds} validation solves (seeds 20000.., alpha draws seed 555), "
+                   f"512^2, tol 1e-8")
+        net.set_alpha_gate(GATE_LO, GATE_HI, flags)
+        gate = {"flags": flags, "stats": stats}
     ev = evaluate(net, args.n, range(10000, 10000 + args.eval))
     summary = {
         "history": hist,
@@ -163,6 +205,7 @@ def main():
         "plain_seconds": float(np.mean([r["plain"]["seconds"] for r in ev])),
         "learned_seconds": float(np.mean([r["learned"]["seconds"] for r in ev])),
         "all_converged": all(r["plain"]["converged"] and r["learned"]["converged"] for r in ev),
+        "gate": gate,
         "rows": ev,
     }
     text = json.dumps(summary)

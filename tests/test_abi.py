@@ -72,6 +72,8 @@ def test_invalid_arguments_fail_before_the_device(lib):
     assert lib.fl_plan_set_tiles(None, tiles) == _lib.FL_INVALID_ARG
     assert lib.fl_plan_autotune(None, tiles) == _lib.FL_INVALID_ARG
     assert lib.fl_net_get_tensor(None, 0, 0, None, 0) == _lib.FL_INVALID_ARG
+    flags = (ctypes.c_uint8 * 2)(1, 0)
+    assert lib.fl_net_set_alpha_gate(None, 0.3, 1.8, 2, flags) == _lib.FL_INVALID_ARG
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

@@ -43,6 +43,32 @@ def test_learned_mode_needs_a_network():
         p.attach_net(Net(128, 128))
 
 
+def test_alpha_gate_falls_back_to_the_mixed_path():
+    """With the plan's alpha band disabled, FL_MODE_LEARNED runs the plain
+    FP32 preconditioned CG of FL_MODE_MIXED (same iterations, bitwise the
+    same solution); with it enabled, the network runs again."""
+    n, alpha = 64, 1.25
+    f = torch.tensor(inputs.gaussian_mixture(n, 2, 8, 12), dtype=torch.float64, device="cuda:0")
+    p = Plan(2, (n, n), 1.0 / (n + 1), alpha)
+    net = Net(n, n, seed=3)
+    p.attach_net(net)
+    mixed = _lib.FL_MODE_MIXED | _lib.FL_PRECOND_AUTO
+    learn = _lib.FL_MODE_LEARNED | _lib.FL_PRECOND_AUTO
+    u_m, i_m = p.solve(f, tol=1e-8, mode=mixed)
+    u_l, i_l = p.solve(f, tol=1e-8, mode=learn)
+    net.set_alpha_gate(0.3, 1.8, [1, 0, 1])          # bands of 0.5: alpha = 1.25 in the off band
+    u_g, i_g = p.solve(f, tol=1e-8, mode=learn)
+    assert i_g["iterations"] == i_m["iterations"]
+    assert torch.equal(u_g, u_m)
+    net.set_alpha_gate(0.3, 1.8, [0, 1, 0])
+    u_g2, i_g2 = p.solve(f, tol=1e-8, mode=learn)
+    assert i_g2["iterations"] == i_l["iterations"]
+    assert torch.equal(u_g2, u_l)
+    net.set_alpha_gate()                              # no gate: the network serves every alpha
+    u_n, _ = p.solve(f, tol=1e-8, mode=learn)
+    assert torch.equal(u_n, u_l)
+
+
 def test_training_pipeline_reduces_loss_and_solves():
     net, hist = learned.train(n=64, pairs=96, batch=4, lr=2e-3, seed=5, pool=4, log_every=1)
     losses = [h[1] for h in hist]
