@@ -9,8 +9,9 @@ the same GPU, the end-to-end time through the host-array C-ABI call (same
 right-hand sides, same L2 flush), the roofline of the dominant kernel, the
 learned-preconditioner arm (512^2, alpha ~ U(0.3, 1.8), held-out seeds:
 plain FP64 CG, mixed, mixed + learned), the 3D 256^3 backward-Euler run with
-the FP32 apply's roofline there, and the FP64 CPU oracle timed on the host
-(one full solve per alpha).
+the FP32 apply's roofline there, the 64-problem batch of uneven grids (one
+persistent launch per refinement step against one launch per pass), and the
+FP64 CPU oracle timed on the host (one full solve per alpha).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun every rank solves its own seeds (weak scaling, no collective
@@ -137,21 +138,26 @@ def make_rhs(seed):
 # from: it is keyed by the SHA-256 of the CUDA sources (kernel_source_sha)
 # and reported as null for any other source.
 NCU_DRAM_BYTES = {
-    # k_dst_rows<float, 128, 16>, 1024^2: 16920832 (first pass) and 8570112
-    # (last pass) bytes read, 0 written (profiles/dst_rows_f32_2d1024.md)
-    "dst_rows<f32>": ("e2451693f203ddda", 12745472),
+    # k_dst_rows<float, 128, 16>, 1024^2, mean of four launches: 16920576 /
+    # 16921344 (first pass) and 8557824 / 8558080 (last pass) bytes read, 0
+    # written (profiles/dst_rows_f32_2d1024.md)
+    "dst_rows<f32>": ("5ec2b7548f5cbcd9", 12739456),
 }
 
 
+# the sources that make up the single-plan pass kernels and their launch
+# shapes (the roofline kernel's code and configuration)
+PASS_KERNEL_SOURCES = ("chain.cuh", "fft_core.cuh", "internal.h", "kernels.cuh", "ops.cu")
+
+
 def kernel_source_sha():
-    """SHA-256 (first 16 hex digits) of the library's CUDA sources."""
+    """SHA-256 (first 16 hex digits) of the pass kernels' CUDA sources."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_1802_03770_gb300", "csrc")
     h = hashlib.sha256()
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
-            with open(os.path.join(csrc, name), "rb") as fh:
-                h.update(name.encode() + b"\0" + fh.read())
+    for name in PASS_KERNEL_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(name.encode() + b"\0" + fh.read())
     return h.hexdigest()[:16]
 
 
@@ -411,6 +417,7 @@ def run_ours(args, rank, world, local):
                      for k, (c, t) in top[:10]}
     learned = learned_arm(dev) if not args.no_learned else None
     td3 = timestep_3d(dev, peak, peak_kind) if not args.no_3d else None
+    b64 = batched_64() if not args.no_batch64 else None
     its_mixed = [i["iterations"] for i in infos_mixed[: len(ALPHAS)]]
     its_f64 = [i["iterations"] for i in infos_f64[: len(ALPHAS)]]
     return {
@@ -421,7 +428,8 @@ def run_ours(args, rank, world, local):
         "speedup_vs_fp64_pcg": value / value_f64,
         "batched": {"value": job_rate(world, len(ALPHAS), ms_batched / 1e3), "unit": UNIT,
                     "ms_per_step": ms_batched,
-                    "how": "the step's three solves in one fl_solve_elliptic_batched call (lockstep)",
+                    "how": "the step's three solves in one fl_solve_elliptic_batched call (one "
+                           "launch per pass over all problems, CG iterations as a CUDA graph)",
                     "iterations": [i["iterations"] for i in infos_batched[: len(ALPHAS)]]},
         "balanced_shift": {
             "value": value_shift, "unit": UNIT, "ms_per_step": ms_shift,
@@ -432,8 +440,26 @@ def run_ours(args, rank, world, local):
         "iterations_mixed": its_mixed,
         "refinements": [i["outer_iterations"] for i in infos_mixed[: len(ALPHAS)]],
         "kernels": kernel_shares, "apply": apply, "tiles": tiles,
-        "learned": learned, "timestep_3d": td3,
+        "learned": learned, "timestep_3d": td3, "batched_64": b64,
     }
+
+
+def batched_64():
+    """The 64-problem batch: sides uniform in {96, 128, ..., 768}, alpha ~
+    U(0.3, 1.8), seeded Gaussian-mixture right-hand sides, FP32 inner CG +
+    FP64 refinement to 1e-8, the inner CG of every refinement step in one
+    persistent launch (graph-captured) with the plans' tuned column tiles;
+    beside it the same batch with one launch per pass (lockstep) and the 64
+    solves one after another (host wall clock, each after a warm-up call)."""
+    from paper_1802_03770_gb300 import workloads
+    r = workloads.batched(count=64, seed=7, precond="auto", autotune=True)
+    return {"workload": r["workload"], "value": r["batched_solves_per_s"], "unit": UNIT,
+            "how": r["batched_how"] + ", autotuned column tiles",
+            "lockstep": r["lockstep_solves_per_s"], "sequential": r["sequential_solves_per_s"],
+            "mean_iterations": r["mean_iterations"],
+            "lockstep_mean_iterations": r["lockstep_mean_iterations"],
+            "autotune_seconds": r["autotune_seconds"], "total_dof": r["total_dof"],
+            "all_converged": r["all_converged"]}
 
 
 LEARNED_N = 512
@@ -619,6 +645,22 @@ def profile_case():
     print(json.dumps(info))
 
 
+def profile_case_unet(n=512):
+    """Five forwards of the learned preconditioner's U-Net at 512^2 on the
+    tensor cores (seeded weights and features); each launches the tcgen05
+    3x3 convolutions of every layer."""
+    import torch
+    from paper_1802_03770_gb300.api import Net
+    net = Net(n, n, seed=1)
+    net.tensor_cores(True)
+    g = torch.Generator().manual_seed(5)
+    x = torch.randn(3 * n * n, generator=g).to("cuda:0")
+    for _ in range(5):
+        y = net.forward(x)
+    torch.cuda.synchronize()
+    print(json.dumps({"y_norm": float(y.norm())}))
+
+
 def profile_case_3d(n=256):
     """Five FP32 applies on the 3D time-step grid (n^3 interior, (2n)^3 padded
     FFT), from a seeded field; the passes of the first are the captured ones."""
@@ -652,16 +694,22 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner arm")
     ap.add_argument("--no-3d", action="store_true", help="skip the 3D 256^3 time-step entry")
+    ap.add_argument("--no-batch64", action="store_true", help="skip the 64-problem batch entry")
     ap.add_argument("--profile-case", action="store_true",
                     help="run two mixed solves at alpha = 1.5 and exit (for ncu captures)")
     ap.add_argument("--profile-case-3d", action="store_true",
                     help="run five FP32 applies on the 256^3 grid and exit (for ncu captures)")
+    ap.add_argument("--profile-case-unet", action="store_true",
+                    help="run five 512^2 U-Net forwards on the tensor cores and exit (for ncu)")
     args = ap.parse_args()
     if args.profile_case:
         profile_case()
         return
     if args.profile_case_3d:
         profile_case_3d()
+        return
+    if args.profile_case_unet:
+        profile_case_unet()
         return
     rank, world, local = dist_env()
     config = {"workload": WORKLOAD, "n": N_SIDE, "fft_len": 2 * N_SIDE, "alphas": list(ALPHAS),
@@ -735,7 +783,7 @@ def main():
                 "iterations_mixed": res["iterations_mixed"], "refinements": res["refinements"],
                 "t_con_s": res["t_con_s"], "apply": res["apply"], "kernels": res["kernels"],
                 "tiles": res["tiles"], "learned": res["learned"],
-                "timestep_3d": res["timestep_3d"]}
+                "timestep_3d": res["timestep_3d"], "batched_64": res["batched_64"]}
         print(json.dumps(line))
     if world > 1:
         import torch

@@ -66,9 +66,13 @@ enum {
                                 fl_precond_params (not in the paper)       */
   FL_PRECOND_STENCIL = 0x40, /* the (2d+1)-point stencil part of M itself,
                                 the alternative remarked on in Sec. 3.1    */
-  FL_PRECOND_BOX = 0x50      /* occluded domains: the box FD solve restricted
+  FL_PRECOND_BOX = 0x50,     /* occluded domains: the box FD solve restricted
                                 to Omega, R B^{-1} R^T (cheaper per
                                 application, not the paper's choice)       */
+  FL_BATCH_PERSISTENT = 0x100 /* fl_solve_elliptic_batched, FL_MODE_MIXED:
+                                 all inner CG iterations of a refinement step
+                                 in one persistent launch instead of one
+                                 launch per pass and iteration              */
 };
 
 typedef struct fl_plan fl_plan;
@@ -286,11 +290,18 @@ int fl_profile_read(fl_plan* plan, fl_kernel_stat* stats, int max_stats);
 fl_status fl_apply_f32_static(fl_plan* plan, const float* u_dev, float* y_dev);
 
 /* Solve count independent problems M_i u_i = f_i (each eq. matelliptic with
- * its own plan: size, h, alpha) to ||f_i - M_i u_i|| <= tol ||f_i||, in
- * lockstep.  With FL_MODE_MIXED every pass of the FP64 residual, of the FP32
- * CG start-up and of a CG iteration is one launch over all problems, and the
- * CG iterations run as a captured CUDA graph on a private stream (ordered
- * after and before the plans' streams).  FL_MODE_F64 solves the problems one
+ * its own plan: size, h, alpha) to ||f_i - M_i u_i|| <= tol ||f_i||, all at
+ * once.  With FL_MODE_MIXED every pass of the FP64 residual, of the FP32 CG
+ * start-up and of a CG iteration is one launch over all problems
+ * (lockstep), and the CG iterations run as a captured CUDA graph of 8
+ * iterations, replayed until every problem is done, on a private stream
+ * (ordered after and before the plans' streams).  With FL_BATCH_PERSISTENT
+ * added to mode (batches of fewer than 2048 problems) all inner CG
+ * iterations of one refinement step, of every problem, instead run in ONE
+ * persistent cooperative launch (all its CTAs resident; bounded grid
+ * barriers between the passes; it ends when every problem's inner CG is
+ * done), captured once into a CUDA graph.  Both give the same iterates up
+ * to the order of the partial sums.  FL_MODE_F64 solves the problems one
  * after another with fl_solve_elliptic.
  *   plans : host array of count distinct plans, all of the same d
  *   f_dev : host array of count device pointers (N_i doubles each)
@@ -299,7 +310,9 @@ fl_status fl_apply_f32_static(fl_plan* plan, const float* u_dev, float* y_dev);
  * Mixed batches need padded lengths <= 2048 (n_i <= 1024), and masked plans
  * in them take FL_PRECOND_BOX or no preconditioner.
  * Returns FL_OK when every problem converged, FL_NOT_CONVERGED if one did
- * not (all solutions are written), FL_INVALID_ARG, FL_CUDA_ERROR. */
+ * not (all solutions are written), FL_INVALID_ARG, FL_CUDA_ERROR, and
+ * FL_DEVICE_TIMEOUT if a CTA of the persistent launch waited more than 2 s
+ * at a grid barrier (the launch then ends; the solutions are not valid). */
 fl_status fl_solve_elliptic_batched(fl_plan* const* plans, int count, const double* const* f_dev,
                                     double* const* u_dev, double tol, int maxit, int mode,
                                     fl_solve_info* infos);

@@ -30,6 +30,7 @@ FL_PRECOND_AUTO = 0x20
 FL_PRECOND_SHIFTED = 0x30
 FL_PRECOND_STENCIL = 0x40
 FL_PRECOND_BOX = 0x50
+FL_BATCH_PERSISTENT = 0x100
 
 
 class FlOpts(ctypes.Structure):

@@ -16,13 +16,18 @@ ROOT = os.path.dirname(HERE)
 OUT = os.path.join(HERE, "libfraclap.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# the persistent batched kernel and its pass bodies are relocatable device
+# code, device-linked together (each body function is register-allocated on
+# its own; 80 registers keep three 256-thread CTAs per SM)
+RDC = ["-rdc=true", "-maxrregcount=80"]
 # (source, extra flags, object): ops.cu and batch.cu are compiled in two
 # halves each (FP32 and FP64 instantiations) so that their largest parts run
 # in parallel
 CUDA_SOURCES = [("ops.cu", ["-DFL_OPS_PART=1"], "ops_f32.o"), ("ops.cu", ["-DFL_OPS_PART=2"], "ops_f64.o"),
                 ("plan.cu", [], "plan.o"), ("batch.cu", ["-DFL_BATCH_PART=1"], "batch_f32.o"),
                 ("batch.cu", ["-DFL_BATCH_PART=2"], "batch_f64.o"), ("unet.cu", [], "unet.o"),
-                ("learned.cu", [], "learned.o"), ("domain.cu", [], "domain.o")]
+                ("learned.cu", [], "learned.o"), ("domain.cu", [], "domain.o"),
+                ("persist.cu", RDC, "persist.o"), ("persist_body.cu", RDC, "persist_body.o")]
 CXX_SOURCES = ["consts.cpp"]
 
 
@@ -67,7 +72,10 @@ def build(verbose=False, ptxas_info=False):
     if ptxas_info:
         for r in results:
             sys.stdout.write(r.stderr)
-    _run([nvcc(), *ARCH, "-shared", "-o", OUT, *objs, "-lcudart"], verbose)
+    rdc_objs = [os.path.join(BUILD, o) for _, f, o in CUDA_SOURCES if f is RDC]
+    dlink = os.path.join(BUILD, "persist_dlink.o")
+    _run([nvcc(), *ARCH, "-dlink", "-Xcompiler", "-fPIC", "-o", dlink, *rdc_objs], verbose)
+    _run([nvcc(), *ARCH, "-shared", "-o", OUT, *objs, dlink, "-lcudart"], verbose)
     return OUT
 
 

@@ -83,31 +83,6 @@ __global__ void __launch_bounds__(kVecThreads) kb_cg_start(const BVecArgs<T>* __
   if (threadIdx.x == 0) a.part[bx] = s;
 }
 
-// CG update without preconditioner (z aliases r): x += alpha p, r -= alpha q
-// with alpha from the state (set by the apply's last CTA), partials of
-// ||r||^2; the last CTA of the problem takes the CG scalar step.  bx of gx
-// CTAs of the problem.
-template <typename T>
-__device__ __forceinline__ void body_b_noprec(const BVecArgs<T>& a, int bx, int gx) {
-  __shared__ double red[32];
-  if (a.st->done) return;
-  const T al = (T)a.st->alpha;
-  DotAcc<T> rr;
-  for (long long k = (long long)bx * blockDim.x + threadIdx.x; k < a.N;
-       k += (long long)gx * blockDim.x) {
-    a.x[k] += al * a.p[k];
-    const T rn = a.r[k] - al * a.q[k];
-    a.r[k] = rn;
-    rr.add(rn * rn);
-  }
-  const double s = rr.cta_total(red);
-  if (threadIdx.x == 0) a.part[bx] = s;
-  if (arrive_last(&a.st->arrive, gx)) {
-    const double rrv = cta_sum_partials(a.part, gx, red);
-    if (threadIdx.x == 0) pcg_step(a.st, rrv, rrv);
-  }
-}
-
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads) kb_noprec_update(const BVecArgs<T>* __restrict__ args,
                                                                const int* __restrict__ off, int nprob) {

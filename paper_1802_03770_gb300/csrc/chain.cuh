@@ -74,6 +74,13 @@ template <typename T> inline int col_threads(int L) {
   return L <= Cfg<T>::CT * Cfg<T>::CV ? Cfg<T>::CT : L / Cfg<T>::CV;
 }
 template <typename T> inline int row_lines(int L) { return (row_threads<T>(L) * Cfg<T>::RV) / L; }
+// lines per CTA of a row pass whose CTAs have rt threads (rt = 0: the Cfg
+// shape) while such a CTA holds at least one line
+template <typename T> inline int row_lines_at(int L, int rt) {
+  if (rt <= 0) return row_lines<T>(L);
+  const int th = L <= rt * Cfg<T>::RV ? rt : L / Cfg<T>::RV;
+  return (th * Cfg<T>::RV) / L;
+}
 template <typename T> inline int col_tx(int L) {
   return std::min(kMaxTx, (col_threads<T>(L) * Cfg<T>::CV) / L);
 }
@@ -85,6 +92,12 @@ template <typename T> inline int min_tx() {
 // if set, else the widest tile that fits the CTA
 template <typename T> inline int plan_tx(const Tables<T>& tb, int axis, int L) {
   return tb.tx[axis] > 0 ? tb.tx[axis] : col_tx<T>(L);
+}
+// a column-tile width tx narrowed to what a CTA of ct threads holds (ct = 0:
+// tx unchanged)
+template <typename T> inline int tile_at(int tx, int L, int ct) {
+  if (ct <= 0) return tx;
+  return std::max(1, std::min(tx, std::min(kMaxTx, (ct * Cfg<T>::CV) / L)));
 }
 // shared-memory bytes of `lines` lines of L complex values (padded, SBuf)
 template <typename T> inline size_t smem_bytes(int lines, int L) {
@@ -160,6 +173,31 @@ struct BVecArgs {
   long long N;
 };
 
+// CG update without preconditioner (z aliases r): x += alpha p, r -= alpha q
+// with alpha from the state (set by the apply's last CTA), partials of
+// ||r||^2; the last CTA of the problem takes the CG scalar step.  bx of gx
+// CTAs of the problem.
+template <typename T>
+__device__ __forceinline__ void body_b_noprec(const BVecArgs<T>& a, int bx, int gx) {
+  __shared__ double red[32];
+  if (a.st->done) return;
+  const T al = (T)a.st->alpha;
+  DotAcc<T> rr;
+  for (long long k = (long long)bx * blockDim.x + threadIdx.x; k < a.N;
+       k += (long long)gx * blockDim.x) {
+    a.x[k] += al * a.p[k];
+    const T rn = a.r[k] - al * a.q[k];
+    a.r[k] = rn;
+    rr.add(rn * rn);
+  }
+  const double s = rr.cta_total(red);
+  if (threadIdx.x == 0) a.part[bx] = s;
+  if (arrive_last(&a.st->arrive, gx)) {
+    const double rrv = cta_sum_partials(a.part, gx, red);
+    if (threadIdx.x == 0) pcg_step(a.st, rrv, rrv);
+  }
+}
+
 // Per-problem arguments of the batched scalar kernels (one CTA each).
 struct BScalarArgs {
   PcgState* st;
@@ -197,6 +235,52 @@ cudaError_t launch_cast_rhs(const BatchPass& bp, float* const* out32, cudaStream
 cudaError_t launch_batched_scalar(int which, const BScalarArgs* args, double* out, int nprob,
                                   cudaStream_t s);
 cudaError_t configure_batched_kernels();
+
+// --- one persistent launch for the CG iterations of a batch (persist.cu) -----
+//
+// A phase is one pass of a CG iteration over the batch: one or two items,
+// each a set of per-problem argument structs (as in a BatchPass) that the
+// phase runs side by side (they touch different problems).  Logical block b
+// of a phase belongs to item k when it falls in that item's block range.
+struct PItem {
+  int kind = 0;              // BK_* (the FP32 CG iteration's passes)
+  int nprob = 0;
+  int blocks = 0;
+  const void* args = nullptr;
+  const int* off = nullptr;  // nprob + 1 block offsets
+  const int* gx = nullptr;   // per-problem grid x-extent (2D block index)
+  const int* map = nullptr;  // per logical block: problem << 20 | block within it
+};
+constexpr int kPItems = 2;
+struct PPhase {
+  int nitems = 0;
+  int blocks = 0;            // sum of the items' blocks
+  PItem item[kPItems];
+};
+// Grid barrier state (zeroed before the first launch and after a failure).
+struct PBarrier {
+  unsigned int count;
+  unsigned int gen;
+  int err;                   // 1: a CTA gave up waiting at a barrier
+  int pad;
+};
+// The persistent kernel's CTA shape: the row passes hold
+// row_lines_at(L, kPersistThreads) lines per CTA, the strided passes tiles
+// of at most tile_at(., L, kPersistThreads) columns and the tridiagonal
+// pass kPersistTriCols columns.
+constexpr int kPersistThreads = 256;
+constexpr int kPersistTriCols = kPersistThreads / kTriSeg;
+// padded lengths the persistent kernel takes: every plan's (2^4 .. 2^11)
+constexpr int kPersistLgMin = 4, kPersistLgMax = 11;
+// Sets the kernel's shared-memory attributes for `smem` dynamic bytes and
+// returns in *grid the co-resident CTA count (blocks per SM x SMs of the
+// current device); 0 when the device cannot launch it cooperatively.
+cudaError_t persist_configure(size_t smem, int* grid);
+// Runs up to max_iters CG iterations (every phase in order, a grid barrier
+// after each), stopping after the first iteration at whose end every state
+// in states[0..nprob) is done.  Cooperative launch of `grid` CTAs.
+cudaError_t launch_persist_cg(const PPhase* phases, int nphases, PcgState* const* states, int nprob,
+                              int max_iters, PBarrier* bar, int grid, size_t smem, cudaStream_t s);
 
 template <typename T>
 ApplyChain<T> build_apply(const Geo& g, const Tables<T>& tb, const ApplyIO<T>& io);

@@ -29,6 +29,14 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+// Qualifier of the pass bodies' pointers: __restrict__ by default.  A kernel
+// that runs several passes in one launch (a pass reading what an earlier
+// pass of the same launch wrote) defines it empty before including this
+// file, so that no input is taken as read-only for the whole launch.
+#ifndef FL_RESTRICT
+#define FL_RESTRICT __restrict__
+#endif
+
 namespace fl {
 
 template <typename T> struct Cplx;
@@ -178,7 +186,7 @@ template <> struct LogR<16> { static constexpr int v = 4; };
 // table load on the stage's critical path (measured 3 % faster solves on
 // the 1024^2 workload than the table, at unchanged iteration counts).
 template <int R, bool TWT = false, typename C>
-__device__ __forceinline__ void twiddles(const C* __restrict__ tw, int step, bool inv, C* w, int lgmax) {
+__device__ __forceinline__ void twiddles(const C* FL_RESTRICT tw, int step, bool inv, C* w, int lgmax) {
   auto ld = [&](int i) {
     C t;
     if constexpr (sizeof(t.x) == 4 && !TWT) {
@@ -240,7 +248,7 @@ __host__ __device__ constexpr int clog2(int x) { return x <= 1 ? 0 : 1 + clog2(x
 template <int R, int VPT, bool IL, int LG, int NS, int MODE, bool HALF, bool TWT, typename C,
           typename Load, typename Epi>
 __device__ __forceinline__ void stage_ct(SBuf<C> buf, int ls, int ltx, int nlines,
-                                         const C* __restrict__ tw, int lgmax, bool inv, Load& load,
+                                         const C* FL_RESTRICT tw, int lgmax, bool inv, Load& load,
                                          Epi& epi, bool sync_io) {
   constexpr int NB = VPT / R;
   constexpr int LGLR = LG - LogR<R>::v;
@@ -337,7 +345,7 @@ struct FftPlan {
 
 template <int LG, int VPT, bool IL, bool HALF, bool TWT, int ST, typename C, typename Load, typename Epi>
 __device__ __forceinline__ void fft_io_stage(SBuf<C> buf, int ls, int ltx, int nlines,
-                                             const C* __restrict__ tw, int lgmax, bool inv, Load load,
+                                             const C* FL_RESTRICT tw, int lgmax, bool inv, Load load,
                                              bool sync_load, Epi epi, bool sync_epi) {
   typedef FftPlan<LG, VPT> P;
   constexpr int R = P::radix(ST);
@@ -358,7 +366,7 @@ __device__ __forceinline__ void fft_io_stage(SBuf<C> buf, int ls, int ltx, int n
 // free again after a barrier that follows the call.
 template <int LG, int VPT, bool IL, bool HALF, bool TWT, typename C, typename Load, typename Epi>
 __device__ __forceinline__ void fft_io_ct(SBuf<C> buf, int ls, int ltx, int nlines,
-                                          const C* __restrict__ tw, int lgmax, bool inv, Load load,
+                                          const C* FL_RESTRICT tw, int lgmax, bool inv, Load load,
                                           bool sync_load, Epi epi, bool sync_epi) {
   if constexpr (FftPlan<LG, VPT>::S >= 2) {
     fft_io_stage<LG, VPT, IL, HALF, TWT, 0>(buf, ls, ltx, nlines, tw, lgmax, inv, load, sync_load, epi,
@@ -395,7 +403,7 @@ __device__ __forceinline__ void fft_io_ct(SBuf<C> buf, int ls, int ltx, int nlin
 template <int VPT, bool IL, bool HALF = false, int LGHI = 11, int LGLO = 4, bool TWT = false, typename C,
           typename Load, typename Epi>
 __device__ __forceinline__ void fft_io(SBuf<C> buf, int lg, int ls, int ltx, int nlines,
-                                       const C* __restrict__ tw, int lgmax, bool inv, Load load,
+                                       const C* FL_RESTRICT tw, int lgmax, bool inv, Load load,
                                        bool sync_load, Epi epi, bool sync_epi) {
   FL_FFT_LEN(13)
   FL_FFT_LEN(12)
@@ -414,7 +422,7 @@ __device__ __forceinline__ void fft_io(SBuf<C> buf, int lg, int ls, int ltx, int
 // with the compile-time stage plan; ends with a barrier.
 template <int VPT, bool IL, int LGHI = 11, int LGLO = 4, bool TWT = false, typename C>
 __device__ __forceinline__ void fft_smem(SBuf<C> buf, int lg, int ls, int ltx, int nlines,
-                                         const C* __restrict__ tw, int lgmax, bool inv) {
+                                         const C* FL_RESTRICT tw, int lgmax, bool inv) {
   auto ld = [=](int q, int k) -> C { return IL ? buf[(k << ltx) + q] : buf[q * ls + k]; };
   auto st = [=](int q, int k, C v) {
     if (IL) buf[(k << ltx) + q] = v;

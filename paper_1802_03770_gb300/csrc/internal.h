@@ -70,6 +70,8 @@ struct ApplyIO {
   int dot_self = 0;
   int fin = 0;                // FIN_PQ: the last CTA sets st->pq and st->alpha
   T* outm = nullptr;          // nullable: M x (the apply itself) as well
+  int row_threads = 0;        // threads of a row-pass CTA; 0: the default shape
+  int col_threads = 0;        // threads of a strided-pass CTA; 0: the default shape
 };
 
 // Inputs and outputs of one preconditioner solve.
@@ -88,6 +90,9 @@ struct PrecIO {
   bool input_unmasked = false;    // keep the input outside Omega (mask applies to the output only)
   bool keep_outside = false;      // keep the output outside Omega (mask applies to the input only)
   const T* add = nullptr;         // nullable: out = mask ? (B^{-1} in + add) : 0
+  int row_threads = 0;            // threads of a row-pass CTA; 0: the default shape
+  int col_threads = 0;            // threads of a strided-pass CTA; 0: the default shape
+  int tri_cols = 0;               // columns per tridiagonal-pass CTA; 0: kTriCols
 };
 
 // --- ops.cu: launchers (return the first CUDA error) --------------------------

@@ -82,7 +82,7 @@ enum { FIN_NONE = 0, FIN_PQ = 1, FIN_STEP = 2 };
 // thread of the CTA gets the result.  The loads bypass L1, so partials
 // stored by other CTAs of the running grid are seen (after arrive_last).
 // Uses `red` (>= 32 doubles) of shared memory.
-__device__ __forceinline__ double thread_sum_partials(const double* __restrict__ part, int count) {
+__device__ __forceinline__ double thread_sum_partials(const double* FL_RESTRICT part, int count) {
   // eight loads in flight per thread, then the adds (fixed order)
   double s = 0.0;
   const int nt = blockDim.x;
@@ -98,7 +98,7 @@ __device__ __forceinline__ double thread_sum_partials(const double* __restrict__
   return s;
 }
 
-__device__ __forceinline__ double cta_sum_partials(const double* __restrict__ part, int count,
+__device__ __forceinline__ double cta_sum_partials(const double* FL_RESTRICT part, int count,
                                                    double* red) {
   double s = thread_sum_partials(part, count);
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -358,9 +358,9 @@ __device__ __forceinline__ void body_rows_fwd_at(const RowsFwdArgs<T>& a, int bx
   for (int q = 0; q < nl; ++q) {
     const int ra = 2 * (pair0 + q), rb = ra + 1;
     const bool hb = rb < a.rows;
-    typename Cplx<T>::type* __restrict__ Sa =
+    typename Cplx<T>::type* FL_RESTRICT Sa =
         a.S + ((size_t)(ra / a.rows_per_plane) * a.plane_stride + ra % a.rows_per_plane) * a.H;
-    typename Cplx<T>::type* __restrict__ Sb =
+    typename Cplx<T>::type* FL_RESTRICT Sb =
         hb ? a.S + ((size_t)(rb / a.rows_per_plane) * a.plane_stride + rb % a.rows_per_plane) * a.H
            : nullptr;
     const SBuf<C> lb = buf.at(q * ls);
@@ -456,7 +456,7 @@ __device__ __forceinline__ void body_cols_at(const ColsArgs<T>& a, int kx0, int 
   const int twlg = TWT ? lg : a.lgmax;
   if constexpr (TWT)
     for (int m = threadIdx.x; m < L; m += THREADS) cp_async<sizeof(C)>(&stw[m], &a.tw[m << (a.lgmax - lg)]);
-  const T* __restrict__ sig = a.sig + kx0;
+  const T* FL_RESTRICT sig = a.sig + kx0;
   if (a.mode == COLS_CONV && a.Lo) sig += (size_t)min(o, a.Lo - o) * a.sig_outer;
   const int nsym = a.mode == COLS_CONV ? ((hL + 1) << ltx) : 0;
   for (int e = threadIdx.x; e < nsym; e += THREADS) {
@@ -625,8 +625,8 @@ __device__ __forceinline__ void body_rows_inv_at(const RowsInvArgs<T>& a, int bx
   } else {
     for (int q = 0; q < nl; ++q) {
       const int ra = 2 * (pair0 + q);
-      const C* __restrict__ Sa = spec_row(ra);
-      const C* __restrict__ Sb = ra + 1 < a.rows ? spec_row(ra + 1) : nullptr;
+      const C* FL_RESTRICT Sa = spec_row(ra);
+      const C* FL_RESTRICT Sb = ra + 1 < a.rows ? spec_row(ra + 1) : nullptr;
 #pragma unroll 4
       for (int k = threadIdx.x; k < a.H; k += THREADS)
         put(q, k, Sa[k], Sb ? Sb[k] : cmake<C>((T)0, (T)0));
@@ -635,11 +635,11 @@ __device__ __forceinline__ void body_rows_inv_at(const RowsInvArgs<T>& a, int bx
   __syncthreads();
   fft_smem<VPT, false, LGHI, LGLO>(buf, lg, ls, 0, nl, a.tw, a.lgmax, true);
   DotAcc<T> part;
-  const T* __restrict__ xin = (a.cx != 0.0) ? a.x : nullptr;
-  const T* __restrict__ bin = (a.cb != 0.0) ? a.b : nullptr;
-  const T* __restrict__ win = a.dot_self ? nullptr : a.dotw;
-  T* __restrict__ out = a.out;
-  float* __restrict__ out32 = a.out32;
+  const T* FL_RESTRICT xin = (a.cx != 0.0) ? a.x : nullptr;
+  const T* FL_RESTRICT bin = (a.cb != 0.0) ? a.b : nullptr;
+  const T* FL_RESTRICT win = a.dot_self ? nullptr : a.dotw;
+  T* FL_RESTRICT out = a.out;
+  float* FL_RESTRICT out32 = a.out32;
   const T cm = (T)a.cm, cx = (T)a.cx, cb = (T)a.cb;
   for (int q = 0; q < 2 * nl; ++q) {
     const int row = 2 * pair0 + q;
@@ -708,7 +708,7 @@ __global__ void __launch_bounds__(THREADS, min_ctas(THREADS, LGLO)) k_rows_inv(R
 // multiply is done by the forward transform's last stage.
 template <int VPT, int LGHI, bool TWT = false, typename C>
 __device__ __forceinline__ void chirp_conv_il(SBuf<C> buf, int ltx, int L, int lg, int lgmax,
-                                              const C* __restrict__ tw, const C* __restrict__ bhat) {
+                                              const C* FL_RESTRICT tw, const C* FL_RESTRICT bhat) {
   auto ld = [=](int c, int k) -> C { return buf[(k << ltx) + c]; };
   auto epi = [=](int c, int k, C v) { buf[(k << ltx) + c] = cmul(v, bhat[k]); };
   fft_io<VPT, true, false, LGHI, 4, TWT>(buf, lg, 0, ltx, 1 << ltx, tw, lgmax, false, ld, true, epi, true);
@@ -773,10 +773,10 @@ __device__ __forceinline__ void body_dst_rows_at(const DstRowsArgs<T>& a, int bx
   const int tot = nl * hL;
   if (a.pre == DPRE_UPDATE) {
     const T al = (T)a.st->alpha;
-    T* __restrict__ xv = a.x;
-    T* __restrict__ rv = a.r;
-    const T* __restrict__ pv = a.p;
-    const T* __restrict__ qv = a.q;
+    T* FL_RESTRICT xv = a.x;
+    T* FL_RESTRICT rv = a.r;
+    const T* FL_RESTRICT pv = a.p;
+    const T* FL_RESTRICT qv = a.q;
     constexpr int U = 4;   // elements in flight per thread
     for (int e0 = threadIdx.x; e0 < tot; e0 += THREADS * U) {
       T xo[U], ro[U], po[U], qo[U];
@@ -825,7 +825,7 @@ __device__ __forceinline__ void body_dst_rows_at(const DstRowsArgs<T>& a, int bx
   __syncthreads();
   {
     // forward FFT whose last stage multiplies by bhat on the way out
-    const C* __restrict__ bhat = a.bhat;
+    const C* FL_RESTRICT bhat = a.bhat;
     auto ld = [=](int q, int k) -> C { return k < hL ? buf[q * ls + k] : cmake<C>((T)0, (T)0); };
     auto epi = [=](int q, int k, C v) { buf[q * ls + k] = cmul(v, bhat[k]); };
     fft_io<VPT, false, true, LGHI, LGLO>(buf, lg, ls, 0, nl, a.tw, a.lgmax, false, ld,
@@ -836,11 +836,11 @@ __device__ __forceinline__ void body_dst_rows_at(const DstRowsArgs<T>& a, int bx
   {
     // inverse FFT whose last stage writes the DST coefficients to global
     const T post = (T)a.post;
-    const C* __restrict__ chirp = a.chirp;
-    T* __restrict__ outp = a.out;
-    const T* __restrict__ dw = a.dotw;
-    const uint8_t* __restrict__ mask = a.mask_out;
-    const T* __restrict__ add = a.add;
+    const C* FL_RESTRICT chirp = a.chirp;
+    T* FL_RESTRICT outp = a.out;
+    const T* FL_RESTRICT dw = a.dotw;
+    const uint8_t* FL_RESTRICT mask = a.mask_out;
+    const T* FL_RESTRICT add = a.add;
     const int n = a.n;
     auto ld = [=](int q, int k) -> C { return buf[q * ls + k]; };
     auto epi = [=, &dp](int q, int k, C v) {
@@ -1090,7 +1090,7 @@ __device__ __forceinline__ void body_tri_cols(const TriArgs<T>& a, int bx) {
   const int col = bx * TC + c;
   const bool act = col < a.ncols;
   const int n = a.n, m = a.m, i0 = s * m;
-  T* __restrict__ vc = a.v + col;
+  T* FL_RESTRICT vc = a.v + col;
   const size_t ld = (size_t)a.ncols;
   T y[kTriM];
 #pragma unroll

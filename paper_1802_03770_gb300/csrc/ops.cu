@@ -397,7 +397,7 @@ ApplyChain<T> build_apply(const Geo& g, const Tables<T>& tb, const ApplyIO<T>& i
   const int d = g.d;
   const int Lx = g.L[d - 1];
   const long long rows = g.N / g.n[d - 1];
-  const int NL = row_lines<T>(Lx);
+  const int NL = row_lines_at<T>(Lx, io.row_threads);
   ch.row_blocks = (int)(((rows + 1) / 2 + NL - 1) / NL);
   ch.row_smem = smem_bytes<T>(NL, Lx);
   const int rpp = d == 3 ? g.n[1] : (int)rows;
@@ -418,7 +418,7 @@ ApplyChain<T> build_apply(const Geo& g, const Tables<T>& tb, const ApplyIO<T>& i
     a.rows_in = rows_in; a.rows_out = rows_out; a.lstride = lstride; a.ostride = ostride;
     a.nouter = nouter; a.mode = mode; a.sig_line = sig_line; a.sig_outer = sig_outer; a.Lo = Lo;
     const int L = g.L[axis];
-    const int tx = plan_tx<T>(tb, axis, L);
+    const int tx = tile_at<T>(plan_tx<T>(tb, axis, L), L, io.col_threads);
     a.ltx = ilog2i(tx);
     ch.cols_grid[ch.ncols] = dim3((g.H + tx - 1) / tx, nouter);
     ch.cols_smem[ch.ncols] = mode == COLS_CONV ? conv_tile_bytes<T>(tx, L) : cols_bytes<T>(tx, L);
@@ -471,7 +471,7 @@ PrecChain<T> build_precond(const Geo& g, const Tables<T>& tb, const PrecIO<T>& i
   const int d = g.d;
   const int nx = g.n[d - 1], Lx = g.L[d - 1];
   const long long rows = g.N / nx;
-  const int NL = row_lines<T>(Lx);
+  const int NL = row_lines_at<T>(Lx, io.row_threads);
   ch.row_blocks = (int)((rows + NL - 1) / NL);
   ch.row_smem = smem_bytes<T>(NL, Lx);
   // DST normalisation of every axis but 0 (solved by the tridiagonal pass)
@@ -495,7 +495,7 @@ PrecChain<T> build_precond(const Geo& g, const Tables<T>& tb, const PrecIO<T>& i
     a.n = g.n[axis]; a.ncols = nx; a.lg = g.lg[axis]; a.lgmax = g.lgmax;
     a.ostride = ostride; a.lstride = lstride;
     const int L = g.L[axis];
-    const int tx = plan_tx<T>(tb, axis, L);
+    const int tx = tile_at<T>(plan_tx<T>(tb, axis, L), L, io.col_threads);
     a.ltx = ilog2i(tx);
     ch.cols_grid[ch.ncols] = dim3((nx + tx - 1) / tx, nouter);
     ch.cols_smem[ch.ncols] = cols_bytes<T>(tx, L);
@@ -509,7 +509,8 @@ PrecChain<T> build_precond(const Geo& g, const Tables<T>& tb, const PrecIO<T>& i
     a.n = g.n[0];
     a.ncols = (int)(g.N / g.n[0]);
     a.m = (g.n[0] + kTriSeg - 1) / kTriSeg;
-    ch.tri_blocks = (a.ncols + kTriCols - 1) / kTriCols;
+    const int tc = io.tri_cols > 0 ? io.tri_cols : kTriCols;
+    ch.tri_blocks = (a.ncols + tc - 1) / tc;
   }
   if (d == 2) {
     ch.tri_after = 0;

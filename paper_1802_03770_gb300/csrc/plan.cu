@@ -1551,7 +1551,7 @@ struct PrecPasses {
 };
 
 fl_status solve_batched_mixed(fl_plan* const* plans, int count, const double* const* f,
-                              double* const* u, double tol, int maxit, int prec_mode,
+                              double* const* u, double tol, int maxit, int prec_mode, bool persist,
                               fl_solve_info* infos) {
   const int d = plans[0]->g.d;
   const int ncols = d == 2 ? 1 : 3;
@@ -1617,6 +1617,7 @@ fl_status solve_batched_mixed(fl_plan* const* plans, int count, const double* co
     ioa.pre = PRE_PUPDATE; ioa.u = prec[i] ? p->v32.z : p->v32.r; ioa.p = p->v32.p;
     ioa.mask = p->mask; ioa.st = st; ioa.out = p->v32.q; ioa.x = p->v32.p; ioa.cm = 1.0;
     ioa.dotw = p->v32.p; ioa.partials = p->part[P_PQ]; ioa.fin = FIN_PQ;
+    ioa.row_threads = ioa.col_threads = persist ? kPersistThreads : 0;
     apply32.add(build_apply<float>(g, p->t32, ioa));
     // the x/r update and the CG scalar step (in the last CTA of the last pass)
     if (prec[i]) {
@@ -1625,6 +1626,8 @@ fl_status solve_batched_mixed(fl_plan* const* plans, int count, const double* co
       pu.pre = DPRE_UPDATE; pu.out = p->v32.z; pu.x = p->v32.x; pu.r = p->v32.r; pu.p = p->v32.p;
       pu.q = p->v32.q; pu.rr_part = p->part[P_RR]; pu.dotw = p->v32.r; pu.dot_part = p->part[P_RZ];
       pu.st = st; pu.fin = FIN_STEP; pu.mask = p->mask;
+      pu.row_threads = pu.col_threads = persist ? kPersistThreads : 0;
+      pu.tri_cols = persist ? kPersistTriCols : 0;
       pstep.add(build_precond<float>(g, p->t32, pu));
     } else {
       BVecArgs<float> nu = {};
@@ -1648,7 +1651,63 @@ fl_status solve_batched_mixed(fl_plan* const* plans, int count, const double* co
   PS.upload(ar, pstep);
   ChainPasses<float> A32;
   A32.upload(ar, apply32, ncols);
+  // the persistent launch: the CG iteration's passes as phases (the update
+  // pass of the preconditioned problems and the plain update of the others
+  // side by side), the problems' CG states and the barrier
+  std::vector<PPhase> phases;
+  size_t psmem = 0;
+  bool map_overflow = false;
+  if (persist) {
+    // per logical block of a pass: its problem and its block within the
+    // problem, packed (one load in the kernel instead of a search)
+    auto item = [&](const BatchPass& bp, const std::vector<int>& off) {
+      PItem it;
+      it.kind = bp.kind; it.nprob = bp.nprob; it.blocks = bp.blocks;
+      it.args = bp.args; it.off = bp.off; it.gx = bp.gx;
+      std::vector<int> map(bp.blocks);
+      for (int i = 0; i < bp.nprob; ++i) {
+        if (off[i + 1] - off[i] >= (1 << 20)) map_overflow = true;
+        for (int l = off[i]; l < off[i + 1]; ++l) map[l] = (i << 20) | (l - off[i]);
+      }
+      it.map = ar.upload(map);
+      return it;
+    };
+    auto phase = [&](const BatchPass& a, const std::vector<int>& aoff, const BatchPass* b,
+                     const std::vector<int>* boff) {
+      PPhase ph;
+      const std::pair<const BatchPass*, const std::vector<int>*> xs[2] = {{&a, &aoff}, {b, boff}};
+      for (const auto& xo : xs) {
+        const BatchPass* x = xo.first;
+        if (!x || x->nprob == 0 || x->blocks == 0) continue;
+        ph.item[ph.nitems++] = item(*x, *xo.second);
+        ph.blocks += x->blocks;
+        psmem = std::max(psmem, x->smem);
+      }
+      if (ph.nitems) phases.push_back(ph);
+    };
+    phase(A32.fwd, apply32.fwd.off, nullptr, nullptr);
+    for (int j = 0; j < A32.ncols; ++j) phase(A32.cols[j], apply32.cols[j].off, nullptr, nullptr);
+    phase(A32.inv, apply32.inv.off, nullptr, nullptr);
+    phase(PS.first, pstep.first.off, &NOPREC, &noprec.off);
+    for (int j = 0; j <= PS.ncols; ++j) {
+      if (j == PS.tri_after) phase(PS.tri, pstep.tri.off, nullptr, nullptr);
+      if (j < PS.ncols) phase(PS.cols[j], pstep.cols[j].off, nullptr, nullptr);
+    }
+    phase(PS.last, pstep.last.off, nullptr, nullptr);
+  }
+  PPhase* phases_dev = ar.upload(phases);
+  std::vector<PcgState*> states(count);
+  for (int i = 0; i < count; ++i) states[i] = plans[i]->st;
+  PcgState* const* states_dev = persist ? ar.upload(states) : nullptr;
+  PBarrier* pbar = persist ? ar.alloc<PBarrier>(1) : nullptr;
   if (ar.err != cudaSuccess) return cuda_fail(ar.err, "batched argument upload");
+  int pgrid = 0;
+  if (map_overflow)
+    return fail(FL_INVALID_ARG, "FL_BATCH_PERSISTENT: a pass of one problem has 2^20 or more blocks");
+  if (persist) {
+    FL_CUDA(persist_configure(psmem, &pgrid));
+    if (pgrid < 1) return fail(FL_CUDA_ERROR, "the device cannot run the persistent batched launch");
+  }
 
   // a private stream (capturable), ordered after and before the plans' streams
   cudaStream_t bs = nullptr;
@@ -1698,6 +1757,8 @@ fl_status solve_batched_mixed(fl_plan* const* plans, int count, const double* co
     }
   } gguard{&graph, &exec};
   long long kernels_per_chunk = 0;
+  bool persist_direct = false;
+  if (persist) FL_CUDA(cudaMemsetAsync(pbar, 0, sizeof(PBarrier), bs));
   fl_status result = FL_OK;
   fl_plan* p0 = plans[0];
   for (int outer = 0;; ++outer) {
@@ -1721,7 +1782,45 @@ fl_status solve_batched_mixed(fl_plan* const* plans, int count, const double* co
     FL_CUDA(launch_batched<float>(START, bs));
     FL_CUDA(PI.launch(bs));
     FL_CUDA(launch_batched_scalar(0, INIT, nullptr, count, bs));
-    if (!exec) {
+    if (persist) {
+      // every CG iteration of every problem in one cooperative launch,
+      // captured once into a graph (direct launches if the capture fails)
+      const int max_iters = maxit + 1;
+      if (!exec && !persist_direct) {
+        ProfScope off(nullptr);
+        FL_CUDA(cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal));
+        const cudaError_t ce = launch_persist_cg(phases_dev, (int)phases.size(), states_dev, count,
+                                                 max_iters, pbar, pgrid, psmem, bs);
+        const cudaError_t ee = cudaStreamEndCapture(bs, &graph);
+        cudaError_t ie = cudaErrorUnknown;
+        if (ce == cudaSuccess && ee == cudaSuccess) ie = cudaGraphInstantiate(&exec, graph, 0);
+        if (ie != cudaSuccess) {
+          cudaGetLastError();
+          if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
+          if (graph) { cudaGraphDestroy(graph); graph = nullptr; }
+          persist_direct = true;
+        }
+        g_launches.fetch_sub(1);   // counted when the graph runs
+      }
+      if (exec) {
+        FL_CUDA(cudaGraphLaunch(exec, bs));
+        g_launches.fetch_add(1);
+      } else {
+        FL_CUDA(launch_persist_cg(phases_dev, (int)phases.size(), states_dev, count, max_iters, pbar,
+                                  pgrid, psmem, bs));
+      }
+      PBarrier bh = {};
+      for (int i = 0; i < count; ++i)
+        FL_CUDA(cudaMemcpyAsync(&sh[i], plans[i]->st, sizeof(PcgState), cudaMemcpyDeviceToHost, bs));
+      FL_CUDA(cudaMemcpyAsync(&bh, pbar, sizeof(PBarrier), cudaMemcpyDeviceToHost, bs));
+      FL_CUDA(cudaStreamSynchronize(bs));
+      if (bh.err) {
+        cudaMemsetAsync(pbar, 0, sizeof(PBarrier), bs);
+        cudaStreamSynchronize(bs);
+        return fail(FL_DEVICE_TIMEOUT, "persistent batched launch: a CTA gave up at a grid barrier");
+      }
+    }
+    if (!persist && !exec) {
       const long long before = fl_launch_count();
       ProfScope off(nullptr);
       FL_CUDA(cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal));
@@ -1738,7 +1837,7 @@ fl_status solve_batched_mixed(fl_plan* const* plans, int count, const double* co
       kernels_per_chunk = fl_launch_count() - before;
       g_launches.fetch_sub(kernels_per_chunk);   // counted when the graph runs
     }
-    for (;;) {
+    for (; !persist;) {
       FL_CUDA(cudaGraphLaunch(exec, bs));
       g_launches.fetch_add(kernels_per_chunk);
       bool alldone = true;
@@ -1819,7 +1918,9 @@ fl_status fl_solve_elliptic_batched(fl_plan* const* plans, int count, const doub
         return fail(FL_INVALID_ARG, "batched mixed solves need padded lengths <= 2048 (n_i <= 1024)");
   cudaError_t e = configure_batched_kernels();
   if (e != cudaSuccess) return cuda_fail(e, "configure_batched_kernels");
-  return solve_batched_mixed(plans, count, f_dev, u_dev, tol, maxit, prec_mode, infos);
+  // the persistent launch packs the problem index into 11 bits
+  const bool persist = (mode & FL_BATCH_PERSISTENT) != 0 && count < 2048;
+  return solve_batched_mixed(plans, count, f_dev, u_dev, tol, maxit, prec_mode, persist, infos);
 }
 
 }  // extern "C"

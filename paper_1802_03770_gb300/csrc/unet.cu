@@ -232,18 +232,31 @@ __global__ void k_to_bf16(const float* __restrict__ w, __nv_bfloat16* __restrict
 // --- 3 x 3 convolution on the tensor cores (tcgen05, kind::f16) ----------------
 //
 // Implicit GEMM: D[128 pixels][N = cout] += A[128][K] B[N][K]^T with
-// K = 9 cin (k = 9 ci + 3 dy + dx) in chunks of 64.  A (the im2col tile of
-// 8 x 16 output pixels) and B (the weights) are converted to BF16 by the
-// CTA's threads and stored K-major in the canonical no-swizzle layout (core
-// matrices of 8 rows x 8 elements, 128 contiguous bytes; adjacent along K:
-// 128 B, adjacent along rows: 1024 B).  One thread issues four 128 x N x 16
-// MMAs per chunk into a TMEM accumulator; completion is signalled through an
-// mbarrier (bounded wait).  The epilogue reads TMEM lane p (= pixel p) with
-// tcgen05.ld, adds the bias and applies the ReLU.
+// K = 9 cin (k = 9 ci + 3 dy + dx) in chunks of 64.  The CTA first stages
+// the input halo of its 8 x 16 output pixels (10 x 18 pixels of every input
+// channel, through the sources' direct / pooled / upsampled reads) in
+// shared memory as BF16, once; each K-chunk's A (im2col rows of the tile)
+// is then gathered from that halo and B (the weights) from global memory,
+// both stored K-major in the canonical no-swizzle layout (core matrices of
+// 8 rows x 8 elements, 128 contiguous bytes; adjacent along K: 128 B,
+// adjacent along rows: 1024 B) with 16-byte stores.  A and B have two
+// stages: one thread issues the four 128 x N x 16 MMAs of chunk c into a
+// TMEM accumulator and commits them to the stage's mbarrier while the CTA
+// gathers chunk c + 1 into the other stage; a stage is refilled only after
+// the commit of the MMAs that read it (bounded waits).  The epilogue reads
+// TMEM lane p (= pixel p) with tcgen05.ld, adds the bias and applies the
+// ReLU.  Operands are the same BF16 values in the same order as a gather
+// straight from global memory, so the result is too.
 namespace {
 
 constexpr int TC_M = 128, TC_KC = 64, TC_NMAX = 96;
-constexpr int TC_SMEM = TC_M * TC_KC * 2 + TC_NMAX * TC_KC * 2 + 64;
+constexpr int TC_CIN_MAX = 96;                  // input channels the halo holds
+constexpr int TC_HALO_H = 10, TC_HALO_W = 18;   // 8 x 16 tile + 1-pixel border
+constexpr int TC_HALO_PIX = TC_HALO_H * TC_HALO_W;
+constexpr int TC_STAGE_A = TC_M * TC_KC, TC_STAGE_B = TC_NMAX * TC_KC;   // BF16 elements
+constexpr int TC_SMEM = 2 * (TC_STAGE_A + TC_STAGE_B) * 2 + TC_CIN_MAX * TC_HALO_PIX * 2 + 64;
+static_assert((2 * (TC_STAGE_A + TC_STAGE_B) * 2 + TC_CIN_MAX * TC_HALO_PIX * 2) % 8 == 0,
+              "mbarriers 8-byte aligned");
 constexpr int kWaitLimit = 1 << 24;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -274,23 +287,54 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
   return false;
 }
 
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
 __global__ void __launch_bounds__(TC_M) k_conv_tc(ConvArgs a, int tmem_cols) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
-  __nv_bfloat16* sa = reinterpret_cast<__nv_bfloat16*>(tc_smem);
-  __nv_bfloat16* sb = sa + TC_M * TC_KC;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sb + TC_NMAX * TC_KC);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
+  __nv_bfloat16* sa0 = reinterpret_cast<__nv_bfloat16*>(tc_smem);   // 2 stages of A
+  __nv_bfloat16* sb0 = sa0 + 2 * TC_STAGE_A;                         // 2 stages of B
+  __nv_bfloat16* halo = sb0 + 2 * TC_STAGE_B;                        // [cin][10][18]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(halo + TC_CIN_MAX * TC_HALO_PIX);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 2);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int x0 = blockIdx.x * 16, y0 = blockIdx.y * 8;
   const int N = a.cout;
   const int K = a.cin * 9;
   const int nchunks = (K + TC_KC - 1) / TC_KC;
-  const uint32_t mb = smem_addr(mbar);
-  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb));
+  const uint32_t mb0 = smem_addr(mbar), mb1 = smem_addr(mbar + 1);
+  auto mbs = [=](int s) { return s ? mb1 : mb0; };   // mbarrier of stage s
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb0));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb1));
+  }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                  :: "r"(smem_addr(tmem_slot)), "r"(tmem_cols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  // input halo, BF16: sixteen independent source reads in flight per thread
+  {
+    const int total = a.cin * TC_HALO_PIX;
+    for (int e0 = tid; e0 < total; e0 += 16 * TC_M) {
+      float v[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int e = e0 + u * TC_M;
+        v[u] = 0.f;
+        if (e < total) {
+          const int ci = e / TC_HALO_PIX, r = e - ci * TC_HALO_PIX;
+          const int hy = r / TC_HALO_W, hx = r - hy * TC_HALO_W;
+          v[u] = src_value(a, ci, y0 + hy - 1, x0 + hx - 1);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int e = e0 + u * TC_M;
+        if (e < total) halo[e] = __float2bfloat16(v[u]);
+      }
+    }
   }
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   __syncthreads();
@@ -298,32 +342,74 @@ __global__ void __launch_bounds__(TC_M) k_conv_tc(ConvArgs a, int tmem_cols) {
   const uint32_t tmem = *tmem_slot;
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
                          ((uint32_t)(TC_M >> 4) << 24);
+  // this thread's 8-wide K group of every chunk, and its first tile row
+  const int g = tid & 7;
+  const int row0 = tid >> 3;
   bool ok = true;
-  uint32_t fail_phase = 0;
+  int issued = 0;   // chunks whose MMAs were issued (and committed)
   for (int ch = 0; ch < nchunks; ++ch) {
-    const int k0 = ch * TC_KC;
-    // A: im2col of the 8 x 16 pixel tile
-    for (int e = tid; e < TC_M * TC_KC; e += TC_M) {
-      const int p = e >> 6, kl = e & 63;
-      const int k = k0 + kl;
-      float v = 0.f;
-      if (k < K) {
+    const int s = ch & 1;
+    if (ch >= 2) {
+      // the MMAs of chunk ch - 2 read stage s: wait for their commit.  A
+      // wait that gives up (in any thread) ends the loop for the whole CTA:
+      // no more refills, no more MMAs.
+      const bool got = mbar_wait(mbs(s), (uint32_t)(((ch - 2) >> 1) & 1));
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (__syncthreads_or(!got)) {
+        ok = false;
+        break;
+      }
+    }
+    __nv_bfloat16* sa = sa0 + s * TC_STAGE_A;
+    __nv_bfloat16* sb = sb0 + s * TC_STAGE_B;
+    const int kg = ch * TC_KC + 8 * g;   // first k of the group
+    // A: tile rows row0, row0 + 16, ..., the group's 8 k from the halo
+    {
+      int off[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int k = kg + u;
         const int ci = k / 9, t = k - ci * 9;
         const int dy = t / 3, dx = t - dy * 3;
-        v = src_value(a, ci, y0 + (p >> 4) + dy - 1, x0 + (p & 15) + dx - 1);
+        off[u] = k < K ? ci * TC_HALO_PIX + dy * TC_HALO_W + dx : -1;
       }
-      sa[canon64(p, kl)] = __float2bfloat16(v);
+      const __nv_bfloat16 zero = __float2bfloat16(0.f);
+#pragma unroll 2
+      for (int p = row0; p < TC_M; p += 16) {
+        const int base = (p >> 4) * TC_HALO_W + (p & 15);
+        __nv_bfloat16 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = off[u] >= 0 ? halo[off[u] + base] : zero;
+        uint4 q;
+        q.x = pack_bf16(v[0], v[1]);
+        q.y = pack_bf16(v[2], v[3]);
+        q.z = pack_bf16(v[4], v[5]);
+        q.w = pack_bf16(v[6], v[7]);
+        *reinterpret_cast<uint4*>(sa + canon64(p, 8 * g)) = q;
+      }
     }
-    // B: weights of the chunk
-    for (int e = tid; e < N * TC_KC; e += TC_M) {
-      const int o = e >> 6, kl = e & 63;
-      const int k = k0 + kl;
-      float v = 0.f;
-      if (k < K) {
-        const int ci = k / 9, t = k - ci * 9;
-        v = weight(a, o, ci, t);
+    // B: the weights of the group's 8 k for output channels o = row0, row0 + 16,
+    // ... (all of this thread's loads issued together)
+#pragma unroll
+    for (int o = row0; o < TC_NMAX; o += 16) {
+      if (o >= N) break;
+      __nv_bfloat16 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int k = kg + u;
+        float w = 0.f;
+        if (k < K) {
+          const int ci = k / 9, t = k - ci * 9;
+          w = weight(a, o, ci, t);
+        }
+        v[u] = __float2bfloat16(w);
       }
-      sb[canon64(o, kl)] = __float2bfloat16(v);
+      uint4 q;
+      q.x = pack_bf16(v[0], v[1]);
+      q.y = pack_bf16(v[2], v[3]);
+      q.z = pack_bf16(v[4], v[5]);
+      q.w = pack_bf16(v[6], v[7]);
+      *reinterpret_cast<uint4*>(sb + canon64(o, 8 * g)) = q;
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
@@ -340,23 +426,19 @@ __global__ void __launch_bounds__(TC_M) k_conv_tc(ConvArgs a, int tmem_cols) {
             :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                   :: "r"(mb) : "memory");
+                   :: "r"(mbs(s)) : "memory");
     }
-    // the MMAs read sa / sb: wait before the next chunk overwrites them.
-    // A wait that gives up (in any thread) ends the loop for the whole CTA:
-    // no more refills of sa / sb, no more MMAs.
-    const bool got = mbar_wait(mb, (uint32_t)(ch & 1));
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (__syncthreads_or(!got)) {
-      ok = false;
-      fail_phase = (uint32_t)(ch & 1);
-      break;
-    }
+    issued = ch + 1;
   }
-  if (!ok) {
-    // one more bounded wait for the MMAs in flight before TMEM is released
-    if (tid == 0) {
-      mbar_wait(mb, fail_phase);
+  // the last commit covers every MMA issued before it
+  if (issued > 0) {
+    const int last = issued - 1;
+    const bool got = mbar_wait(mbs(last & 1), (uint32_t)((last >> 1) & 1));
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (__syncthreads_or(!got)) ok = false;
+    if (!ok && tid == 0) {
+      // one more bounded wait for the MMAs in flight before TMEM is released
+      mbar_wait(mbs(last & 1), (uint32_t)((last >> 1) & 1));
       if (a.err) atomicExch(a.err, 1);
     }
     __syncthreads();
@@ -399,8 +481,8 @@ cudaError_t configure_unet_kernels() {
 }
 
 cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s) {
-  if (a.tensor_cores && a.k == 3 && a.cout % 16 == 0 && a.cout <= TC_NMAX && a.H % 8 == 0 &&
-      a.W % 16 == 0) {
+  if (a.tensor_cores && a.k == 3 && a.cout % 16 == 0 && a.cout <= TC_NMAX && a.cin <= TC_CIN_MAX &&
+      a.H % 8 == 0 && a.W % 16 == 0) {
     const int cols = a.cout <= 32 ? 32 : (a.cout <= 64 ? 64 : 128);
     dim3 grid(a.W / 16, a.H / 8);
     FL_KERNEL("unet_conv3_tc", s, k_conv_tc<<<grid, TC_M, TC_SMEM, s>>>(a, cols));

@@ -13,7 +13,9 @@ every step an FP32-CG + FP64-refinement solve of (I + dt M) u = u_prev to
 1e-8 (preconditioner I + dt C h^d L), warm-started.
 batched: 64 problems with sides uniform in {96, 128, ..., 768} and alpha ~
 U(0.3, 1.8), seeded Gaussian-mixture right-hand sides, to 1e-8, solved in
-lockstep (fl_solve_elliptic_batched) and, for comparison, one after another.
+one call (fl_solve_elliptic_batched: one launch per pass over all problems,
+and with FL_BATCH_PERSISTENT one persistent launch per refinement step) and,
+for comparison, one after another.
 lshape: the occluded-domain example (Sec. 4.4) at n = 128 .. 1024, alpha =
 1.75, FP64 CG with and without the FD preconditioner (and with its
 balanced shift), to 1e-6 and 1e-9; octagon: the same on the paper's
@@ -87,12 +89,17 @@ def batched(count=64, seed=7, precond="auto", autotune=False):
             p.autotune()
         t_tune = time.perf_counter() - t0
     mode = L.FL_MODE_MIXED | PRECONDS[precond]
-    solve_batched(plans, fs, tol=1e-8, mode=mode)         # warm-up (graph capture)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    _, infos = solve_batched(plans, fs, tol=1e-8, mode=mode)
-    torch.cuda.synchronize()
-    tb = time.perf_counter() - t0
+
+    def timed(m):
+        solve_batched(plans, fs, tol=1e-8, mode=m)        # warm-up (graph capture)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, inf = solve_batched(plans, fs, tol=1e-8, mode=m)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, inf
+
+    tb, infos = timed(mode | L.FL_BATCH_PERSISTENT)       # one persistent launch per step
+    tl, infos_l = timed(mode)                             # one launch per pass
     for p, f in zip(plans, fs):                          # warm-up (per-plan graph capture)
         p.solve(f, tol=1e-8, mode=mode)
     torch.cuda.synchronize()
@@ -104,8 +111,13 @@ def batched(count=64, seed=7, precond="auto", autotune=False):
     return {"workload": f"{count} 2D problems, sides 96..768, alpha U(0.3,1.8)", "precond": precond,
             "autotuned_tiles": autotune, "autotune_seconds": t_tune,
             "batched_seconds": tb, "batched_solves_per_s": count / tb,
+            "batched_how": "inner CG of every problem in one persistent cooperative launch "
+                           "per refinement step (CUDA graph)",
+            "lockstep_seconds": tl, "lockstep_solves_per_s": count / tl,
             "sequential_seconds": ts, "sequential_solves_per_s": count / ts,
-            "all_converged": all(i["converged"] == 1 for i in infos),
+            "mean_iterations": sum(i["iterations"] for i in infos) / count,
+            "lockstep_mean_iterations": sum(i["iterations"] for i in infos_l) / count,
+            "all_converged": all(i["converged"] == 1 for i in infos + infos_l),
             "total_dof": int(sum(n * n for n in sides))}
 
 

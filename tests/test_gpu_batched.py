@@ -1,5 +1,8 @@
-"""Batched solves (many problems of uneven size in lockstep, one launch per
-pass, CG iterations replayed as a CUDA graph) against the FP64 oracle."""
+"""Batched solves (many problems of uneven size at once: one launch per pass
+over all problems, CG iterations replayed as a CUDA graph, or with
+FL_BATCH_PERSISTENT the inner CG iterations of each refinement step in one
+persistent cooperative launch) against the FP64 oracle and against each
+other."""
 
 import numpy as np
 import pytest
@@ -69,3 +72,73 @@ def test_batched_rejects_mixed_dimensions_and_duplicates():
         solve_batched([a, b], [f2, f3])
     with pytest.raises(_lib.FracLapError, match="INVALID_ARG"):
         solve_batched([a, a], [f2, f2])
+
+
+def _batch_2d(sides, alphas, seed0):
+    plans, fd, fs = [], [], []
+    for i, (n, a) in enumerate(zip(sides, alphas)):
+        f = inputs.gaussian_mixture(n, 2, 16, seed0 + i)
+        fs.append(f)
+        plans.append(Plan(2, (n, n), 1.0 / (n + 1), a))
+        fd.append(torch.tensor(f, dtype=torch.float64, device="cuda:0").view(-1))
+    return plans, fd, fs
+
+
+@pytest.mark.parametrize("prec", [_lib.FL_PRECOND_AUTO, _lib.FL_PRECOND_FD, _lib.FL_PRECOND_NONE])
+def test_persistent_launch_matches_lockstep(prec):
+    """The persistent launch runs the same pass bodies as the lockstep
+    launches (other row-pass CTA shapes, so other partial-sum groupings):
+    both converge to 1e-8 in the oracle's FP64 residual, with iteration
+    counts within two of each other and solutions that agree to the solve
+    tolerance; one kernel launch per refinement step covers the CG."""
+    sides = [96, 64, 160, 33, 128, 200, 17, 255]
+    alphas = inputs.alpha_draws(len(sides), 5)
+    plans, fd, fs = _batch_2d(sides, alphas, 300)
+    lib = _lib.load()
+    before = lib.fl_launch_count()
+    us_p, inf_p = solve_batched(plans, fd, tol=1e-8,
+                                mode=_lib.FL_MODE_MIXED | prec | _lib.FL_BATCH_PERSISTENT)
+    torch.cuda.synchronize()
+    launches_p = lib.fl_launch_count() - before
+    before = lib.fl_launch_count()
+    us_l, inf_l = solve_batched(plans, fd, tol=1e-8, mode=_lib.FL_MODE_MIXED | prec)
+    torch.cuda.synchronize()
+    launches_l = lib.fl_launch_count() - before
+    for n, a, f, up, ul, ip, il in zip(sides, alphas, fs, us_p, us_l, inf_p, inf_l):
+        assert ip["converged"] == 1 and il["converged"] == 1, (ip, il)
+        assert abs(ip["iterations"] - il["iterations"]) <= 2, (n, a, ip, il)
+        up = up.cpu().numpy().reshape(n, n)
+        ul = ul.cpu().numpy().reshape(n, n)
+        op = OPlan(2, n, 1.0 / (n + 1), a)
+        res = np.linalg.norm(op.apply(up) - f) / np.linalg.norm(f)
+        assert res <= 1.05e-8, (n, a, res)
+        assert np.linalg.norm(up - ul) <= 1e-6 * np.linalg.norm(ul), (n, a)
+    # per refinement step: start-up passes, the one CG launch, FP64 residual
+    outer = max(i["outer_iterations"] for i in inf_p)
+    its = max(i["iterations"] for i in inf_p)
+    assert launches_p < launches_l
+    assert launches_p <= 16 * (outer + 1), (launches_p, outer)
+    assert launches_l >= its, (launches_l, its)
+
+
+def test_persistent_launch_3d():
+    shapes = [(24, 20, 28), (16, 16, 16), (33, 17, 9)]
+    alphas = [0.6, 1.2, 1.7]
+    plans, fd, fs = [], [], []
+    for i, (n, a) in enumerate(zip(shapes, alphas)):
+        f = inputs.gaussian_mixture(n, 3, 8, 500 + i)
+        fs.append(f)
+        plans.append(Plan(3, n, 1.0 / (max(n) + 1), a))
+        fd.append(torch.tensor(f, dtype=torch.float64, device="cuda:0").view(-1))
+    us_p, inf_p = solve_batched(plans, fd, tol=1e-8,
+                                mode=_lib.FL_MODE_MIXED | _lib.FL_PRECOND_AUTO | _lib.FL_BATCH_PERSISTENT)
+    us_l, inf_l = solve_batched(plans, fd, tol=1e-8)
+    torch.cuda.synchronize()
+    for n, a, f, up, ul, ip, il in zip(shapes, alphas, fs, us_p, us_l, inf_p, inf_l):
+        assert ip["converged"] == 1 and il["converged"] == 1, (ip, il)
+        assert abs(ip["iterations"] - il["iterations"]) <= 2, (n, a, ip, il)
+        up = up.cpu().numpy().reshape(n)
+        op = OPlan(3, n, 1.0 / (max(n) + 1), a)
+        res = np.linalg.norm(op.apply(up) - f) / np.linalg.norm(f)
+        assert res <= 1.05e-8, (n, a, res)
+        assert np.linalg.norm(up - ul.cpu().numpy().reshape(n)) <= 1e-6 * np.linalg.norm(up)
