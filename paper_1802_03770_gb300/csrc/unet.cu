@@ -250,13 +250,23 @@ __global__ void k_to_bf16(const float* __restrict__ w, __nv_bfloat16* __restrict
 namespace {
 
 constexpr int TC_M = 128, TC_KC = 64, TC_NMAX = 96;
+// threads per CTA: two per pixel row of the tile for the gathers; in the
+// epilogue warps w and w + 4 read the same TMEM lane quadrant, halves of
+// the columns
+constexpr int TC_THREADS = 256;
 constexpr int TC_CIN_MAX = 96;                  // input channels the halo holds
 constexpr int TC_HALO_H = 10, TC_HALO_W = 18;   // 8 x 16 tile + 1-pixel border
 constexpr int TC_HALO_PIX = TC_HALO_H * TC_HALO_W;
-constexpr int TC_STAGE_A = TC_M * TC_KC, TC_STAGE_B = TC_NMAX * TC_KC;   // BF16 elements
-constexpr int TC_SMEM = 2 * (TC_STAGE_A + TC_STAGE_B) * 2 + TC_CIN_MAX * TC_HALO_PIX * 2 + 64;
-static_assert((2 * (TC_STAGE_A + TC_STAGE_B) * 2 + TC_CIN_MAX * TC_HALO_PIX * 2) % 8 == 0,
-              "mbarriers 8-byte aligned");
+constexpr int TC_STAGE_A = TC_M * TC_KC;   // BF16 elements of one A stage
+// halo bytes of cin channels, rounded up to 16 (the mbarriers follow it)
+__host__ __device__ constexpr int tc_halo_bytes(int cin) { return (cin * TC_HALO_PIX * 2 + 15) & ~15; }
+// dynamic shared memory of a launch with cout = n, cin input channels: the
+// A stages (32 KB), the B stages (256 n bytes: 16-byte multiples for n a
+// multiple of 16), the halo, two mbarriers and the TMEM address slot
+__host__ __device__ constexpr int tc_smem_bytes(int n, int cin) {
+  return 2 * TC_STAGE_A * 2 + 2 * n * TC_KC * 2 + tc_halo_bytes(cin) + 32;
+}
+constexpr int TC_SMEM = tc_smem_bytes(TC_NMAX, TC_CIN_MAX);   // the largest launch
 constexpr int kWaitLimit = 1 << 24;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -291,16 +301,20 @@ __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi
   return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
-__global__ void __launch_bounds__(TC_M) k_conv_tc(ConvArgs a, int tmem_cols) {
+__global__ void __launch_bounds__(TC_THREADS) k_conv_tc(ConvArgs a, int tmem_cols) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
-  __nv_bfloat16* sa0 = reinterpret_cast<__nv_bfloat16*>(tc_smem);   // 2 stages of A
-  __nv_bfloat16* sb0 = sa0 + 2 * TC_STAGE_A;                         // 2 stages of B
-  __nv_bfloat16* halo = sb0 + 2 * TC_STAGE_B;                        // [cin][10][18]
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(halo + TC_CIN_MAX * TC_HALO_PIX);
+  const int N = a.cout;
+  // shared memory sized for this layer (tc_smem_bytes): two stages of A,
+  // two of B (N rows), the halo [cin][10][18], two mbarriers, the TMEM slot
+  __nv_bfloat16* sa0 = reinterpret_cast<__nv_bfloat16*>(tc_smem);
+  __nv_bfloat16* sb0 = sa0 + 2 * TC_STAGE_A;
+  const int stage_b = N * TC_KC;
+  __nv_bfloat16* halo = sb0 + 2 * stage_b;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(
+      reinterpret_cast<unsigned char*>(halo) + tc_halo_bytes(a.cin));
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 2);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int x0 = blockIdx.x * 16, y0 = blockIdx.y * 8;
-  const int N = a.cout;
   const int K = a.cin * 9;
   const int nchunks = (K + TC_KC - 1) / TC_KC;
   const uint32_t mb0 = smem_addr(mbar), mb1 = smem_addr(mbar + 1);
@@ -317,11 +331,11 @@ __global__ void __launch_bounds__(TC_M) k_conv_tc(ConvArgs a, int tmem_cols) {
   // input halo, BF16: sixteen independent source reads in flight per thread
   {
     const int total = a.cin * TC_HALO_PIX;
-    for (int e0 = tid; e0 < total; e0 += 16 * TC_M) {
+    for (int e0 = tid; e0 < total; e0 += 16 * TC_THREADS) {
       float v[16];
 #pragma unroll
       for (int u = 0; u < 16; ++u) {
-        const int e = e0 + u * TC_M;
+        const int e = e0 + u * TC_THREADS;
         v[u] = 0.f;
         if (e < total) {
           const int ci = e / TC_HALO_PIX, r = e - ci * TC_HALO_PIX;
@@ -331,7 +345,7 @@ __global__ void __launch_bounds__(TC_M) k_conv_tc(ConvArgs a, int tmem_cols) {
       }
 #pragma unroll
       for (int u = 0; u < 16; ++u) {
-        const int e = e0 + u * TC_M;
+        const int e = e0 + u * TC_THREADS;
         if (e < total) halo[e] = __float2bfloat16(v[u]);
       }
     }
@@ -343,6 +357,7 @@ __global__ void __launch_bounds__(TC_M) k_conv_tc(ConvArgs a, int tmem_cols) {
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
                          ((uint32_t)(TC_M >> 4) << 24);
   // this thread's 8-wide K group of every chunk, and its first tile row
+  constexpr int kRowStep = TC_THREADS / 8;
   const int g = tid & 7;
   const int row0 = tid >> 3;
   bool ok = true;
@@ -361,9 +376,9 @@ __global__ void __launch_bounds__(TC_M) k_conv_tc(ConvArgs a, int tmem_cols) {
       }
     }
     __nv_bfloat16* sa = sa0 + s * TC_STAGE_A;
-    __nv_bfloat16* sb = sb0 + s * TC_STAGE_B;
+    __nv_bfloat16* sb = sb0 + s * stage_b;
     const int kg = ch * TC_KC + 8 * g;   // first k of the group
-    // A: tile rows row0, row0 + 16, ..., the group's 8 k from the halo
+    // A: tile rows row0, row0 + kRowStep, ..., the group's 8 k from the halo
     {
       int off[8];
 #pragma unroll
@@ -375,7 +390,7 @@ __global__ void __launch_bounds__(TC_M) k_conv_tc(ConvArgs a, int tmem_cols) {
       }
       const __nv_bfloat16 zero = __float2bfloat16(0.f);
 #pragma unroll 2
-      for (int p = row0; p < TC_M; p += 16) {
+      for (int p = row0; p < TC_M; p += kRowStep) {
         const int base = (p >> 4) * TC_HALO_W + (p & 15);
         __nv_bfloat16 v[8];
 #pragma unroll
@@ -388,10 +403,10 @@ __global__ void __launch_bounds__(TC_M) k_conv_tc(ConvArgs a, int tmem_cols) {
         *reinterpret_cast<uint4*>(sa + canon64(p, 8 * g)) = q;
       }
     }
-    // B: the weights of the group's 8 k for output channels o = row0, row0 + 16,
-    // ... (all of this thread's loads issued together)
+    // B: the weights of the group's 8 k for output channels o = row0,
+    // row0 + kRowStep, ... (all of this thread's loads issued together)
 #pragma unroll
-    for (int o = row0; o < TC_NMAX; o += 16) {
+    for (int o = row0; o < TC_NMAX; o += kRowStep) {
       if (o >= N) break;
       __nv_bfloat16 v[8];
 #pragma unroll
@@ -443,16 +458,18 @@ __global__ void __launch_bounds__(TC_M) k_conv_tc(ConvArgs a, int tmem_cols) {
     }
     __syncthreads();
   }
-  // epilogue: lane p of TMEM holds pixel p
-  const int p = warp * 32 + (tid & 31);
+  // epilogue: lane p of TMEM holds pixel p; warp w reads lanes 32 (w mod 4)
+  // .. + 31 (its quadrant) and the 16-column groups 16 (w / 4), + 32, ...
+  const int quad = warp & 3;
+  const int p = quad * 32 + (tid & 31);
   const int y = y0 + (p >> 4), x = x0 + (p & 15);
-  for (int c0 = 0; c0 < N; c0 += 16) {
+  for (int c0 = 16 * (warp >> 2); c0 < N; c0 += 16 * (TC_THREADS / TC_M)) {
     if (!ok) {   // outputs of a tile whose MMAs did not complete are zeroed
       for (int j = 0; j < 16; ++j) a.out[((size_t)(c0 + j) * a.H + y) * a.W + x] = 0.f;
       continue;
     }
     uint32_t v[16];
-    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+    const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0;
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
@@ -485,7 +502,8 @@ cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s) {
       a.H % 8 == 0 && a.W % 16 == 0) {
     const int cols = a.cout <= 32 ? 32 : (a.cout <= 64 ? 64 : 128);
     dim3 grid(a.W / 16, a.H / 8);
-    FL_KERNEL("unet_conv3_tc", s, k_conv_tc<<<grid, TC_M, TC_SMEM, s>>>(a, cols));
+    FL_KERNEL("unet_conv3_tc", s,
+              k_conv_tc<<<grid, TC_THREADS, tc_smem_bytes(a.cout, a.cin), s>>>(a, cols));
     return cudaGetLastError();
   }
   dim3 grid(a.W / TILE, a.H / TILE, (a.cout + CO - 1) / CO);

@@ -24,6 +24,9 @@ octagonal domain.
 paper's; batched default: auto, none for alpha < 1), shifted (FD with the
 balanced shift) or stencil (the stencil part of M).  --autotune tunes the
 column tiles of every batched plan (fl_plan_autotune) before timing.
+persistent: one 1024^2 and one 256^2 problem (alpha = 1.5) through the
+batched call, with the persistent launch and with the lockstep launches,
+without and with the FD preconditioner: time per CG iteration.
 tiles: one FP32 apply + FD preconditioner solve (the work of a CG
 iteration) on square 2D grids of side 96 .. 1024 and cubes of side 64 .. 256,
 alpha = 1, timed with the widest column tiles and after fl_plan_autotune.
@@ -46,7 +49,7 @@ from .api import Plan, solve_batched
 
 
 PRECONDS = {"fd": L.FL_PRECOND_FD, "auto": L.FL_PRECOND_AUTO, "shifted": L.FL_PRECOND_SHIFTED,
-            "stencil": L.FL_PRECOND_STENCIL}
+            "stencil": L.FL_PRECOND_STENCIL, "none": L.FL_PRECOND_NONE}
 
 
 def timestep(n=256, steps=100, alpha=1.5, dt=1e-3, seed=3, precond="fd"):
@@ -267,10 +270,39 @@ def richardson(alphas=(1.25, 1.5, 1.75), parts=("2d", "3d", "td2", "td3")):
     return {"workload": "grid error estimates (eq. rich)", "rows": rows}
 
 
+def persistent(sides=(1024, 256), alpha=1.5, reps=3):
+    """Time per CG iteration of one problem solved through
+    fl_solve_elliptic_batched with the persistent launch and with the
+    lockstep launches, without and with the FD preconditioner (four and six
+    passes per iteration)."""
+    import torch
+    rows = []
+    for n in sides:
+        plans = [Plan(2, (n, n), 1.0 / (n + 1), alpha)]
+        fs = [torch.tensor(inputs.gaussian_mixture(n, 2, 32, 41), dtype=torch.float64,
+                           device="cuda").view(-1)]
+        for pname in ("none", "fd"):
+            row = {"n": n, "precond": pname}
+            for launch, extra in (("persistent", L.FL_BATCH_PERSISTENT), ("lockstep", 0)):
+                mode = L.FL_MODE_MIXED | PRECONDS[pname] | extra
+                solve_batched(plans, fs, tol=1e-8, mode=mode)    # warm-up (graph capture)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for _ in range(reps):
+                    _, inf = solve_batched(plans, fs, tol=1e-8, mode=mode)
+                torch.cuda.synchronize()
+                dt = (time.perf_counter() - t0) / reps
+                its = inf[0]["iterations"]
+                row[launch] = {"ms_per_solve": 1e3 * dt, "iterations": its,
+                               "us_per_iteration": 1e6 * dt / max(1, its)}
+            rows.append(row)
+    return {"workload": f"one 2D problem per batched call, alpha {alpha}, to 1e-8", "rows": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("which", choices=["timestep", "batched", "lshape", "octagon", "tiles",
-                                      "richardson"])
+                                      "richardson", "persistent"])
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--count", type=int, default=64)
     ap.add_argument("--precond", choices=sorted(PRECONDS), default=None)
@@ -283,6 +315,8 @@ def main():
         res = batched(args.count, precond=args.precond or "auto", autotune=args.autotune)
     elif args.which == "tiles":
         res = tiles()
+    elif args.which == "persistent":
+        res = persistent()
     elif args.which == "richardson":
         res = richardson()
     elif args.which == "octagon":
