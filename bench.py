@@ -645,20 +645,32 @@ def profile_case():
     print(json.dumps(info))
 
 
-def profile_case_unet(n=512):
-    """Five forwards of the learned preconditioner's U-Net at 512^2 on the
-    tensor cores (seeded weights and features); each launches the tcgen05
-    3x3 convolutions of every layer."""
+def profile_case_unet(n=512, reps=20):
+    """U-Net forwards of the learned preconditioner at 512^2 (seeded weights
+    and features): five on the tensor cores (the ncu captures take their
+    tcgen05 3x3 convolutions), then `reps` timed forwards (CUDA events) on
+    the tensor cores and on the CUDA cores."""
     import torch
     from paper_1802_03770_gb300.api import Net
     net = Net(n, n, seed=1)
-    net.tensor_cores(True)
     g = torch.Generator().manual_seed(5)
     x = torch.randn(3 * n * n, generator=g).to("cuda:0")
-    for _ in range(5):
-        y = net.forward(x)
-    torch.cuda.synchronize()
-    print(json.dumps({"y_norm": float(y.norm())}))
+    out = {}
+    for tc in (True, False):
+        net.tensor_cores(tc)
+        for _ in range(5):
+            y = net.forward(x)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            y = net.forward(x)
+        e1.record()
+        torch.cuda.synchronize()
+        out["tcgen05" if tc else "cuda_cores"] = {"ms_per_forward": e0.elapsed_time(e1) / reps,
+                                                  "y_norm": float(y.norm())}
+    print(json.dumps({"unet512_forward": out}))
 
 
 def profile_case_3d(n=256):
@@ -700,7 +712,7 @@ def main():
     ap.add_argument("--profile-case-3d", action="store_true",
                     help="run five FP32 applies on the 256^3 grid and exit (for ncu captures)")
     ap.add_argument("--profile-case-unet", action="store_true",
-                    help="run five 512^2 U-Net forwards on the tensor cores and exit (for ncu)")
+                    help="time 512^2 U-Net forwards (tensor cores, CUDA cores) and exit")
     args = ap.parse_args()
     if args.profile_case:
         profile_case()
