@@ -261,6 +261,15 @@ long long fl_launch_count(void);
 fl_status fl_profile_enable(fl_plan* plan, int enable);
 int fl_profile_read(fl_plan* plan, fl_kernel_stat* stats, int max_stats);
 
+/* Check of the bounded grid barrier of the FL_BATCH_PERSISTENT launch (no
+ * counterpart in the paper): one cooperative launch on the current device,
+ * one CTA per SM, all arriving at a barrier that waits for `missing` (0 ..
+ * 1024) arrivals more than the grid has.  missing = 0: FL_OK.  missing > 0:
+ * the barrier never completes; every CTA gives up after its bounded wait
+ * (2 s) and the call returns FL_DEVICE_TIMEOUT with the context intact.
+ * Synchronous; allocates and frees a 16-byte device buffer. */
+fl_status fl_check_grid_barrier(int missing);
+
 /* y = M u in FP32, like fl_apply_f32, but its one scratch buffer (the
  * half-spectrum workspace of the FFT passes) is a fixed, library-owned
  * device array instead of the plan's workspace, and the call allocates

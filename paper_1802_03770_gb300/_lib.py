@@ -86,6 +86,7 @@ SIGNATURES = {
                                        ctypes.POINTER(FlSolveInfo)]),
     "fl_sync": (_I, [_P]),
     "fl_launch_count": (ctypes.c_longlong, []),
+    "fl_check_grid_barrier": (_I, [_I]),
     "fl_profile_enable": (_I, [_P, _I]),
     "fl_profile_read": (_I, [_P, ctypes.POINTER(FlKernelStat), _I]),
     "fl_net_create": (_I, [_I, _I, ctypes.c_uint64, _P, ctypes.POINTER(_P)]),

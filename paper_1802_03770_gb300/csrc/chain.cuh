@@ -281,6 +281,11 @@ cudaError_t persist_configure(size_t smem, int* grid);
 // in states[0..nprob) is done.  Cooperative launch of `grid` CTAs.
 cudaError_t launch_persist_cg(const PPhase* phases, int nphases, PcgState* const* states, int nprob,
                               int max_iters, PBarrier* bar, int grid, size_t smem, cudaStream_t s);
+// One cooperative launch (one CTA per SM) whose CTAs all arrive at one grid
+// barrier that waits for `missing` arrivals more than the grid has;
+// *gave_up = 1 when the CTAs gave up waiting (always, for missing > 0,
+// after the bounded wait).  Synchronous; on the current device.
+cudaError_t persist_barrier_check(int missing, int* gave_up);
 
 template <typename T>
 ApplyChain<T> build_apply(const Geo& g, const Tables<T>& tb, const ApplyIO<T>& io);

@@ -137,7 +137,45 @@ __global__ void __launch_bounds__(kPT, 1)
   }
 }
 
+// Diagnostic: every CTA of the grid arrives at one grid barrier that waits
+// for gridDim.x + extra arrivals.
+__global__ void k_barrier_check(PBarrier* bar, unsigned int extra) {
+  grid_barrier(bar, gridDim.x + extra);
+}
+
 }  // namespace
+
+cudaError_t persist_barrier_check(int missing, int* gave_up) {
+  *gave_up = 0;
+  int dev = 0, sms = 0, coop = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (e != cudaSuccess) return e;
+  if (!coop) return cudaErrorNotSupported;
+  PBarrier* bar = nullptr;
+  e = cudaMalloc(&bar, sizeof(PBarrier));
+  if (e != cudaSuccess) return e;
+  e = cudaMemset(bar, 0, sizeof(PBarrier));
+  if (e == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(sms);
+    cfg.blockDim = dim3(kPT);
+    cfg.stream = nullptr;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    FL_KERNEL("barrier_check", nullptr,
+              e = cudaLaunchKernelEx(&cfg, k_barrier_check, bar, (unsigned int)missing));
+  }
+  PBarrier h = {};
+  if (e == cudaSuccess) e = cudaMemcpy(&h, bar, sizeof(PBarrier), cudaMemcpyDeviceToHost);
+  cudaFree(bar);
+  if (e == cudaSuccess) *gave_up = h.err;
+  return e;
+}
 
 cudaError_t persist_configure(size_t smem, int* grid) {
   *grid = 0;

@@ -1324,6 +1324,14 @@ fl_status fl_time_step(fl_plan* p, double dt, double theta, const double* u_prev
 
 long long fl_launch_count(void) { return g_launches.load(); }
 
+fl_status fl_check_grid_barrier(int missing) {
+  if (missing < 0 || missing > 1024) return fail(FL_INVALID_ARG, "missing must be in [0, 1024]");
+  int gave_up = 0;
+  FL_CUDA(persist_barrier_check(missing, &gave_up));
+  if (gave_up) return fail(FL_DEVICE_TIMEOUT, "grid barrier: the CTAs gave up waiting");
+  return FL_OK;
+}
+
 fl_status fl_profile_enable(fl_plan* p, int enable) {
   if (!check_plan(p)) return fail(FL_INVALID_ARG, "NULL plan");
   if (enable && !p->prof) p->prof = new Profiler();

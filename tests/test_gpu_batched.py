@@ -142,3 +142,25 @@ def test_persistent_launch_3d():
         res = np.linalg.norm(op.apply(up) - f) / np.linalg.norm(f)
         assert res <= 1.05e-8, (n, a, res)
         assert np.linalg.norm(up - ul.cpu().numpy().reshape(n)) <= 1e-6 * np.linalg.norm(up)
+
+
+def test_grid_barrier_wait_is_bounded():
+    """The persistent launch's grid barrier: with every CTA arriving it
+    completes; with one arrival too few nobody releases it, every CTA gives
+    up after its bounded wait (2 s) and the call reports FL_DEVICE_TIMEOUT;
+    the context stays usable (a persistent batched solve after it
+    converges)."""
+    import time
+    lib = _lib.load()
+    assert lib.fl_check_grid_barrier(0) == _lib.FL_OK, _lib.last_error()
+    t0 = time.perf_counter()
+    st = lib.fl_check_grid_barrier(1)
+    dt = time.perf_counter() - t0
+    assert st == _lib.FL_DEVICE_TIMEOUT, _lib.last_error()
+    assert "gave up" in _lib.last_error()
+    assert 1.5 < dt < 60.0, dt
+    assert lib.fl_check_grid_barrier(-1) == _lib.FL_INVALID_ARG
+    plans, fd, fs = _batch_2d([48, 80], [0.7, 1.4], 600)
+    _, infos = solve_batched(plans, fd, tol=1e-8,
+                             mode=_lib.FL_MODE_MIXED | _lib.FL_PRECOND_AUTO | _lib.FL_BATCH_PERSISTENT)
+    assert all(i["converged"] == 1 for i in infos), infos
