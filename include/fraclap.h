@@ -275,10 +275,11 @@ fl_status fl_check_grid_barrier(int missing);
  * device array instead of the plan's workspace, and the call allocates
  * nothing: no cudaMalloc, cudaFree or allocating library routine.  The
  * paper has no counterpart; this entry exists for callers that cannot call
- * cudaMalloc at the point where they apply the operator -- code that runs
- * while a CUDA stream is being captured into a graph, or a host whose device
- * memory is owned by another runtime's allocator -- and who created the plan
- * earlier, at set-up time.
+ * cudaMalloc at the point where they apply the operator -- a host whose
+ * device memory is owned by another runtime's allocator or pool, or a
+ * service that reserves all of its device memory at start-up and may not
+ * allocate while it serves requests -- and who created the plan earlier, at
+ * set-up time.
  *   - Limit: the plan's spectrum must fit the array, 2^21 complex floats
  *     (16 MiB): n_0 * (L_1/2 + 1) <= 2^21 in 2D (1024 x 1024 fits),
  *     n_0 * L_1 * (L_2/2 + 1) <= 2^21 in 3D (64^3 fits).  Larger plans get

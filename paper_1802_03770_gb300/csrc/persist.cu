@@ -22,7 +22,7 @@
 // bar->err and returns, and every other CTA returns at its next barrier, so
 // the launch always ends; the host reads bar->err and reports a timeout.
 #define FL_RESTRICT
-#include "chain.cuh"
+#include "persist.h"
 
 namespace fl {
 

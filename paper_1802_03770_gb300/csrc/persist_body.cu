@@ -8,7 +8,7 @@
 // registers; compiled into the kernel's own module the same bodies spilled
 // kilobytes per thread and took minutes to compile.
 #define FL_RESTRICT
-#include "chain.cuh"
+#include "persist.h"
 
 namespace fl {
 

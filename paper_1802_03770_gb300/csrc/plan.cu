@@ -14,6 +14,7 @@
 #include "internal.h"
 #include "chain.cuh"
 #include "learned.h"
+#include "persist.h"
 #include "domain.h"
 
 using namespace fl;
@@ -1368,7 +1369,7 @@ int fl_profile_read(fl_plan* p, fl_kernel_stat* stats, int max_stats) {
 namespace {
 constexpr long long kStaticSpecElems = 1LL << 21;  // complex floats, 16 MiB
 constexpr int kMaxDevices = 256;
-__device__ __align__(256) float2 g_static_spec[kStaticSpecElems];
+static __device__ __align__(256) float2 g_static_spec[kStaticSpecElems];
 std::mutex g_static_mu;
 float2* g_static_addr[kMaxDevices] = {nullptr};
 

@@ -1,8 +1,8 @@
 """The allocation-free FP32 apply, fl_apply_f32_static.
 
-Callers that cannot call cudaMalloc when they apply the operator (for
-example code running while a stream is captured into a CUDA graph, or a
-host whose device memory belongs to another runtime's allocator) create the
+Callers that cannot call cudaMalloc when they apply the operator (a host
+whose device memory belongs to another runtime's allocator or pool, or a
+service that reserves all of its device memory at start-up) create the
 plan at set-up time and then call fl_apply_f32_static, whose scratch is a
 fixed library-owned device array.  This file is collected last so that a
 run stopping at the first failure has already run every other test; it
