@@ -262,9 +262,10 @@ constexpr int TC_STAGE_A = TC_M * TC_KC;   // BF16 elements of one A stage
 __host__ __device__ constexpr int tc_halo_bytes(int cin) { return (cin * TC_HALO_PIX * 2 + 15) & ~15; }
 // dynamic shared memory of a launch with cout = n, cin input channels: the
 // A stages (32 KB), the B stages (256 n bytes: 16-byte multiples for n a
-// multiple of 16), the halo, two mbarriers and the TMEM address slot
+// multiple of 16), the halo of cin padded to 8 channels, two mbarriers and
+// the TMEM address slot
 __host__ __device__ constexpr int tc_smem_bytes(int n, int cin) {
-  return 2 * TC_STAGE_A * 2 + 2 * n * TC_KC * 2 + tc_halo_bytes(cin) + 32;
+  return 2 * TC_STAGE_A * 2 + 2 * n * TC_KC * 2 + tc_halo_bytes((cin + 7) & ~7) + 32;
 }
 constexpr int TC_SMEM = tc_smem_bytes(TC_NMAX, TC_CIN_MAX);   // the largest launch
 constexpr int kWaitLimit = 1 << 24;
@@ -304,18 +305,22 @@ __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi
 __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(ConvArgs a, int tmem_cols) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   const int N = a.cout;
+  // input channels padded to a multiple of 8 (zero channels), so that the
+  // 8-wide K groups of the tap-major order k = cinp t + ci stay in one tap
+  const int cinp = (a.cin + 7) & ~7;
   // shared memory sized for this layer (tc_smem_bytes): two stages of A,
-  // two of B (N rows), the halo [cin][10][18], two mbarriers, the TMEM slot
+  // two of B (N rows), the channel-last halo [10][18][cinp], two
+  // mbarriers, the TMEM slot
   __nv_bfloat16* sa0 = reinterpret_cast<__nv_bfloat16*>(tc_smem);
   __nv_bfloat16* sb0 = sa0 + 2 * TC_STAGE_A;
   const int stage_b = N * TC_KC;
   __nv_bfloat16* halo = sb0 + 2 * stage_b;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(
-      reinterpret_cast<unsigned char*>(halo) + tc_halo_bytes(a.cin));
+      reinterpret_cast<unsigned char*>(halo) + tc_halo_bytes(cinp));
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 2);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int x0 = blockIdx.x * 16, y0 = blockIdx.y * 8;
-  const int K = a.cin * 9;
+  const int K = cinp * 9;
   const int nchunks = (K + TC_KC - 1) / TC_KC;
   const uint32_t mb0 = smem_addr(mbar), mb1 = smem_addr(mbar + 1);
   auto mbs = [=](int s) { return s ? mb1 : mb0; };   // mbarrier of stage s
@@ -328,25 +333,41 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(ConvArgs a, int tmem_col
                  :: "r"(smem_addr(tmem_slot)), "r"(tmem_cols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  // input halo, BF16: sixteen independent source reads in flight per thread
+  // input halo, BF16, channel-last: item i = (pixel r, group of 8
+  // channels) is read from the sources (consecutive threads: consecutive
+  // pixels of the same channels), packed and stored with one 16-byte store;
+  // two items (sixteen reads) in flight per thread; padded channels are
+  // zero.  Group cg of pixel r sits at 16-byte slot cg ^ (r & hmask) of the
+  // pixel (hmask + 1: the largest power of two dividing cinp / 8), so that
+  // reads of one group at consecutive pixels spread over the banks.
+  const int ncg = cinp >> 3;
+  const int hmask = (ncg & -ncg) - 1;
   {
-    const int total = a.cin * TC_HALO_PIX;
-    for (int e0 = tid; e0 < total; e0 += 16 * TC_THREADS) {
-      float v[16];
+    const int items = (cinp >> 3) * TC_HALO_PIX;
+    for (int i0 = tid; i0 < items; i0 += 2 * TC_THREADS) {
+      float v[2][8];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int e = e0 + u * TC_THREADS;
-        v[u] = 0.f;
-        if (e < total) {
-          const int ci = e / TC_HALO_PIX, r = e - ci * TC_HALO_PIX;
-          const int hy = r / TC_HALO_W, hx = r - hy * TC_HALO_W;
-          v[u] = src_value(a, ci, y0 + hy - 1, x0 + hx - 1);
+      for (int h = 0; h < 2; ++h) {
+        const int i = i0 + h * TC_THREADS;
+        const int cg = i / TC_HALO_PIX, r = i - cg * TC_HALO_PIX;
+        const int hy = r / TC_HALO_W, hx = r - hy * TC_HALO_W;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int ci = 8 * cg + k;
+          v[h][k] = (i < items && ci < a.cin) ? src_value(a, ci, y0 + hy - 1, x0 + hx - 1) : 0.f;
         }
       }
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int e = e0 + u * TC_THREADS;
-        if (e < total) halo[e] = __float2bfloat16(v[u]);
+      for (int h = 0; h < 2; ++h) {
+        const int i = i0 + h * TC_THREADS;
+        if (i >= items) continue;
+        const int cg = i / TC_HALO_PIX, r = i - cg * TC_HALO_PIX;
+        uint4 q;
+        q.x = pack_bf16(__float2bfloat16(v[h][0]), __float2bfloat16(v[h][1]));
+        q.y = pack_bf16(__float2bfloat16(v[h][2]), __float2bfloat16(v[h][3]));
+        q.z = pack_bf16(__float2bfloat16(v[h][4]), __float2bfloat16(v[h][5]));
+        q.w = pack_bf16(__float2bfloat16(v[h][6]), __float2bfloat16(v[h][7]));
+        *reinterpret_cast<uint4*>(halo + r * cinp + 8 * (cg ^ (r & hmask))) = q;
       }
     }
   }
@@ -356,10 +377,12 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(ConvArgs a, int tmem_col
   const uint32_t tmem = *tmem_slot;
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
                          ((uint32_t)(TC_M >> 4) << 24);
-  // this thread's 8-wide K group of every chunk, and its first tile row
-  constexpr int kRowStep = TC_THREADS / 8;
-  const int g = tid & 7;
-  const int row0 = tid >> 3;
+  // this thread's 8-wide K group g of every chunk and its tile rows
+  // 8 (oct0 + 4 j) + (tid & 7), j = 0 .. 3: the eight threads of a
+  // quarter warp store eight consecutive rows of one group (16 bytes apart
+  // in the canonical layout: no bank conflicts)
+  const int g = (tid >> 3) & 7;
+  const int oct0 = tid >> 6, rlo = tid & 7;
   bool ok = true;
   int issued = 0;   // chunks whose MMAs were issued (and committed)
   for (int ch = 0; ch < nchunks; ++ch) {
@@ -377,47 +400,34 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(ConvArgs a, int tmem_col
     }
     __nv_bfloat16* sa = sa0 + s * TC_STAGE_A;
     __nv_bfloat16* sb = sb0 + s * stage_b;
-    const int kg = ch * TC_KC + 8 * g;   // first k of the group
-    // A: tile rows row0, row0 + kRowStep, ..., the group's 8 k from the halo
+    // the group's 8 k: tap t, channels ci0 .. ci0 + 7
+    const int kg = ch * TC_KC + 8 * g;
+    const bool kvalid = kg < K;
+    const int t = kg / cinp, ci0 = kg - t * cinp;
+    // A: the thread's four tile rows, one 16-byte halo read each
     {
-      int off[8];
+      const int dy = t / 3, dx = t - 3 * dy;
+      const int cg = ci0 >> 3;
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int k = kg + u;
-        const int ci = k / 9, t = k - ci * 9;
-        const int dy = t / 3, dx = t - dy * 3;
-        off[u] = k < K ? ci * TC_HALO_PIX + dy * TC_HALO_W + dx : -1;
-      }
-      const __nv_bfloat16 zero = __float2bfloat16(0.f);
-#pragma unroll 2
-      for (int p = row0; p < TC_M; p += kRowStep) {
-        const int base = (p >> 4) * TC_HALO_W + (p & 15);
-        __nv_bfloat16 v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = off[u] >= 0 ? halo[off[u] + base] : zero;
-        uint4 q;
-        q.x = pack_bf16(v[0], v[1]);
-        q.y = pack_bf16(v[2], v[3]);
-        q.z = pack_bf16(v[4], v[5]);
-        q.w = pack_bf16(v[6], v[7]);
-        *reinterpret_cast<uint4*>(sa + canon64(p, 8 * g)) = q;
+      for (int j = 0; j < 4; ++j) {
+        const int p = ((oct0 + 4 * j) << 3) + rlo;
+        const int q = ((p >> 4) + dy) * TC_HALO_W + (p & 15) + dx;   // halo pixel
+        uint4 v4 = make_uint4(0u, 0u, 0u, 0u);
+        if (kvalid) v4 = *reinterpret_cast<const uint4*>(halo + q * cinp + 8 * (cg ^ (q & hmask)));
+        *reinterpret_cast<uint4*>(sa + canon64(p, 8 * g)) = v4;
       }
     }
-    // B: the weights of the group's 8 k for output channels o = row0,
-    // row0 + kRowStep, ... (all of this thread's loads issued together)
+    // B: the weights of the group's 8 k for the thread's output channels
+    // o = 8 (oct0 + 4 j) + (tid & 7) < N (all its loads issued together)
 #pragma unroll
-    for (int o = row0; o < TC_NMAX; o += kRowStep) {
+    for (int j = 0; j < 4; ++j) {
+      const int o = ((oct0 + 4 * j) << 3) + rlo;
       if (o >= N) break;
       __nv_bfloat16 v[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        const int k = kg + u;
-        float w = 0.f;
-        if (k < K) {
-          const int ci = k / 9, t = k - ci * 9;
-          w = weight(a, o, ci, t);
-        }
-        v[u] = __float2bfloat16(w);
+        const int ci = ci0 + u;
+        v[u] = __float2bfloat16(kvalid && ci < a.cin ? weight(a, o, ci, t) : 0.f);
       }
       uint4 q;
       q.x = pack_bf16(v[0], v[1]);
