@@ -393,6 +393,20 @@ fl_status fl_net_set_alpha_gate(fl_net* net, double lo, double hi, int bands, co
  * (its outputs were zeroed), else FL_OK; waits for the net's stream. */
 fl_status fl_net_check(fl_net* net);
 
+/* One training pair of the network from a plan's solves (no counterpart in
+ * the paper): given the right-hand side f, the converged solution u* and an
+ * iterate x (N doubles each, device), forms on the plan's stream
+ *   r = f - M x (FP64 apply),  z0 = B r (the FD-Laplacian solve of
+ *   fl_precond for alpha >= 1, r / M_ii below),
+ *   s_r, s_z = max(root mean square of r, z0; 1e-300),
+ *   feat_dev[3 N] = [r / s_r, z0 / s_z, alpha],
+ *   target_dev[N] = (u* - x - z0) / s_z      (FP32),
+ * so that z = z0 + s_z N(feat) approximates M^{-1} r.  Box plans only
+ * (FL_INVALID_ARG for a masked plan).  Uses the plan's FP64 work vectors:
+ * not concurrently with a solve on the same plan. */
+fl_status fl_net_training_pair(fl_plan* plan, const double* f_dev, const double* u_star_dev,
+                               const double* x_dev, float* feat_dev, float* target_dev);
+
 /* Attach (net != NULL) or detach a network for FL_MODE_LEARNED solves on a
  * 2D plan without mask; the network's H x W must equal n_0 x n_1.  Allocates
  * the plan's feature buffers on first attach.  The plan does not own the

@@ -103,6 +103,7 @@ SIGNATURES = {
     "fl_net_set_tensor_cores": (_I, [_P, _I]),
     "fl_net_set_alpha_gate": (_I, [_P, ctypes.c_double, ctypes.c_double, _I, _P]),
     "fl_net_check": (_I, [_P]),
+    "fl_net_training_pair": (_I, [_P, _P, _P, _P, _P, _P]),
     "fl_net_get_tensor": (_I, [_P, _I, _I, _P, ctypes.c_longlong]),
     "fl_last_error_string": (ctypes.c_char_p, []),
 }

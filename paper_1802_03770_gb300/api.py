@@ -306,6 +306,18 @@ class Plan:
         L.check(st, "fl_time_step")
         return u_next, info.as_dict()
 
+    def training_pair(self, f, u_star, x):
+        """fl_net_training_pair: features [3, N] and target [N] (float32 CUDA
+        tensors) of the pair (r = f - M x, e = u* - x)."""
+        import torch
+        for t, name in ((f, "f"), (u_star, "u_star"), (x, "x")):
+            _check_tensor(t, torch.float64, self.N, name)
+        feat = torch.empty(3 * self.N, dtype=torch.float32, device=f.device)
+        target = torch.empty(self.N, dtype=torch.float32, device=f.device)
+        L.check(self._lib.fl_net_training_pair(self._h, _ptr(f), _ptr(u_star), _ptr(x), _ptr(feat),
+                                               _ptr(target)), "fl_net_training_pair")
+        return feat.view(3, self.N), target
+
     def attach_net(self, net):
         """Use `net` (api.Net, or None to detach) for FL_MODE_LEARNED solves."""
         L.check(self._lib.fl_plan_attach_net(self._h, net._h if net is not None else None),

@@ -480,7 +480,79 @@ __global__ void k_fpcg_scalar(PcgState* st, const double* rr_part, int rr_count,
 
 constexpr int kFBlocks = 608;
 
+// Training pairs (fl_net_training_pair).  z0 = r / k0: the diagonal base
+// preconditioner of orders alpha < 1.
+__global__ void __launch_bounds__(256) k_div_scalar(const double* __restrict__ r, double k0,
+                                                     double* __restrict__ z0, long long N) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    z0[i] = r[i] / k0;
+}
+
+// Per-CTA partial sums of r^2 (part[b]) and z0^2 (part[G + b]).
+__global__ void __launch_bounds__(256) k_pair_sums(const double* __restrict__ r,
+                                                    const double* __restrict__ z0, long long N,
+                                                    double* __restrict__ part) {
+  __shared__ double red[32];
+  double a = 0.0, b = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    a += r[i] * r[i];
+    b += z0[i] * z0[i];
+  }
+  a = cta_sum(a, red);
+  __syncthreads();
+  b = cta_sum(b, red);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = a;
+    part[gridDim.x + blockIdx.x] = b;
+  }
+}
+
+// Features [r / s_r, z0 / s_z, alpha] and target (u* - x - z0) / s_z, in
+// FP32, with s = max(root mean square, 1e-300) from the partials (summed in
+// a fixed order by every CTA).
+__global__ void __launch_bounds__(256) k_pair_write(const double* __restrict__ r,
+                                                     const double* __restrict__ z0,
+                                                     const double* __restrict__ u_star,
+                                                     const double* __restrict__ x,
+                                                     const double* __restrict__ part, int G,
+                                                     double alpha, float* __restrict__ feat,
+                                                     float* __restrict__ target, long long N) {
+  __shared__ double red[32];
+  const double rr = cta_sum_partials(part, G, red);
+  const double zz = cta_sum_partials(part + G, G, red);
+  const double sr = fmax(sqrt(rr / (double)N), 1e-300);
+  const double sz = fmax(sqrt(zz / (double)N), 1e-300);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    feat[i] = (float)(r[i] / sr);
+    feat[N + i] = (float)(z0[i] / sz);
+    feat[2 * N + i] = (float)alpha;
+    target[i] = (float)(((u_star[i] - x[i]) - z0[i]) / sz);
+  }
+}
+
+constexpr int kPairBlocks = 256;
+
 }  // namespace
+
+cudaError_t launch_div_scalar(const double* r, double k0, double* z0, long long N, cudaStream_t s) {
+  FL_KERNEL("div_scalar", s, k_div_scalar<<<kFBlocks, 256, 0, s>>>(r, k0, z0, N));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_training_pair(const double* r, const double* z0, const double* u_star, const double* x,
+                                 double alpha, float* feat, float* target, long long N, double* part,
+                                 cudaStream_t s) {
+  FL_KERNEL("pair_sums", s, k_pair_sums<<<kPairBlocks, 256, 0, s>>>(r, z0, N, part));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  FL_KERNEL("pair_write", s,
+            k_pair_write<<<kFBlocks, 256, 0, s>>>(r, z0, u_star, x, part, kPairBlocks, alpha, feat,
+                                                  target, N));
+  return cudaGetLastError();
+}
 
 cudaError_t launch_features(const float* r, const float* z0, const double* rr_part, int rr_count,
                             const double* zz_part, int zz_count, float alpha, float* x, long long N,

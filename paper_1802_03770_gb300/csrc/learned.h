@@ -64,6 +64,12 @@ struct NetState {
 
 namespace fl {
 struct PcgState;
+// Training pairs: z0 = r / k0, and the pair's features and target from r, z0,
+// u*, x (2 * 256 partials in part).
+cudaError_t launch_div_scalar(const double* r, double k0, double* z0, long long N, cudaStream_t s);
+cudaError_t launch_training_pair(const double* r, const double* z0, const double* u_star, const double* x,
+                                 double alpha, float* feat, float* target, long long N, double* part,
+                                 cudaStream_t s);
 cudaError_t launch_features(const float* r, const float* z0, const double* rr_part, int rr_count,
                             const double* zz_part, int zz_count, float alpha, float* x, long long N,
                             const PcgState* st, cudaStream_t s);

@@ -1936,6 +1936,39 @@ fl_status fl_solve_elliptic_batched(fl_plan* const* plans, int count, const doub
 
 extern "C" {
 
+fl_status fl_net_training_pair(fl_plan* p, const double* f, const double* u_star, const double* x,
+                               float* feat, float* target) {
+  ProfScope prof_scope(p);
+  if (!check_plan(p) || !f || !u_star || !x || !feat || !target)
+    return fail(FL_INVALID_ARG, "NULL argument");
+  if (p->has_mask) return fail(FL_INVALID_ARG, "training pairs are formed on box plans");
+  const Geo& g = p->g;
+  cudaStream_t s = p->stream;
+  double* r = p->v64.r;
+  double* z0 = p->v64.z;
+  // r = f - M x (FP64 apply, the epilogue forms the residual)
+  ApplyIO<double> io;
+  io.u = x; io.out = r; io.x = x; io.b = f; io.cm = -1.0; io.cx = 0.0; io.cb = 1.0;
+  FL_CUDA(launch_apply<double>(g, p->t64, s, io));
+  // z0 = B r: the FD-Laplacian solve for alpha >= 1, r / M_ii below
+  if (p->alpha >= 1.0) {
+    if (!precond_fits(p)) return fail(FL_INVALID_ARG, kPrecondLimit);
+    PrecChoice pc;
+    const fl_status ps = precond_params(p, FL_PRECOND_FD, 0.0, 1.0, &pc);
+    if (ps != FL_OK) return ps;
+    const fl_status pp = prepare_prec<double>(p, pc);
+    if (pp != FL_OK) return pp;
+    PrecIO<double> pi;
+    pi.in = r; pi.out = z0; pi.shift = 0.0; pi.scale = 1.0;
+    FL_CUDA(apply_prec<double>(p, pc, pi, s));
+  } else {
+    const double k0 = p->c * (p->Z - 2.0 * g.dphys * p->a);
+    FL_CUDA(launch_div_scalar(r, k0, z0, g.N, s));
+  }
+  FL_CUDA(launch_training_pair(r, z0, u_star, x, p->alpha, feat, target, g.N, p->part[P_AUX], s));
+  return FL_OK;
+}
+
 fl_status fl_plan_attach_net(fl_plan* p, fl_net* net) {
   if (!check_plan(p)) return fail(FL_INVALID_ARG, "NULL plan");
   if (!net) {

@@ -27,28 +27,22 @@ from .api import Net, Plan
 STAGES = (1e-1, 1e-2, 1e-3, 1e-4)
 
 
-def base_precond(plan, r, alpha, kernel0):
-    """z0 = B r in float64 (CUDA tensors)."""
-    if alpha >= 1.0:
-        return plan.precond(r)
-    return r / kernel0
-
-
 def make_pairs(plan, alpha, f, kernel0, stages=STAGES):
-    """Features [len(stages), 3, n, n] and targets [len(stages), n, n] (float32)."""
+    """Features [len(stages), 3, n, n] and targets [len(stages), n, n] (float32):
+    the converged solution u* and the CG iterates x stopped at each stage's
+    tolerance, turned into pairs by fl_net_training_pair (residual, base
+    preconditioner, scales, features and target in the library's kernels).
+    alpha and kernel0 are the plan's (kept for the callers' signature)."""
     import torch
+    n0, n1 = plan.n[0], plan.n[1]
     u_star, info = plan.solve(f, tol=1e-11, mode=L.FL_MODE_F64 | L.FL_PRECOND_AUTO, maxit=4000)
     feats, targets = [], []
     for tau in stages:
         x, _ = plan.solve(f, tol=tau, mode=L.FL_MODE_F64 | L.FL_PRECOND_AUTO, maxit=4000,
                           raise_on_fail=False)
-        e = u_star - x
-        r = f - plan.apply(x)
-        z0 = base_precond(plan, r, alpha, kernel0)
-        s_r = torch.sqrt(torch.mean(r * r)).clamp_min(1e-300)
-        s_z = torch.sqrt(torch.mean(z0 * z0)).clamp_min(1e-300)
-        feats.append(torch.stack([r / s_r, z0 / s_z, torch.full_like(r, alpha)]).float())
-        targets.append(((e - z0) / s_z).float())
+        feat, target = plan.training_pair(f, u_star, x)
+        feats.append(feat.view(3, n0, n1))
+        targets.append(target.view(n0, n1))
     return torch.stack(feats), torch.stack(targets)
 
 

@@ -90,3 +90,44 @@ def test_trained_network_gain_on_held_out_seeds():
     print(f"mean CG iterations: plain {plain:.1f}, learned {lrn:.1f}")
     for row in ev:
         assert row["plain"]["converged"] and row["learned"]["converged"], row
+
+
+@pytest.mark.parametrize("alpha", [0.6, 1.4])
+def test_training_pair_matches_oracle(alpha):
+    """fl_net_training_pair against the pair formed from the oracle: r = f -
+    M x (oracle apply), z0 = the FD-Laplacian box solve (DST-I) for alpha >=
+    1, r / M_ii below, RMS scales, features [r/s_r, z0/s_z, alpha] and target
+    (u* - x - z0)/s_z; FP32 outputs within FP32 rounding (1e-6 relative)."""
+    from oracle import precond as oprec
+    n = 40
+    h = 1.0 / (n + 1)
+    op = OPlan(2, n, h, alpha)
+    plan = Plan(2, (n, n), h, alpha)
+    f = inputs.gaussian_mixture(n, 2, 8, 71)
+    rng = np.random.default_rng(72)
+    u_star = rng.standard_normal((n, n))
+    x = u_star + 0.1 * rng.standard_normal((n, n))
+    dev = [torch.tensor(v, dtype=torch.float64, device="cuda:0").view(-1) for v in (f, u_star, x)]
+    feat, target = plan.training_pair(*dev)
+    torch.cuda.synchronize()
+    feat = feat.cpu().numpy().astype(np.float64).reshape(3, n, n)
+    target = target.cpu().numpy().astype(np.float64).reshape(n, n)
+    r = f - op.apply(x).reshape(n, n)
+    z0 = oprec.solve_box(op, r) if alpha >= 1.0 else r / op.entry(np.zeros(2))
+    s_r = np.sqrt(np.mean(r * r))
+    s_z = np.sqrt(np.mean(z0 * z0))
+    refs = [r / s_r, z0 / s_z, np.full((n, n), alpha)]
+    for k in range(3):
+        assert np.linalg.norm(feat[k] - refs[k]) <= 1e-6 * np.linalg.norm(refs[k]), k
+    ref_t = (u_star - x - z0) / s_z
+    assert np.linalg.norm(target - ref_t) <= 1e-6 * np.linalg.norm(ref_t)
+
+
+def test_training_pair_rejects_masked_plans():
+    n = 16
+    mask = np.ones((n, n), dtype=bool)
+    mask[:4, :4] = False
+    plan = Plan(2, (n, n), 1.0 / (n + 1), 1.2, mask=mask)
+    z = torch.zeros(n * n, dtype=torch.float64, device="cuda:0")
+    with pytest.raises(_lib.FracLapError, match="INVALID_ARG"):
+        plan.training_pair(z, z, z)
