@@ -23,7 +23,8 @@ octagonal domain.
 --precond picks the preconditioner of timestep and batched: fd (the
 paper's; batched default: auto, none for alpha < 1), shifted (FD with the
 balanced shift) or stencil (the stencil part of M).  --autotune tunes the
-column tiles of every batched plan (fl_plan_autotune) before timing.
+column tiles of the batch before timing: every plan's own tuned tiles
+(fl_plan_autotune) or the widest, whichever runs the batched solve faster.
 persistent: one 1024^2 and one 256^2 problem (alpha = 1.5) through the
 batched call, with the persistent launch and with the lockstep launches,
 without and with the FD preconditioner: time per CG iteration.
@@ -76,6 +77,37 @@ def timestep(n=256, steps=100, alpha=1.5, dt=1e-3, seed=3, precond="fd"):
             "all_converged": ok}
 
 
+def tune_batch(plans, fs, mode, reps=2):
+    """Column tiles for a batch: every plan's own tuned tiles
+    (fl_plan_autotune: the fastest for that plan alone) against the widest
+    tiles on every plan, each timed on the batched solve itself (lockstep
+    launches, after a warm-up call); keeps the faster.  A plan tuned alone
+    favours narrow tiles (more CTAs to fill the GPU), which a batch of many
+    problems does not need.  Returns the choice and both times (s)."""
+    import torch
+    tuned = [p.autotune() for p in plans]
+
+    def timed():
+        solve_batched(plans, fs, tol=1e-8, mode=mode)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            solve_batched(plans, fs, tol=1e-8, mode=mode)
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps
+
+    t_tuned = timed()
+    for p in plans:
+        p.set_tiles([0] * 6)
+    t_widest = timed()
+    choice = "widest"
+    if t_tuned < t_widest:
+        for p, tx in zip(plans, tuned):
+            p.set_tiles(tx)
+        choice = "per_plan"
+    return choice, {"per_plan": t_tuned, "widest": t_widest}
+
+
 def batched(count=64, seed=7, precond="auto", autotune=False):
     import torch
     sides = inputs.batch_sides(count, seed)
@@ -86,12 +118,12 @@ def batched(count=64, seed=7, precond="auto", autotune=False):
         fs.append(torch.tensor(inputs.gaussian_mixture(n, 2, 16, 100 + i), dtype=torch.float64,
                                device="cuda").view(-1))
     t_tune = 0.0
+    mode = L.FL_MODE_MIXED | PRECONDS[precond]
+    tile_choice, tile_times = "widest", {}
     if autotune:
         t0 = time.perf_counter()
-        for p in plans:
-            p.autotune()
+        tile_choice, tile_times = tune_batch(plans, fs, mode)
         t_tune = time.perf_counter() - t0
-    mode = L.FL_MODE_MIXED | PRECONDS[precond]
 
     def timed(m):
         solve_batched(plans, fs, tol=1e-8, mode=m)        # warm-up (graph capture)
@@ -113,6 +145,8 @@ def batched(count=64, seed=7, precond="auto", autotune=False):
     ts = time.perf_counter() - t0
     return {"workload": f"{count} 2D problems, sides 96..768, alpha U(0.3,1.8)", "precond": precond,
             "autotuned_tiles": autotune, "autotune_seconds": t_tune,
+            "tile_choice": tile_choice,
+            "tile_trial_seconds": tile_times,
             "batched_seconds": tb, "batched_solves_per_s": count / tb,
             "batched_how": "inner CG of every problem in one persistent cooperative launch "
                            "per refinement step (CUDA graph)",
