@@ -147,10 +147,23 @@ fl_status fl_plan_describe(const fl_plan* plan, fl_plan_desc* desc);
  * pass, every candidate width over a few operator applies and
  * preconditioner solves on the plan's stream (axis by axis, the others
  * kept), keeps the fastest, and writes the choice to tx_out (nullable).
+ * For plans whose rows (the last axis) pad to 256 .. 2048 points it then
+ * times the FP32 row passes in both CTA shapes (row shape 0: 128 threads x
+ * 16 values per line, 1: 256 threads x 8, radix-8 stages) and keeps the
+ * faster (fl_plan_row_shape reads the choice).
  * It uses the plan's workspaces, waits for the stream, and invalidates the
  * plan's captured CG graphs; run it before solves, not during one. */
 fl_status fl_plan_set_tiles(fl_plan* plan, const int tx[6]);
 fl_status fl_plan_autotune(fl_plan* plan, int tx_out[6]);
+
+/* CTA shape of the FP32 row passes (no counterpart in the paper): 0 = 128
+ * threads x 16 values per line (the default), 1 = 256 threads x 8 (rows
+ * padded to 256 .. 2048 points only, else FL_INVALID_ARG).  Results agree
+ * to FP32 rounding (other radix plan), not bit for bit.  Invalidates the
+ * plan's captured CG graphs.  fl_plan_row_shape returns the current shape
+ * (-1 for a NULL plan).  Batched solves use shape 0. */
+fl_status fl_plan_set_row_shape(fl_plan* plan, int shape);
+int fl_plan_row_shape(const fl_plan* plan);
 
 /* y = M u (Sec. 3.1, BTTB apply by FFT), FP64 throughout.  u_dev, y_dev:
  * device arrays of N doubles; they may not alias. */

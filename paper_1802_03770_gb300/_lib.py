@@ -77,6 +77,8 @@ SIGNATURES = {
     "fl_precond_params": (_I, [_P, _I, _D, _D, _P, _P]),
     "fl_plan_set_tiles": (_I, [_P, _P]),
     "fl_plan_autotune": (_I, [_P, _P]),
+    "fl_plan_set_row_shape": (_I, [_P, _I]),
+    "fl_plan_row_shape": (_I, [_P]),
     "fl_solve_elliptic": (_I, [_P, _P, _P, _I, _D, _I, _I, ctypes.POINTER(FlSolveInfo)]),
     "fl_solve_elliptic_host": (_I, [_P, _P, _P, _D, _I, _I, ctypes.POINTER(FlSolveInfo)]),
     "fl_time_step": (_I, [_P, _D, _D, _P, _P, _P, _P, _D, _I, _I, ctypes.POINTER(FlSolveInfo)]),

@@ -255,6 +255,13 @@ class Plan:
         L.check(self._lib.fl_plan_autotune(self._h, arr), "fl_plan_autotune")
         return list(arr)
 
+    def set_row_shape(self, shape):
+        """CTA shape of the FP32 row passes: 0 = 128 x 16, 1 = 256 x 8."""
+        L.check(self._lib.fl_plan_set_row_shape(self._h, int(shape)), "fl_plan_set_row_shape")
+
+    def row_shape(self):
+        return int(self._lib.fl_plan_row_shape(self._h))
+
     def precond_params(self, mode, shift=0.0, scale=1.0):
         """(pshift, pscale) of the preconditioner (pshift I + pscale C h^d L)^-1
         that a solve in `mode` uses for shift I + scale M; (0, 0) for none."""

@@ -27,6 +27,7 @@ CUDA_SOURCES = [("ops.cu", ["-DFL_OPS_PART=1"], "ops_f32.o"), ("ops.cu", ["-DFL_
                 ("plan.cu", [], "plan.o"), ("batch.cu", ["-DFL_BATCH_PART=1"], "batch_f32.o"),
                 ("batch.cu", ["-DFL_BATCH_PART=2"], "batch_f64.o"), ("unet.cu", [], "unet.o"),
                 ("learned.cu", [], "learned.o"), ("domain.cu", [], "domain.o"),
+                ("rows_w8.cu", [], "rows_w8.o"),
                 ("persist.cu", RDC, "persist.o"), ("persist_body.cu", RDC, "persist_body.o")]
 CXX_SOURCES = ["consts.cpp"]
 

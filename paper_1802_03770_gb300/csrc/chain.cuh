@@ -236,6 +236,18 @@ cudaError_t launch_batched_scalar(int which, const BScalarArgs* args, double* ou
                                   cudaStream_t s);
 cudaError_t configure_batched_kernels();
 
+// FP32 row passes in the 256 x 8 shape (rows_w8.cu): the same grid and
+// shared memory as the Cfg shape
+constexpr int kRowsW8Threads = 256;
+void launch_rows_fwd_w8(const RowsFwdArgs<float>& a, int grid, size_t smem, cudaStream_t s);
+void launch_rows_inv_w8(const RowsInvArgs<float>& a, int grid, size_t smem, cudaStream_t s);
+void launch_dst_rows_w8(const DstRowsArgs<float>& a, int grid, size_t smem, cudaStream_t s);
+cudaError_t configure_rows_w8();
+// whether a plan's FP32 row passes on lines of L points take the 256 x 8 shape
+template <typename T> inline bool rows_w8(const Tables<T>& tb, int L) {
+  return sizeof(T) == 4 && tb.rshape == 1 && L >= 256 && L <= 2048;
+}
+
 template <typename T>
 ApplyChain<T> build_apply(const Geo& g, const Tables<T>& tb, const ApplyIO<T>& io);
 template <typename T>

@@ -47,6 +47,8 @@ struct Tables {
   T* tri_tab = nullptr;       // per-column constants of the axis-0 tridiagonal solve
   double tri_shift = -1.0, tri_scale = -1.0;  // the shift and scale tri_tab holds
   int tx[3] = {0, 0, 0};      // column-tile width of the strided passes per axis (0: default)
+  int rshape = 0;             // FP32 row passes: 0 = 128 threads x 16 values per line,
+                              // 1 = 256 x 8 (lines of 256 .. 2048 points; rows_w8.cu)
 };
 
 // Inputs and outputs of one operator apply.

@@ -304,6 +304,7 @@ cudaError_t configure_kernels_f64();
 
 cudaError_t configure_kernels() {
   cudaError_t e = configure_kernels_f64();
+  if (e == cudaSuccess) e = configure_rows_w8();
 #define FL_SET(...)                                                         \
   if (e == cudaSuccess) e = set_smem(reinterpret_cast<const void*>(&__VA_ARGS__));
   FL_SET(k_rows_fwd<float, Cfg<float>::RT, Cfg<float>::RV>);
@@ -453,7 +454,12 @@ cudaError_t launch_apply(const Geo& g, const Tables<T>& tb, cudaStream_t s, cons
   const ApplyChain<T> ch = build_apply<T>(g, tb, io);
   const int Lx = g.L[g.d - 1];
   FL_KERNEL((sizeof(T) == 4 ? "rows_fwd" "<f32>" : "rows_fwd" "<f64>"), s,
-            FL_ROWS_LAUNCH(k_rows_fwd, T, Lx, ch.row_blocks, ch.row_smem, s, ch.fwd));
+            if constexpr (sizeof(T) == 4) {
+              if (rows_w8(tb, Lx)) launch_rows_fwd_w8(ch.fwd, ch.row_blocks, ch.row_smem, s);
+              else FL_ROWS_LAUNCH(k_rows_fwd, T, Lx, ch.row_blocks, ch.row_smem, s, ch.fwd);
+            } else {
+              FL_ROWS_LAUNCH(k_rows_fwd, T, Lx, ch.row_blocks, ch.row_smem, s, ch.fwd);
+            });
   static const char* const kn[2][4] = {{"cols_fwd<f64>", "cols_conv<f64>", "cols_inv<f64>", "cols_full<f64>"},
                                        {"cols_fwd<f32>", "cols_conv<f32>", "cols_inv<f32>", "cols_full<f32>"}};
   for (int j = 0; j < ch.ncols; ++j)
@@ -461,7 +467,12 @@ cudaError_t launch_apply(const Geo& g, const Tables<T>& tb, cudaStream_t s, cons
               FL_COLS_LAUNCH(k_cols, T, 1 << ch.cols[j].lg, ch.cols_grid[j], ch.cols_smem[j], s,
                              ch.cols[j]));
   FL_KERNEL((sizeof(T) == 4 ? "rows_inv" "<f32>" : "rows_inv" "<f64>"), s,
-            FL_ROWS_LAUNCH(k_rows_inv, T, Lx, ch.row_blocks, ch.row_smem, s, ch.inv));
+            if constexpr (sizeof(T) == 4) {
+              if (rows_w8(tb, Lx)) launch_rows_inv_w8(ch.inv, ch.row_blocks, ch.row_smem, s);
+              else FL_ROWS_LAUNCH(k_rows_inv, T, Lx, ch.row_blocks, ch.row_smem, s, ch.inv);
+            } else {
+              FL_ROWS_LAUNCH(k_rows_inv, T, Lx, ch.row_blocks, ch.row_smem, s, ch.inv);
+            });
   return launch_status();
 }
 
@@ -561,7 +572,12 @@ cudaError_t launch_precond(const Geo& g, const Tables<T>& tb, cudaStream_t s, co
   const PrecChain<T> ch = build_precond<T>(g, tb, io);
   const int Lx = g.L[g.d - 1];
   FL_KERNEL((sizeof(T) == 4 ? "dst_rows" "<f32>" : "dst_rows" "<f64>"), s,
-            FL_ROWS_LAUNCH(k_dst_rows, T, Lx, ch.row_blocks, ch.row_smem, s, ch.first));
+            if constexpr (sizeof(T) == 4) {
+              if (rows_w8(tb, Lx)) launch_dst_rows_w8(ch.first, ch.row_blocks, ch.row_smem, s);
+              else FL_ROWS_LAUNCH(k_dst_rows, T, Lx, ch.row_blocks, ch.row_smem, s, ch.first);
+            } else {
+              FL_ROWS_LAUNCH(k_dst_rows, T, Lx, ch.row_blocks, ch.row_smem, s, ch.first);
+            });
   for (int j = 0; j <= ch.ncols; ++j) {
     if (j == ch.tri_after)
       FL_KERNEL((sizeof(T) == 4 ? "tri_cols" "<f32>" : "tri_cols" "<f64>"), s,
@@ -572,7 +588,12 @@ cudaError_t launch_precond(const Geo& g, const Tables<T>& tb, cudaStream_t s, co
                                ch.cols[j]));
   }
   FL_KERNEL((sizeof(T) == 4 ? "dst_rows" "<f32>" : "dst_rows" "<f64>"), s,
-            FL_ROWS_LAUNCH(k_dst_rows, T, Lx, ch.row_blocks, ch.row_smem, s, ch.last));
+            if constexpr (sizeof(T) == 4) {
+              if (rows_w8(tb, Lx)) launch_dst_rows_w8(ch.last, ch.row_blocks, ch.row_smem, s);
+              else FL_ROWS_LAUNCH(k_dst_rows, T, Lx, ch.row_blocks, ch.row_smem, s, ch.last);
+            } else {
+              FL_ROWS_LAUNCH(k_dst_rows, T, Lx, ch.row_blocks, ch.row_smem, s, ch.last);
+            });
   return launch_status();
 }
 

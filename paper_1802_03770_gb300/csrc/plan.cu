@@ -920,6 +920,29 @@ fl_status autotune_precision(fl_plan* p) {
     }
     tb.tx[ax] = best_tx;
   }
+  // FP32 row passes: the 128 x 16 and the 256 x 8 CTA shape (rows_w8.cu)
+  if constexpr (sizeof(T) == 4) {
+    const int Lx = g.L[g.d - 1];
+    if (Lx >= 256 && Lx <= 2048) {
+      int best_rs = 0;
+      float best_ms = -1.0f;
+      for (int rs = 0; rs < 2 && ce == cudaSuccess; ++rs) {
+        tb.rshape = rs;
+        ce = trial();
+        if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
+        for (int r = 0; r < kReps && ce == cudaSuccess; ++r) ce = trial();
+        if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+        if (ce == cudaSuccess && (best_ms < 0.0f || ms < best_ms)) {
+          best_ms = ms;
+          best_rs = rs;
+        }
+      }
+      tb.rshape = best_rs;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (ce != cudaSuccess) return cuda_fail(ce, "tile autotuning");
@@ -1147,6 +1170,20 @@ fl_status fl_plan_set_tiles(fl_plan* p, const int tx[6]) {
   p->gcache[1].release();
   return FL_OK;
 }
+
+fl_status fl_plan_set_row_shape(fl_plan* p, int shape) {
+  if (!check_plan(p)) return fail(FL_INVALID_ARG, "NULL plan");
+  const int Lx = p->g.L[p->g.d - 1];
+  if (shape != 0 && shape != 1) return fail(FL_INVALID_ARG, "row shape must be 0 or 1");
+  if (shape == 1 && !(Lx >= 256 && Lx <= 2048))
+    return fail(FL_INVALID_ARG, "row shape 1 needs padded rows of 256 .. 2048 points");
+  p->t32.rshape = shape;
+  p->gcache[0].release();
+  p->gcache[1].release();
+  return FL_OK;
+}
+
+int fl_plan_row_shape(const fl_plan* p) { return p ? p->t32.rshape : -1; }
 
 fl_status fl_plan_autotune(fl_plan* p, int tx_out[6]) {
   ProfScope prof_scope(nullptr);

@@ -30,7 +30,8 @@ batched call, with the persistent launch and with the lockstep launches,
 without and with the FD preconditioner: time per CG iteration.
 tiles: one FP32 apply + FD preconditioner solve (the work of a CG
 iteration) on square 2D grids of side 96 .. 1024 and cubes of side 64 .. 256,
-alpha = 1, timed with the widest column tiles and after fl_plan_autotune.
+alpha = 1, timed with the widest column tiles (row shape 0) and after
+fl_plan_autotune (column tiles and the FP32 row-pass shape).
 richardson: the paper's grid error estimates (eq. rich) on the GPU:
 f = M g_1 and u = M^-1 1 on 255^2 / 511^2 / 1023^2 (Sec. 4.2) and
 63^3 / 127^3 / 255^3 (Sec. 4.3), and Crank-Nicolson to T = 0.25 with
@@ -243,7 +244,7 @@ def tiles(shapes=((2, 96), (2, 128), (2, 192), (2, 256), (2, 384), (2, 512), (2,
         t_tune = time.perf_counter() - t0
         rows.append({"d": d, "n": n, "us_widest": round(t_default, 1),
                      "us_tuned": round(per_iteration_us(p, n ** d), 1), "tiles": tx,
-                     "tune_seconds": round(t_tune, 3)})
+                     "row_shape": p.row_shape(), "tune_seconds": round(t_tune, 3)})
         p.close()
     return {"workload": "FP32 apply + FD preconditioner solve, alpha 1", "rows": rows}
 

@@ -1,10 +1,12 @@
-"""Column tiles of the strided passes (fl_plan_set_tiles, fl_plan_autotune).
+"""Column tiles of the strided passes and the FP32 row-pass shape
+(fl_plan_set_tiles, fl_plan_set_row_shape, fl_plan_autotune).
 
 Each line of a strided pass is transformed by the same arithmetic whatever
 the tile width, so every width must give bit-identical applies and
-preconditioner solves (FP32 and FP64); the tuner must return widths in
-range, and solves after it must still converge (it discards the plan's
-captured CG graphs)."""
+preconditioner solves (FP32 and FP64); the second row-pass shape (256 x 8,
+radix-8 stages) must agree with the oracle to FP32 rounding; the tuner must
+return widths in range, and solves after it must still converge (it
+discards the plan's captured CG graphs)."""
 
 import numpy as np
 import pytest
@@ -105,13 +107,64 @@ def test_autotune_keeps_results_and_solves(d, n):
             assert tx[a] in widths(L[a], True) and tx[3 + a] in widths(L[a], False)
         else:
             assert tx[a] == 0 and tx[3 + a] == 0
+    # the column widths alone change no result: compare bit for bit in the
+    # default row shape (the tuned row shape agrees to FP32 rounding only,
+    # test_row_shape_256x8_matches_oracle), then solve in the tuned shape
+    shape = p.row_shape()
+    assert shape in (0, 1)
+    p.set_row_shape(0)
     got = outputs(p, fields)
     for a, b in zip(got, ref):
         assert torch.equal(a, b)
+    p.set_row_shape(shape)
     u, info = p.solve(f, tol=1e-9)
-    assert info["converged"] == 1 and info["iterations"] == info0["iterations"]
+    assert info["converged"] == 1
+    assert abs(info["iterations"] - info0["iterations"]) <= (0 if shape == 0 else 2)
     op = OPlan(d, n, h, 1.25)
     fh = f.cpu().numpy().reshape(n)
     res = op.apply(u.cpu().numpy().reshape(n)) - fh
     assert np.linalg.norm(res) <= 1.05e-9 * np.linalg.norm(fh)
-    print(f"{d}D {n}: tuned column tiles {tx}")
+    print(f"{d}D {n}: tuned column tiles {tx}, row shape {shape}")
+
+
+@pytest.mark.parametrize("n", [(96, 96), (200, 130), (1024, 1024)])
+def test_row_shape_256x8_matches_oracle(n):
+    """The FP32 row passes in the 256 x 8 CTA shape (radix-8 stages): apply
+    and FD preconditioner solve within the FP32 tolerance (2e-5) of the FP64
+    oracle, and a mixed solve to 1e-8 in the oracle's residual."""
+    from oracle import precond as oprec
+    h = 1.0 / (max(n) + 1)
+    alpha = 1.3
+    p = Plan(2, n, h, alpha)
+    p.set_row_shape(1)
+    assert p.row_shape() == 1
+    op = OPlan(2, n, h, alpha)
+    rng = np.random.default_rng(81)
+    u = rng.standard_normal(n).astype(np.float32).astype(np.float64)
+    y = p.apply(torch.tensor(u.ravel(), dtype=torch.float32, device=DEV)).cpu().numpy()
+    ref = op.apply(u).ravel()
+    assert np.linalg.norm(y - ref) <= 2e-5 * np.linalg.norm(ref)
+    z = p.precond(torch.tensor(u.ravel(), dtype=torch.float32, device=DEV)).cpu().numpy()
+    zref = oprec.solve_box(op, u).ravel()
+    assert np.linalg.norm(z - zref) <= 2e-5 * np.linalg.norm(zref)
+    f = inputs.gaussian_mixture(n, 2, 16, 82)
+    us, info = p.solve(torch.tensor(f, dtype=torch.float64, device=DEV).view(-1), tol=1e-8,
+                       mode=_lib.FL_MODE_MIXED | _lib.FL_PRECOND_FD)
+    assert info["converged"] == 1, info
+    res = np.linalg.norm(op.apply(us.cpu().numpy().reshape(n)) - f) / np.linalg.norm(f)
+    assert res <= 1.05e-8, res
+
+
+def test_row_shape_rejected_outside_its_lengths_and_tuned():
+    p = Plan(2, (50, 50), 1.0 / 51, 1.0)               # rows pad to 128 points
+    with pytest.raises(_lib.FracLapError, match="INVALID_ARG"):
+        p.set_row_shape(1)
+    with pytest.raises(_lib.FracLapError, match="INVALID_ARG"):
+        p.set_row_shape(2)
+    q = Plan(2, (160, 160), 1.0 / 161, 1.0)             # rows pad to 512 points
+    q.autotune()
+    assert q.row_shape() in (0, 1)
+    f = inputs.gaussian_mixture(160, 2, 16, 83)
+    _, info = q.solve(torch.tensor(f, dtype=torch.float64, device=DEV).view(-1), tol=1e-8,
+                      mode=_lib.FL_MODE_MIXED | _lib.FL_PRECOND_FD)
+    assert info["converged"] == 1, info
