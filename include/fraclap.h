@@ -161,7 +161,9 @@ fl_status fl_plan_autotune(fl_plan* plan, int tx_out[6]);
  * padded to 256 .. 2048 points only, else FL_INVALID_ARG).  Results agree
  * to FP32 rounding (other radix plan), not bit for bit.  Invalidates the
  * plan's captured CG graphs.  fl_plan_row_shape returns the current shape
- * (-1 for a NULL plan).  Batched solves use shape 0. */
+ * (-1 for a NULL plan).  Lockstep batched solves use shape 1 when every
+ * plan of the batch has it, else shape 0; the persistent launch has its own
+ * CTA shape. */
 fl_status fl_plan_set_row_shape(fl_plan* plan, int shape);
 int fl_plan_row_shape(const fl_plan* plan);
 

@@ -162,6 +162,14 @@ cudaError_t launch_batched(const BatchPass& bp, cudaStream_t s) {
   if (bp.nprob == 0 || bp.blocks == 0) return cudaSuccess;
   switch (bp.kind) {
     case BK_ROWS_FWD:
+      if constexpr (sizeof(T) == 4) {
+        if (bp.w8) {
+          FL_KERNEL("b_rows_fwd<f32>", s,
+                    pdl_launch(kb_rows_fwd<T, kRowsW8Threads, 8>, bp.blocks, kRowsW8Threads, bp.smem, s,
+                               (const RowsFwdArgs<T>*)bp.args, bp.off, bp.gx, bp.nprob));
+          break;
+        }
+      }
       FL_KERNEL(sizeof(T) == 4 ? "b_rows_fwd<f32>" : "b_rows_fwd<f64>", s,
                 pdl_launch(kb_rows_fwd<T, K::RT, K::RV>, bp.blocks, K::RT, bp.smem, s,
                            (const RowsFwdArgs<T>*)bp.args, bp.off, bp.gx, bp.nprob));
@@ -172,11 +180,27 @@ cudaError_t launch_batched(const BatchPass& bp, cudaStream_t s) {
                            (const ColsArgs<T>*)bp.args, bp.off, bp.gx, bp.nprob));
       break;
     case BK_ROWS_INV:
+      if constexpr (sizeof(T) == 4) {
+        if (bp.w8) {
+          FL_KERNEL("b_rows_inv<f32>", s,
+                    pdl_launch(kb_rows_inv<T, kRowsW8Threads, 8>, bp.blocks, kRowsW8Threads, bp.smem, s,
+                               (const RowsInvArgs<T>*)bp.args, bp.off, bp.gx, bp.nprob));
+          break;
+        }
+      }
       FL_KERNEL(sizeof(T) == 4 ? "b_rows_inv<f32>" : "b_rows_inv<f64>", s,
                 pdl_launch(kb_rows_inv<T, K::RT, K::RV>, bp.blocks, K::RT, bp.smem, s,
                            (const RowsInvArgs<T>*)bp.args, bp.off, bp.gx, bp.nprob));
       break;
     case BK_DST_ROWS:
+      if constexpr (sizeof(T) == 4) {
+        if (bp.w8) {
+          FL_KERNEL("b_dst_rows<f32>", s,
+                    pdl_launch(kb_dst_rows<T, kRowsW8Threads, 8>, bp.blocks, kRowsW8Threads, bp.smem, s,
+                               (const DstRowsArgs<T>*)bp.args, bp.off, bp.gx, bp.nprob));
+          break;
+        }
+      }
       FL_KERNEL(sizeof(T) == 4 ? "b_dst_rows<f32>" : "b_dst_rows<f64>", s,
                 pdl_launch(kb_dst_rows<T, K::RT, K::RV>, bp.blocks, K::RT, bp.smem, s,
                            (const DstRowsArgs<T>*)bp.args, bp.off, bp.gx, bp.nprob));
@@ -247,7 +271,10 @@ cudaError_t configure_batched_kernels() {
                         reinterpret_cast<const void*>(&kb_rows_inv<float, Cfg<float>::RT, Cfg<float>::RV>),
                         reinterpret_cast<const void*>(&kb_cols<float, Cfg<float>::CT, Cfg<float>::CV>),
                         reinterpret_cast<const void*>(&kb_dst_rows<float, Cfg<float>::RT, Cfg<float>::RV>),
-                        reinterpret_cast<const void*>(&kb_dst_cols<float, Cfg<float>::CT, Cfg<float>::CV>)})
+                        reinterpret_cast<const void*>(&kb_dst_cols<float, Cfg<float>::CT, Cfg<float>::CV>),
+                        reinterpret_cast<const void*>(&kb_rows_fwd<float, kRowsW8Threads, 8>),
+                        reinterpret_cast<const void*>(&kb_rows_inv<float, kRowsW8Threads, 8>),
+                        reinterpret_cast<const void*>(&kb_dst_rows<float, kRowsW8Threads, 8>)})
     if (e == cudaSuccess) e = set_batched_smem(f);
   return e;
 }

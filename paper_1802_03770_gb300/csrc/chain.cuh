@@ -225,6 +225,7 @@ struct BatchPass {
   int nprob = 0;
   int blocks = 0;
   size_t smem = 0;
+  int w8 = 0;                // FP32 row passes: the 256 x 8 shape (same grid and memory)
 };
 
 template <typename T>

@@ -1697,6 +1697,15 @@ fl_status solve_batched_mixed(fl_plan* const* plans, int count, const double* co
   PS.upload(ar, pstep);
   ChainPasses<float> A32;
   A32.upload(ar, apply32, ncols);
+  // the lockstep FP32 row passes take the 256 x 8 shape when every plan's
+  // tuned (or set) row shape is that one (fl_plan_set_row_shape)
+  if (!persist) {
+    bool w8 = true;
+    for (int i = 0; i < count && w8; ++i) w8 = rows_w8(plans[i]->t32, plans[i]->g.L[plans[i]->g.d - 1]);
+    if (w8) {
+      for (BatchPass* bp : {&A32.fwd, &A32.inv, &PI.first, &PI.last, &PS.first, &PS.last}) bp->w8 = 1;
+    }
+  }
   // the persistent launch: the CG iteration's passes as phases (the update
   // pass of the preconditioned problems and the plain update of the others
   // side by side), the problems' CG states and the barrier

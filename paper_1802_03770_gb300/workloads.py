@@ -79,14 +79,17 @@ def timestep(n=256, steps=100, alpha=1.5, dt=1e-3, seed=3, precond="fd"):
 
 
 def tune_batch(plans, fs, mode, reps=2):
-    """Column tiles for a batch: every plan's own tuned tiles
-    (fl_plan_autotune: the fastest for that plan alone) against the widest
-    tiles on every plan, each timed on the batched solve itself (lockstep
-    launches, after a warm-up call); keeps the faster.  A plan tuned alone
+    """Launch shapes for a batch: every plan's own tuned column tiles and
+    row-pass shape (fl_plan_autotune: the fastest for that plan alone)
+    against the widest tiles on every plan with either row-pass shape on
+    every plan (the lockstep launches take the 256 x 8 row shape only when
+    every plan has it), each timed on the batched solve itself (lockstep
+    launches, after a warm-up call); keeps the fastest.  A plan tuned alone
     favours narrow tiles (more CTAs to fill the GPU), which a batch of many
-    problems does not need.  Returns the choice and both times (s)."""
+    problems does not need.  Returns the choice and the times (s)."""
     import torch
     tuned = [p.autotune() for p in plans]
+    shapes = [p.row_shape() for p in plans]
 
     def timed():
         solve_batched(plans, fs, tol=1e-8, mode=mode)
@@ -97,16 +100,25 @@ def tune_batch(plans, fs, mode, reps=2):
         torch.cuda.synchronize()
         return (time.perf_counter() - t0) / reps
 
-    t_tuned = timed()
-    for p in plans:
-        p.set_tiles([0] * 6)
-    t_widest = timed()
-    choice = "widest"
-    if t_tuned < t_widest:
-        for p, tx in zip(plans, tuned):
-            p.set_tiles(tx)
-        choice = "per_plan"
-    return choice, {"per_plan": t_tuned, "widest": t_widest}
+    def use(choice):
+        for p, tx, rs in zip(plans, tuned, shapes):
+            if choice == "per_plan":
+                p.set_tiles(tx)
+                p.set_row_shape(rs)
+            else:
+                p.set_tiles([0] * 6)
+                p.set_row_shape(1 if choice == "widest_rows256x8" else 0)
+
+    times = {"per_plan": timed()}
+    candidates = ["widest", "widest_rows256x8"]
+    if any(p.describe()["fft_len"][-1] < 256 for p in plans):
+        candidates = ["widest"]        # the 256 x 8 rows need rows of >= 256 points
+    for choice in candidates:
+        use(choice)
+        times[choice] = timed()
+    best = min(times, key=times.get)
+    use(best)
+    return best, times
 
 
 def batched(count=64, seed=7, precond="auto", autotune=False):

@@ -164,3 +164,23 @@ def test_grid_barrier_wait_is_bounded():
     _, infos = solve_batched(plans, fd, tol=1e-8,
                              mode=_lib.FL_MODE_MIXED | _lib.FL_PRECOND_AUTO | _lib.FL_BATCH_PERSISTENT)
     assert all(i["converged"] == 1 for i in infos), infos
+
+
+def test_lockstep_batch_in_the_256x8_row_shape():
+    """Every plan in the 256 x 8 row shape: the lockstep batch runs its FP32
+    row passes in that shape; it converges to 1e-8 in the oracle's residual
+    with iteration counts within two of the default shape."""
+    sides = [96, 160, 128, 200]
+    alphas = [0.6, 1.1, 1.5, 0.9]
+    plans, fd, fs = _batch_2d(sides, alphas, 700)
+    _, inf0 = solve_batched(plans, fd, tol=1e-8)
+    for p in plans:
+        p.set_row_shape(1)
+    us, inf1 = solve_batched(plans, fd, tol=1e-8)
+    torch.cuda.synchronize()
+    for n, a, f, u, i0, i1 in zip(sides, alphas, fs, us, inf0, inf1):
+        assert i1["converged"] == 1, i1
+        assert abs(i1["iterations"] - i0["iterations"]) <= 2, (n, a, i0, i1)
+        op = OPlan(2, n, 1.0 / (n + 1), a)
+        res = np.linalg.norm(op.apply(u.cpu().numpy().reshape(n, n)) - f) / np.linalg.norm(f)
+        assert res <= 1.05e-8, (n, a, res)
