@@ -139,9 +139,9 @@ def make_rhs(seed):
 # and reported as null for any other source.
 NCU_DRAM_BYTES = {
     # k_dst_rows<float, 128, 16>, 1024^2, mean of four launches: 16920576 /
-    # 16921088 (first pass) and 8559104 / 8559360 (last pass) bytes read, 0
+    # 16920576 (first pass) and 8558080 / 8558336 (last pass) bytes read, 0
     # written (profiles/dst_rows_f32_2d1024.md)
-    "dst_rows<f32>": ("81a1a206b9ad8a11", 12740032),
+    "dst_rows<f32>": ("af3ded8c2bf1acd9", 12739392),
 }
 
 
@@ -477,8 +477,9 @@ def learned_arm(dev, seeds=LEARNED_SEEDS):
     """The learned-preconditioner configuration: 512 x 512, alpha ~
     U(0.3, 1.8) (one draw per held-out seed 10000, 10001, ...), right-hand
     sides of 16 seeded Gaussians, to 1e-8: plain FP64 CG, the mixed path and
-    the mixed path with the trained network, each (plan, mode) warmed up on
-    another right-hand side first.  Solves/s over the timed solves and mean
+    the mixed path with the trained network, each plan's launch shapes tuned
+    at set-up (fl_plan_autotune) and each (plan, mode) warmed up on another
+    right-hand side first.  Solves/s over the timed solves and mean
     iterations per mode.  `learned` runs FL_MODE_LEARNED with the weights'
     alpha gate (the network only in the alpha bands where it lowered the
     validation iteration count, plain preconditioned CG elsewhere);
@@ -505,6 +506,7 @@ def learned_arm(dev, seeds=LEARNED_SEEDS):
     for k in range(seeds):
         a = float(alphas[k])
         p = Plan(2, (n, n), 1.0 / (n + 1), a)
+        p.autotune()                # column tiles and row-pass shape (set-up, untimed)
         p.attach_net(net)
         f = torch.tensor(inputs.gaussian_mixture(n, 2, 16, 10000 + k), dtype=torch.float64,
                          device=dev).view(-1)
