@@ -140,7 +140,7 @@ def make_rhs(seed):
 NCU_DRAM_BYTES = {
     # k_dst_rows<float, 128, 16>, 1024^2, mean of four launches: 16920576 /
     # 16920576 (first pass) and 8558080 / 8558336 (last pass) bytes read, 0
-    # written (profiles/dst_rows_f32_2d1024.md)
+    # written (the launch list of the capture is summarised under profiles/)
     "dst_rows<f32>": ("af3ded8c2bf1acd9", 12739392),
 }
 
