@@ -310,6 +310,17 @@ def run_ours(args, rank, world, local):
     ms_f64, infos_f64, _ = timed(mode_f64, k64, 1)
     for info in infos_f64:
         assert info["converged"] == 1, info
+    # error of the mixed solutions against tight FP64 GPU PCG solutions (the
+    # FP64 path is checked against the oracle by the parity tests), on the
+    # first timed step's right-hand sides; untimed
+    mixed_errors = []
+    for j, p in enumerate(plans):
+        fj = rhs[warm % nsteps][j].view(-1)
+        um = torch.zeros_like(fj)
+        p.solve(fj, um, tol=TOL, mode=mode_mixed)
+        ur = torch.zeros_like(fj)
+        p.solve(fj, ur, tol=1e-12, mode=mode_f64, maxit=4000)
+        mixed_errors.append(float(torch.linalg.norm(um - ur) / torch.linalg.norm(ur)))
 
     # the same step as one batched call: the three problems advance in
     # lockstep, one launch per pass over all of them (CG iterations replayed
@@ -437,6 +448,8 @@ def run_ours(args, rank, world, local):
             "x": [p.precond_params(mode_shift)[0] for p in plans],
             "iterations": [i["iterations"] for i in infos_shift[: len(ALPHAS)]],
             "refinements": [i["outer_iterations"] for i in infos_shift[: len(ALPHAS)]]},
+        "mixed_error_vs_fp64": {"alphas": list(ALPHAS), "rel_error": mixed_errors,
+                                "reference": "FP64 PCG on the GPU to 1e-12 relative residual"},
         "iterations_mixed": its_mixed,
         "refinements": [i["outer_iterations"] for i in infos_mixed[: len(ALPHAS)]],
         "kernels": kernel_shares, "apply": apply, "tiles": tiles,
@@ -798,6 +811,7 @@ def main():
                 "fp64_pcg": res["fp64_pcg"], "speedup_vs_fp64_pcg": res["speedup_vs_fp64_pcg"],
                 "batched": res["batched"], "balanced_shift": res["balanced_shift"],
                 "iterations_mixed": res["iterations_mixed"], "refinements": res["refinements"],
+                "mixed_error_vs_fp64": res["mixed_error_vs_fp64"],
                 "t_con_s": res["t_con_s"], "apply": res["apply"], "kernels": res["kernels"],
                 "tiles": res["tiles"], "learned": res["learned"],
                 "timestep_3d": res["timestep_3d"], "batched_64": res["batched_64"]}
