@@ -39,9 +39,11 @@ def test_batched_matches_single_solves():
         assert np.linalg.norm(u - u1) <= 1e-6 * np.linalg.norm(u1)
 
 
-def test_batched_64_uneven_problems():
+@pytest.mark.parametrize("launch", [0, _lib.FL_BATCH_PERSISTENT])
+def test_batched_64_uneven_problems(launch):
     """64 problems, sides uniform in {96, 128, ..., 768}, alpha ~ U(0.3, 1.8),
-    seeded Gaussian-mixture right-hand sides, to 1e-8."""
+    seeded Gaussian-mixture right-hand sides, to 1e-8; lockstep launches and
+    the one persistent launch per refinement step."""
     sides = inputs.batch_sides(64, 7)
     alphas = inputs.alpha_draws(64, 8)
     plans, fd, fs = [], [], []
@@ -50,7 +52,8 @@ def test_batched_64_uneven_problems():
         fs.append(f)
         plans.append(Plan(2, (n, n), 1.0 / (n + 1), a))
         fd.append(torch.tensor(f, dtype=torch.float64, device="cuda:0").view(-1))
-    us, infos = solve_batched(plans, fd, tol=1e-8)
+    us, infos = solve_batched(plans, fd, tol=1e-8,
+                              mode=_lib.FL_MODE_MIXED | _lib.FL_PRECOND_AUTO | launch)
     torch.cuda.synchronize()
     rng = np.random.default_rng(9)
     for i in rng.choice(64, 8, replace=False):
